@@ -1,0 +1,290 @@
+"""Throughput of the infinite-domain Poisson solve (grid points / s at 6th order).
+
+Workload: the 3-D FP64 6th-order problem of 129^3 nodes on [-1,1]^3 with
+rho = (1 - r^2/0.49)^10 for r < 0.7 around (0.05, 0.1, -0.08) (synthetic,
+seeded, generated on the host, resident in HBM before timing).  One step =
+one complete solve phi = phi* + phi_H (boundary convolutions, three sine
+solves, 6th-order correction) through the C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 129]
+
+--impl reference times the CPU oracle on the host cores (the reference arm of
+this comparison: there is no runnable reference implementation, only the
+paper).  One JSON line is printed by rank 0.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as w  # noqa: E402
+
+METRIC = "grid points/s at 6th order, FP64 vs mixed-precision at stated max error"
+UNIT = "grid points/s"
+L2_FLUSH_BYTES = 512 << 20          # > 129 MB of L2
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 4 FP64 flop/clk x 2.07 GHz
+FP64_PROBE_TFLOPS = 1.198           # FMA-chain probe on this GPU model, 1995 MHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=129)
+    ap.add_argument("--order", type=int, default=6)
+    return ap.parse_args()
+
+
+def workload(n):
+    return w.c2_3d(n)
+
+
+def config_of(prob, order, extra=None):
+    c = {"workload": "3-D FP64 order-%d solve, %d^3 nodes on [-1,1]^3, bump (1-r^2/0.49)^10, "
+                     "r<0.7, centre (0.05,0.1,-0.08)" % (order, prob.n[0]),
+         "nodes": prob.points, "order": order, "grid": list(prob.n), "h": list(prob.h),
+         "l2": "flushed between timed steps (512 MiB write)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r.split(",") for r in self.out.strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        load = [v for v in sm if v > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle timing
+def oracle_step(rho, h, order):
+    from oracle import solve as osolve
+    t = time.perf_counter()
+    osolve.solve(rho, h, order, boundary="convolution")
+    return time.perf_counter() - t
+
+
+def cpu_baseline(prob, order, reps=1):
+    rho = prob.rho()
+    ts = [oracle_step(rho, prob.h, order) for _ in range(reps)]
+    t = min(ts)
+    return {"value": prob.points / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "one complete oracle solve of the same %d^3 workload (convolution form of the "
+                      "boundary sum, numpy BLAS sine sums), %.1f s" % (prob.n[0], t)}
+
+
+def run_reference(args, rank, world):
+    prob = workload(args.n)
+    if rank != 0:
+        return
+    rho = prob.rho()
+    for _ in range(args.warmup):
+        oracle_step(rho, prob.h, args.order)
+    ts = [oracle_step(rho, prob.h, args.order) for _ in range(args.steps)]
+    t = sum(ts)
+    value = prob.points * args.steps / t
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": config_of(prob, args.order),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "%d complete oracle solves of the workload" % args.steps},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def dst_flops_per_launch(prob):
+    """Algorithmic FP64 flops of one sine-transform pass: 2.5 log2(2M) per interior point."""
+    M = prob.n[0] - 1
+    return 2.5 * np.log2(2 * M) * float(np.prod([k - 2 for k in prob.n]))
+
+
+def run_ours(args, rank, world):
+    import torch
+    import torch.distributed as dist
+    import ctypes
+    import paper_2108_11871_gb300 as idp
+
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prob = workload(args.n)
+    plan = idp.create_plan(3, prob.n, prob.h, args.order)
+    rho_h = prob.rho()
+    rho = torch.from_numpy(rho_h).to(dev)
+    phi = torch.empty_like(rho)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        idp.solve(plan, rho, phi, stream)
+    torch.cuda.synchronize()
+    idp.plan_status(plan)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            starts[i].record(stream)
+            idp.solve(plan, rho, phi, stream)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    idp.plan_status(plan)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    launches = ctypes.c_int64()
+    idp.library().idp_plan_launches(plan.handle, ctypes.byref(launches))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * prob.points * args.steps / (total_ms / 1e3)
+
+    # per-kernel durations (plain launches, events on the launch stream)
+    cap = 256
+    kinds = (ctypes.c_int * cap)()
+    ms = (ctypes.c_float * cap)()
+    per_kind = {}
+    for i in range(max(3, min(args.steps, 10))):
+        flush.fill_(float(i))
+        n = idp.library().idp_profile_solve(plan.handle, ctypes.c_void_p(rho.data_ptr()),
+                                            ctypes.c_void_p(phi.data_ptr()),
+                                            ctypes.c_void_p(stream.cuda_stream), cap, kinds, ms)
+        if n < 0:
+            raise RuntimeError("idp_profile_solve: %s" % idp.strerror(n))
+        for j in range(n):
+            per_kind.setdefault(kinds[j], []).append(ms[j])
+    names = {1: "dst_pass", 2: "rfft", 3: "face", 4: "face_invb", 5: "face_c2r", 6: "gtilde",
+             7: "rhs6_w", 8: "rhs6_core", 9: "rhs6_extrap"}
+    prof_steps = max(3, min(args.steps, 10))
+    shares = {names[k]: sum(v) / prof_steps for k, v in per_kind.items()}
+    dom = max(per_kind, key=lambda k: sum(per_kind[k]))
+    dst_ms = statistics.mean(per_kind[1])
+    achieved = dst_flops_per_launch(prob) / (dst_ms / 1e3) / 1e12
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    rho_pin = torch.from_numpy(rho_h).pin_memory()
+    phi_pin = torch.empty_like(rho_pin).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    idp.solve_host(plan, rho_pin.data_ptr(), phi_pin.data_ptr(), stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        idp.solve_host(plan, rho_pin.data_ptr(), phi_pin.data_ptr(), stream)
+    torch.cuda.synchronize()
+    e2e_t = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": world * prob.points / e2e_t, "unit": UNIT,
+           "h2d_bytes_per_step": 8 * prob.points, "d2h_bytes_per_step": 8 * prob.points}
+
+    if rank != 0:
+        return
+    out = phi.cpu().numpy()
+    from oracle import closed_form
+    exact = closed_form.bump_potential_on_grid(prob)
+    err_exact = float(np.abs(out - exact).max() / np.abs(exact).max())
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(prob, args.order, {"parallelism": "replicas" if world > 1 else "single"}),
+            "precision": {"variant": "fp64", "max_rel_error_vs_exact_potential": err_exact},
+            "e2e": e2e,
+            "gpu_launches": int(launches.value) * args.steps,
+            "roofline": {"bound": "alu", "kernel": "dst_pass (FP64 sine-transform pass)",
+                         "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS,
+                         "peak_note": "FP64 derived: 152 SMs x 4 flop/clk x 2.07 GHz; "
+                                      "FMA-chain probe measured %.3f" % FP64_PROBE_TFLOPS,
+                         "traffic": None, "avg_launch_ms": dst_ms,
+                         "flops_per_launch": dst_flops_per_launch(prob)},
+            "kernel_ms_per_step": shares, "dominant_kernel": names[dom],
+            "clocks": clk.summary()}
+    if world == 1:
+        line["cpu_baseline"] = cpu_baseline(prob, args.order)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if world > 1:
+        import torch.distributed as dist
+        if args.impl == "ours":
+            import torch
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,151 @@
+/*
+ * idp.h -- C ABI of the GB300 infinite-domain Poisson solver.
+ *
+ * The library evaluates, at every node of a uniform 2-D or 3-D grid, the
+ * convolution of the free-space Green's function of the Laplacian with a
+ * density rho whose support lies inside the grid (arXiv 2108.11871, section 1,
+ * eqs. GreensFcnIntegral / InfDomainPoisson):
+ *
+ *     phi = phi* + phi_H                       (section 2, eqs. PhiStarEqn, PhiHeqn)
+ *
+ *   phi*  : Dirichlet-0 Poisson solve by discrete sine transforms (section 3);
+ *   g     : phi_H on the boundary, the trapezoid sum of G * rho evaluated as
+ *           per-slice FFT convolutions (section 4, eqs. TrapOrig2D, Trap2D,
+ *           convolution);
+ *   gtilde: the boundary data moved to the right-hand side of the compact
+ *           4th-order operator (section 5, eq. harmonic4thOrderNH2D);
+ *   u1    : the 4th-order harmonic solve (section 5, eigenvectors = sines);
+ *   R, u2 : the 6th-order deferred correction with cubic extrapolation next
+ *           to the boundary (section 5, eqs. 6thOrderRelation2D/3D).
+ *
+ * Conventions shared by every entry point
+ *   - Grids: d in {2, 3}; n[s] = node count along array axis s INCLUDING the
+ *     two boundary nodes (n[s] = M_s + 1, M_s panels); h[s] > 0 is the mesh
+ *     width.  Arrays are FP64, C order, last axis contiguous, prod(n) entries.
+ *   - Supported sizes: M_s a power of two with 16 <= M_s <= 512.
+ *   - rho is read on interior nodes only; its boundary entries are ignored.
+ *     The method assumes rho vanishes near the boundary (section 2); the
+ *     library does not check it.
+ *   - Device pointers are CUDA device memory owned by the caller and must
+ *     stay valid until the work queued on `stream` has finished.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     All device work is queued on it; calls return before it completes.
+ *   - Return value: IDP_OK (0) or a negative IDP_E* code.  Errors in the
+ *     arguments are reported synchronously and nothing is queued.  Errors
+ *     raised later by queued work are reported by idp_plan_status().
+ *   - A plan may be used by one stream at a time; calls on one plan must not
+ *     overlap on the device.
+ */
+#ifndef IDP_H
+#define IDP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    IDP_OK = 0,
+    IDP_EINVAL = -1,     /* bad argument (dimension, size, order, null pointer) */
+    IDP_ENOMEM = -2,     /* device or host allocation failed */
+    IDP_ECUDA = -3,      /* a CUDA call failed; see idp_last_cuda_error() */
+    IDP_EALIAS = -4,     /* rho and phi overlap */
+    IDP_ESUPPORT = -5    /* size or option outside the supported set */
+};
+
+/* keys for idp_plan_set */
+enum {
+    IDP_KEY_USE_GRAPH = 1   /* 1 (default): replay solves from a CUDA graph; 0: plain launches */
+};
+
+/* stages for idp_solve_stage */
+enum {
+    IDP_STAGE_BOUNDARY = 1, /* out: node array, g on the boundary, 0 inside (section 4) */
+    IDP_STAGE_GTILDE = 2,   /* out: interior array prod(n[s]-2), gtilde (eq. harmonic4thOrderNH2D) */
+    IDP_STAGE_PHISTAR = 3,  /* out: node array, phi* (section 3), 0 on the boundary */
+    IDP_STAGE_U1 = 4,       /* out: node array, u1 inside, g on the boundary (section 5) */
+    IDP_STAGE_R = 5,        /* out: interior array, 6th-order right-hand side R incl. extrapolation */
+    IDP_STAGE_PHI = 6       /* out: node array, phi (same as idp_solve) */
+};
+
+typedef struct idp_plan_s *idp_plan;
+
+/* Create a plan for one grid (section 3 grid, section 5 order).
+ *   out   : receives the plan handle (owned by the caller; free with idp_destroy_plan)
+ *   d     : 2 or 3
+ *   n[d]  : node counts including boundary nodes
+ *   h[d]  : mesh widths
+ *   order : 4 or 6 (accuracy order of the harmonic correction, section 5)
+ * Allocates all device workspace and precomputes the sine/twiddle tables,
+ * the eigenvalue tables and the spectra of the boundary convolution kernels
+ * on the current CUDA device; synchronises that device before returning. */
+int idp_create_plan(idp_plan *out, int d, const int64_t n[], const double h[], int order);
+
+/* Set a plan option (IDP_KEY_*). */
+int idp_plan_set(idp_plan plan, int key, int64_t value);
+
+/* phi = G * rho on every node (section 2).  rho, phi: device arrays of prod(n)
+ * doubles; they must not overlap (IDP_EALIAS). */
+int idp_solve(idp_plan plan, const double *rho, double *phi, void *stream);
+
+/* Same as idp_solve with HOST arrays: copies rho to the device, solves, copies
+ * phi back and waits for the stream.  The plan allocates its device staging
+ * buffers on the first call. */
+int idp_solve_host(idp_plan plan, const double *rho_host, double *phi_host, void *stream);
+
+/* Solve `count` independent problems, plans[i] with rho[i] -> phi[i]
+ * (device arrays), all queued on `stream`.  The plans must be distinct. */
+int idp_solve_batched(int count, const idp_plan plans[], const double *const rho[],
+                      double *const phi[], void *stream);
+
+/* Run the method up to one intermediate stage and write it to `out`
+ * (device array; layout given by the IDP_STAGE_* comment).  For checking
+ * the components against a reference. */
+int idp_solve_stage(idp_plan plan, int stage, const double *rho, double *out, void *stream);
+
+/* Device-side status of the plan's last queued work: IDP_OK or IDP_ECUDA if a
+ * launch or asynchronous error was recorded.  Synchronises the plan's last stream. */
+int idp_plan_status(idp_plan plan);
+
+/* kernel families reported by idp_profile_solve */
+enum {
+    IDP_KERNEL_DST = 1,          /* sine-transform pass along one axis (sections 3, 5) */
+    IDP_KERNEL_RFFT = 2,         /* boundary stage 1: real FFT of zero-padded lines (section 4) */
+    IDP_KERNEL_FACE = 3,         /* boundary stage 2: per-slice FFT x kernel spectrum, summed over slices */
+    IDP_KERNEL_FACE_INVB = 4,    /* boundary stage 3a: inverse FFT across the face */
+    IDP_KERNEL_FACE_C2R = 5,     /* boundary stage 3b: inverse real FFT and scatter to the face nodes */
+    IDP_KERNEL_GTILDE = 6,       /* gtilde stencil (eq. harmonic4thOrderNH2D) */
+    IDP_KERNEL_RHS6_W = 7,       /* 6th-order RHS, second differences (eqs. 6thOrderRelation2D/3D) */
+    IDP_KERNEL_RHS6_CORE = 8,    /* 6th-order RHS on the core */
+    IDP_KERNEL_RHS6_EXTRAP = 9   /* cubic extrapolation next to the boundary */
+};
+
+/* Run one solve (as idp_solve, but with plain launches) and time every kernel
+ * launch with CUDA events recorded on `stream`.  kinds[i] receives the
+ * IDP_KERNEL_* family and ms[i] the duration of launch i, for at most
+ * `capacity` launches.  Synchronises the stream.  Returns the number of
+ * launches timed (>= 0) or a negative IDP_E* code. */
+int idp_profile_solve(idp_plan plan, const double *rho, double *phi, void *stream, int capacity,
+                      int *kinds, float *ms);
+
+/* Number of kernel launches one solve of this plan queues (valid after the
+ * first solve). */
+int idp_plan_launches(idp_plan plan, int64_t *launches);
+
+/* Query the plan: node count, interior count and device workspace bytes. */
+int idp_plan_info(idp_plan plan, int64_t *nodes, int64_t *interior, int64_t *workspace_bytes);
+
+/* Release the plan and all its device memory (synchronises the device). */
+int idp_destroy_plan(idp_plan plan);
+
+/* Static description of an IDP_* code. */
+const char *idp_strerror(int code);
+
+/* Name of the last CUDA error seen by the library in this thread ("" if none). */
+const char *idp_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IDP_H */

@@ -1,0 +1,424 @@
+// Boundary values of the harmonic correction (section 4): the trapezoid sum
+// of G * rho on every boundary node, evaluated as the paper rearranges it
+// (eqs. Trap2D, Trap2Dconvolution, convolution): for each face, a sum over the
+// slices parallel to it of aperiodic convolutions of the rho slice with
+// G(sqrt(dist^2 + |.|^2)), done with zero-padded FFTs of length 2M.
+//
+// 3-D data flow (faces of axis a; b < c the other two axes):
+//   stage 1  real FFT (length 2M_c) along c of every interior line of rho
+//   stage 2  FFT (length 2M_b) along b of every slice p, multiplied by the
+//            kernel spectra of distance p h_a and (M_a - p) h_a, summed over p
+//   stage 3  inverse FFT along b, inverse real FFT along c, scatter to nodes.
+// The kernel spectra are real and even (the cyclic kernel is even), so only
+// frequencies 0..M are stored; they are computed once per plan.
+#include "fft.cuh"
+
+namespace idp {
+
+namespace {
+constexpr int NT = 256;
+
+// lines per block so that 2 buffers of LB x L complex fit in 64 KB
+template <int L>
+struct LineCfg {
+    static constexpr int LB = (2048 / L) > 32 ? 32 : ((2048 / L) < 1 ? 1 : 2048 / L);
+};
+
+// ---------------------------------------------------------------- stage 1
+// L = M: complex FFT length; input line has M-1 reals at positions 1..M-1 of
+// a zero-padded sequence of length 2M; output X'_m = 2 X_m, m = 0..M.
+template <int L>
+__global__ void __launch_bounds__(NT) rfft_kernel(const RfftPass a)
+{
+    constexpr int M = L, N = M - 1, LB = LineCfg<L>::LB;
+    extern __shared__ double2 smem[];
+    double2 *bufA = smem, *bufB = smem + LB * L;
+    int nu, nv;
+    int64_t isu, isv, ise, osu, osv, ose;
+    if (a.axis == 2) {
+        nu = a.n0; nv = a.n1;
+        isu = a.is0; isv = a.is1; ise = a.is2; osu = a.os0; osv = a.os1; ose = a.os2;
+    } else if (a.axis == 1) {
+        nu = a.n0; nv = a.n2;
+        isu = a.is0; isv = a.is2; ise = a.is1; osu = a.os0; osv = a.os2; ose = a.os1;
+    } else {
+        nu = a.n1; nv = a.n2;
+        isu = a.is1; isv = a.is2; ise = a.is0; osu = a.os1; osv = a.os2; ose = a.os0;
+    }
+    const int u = blockIdx.y, v0 = blockIdx.x * LB;
+    const int nl = min(LB, nv - v0);
+    const bool contig = (ise == 1);
+    double *zf = reinterpret_cast<double *>(bufA);   // [LB][2L] reals
+    const double *inb = a.in + (int64_t)u * isu + (int64_t)v0 * isv;
+    for (int f = threadIdx.x; f < LB * 2 * L; f += NT) {
+        const int l = f / (2 * L), q = f - l * 2 * L;
+        if (q == 0 || q >= M) zf[f] = 0.0;
+    }
+    for (int f = threadIdx.x; f < LB * N; f += NT) {
+        int l, e;
+        if (contig) { l = f / N; e = f - l * N; }
+        else { e = f / LB; l = f - e * LB; }
+        double x = 0.0;
+        if (l < nl) x = inb[(int64_t)l * isv + (int64_t)e * ise];
+        zf[l * 2 * L + e + 1] = x;
+    }
+    __syncthreads();
+    double2 *Z = cta_fft<L, LB, NT, false>(bufA, bufB, a.t.fwd, true);
+    double2 *outb = a.out + (int64_t)u * osu + (int64_t)v0 * osv;
+    for (int f = threadIdx.x; f < LB * (L / 2); f += NT) {
+        const int l = f / (L / 2);
+        const int m = f - l * (L / 2) + 1;   // 1..L/2
+        if (l >= nl) continue;
+        const double2 *zl = Z + l * L;
+        const double2 zm = zl[m], zc = zl[L - m];
+        const double Er = zm.x + zc.x, Ei = zm.y - zc.y;
+        const double Or = zm.x - zc.x, Oi = zm.y + zc.y;
+        const double2 w = a.t.half[m];
+        const double Pr = fma(w.x, Or, -w.y * Oi);
+        const double Pi = fma(w.x, Oi, w.y * Or);
+        double2 *ol = outb + (int64_t)l * osv;
+        ol[(int64_t)m * ose] = make_double2(Er + Pi, Ei - Pr);
+        ol[(int64_t)(M - m) * ose] = make_double2(Er - Pi, -(Ei + Pr));
+        if (m == 1) {
+            const double2 z0 = zl[0];
+            ol[0] = make_double2(2.0 * (z0.x + z0.y), 0.0);
+            ol[(int64_t)M * ose] = make_double2(2.0 * (z0.x - z0.y), 0.0);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- stage 2
+// columns per block of the face pass: TC x L = 1024 complex per block
+template <int L>
+struct FaceCfg {
+    static constexpr int TC = (1024 / L) > 32 ? 32 : ((1024 / L) < 1 ? 1 : 1024 / L);
+};
+
+// L = 2 Mb.  Block: TC consecutive frequencies c, one chunk of slices p.
+template <int L>
+__global__ void __launch_bounds__(NT) face_kernel(const FacePass a)
+{
+    constexpr int TC = FaceCfg<L>::TC;
+    constexpr int Mb = L / 2;
+    constexpr int OPT = (TC * L + NT - 1) / NT;   // outputs per thread
+    extern __shared__ double2 smem[];
+    double2 *bufA = smem, *bufB = smem + TC * L;
+    const int c0 = blockIdx.x * TC;
+    const int ncl = min(TC, a.nc - c0);
+    const int chunk = blockIdx.y;
+    const int p0 = chunk * a.pchunk;
+    const int p1 = min(a.np, p0 + a.pchunk);
+    double2 acc_lo[OPT], acc_hi[OPT];
+#pragma unroll
+    for (int r = 0; r < OPT; ++r) {
+        acc_lo[r] = make_double2(0.0, 0.0);
+        acc_hi[r] = make_double2(0.0, 0.0);
+    }
+    const int64_t kstride = (int64_t)(Mb + 1) * a.nc;
+    for (int p = p0; p < p1; ++p) {
+        // load TC columns: positions 1..Mb-1 (interior index 0..Mb-2), rest zero
+        const double2 *Dp = a.D + (int64_t)p * a.sp + (int64_t)c0 * a.sc;
+        for (int f = threadIdx.x; f < TC * L; f += NT) {
+            const int q = f / TC, t = f - q * TC;
+            double2 x = make_double2(0.0, 0.0);
+            if (q >= 1 && q <= Mb - 1 && t < ncl) x = Dp[(int64_t)(q - 1) * a.sb + (int64_t)t * a.sc];
+            bufA[t * L + q] = x;
+        }
+        __syncthreads();
+        const double2 *Z = cta_fft<L, TC, NT, false>(bufA, bufB, a.t.fwd, true);
+        const double *klo = a.khat + (int64_t)p * kstride + c0;
+        const double *khi = a.khat + (int64_t)(a.np - 1 - p) * kstride + c0;
+#pragma unroll
+        for (int r = 0; r < OPT; ++r) {
+            const int o = threadIdx.x + r * NT;
+            if (o < TC * L) {
+                const int m = o / TC, t = o - m * TC;
+                if (t < ncl) {
+                    const int mm = m <= Mb ? m : L - m;
+                    const double2 X = Z[t * L + m];
+                    const double kl = klo[(int64_t)mm * a.nc + t];
+                    const double kh = khi[(int64_t)mm * a.nc + t];
+                    acc_lo[r].x = fma(kl, X.x, acc_lo[r].x);
+                    acc_lo[r].y = fma(kl, X.y, acc_lo[r].y);
+                    acc_hi[r].x = fma(kh, X.x, acc_hi[r].x);
+                    acc_hi[r].y = fma(kh, X.y, acc_hi[r].y);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // partial sums: part[chunk][face][m][c]
+    double2 *plo = a.part + ((int64_t)chunk * 2 + 0) * L * a.nc + c0;
+    double2 *phi = a.part + ((int64_t)chunk * 2 + 1) * L * a.nc + c0;
+#pragma unroll
+    for (int r = 0; r < OPT; ++r) {
+        const int o = threadIdx.x + r * NT;
+        if (o < TC * L) {
+            const int m = o / TC, t = o - m * TC;
+            if (t < ncl) {
+                plo[(int64_t)m * a.nc + t] = acc_lo[r];
+                phi[(int64_t)m * a.nc + t] = acc_hi[r];
+            }
+        }
+    }
+}
+
+// 2-D contraction over slices (no second FFT)
+__global__ void face2d_kernel(const FacePass2D a)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= a.nm) return;
+    double2 lo = make_double2(0.0, 0.0), hi = make_double2(0.0, 0.0);
+    for (int p = 0; p < a.np; ++p) {
+        const double2 x = a.T[(int64_t)p * a.sp + (int64_t)m * a.sm];
+        const double kl = a.khat[(int64_t)p * a.nm + m];
+        const double kh = a.khat[(int64_t)(a.np - 1 - p) * a.nm + m];
+        lo.x = fma(kl, x.x, lo.x); lo.y = fma(kl, x.y, lo.y);
+        hi.x = fma(kh, x.x, hi.x); hi.y = fma(kh, x.y, hi.y);
+    }
+    a.acc[m] = lo;
+    a.acc[a.nm + m] = hi;
+}
+
+// ---------------------------------------------------------------- stage 3a
+template <int L>
+__global__ void __launch_bounds__(NT) face_invb_kernel(const FaceInvB a)
+{
+    constexpr int TC = LineCfg<L>::LB;
+    constexpr int Mb = L / 2;
+    extern __shared__ double2 smem[];
+    double2 *bufA = smem, *bufB = smem + TC * L;
+    const int c0 = blockIdx.x * TC;
+    const int face = blockIdx.y;
+    const int ncl = min(TC, a.nc - c0);
+    for (int f = threadIdx.x; f < TC * L; f += NT) {
+        const int m = f / TC, t = f - m * TC;
+        double2 s = make_double2(0.0, 0.0);
+        if (t < ncl) {
+            for (int ch = 0; ch < a.nchunk; ++ch) {
+                const double2 v = a.part[(((int64_t)ch * 2 + face) * L + m) * a.nc + c0 + t];
+                s.x += v.x;
+                s.y += v.y;
+            }
+        }
+        bufA[t * L + m] = s;
+    }
+    __syncthreads();
+    const double2 *Z = cta_fft<L, TC, NT, true>(bufA, bufB, a.t.inv, false);
+    for (int f = threadIdx.x; f < TC * (Mb + 1); f += NT) {
+        const int j = f / TC, t = f - j * TC;
+        if (t < ncl) a.out[((int64_t)face * (Mb + 1) + j) * a.nc + c0 + t] = Z[t * L + j];
+    }
+}
+
+// ---------------------------------------------------------------- stage 3b
+// L = Mc.  One line = one row of one face.
+template <int L>
+__global__ void __launch_bounds__(NT) face_c2r_kernel(const FaceC2R a)
+{
+    constexpr int LB = LineCfg<L>::LB;
+    extern __shared__ double2 smem[];
+    double2 *bufA = smem, *bufB = smem + LB * L;
+    const int face = blockIdx.y;
+    const int r0 = blockIdx.x * LB;
+    const int64_t fbase = face ? a.base[1] : a.base[0];
+    const int nl = min(LB, a.nrows - r0);
+    const double2 *inb = a.in + ((int64_t)face * a.nrows + r0) * (L + 1);
+    for (int f = threadIdx.x; f < LB * L; f += NT) {
+        const int l = f / L, k = f - l * L;
+        double2 z = make_double2(0.0, 0.0);
+        if (l < nl) {
+            const double2 xk = inb[(int64_t)l * (L + 1) + k];
+            const double2 xc = inb[(int64_t)l * (L + 1) + (L - k)];
+            // A = X_k + conj X_{L-k};  B = e^{+i pi k/L} (X_k - conj X_{L-k});  Z' = A + i B
+            const double Ar = xk.x + xc.x, Ai = xk.y - xc.y;
+            const double Dr = xk.x - xc.x, Di = xk.y + xc.y;
+            const double2 w = a.t.half[k];   // (cos, -sin)
+            const double Br = fma(w.x, Dr, w.y * Di);     // cos*Dr + sin*Di
+            const double Bi = fma(w.x, Di, -w.y * Dr);    // cos*Di - sin*Dr
+            z = make_double2(Ar - Bi, Ai + Br);
+        }
+        bufA[l * L + k] = z;
+    }
+    __syncthreads();
+    const double2 *Z = cta_fft<L, LB, NT, true>(bufA, bufB, a.t.inv, false);
+    for (int f = threadIdx.x; f < LB * (L + 1); f += NT) {
+        const int l = f / (L + 1), t = f - l * (L + 1);
+        if (l >= nl) continue;
+        const int row = r0 + l;
+        if (a.skip_row_edges && (row == 0 || row == a.nrows - 1)) continue;
+        if (a.skip_col_edges && (t == 0 || t == L)) continue;
+        const double2 z = Z[l * L + ((t >> 1) & (L - 1))];
+        const double v = (t & 1) ? z.y : z.x;
+        const int64_t node = fbase + (int64_t)row * a.row_stride + (int64_t)t * a.col_stride;
+        a.dst0[node] = v;
+        if (a.dst1) a.dst1[node] = v;
+    }
+}
+
+// ---------------------------------------------------------------- kernel spectra
+__global__ void kernel_fill_kernel(const KernelFill a)
+{
+    const int64_t total = (int64_t)a.np * (a.Mb + 1) * (a.Mc + 1);
+    const double inv4pi = 1.0 / (4.0 * 3.14159265358979323846);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int tc = (int)(i % (a.Mc + 1));
+        const int64_t r = i / (a.Mc + 1);
+        const int tb = (int)(r % (a.Mb + 1));
+        const int p = (int)(r / (a.Mb + 1));
+        const double da = (a.p0 + p + 1) * a.ha, db = tb * a.hb, dc = tc * a.hc;
+        const double r2 = da * da + db * db + dc * dc;
+        double g;
+        if (a.d == 3) g = -inv4pi / sqrt(r2);
+        else g = inv4pi * log(r2);   // log(r)/(2 pi) = log(r^2)/(4 pi)
+        a.k[i] = g;
+    }
+}
+
+// ---------------------------------------------------------------- FP64 batched GEMM (plan set-up only)
+constexpr int GT = 32;
+__global__ void gemm_kernel(int m, int n, int k, const double *A, int64_t lda, int64_t sA,
+                            const double *B, int64_t ldb, int64_t sB, double *C, int64_t ldc, int64_t sC)
+{
+    __shared__ double As[GT][GT + 1], Bs[GT][GT + 1];
+    const int b = blockIdx.z;
+    A += b * sA; B += b * sB; C += b * sC;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;   // 16 x 16 threads, 2 x 2 outputs each
+    const int row0 = blockIdx.y * GT, col0 = blockIdx.x * GT;
+    double acc[2][2] = {{0, 0}, {0, 0}};
+    for (int k0 = 0; k0 < k; k0 += GT) {
+        for (int f = threadIdx.x; f < GT * GT; f += 256) {
+            const int i = f / GT, j = f % GT;
+            As[i][j] = (row0 + i < m && k0 + j < k) ? A[(int64_t)(row0 + i) * lda + k0 + j] : 0.0;
+            Bs[i][j] = (k0 + i < k && col0 + j < n) ? B[(int64_t)(k0 + i) * ldb + col0 + j] : 0.0;
+        }
+        __syncthreads();
+        for (int kk = 0; kk < GT; ++kk) {
+            const double a0 = As[ty][kk], a1 = As[ty + 16][kk];
+            const double b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+            acc[0][0] = fma(a0, b0, acc[0][0]);
+            acc[0][1] = fma(a0, b1, acc[0][1]);
+            acc[1][0] = fma(a1, b0, acc[1][0]);
+            acc[1][1] = fma(a1, b1, acc[1][1]);
+        }
+        __syncthreads();
+    }
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            const int r = row0 + ty + 16 * i, c = col0 + tx + 16 * j;
+            if (r < m && c < n) C[(int64_t)r * ldc + c] = acc[i][j];
+        }
+}
+
+template <int L>
+size_t smem_lines() { return 2 * sizeof(double2) * LineCfg<L>::LB * L; }
+template <int L>
+size_t smem_face() { return 2 * sizeof(double2) * FaceCfg<L>::TC * L; }
+
+template <int L>
+cudaError_t attrs_len()
+{
+    cudaError_t e;
+    const int sm = (int)smem_lines<L>();
+    if ((e = cudaFuncSetAttribute(rfft_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
+    if ((e = cudaFuncSetAttribute(face_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_face<L>())))
+        return e;
+    if ((e = cudaFuncSetAttribute(face_invb_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
+    return cudaFuncSetAttribute(face_c2r_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+}
+
+#define IDP_LEN_SWITCH(LEN, ...)              \
+    switch (LEN) {                             \
+    case 16: { constexpr int L = 16; __VA_ARGS__; }   \
+    case 32: { constexpr int L = 32; __VA_ARGS__; }   \
+    case 64: { constexpr int L = 64; __VA_ARGS__; }   \
+    case 128: { constexpr int L = 128; __VA_ARGS__; } \
+    case 256: { constexpr int L = 256; __VA_ARGS__; } \
+    case 512: { constexpr int L = 512; __VA_ARGS__; } \
+    case 1024: { constexpr int L = 1024; __VA_ARGS__; } \
+    default: return cudaErrorInvalidValue;     \
+    }
+
+}  // namespace
+
+cudaError_t boundary_set_attributes()
+{
+    cudaError_t e;
+    if ((e = attrs_len<16>())) return e;
+    if ((e = attrs_len<32>())) return e;
+    if ((e = attrs_len<64>())) return e;
+    if ((e = attrs_len<128>())) return e;
+    if ((e = attrs_len<256>())) return e;
+    if ((e = attrs_len<512>())) return e;
+    return attrs_len<1024>();
+}
+
+int face_columns_per_block(int L)
+{
+    IDP_LEN_SWITCH(L, return FaceCfg<L>::TC;)
+}
+
+cudaError_t launch_rfft_pass(const RfftPass &a, cudaStream_t st)
+{
+    int nu, nv;
+    if (a.axis == 2) { nu = a.n0; nv = a.n1; }
+    else if (a.axis == 1) { nu = a.n0; nv = a.n2; }
+    else { nu = a.n1; nv = a.n2; }
+    IDP_LEN_SWITCH(a.M, {
+        dim3 grid((nv + LineCfg<L>::LB - 1) / LineCfg<L>::LB, nu);
+        rfft_kernel<L><<<grid, NT, smem_lines<L>(), st>>>(a);
+        return cudaGetLastError();
+    })
+}
+
+cudaError_t launch_face_pass(const FacePass &a, int nchunk, cudaStream_t st)
+{
+    IDP_LEN_SWITCH(2 * a.Mb, {
+        dim3 grid((a.nc + FaceCfg<L>::TC - 1) / FaceCfg<L>::TC, nchunk);
+        face_kernel<L><<<grid, NT, smem_face<L>(), st>>>(a);
+        return cudaGetLastError();
+    })
+}
+
+cudaError_t launch_face_pass_2d(const FacePass2D &a, cudaStream_t st)
+{
+    face2d_kernel<<<(a.nm + 127) / 128, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_face_inv_b(const FaceInvB &a, cudaStream_t st)
+{
+    IDP_LEN_SWITCH(2 * a.Mb, {
+        dim3 grid((a.nc + LineCfg<L>::LB - 1) / LineCfg<L>::LB, 2);
+        face_invb_kernel<L><<<grid, NT, smem_lines<L>(), st>>>(a);
+        return cudaGetLastError();
+    })
+}
+
+cudaError_t launch_face_c2r(const FaceC2R &a, cudaStream_t st)
+{
+    IDP_LEN_SWITCH(a.Mc, {
+        dim3 grid((a.nrows + LineCfg<L>::LB - 1) / LineCfg<L>::LB, 2);
+        face_c2r_kernel<L><<<grid, NT, smem_lines<L>(), st>>>(a);
+        return cudaGetLastError();
+    })
+}
+
+cudaError_t launch_kernel_fill(const KernelFill &a, cudaStream_t st)
+{
+    kernel_fill_kernel<<<1024, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_batched(int m, int n, int k, const double *A, int64_t lda, int64_t sA,
+                                const double *B, int64_t ldb, int64_t sB, double *C, int64_t ldc,
+                                int64_t sC, int batch, cudaStream_t st)
+{
+    dim3 grid((n + GT - 1) / GT, (m + GT - 1) / GT, batch);
+    gemm_kernel<<<grid, 256, 0, st>>>(m, n, k, A, lda, sA, B, ldb, sB, C, ldc, sC);
+    return cudaGetLastError();
+}
+
+}  // namespace idp

@@ -1,0 +1,158 @@
+// Internal declarations shared by the CUDA translation units of libidp.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace idp {
+
+// One twiddle factor w = c + i s stored for the FMA butterfly
+//   A = a + w b,  B = a - w b
+// with the ratio form w b = m ((P - r Q) + i (Q + r P)) (real part scaled by
+// mre, imaginary by mim), where (P, Q) = (b.re, b.im) if |c| >= |s| and
+// (b.im, b.re) otherwise; |r| <= 1 in both cases.
+struct Tw {
+    double r, mre, mim;
+    int swap, pad;
+};
+
+// Tables for one complex FFT length L (power of two): forward and inverse
+// twiddles e^{-+2 pi i j / L}, j < L/2, and the real-transform post/pre
+// twiddles e^{-i pi k / L}, k <= L (cos, sin pairs).
+struct FftTables {
+    int L;
+    const Tw *fwd;      // device, L/2 entries
+    const Tw *inv;      // device, L/2 entries
+    const double2 *half; // device, L+1 entries: (cos(pi k/L), -sin(pi k/L))
+};
+
+// Strided 3-D view in units of elements: element (i0,i1,i2) at base + i0*s0 + i1*s1 + i2*s2.
+struct View3 {
+    double *p;
+    int64_t s0, s1, s2;
+};
+
+// One sine-transform pass along `axis` of an interior-index box n0 x n1 x n2
+// (every extent along `axis` equals M-1).  Each line x -> U with U = 4 * S x,
+// S_{k,i} = sin(pi k i / M); then the epilogue
+//     out = (tab ? tab * U : U) + (add ? add : 0)
+// with tab laid out densely over the box and `add` a strided view.
+struct DstPass {
+    View3 in, out, add;
+    const double *tab;
+    int n0, n1, n2;
+    int axis;
+    int M;
+    const Tw *tw;          // twiddles for the complex FFT of length M/2
+    const double2 *half;   // half-step twiddles for length M/2 (e^{-i pi k/(M/2)})
+    const double *sin2;    // 2 sin(pi j / M), j = 0..M/2
+};
+
+cudaError_t launch_dst_pass(const DstPass &a, cudaStream_t st);
+cudaError_t dst_set_attributes();
+cudaError_t boundary_set_attributes();
+
+// ---- boundary values (section 4) ------------------------------------------
+
+// Stage 1: real FFT of length 2M of each zero-padded line of interior data along
+// `axis`; output M+1 complex values per line, stored at out view (complex units).
+struct RfftPass {
+    const double *in; int64_t is0, is1, is2;     // real input, interior coords
+    double2 *out; int64_t os0, os1, os2;          // complex output; `axis` coordinate = frequency m
+    int n0, n1, n2;                               // interior box (extent along axis = M-1)
+    int axis, M;
+    FftTables t;                                  // tables for complex length M
+};
+cudaError_t launch_rfft_pass(const RfftPass &a, cudaStream_t st);
+
+// Stage 2 (3-D): for each face axis a, FFT of length 2Mb along b of the
+// stage-1 data of every slice p, times the kernel spectra, summed over p.
+struct FacePass {
+    const double2 *D;          // stage-1 data
+    int64_t sp, sb, sc;        // strides (complex units) of slice p, axis b, frequency c
+    int np;                    // number of slices (M_a - 1)
+    int Mb;                    // panels along b (FFT length 2Mb)
+    int nc;                    // number of frequencies along c (M_c + 1)
+    const double *khat;        // [np][Mb+1][nc] real kernel spectra for distance (p+1) h_a
+    double2 *part;             // partial sums [nchunk][2][2Mb][nc]
+    int pchunk;                // slices per chunk
+    FftTables t;               // tables for complex length 2Mb
+};
+cudaError_t launch_face_pass(const FacePass &a, int nchunk, cudaStream_t st);
+int face_columns_per_block(int L);   // frequencies c per block of the face pass
+
+// 2-D contraction: part[0/1][m] = sum_p khat[p or np-1-p][m] * T[p][m]
+struct FacePass2D {
+    const double2 *T; int64_t sp, sm;
+    int np, nm;
+    const double *khat;        // [np][nm]
+    double2 *acc;              // [2][nm]
+};
+cudaError_t launch_face_pass_2d(const FacePass2D &a, cudaStream_t st);
+
+// Stage 3a (3-D): sum the partials and inverse FFT along b; keep rows 0..Mb.
+struct FaceInvB {
+    const double2 *part; int nchunk;
+    int Mb, nc;
+    double2 *out;              // [2][Mb+1][nc]
+    FftTables t;               // length 2Mb
+};
+cudaError_t launch_face_inv_b(const FaceInvB &a, cudaStream_t st);
+
+// Stage 3b: inverse real FFT of length 2Mc of each row (Mc+1 Hermitian
+// coefficients) and scatter the first Mc+1 values into the face nodes of
+// up to two node arrays.  Row r of face f (lo/hi) maps to nodes
+// base_f + r*row_stride + j*col_stride.
+struct FaceC2R {
+    const double2 *in;         // [2][nrows][Mc+1]
+    int nrows, Mc;
+    double *dst0, *dst1;       // node arrays (dst1 may be null)
+    int64_t base[2];           // node offset of row 0, col 0 for lo / hi
+    int64_t row_stride, col_stride;
+    // ownership: skip rows r with skip_row_lo/hi set (edge already owned by a
+    // lower face axis) and columns with col in {0, Mc} if skip_cols is set.
+    int skip_row_edges, skip_col_edges;
+    FftTables t;               // length Mc
+};
+cudaError_t launch_face_c2r(const FaceC2R &a, cudaStream_t st);
+
+// Cyclic-kernel samples k[p][tb][tc] = G(sqrt(((p0+p+1) h_a)^2 + (tb h_b)^2 + (tc h_c)^2)),
+// tb = 0..Mb, tc = 0..Mc (2-D: Mc = 0).
+struct KernelFill {
+    double *k;                 // [np][Mb+1][Mc+1]
+    int d, np, Mb, Mc;
+    double ha, hb, hc;
+    int p0;
+};
+cudaError_t launch_kernel_fill(const KernelFill &a, cudaStream_t st);
+// batched C[b] = A[b] * B[b] (FP64), row-major, strides in elements
+cudaError_t launch_gemm_batched(int m, int n, int k, const double *A, int64_t lda, int64_t sA,
+                                const double *B, int64_t ldb, int64_t sB, double *C, int64_t ldc,
+                                int64_t sC, int batch, cudaStream_t st);
+
+// ---- stencils (section 5) -------------------------------------------------
+struct Grid3 {
+    int d;                     // 2 or 3 (2-D grids use n0 = 1, axes 1,2)
+    int n0, n1, n2;            // node counts (n0 = 1 for d = 2)
+    double h0, h1, h2;
+};
+// Stencil weights computed once on the host: wf/we = L4 face/edge weights,
+// a = 6th-order pair coefficients (see stencil.cu).
+struct StencilCoef {
+    double wf[3];
+    double we[3][3];
+    double a[3][3];
+};
+StencilCoef make_stencil_coef(const Grid3 &g);
+// gtilde = -L4(g extended by 0) on interior nodes; reads boundary of `U`, writes dense interior `out`.
+cudaError_t launch_gtilde(const Grid3 &g, const StencilCoef &c, const double *U, double *out, cudaStream_t st);
+// W_s = sum_{r != s} a_sr (u(+e_r) + u(-e_r) - 2u) on nodes; W is 3 node arrays (2 for d = 2).
+cudaError_t launch_rhs6_w(const Grid3 &g, const StencilCoef &c, const double *U, double *W, cudaStream_t st);
+// R on the core (indices 2..M-2) into dense interior `R`, then extrapolation to the layers 1, M-1.
+cudaError_t launch_rhs6_core(const Grid3 &g, const double *W, double *R, cudaStream_t st);
+cudaError_t launch_rhs6_extrap(const Grid3 &g, double *R, cudaStream_t st);
+// tabc = sc / lambda_c(k) and tab4 = sc / Lambda4(k) on the dense mode grid;
+// lc / ld hold the per-axis 1-D eigenvalues, axis s at offset off_s (axis 0 at 0).
+cudaError_t launch_eigen_tables(const Grid3 &g, const double *lc, const double *ld, int64_t off1,
+                                int64_t off2, double sc, double *tabc, double *tab4, cudaStream_t st);
+
+}  // namespace idp

@@ -1,0 +1,790 @@
+// C ABI of the infinite-domain Poisson solver: plans, workspace, tables and
+// the order of the stages of one solve (section 2: phi = phi* + phi_H).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "idp_internal.cuh"
+#include "../../include/idp.h"
+
+using namespace idp;
+
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", what, cudaGetErrorString(e));
+    return IDP_ECUDA;
+}
+
+#define IDP_CK(call)                                       \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
+
+// host tables ----------------------------------------------------------------
+// sin(pi m / L) and cos(pi m / L) with the integer argument reduced to [0, 2L).
+double sinpi_frac(int64_t m, int64_t L)
+{
+    m %= 2 * L;
+    if (m < 0) m += 2 * L;
+    return std::sin(M_PI * (double)m / (double)L);
+}
+double cospi_frac(int64_t m, int64_t L)
+{
+    m %= 2 * L;
+    if (m < 0) m += 2 * L;
+    return std::cos(M_PI * (double)m / (double)L);
+}
+
+Tw make_tw(double c, double s)
+{
+    Tw t;
+    if (std::fabs(c) >= std::fabs(s)) {
+        t.r = s / c; t.mre = c; t.mim = c; t.swap = 0;
+    } else {
+        t.r = c / s; t.mre = -s; t.mim = s; t.swap = 1;
+    }
+    t.pad = 0;
+    return t;
+}
+
+struct DevFft {
+    Tw *fwd = nullptr, *inv = nullptr;
+    double2 *half = nullptr;
+    FftTables view(int L) const { return FftTables{L, fwd, inv, half}; }
+};
+
+std::mutex g_attr_mu;
+std::vector<int> g_attr_done;
+
+int ensure_attributes(int dev)
+{
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    for (int d : g_attr_done)
+        if (d == dev) return IDP_OK;
+    IDP_CK(dst_set_attributes());
+    IDP_CK(boundary_set_attributes());
+    g_attr_done.push_back(dev);
+    return IDP_OK;
+}
+
+}  // namespace
+
+struct idp_plan_s {
+    int d = 0, order = 0, dev = 0;
+    int n[3] = {1, 1, 1};      // internal node counts (2-D: n[0] = 1)
+    int M[3] = {0, 0, 0};
+    int ni[3] = {1, 1, 1};     // interior extents
+    int act[3] = {0, 0, 0};
+    double h[3] = {1, 1, 1};
+    int64_t nodes = 0, nint = 0;
+    int64_t ns[3] = {0, 0, 0};  // node strides
+    int64_t is[3] = {0, 0, 0};  // interior strides
+    Grid3 grid{};
+    StencilCoef coef{};
+
+    std::map<int, DevFft> fft;        // by complex length
+    std::map<int, double *> sin2;     // by M: 2 sin(pi j / M), j = 0..M/2
+    std::vector<void *> allocs;
+    int64_t bytes = 0;
+
+    double *A = nullptr, *B = nullptr, *C = nullptr, *U = nullptr, *W = nullptr;
+    double *tabc = nullptr, *tab4 = nullptr;
+    double2 *T0 = nullptr, *T1 = nullptr, *part = nullptr, *F = nullptr;
+    double *khat[3] = {nullptr, nullptr, nullptr};
+    int nchunk[3] = {1, 1, 1}, pchunk[3] = {1, 1, 1};
+
+    // per-launch timing (idp_profile_solve)
+    int profiling = 0;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_kind;
+    int ev_used = 0;
+    int64_t launches = 0;      // kernel launches queued by the last enqueue
+
+    // staging for idp_solve_host
+    double *h_rho = nullptr, *h_phi = nullptr;
+
+    // CUDA graph of one solve for a fixed (rho, phi)
+    int use_graph = 1;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const double *g_rho = nullptr;
+    double *g_phi = nullptr;
+    cudaStream_t last = nullptr;
+    int last_valid = 0;
+
+    template <class T>
+    int alloc(T **p, int64_t count)
+    {
+        void *q = nullptr;
+        const size_t b = (size_t)count * sizeof(T);
+        cudaError_t e = cudaMalloc(&q, b > 0 ? b : 16);
+        if (e != cudaSuccess) {
+            cuda_fail(e, "cudaMalloc");
+            return IDP_ENOMEM;
+        }
+        allocs.push_back(q);
+        bytes += (int64_t)b;
+        *p = (T *)q;
+        return IDP_OK;
+    }
+};
+
+namespace {
+
+// Marks one kernel launch: counts it and, while profiling, brackets it with
+// CUDA events recorded on the launch stream.
+struct Mark {
+    idp_plan p;
+    cudaStream_t st;
+    int idx = -1;
+    Mark(idp_plan p_, int kind, cudaStream_t st_) : p(p_), st(st_)
+    {
+        ++p->launches;
+        if (p->profiling && p->ev_used + 2 <= (int)p->ev.size()) {
+            idx = p->ev_used;
+            p->ev_used += 2;
+            p->ev_kind.push_back(kind);
+            cudaEventRecord(p->ev[idx], st);
+        }
+    }
+    ~Mark()
+    {
+        if (idx >= 0) cudaEventRecord(p->ev[idx + 1], st);
+    }
+};
+
+int get_fft(idp_plan p, int L, FftTables *out)
+{
+    auto it = p->fft.find(L);
+    if (it != p->fft.end()) {
+        *out = it->second.view(L);
+        return IDP_OK;
+    }
+    DevFft t;
+    std::vector<Tw> fw(L / 2), iv(L / 2);
+    for (int j = 0; j < L / 2; ++j) {
+        const double c = cospi_frac(2 * j, L), s = sinpi_frac(2 * j, L);
+        fw[j] = make_tw(c, -s);
+        iv[j] = make_tw(c, s);
+    }
+    std::vector<double2> hf(L + 1);
+    for (int k = 0; k <= L; ++k) hf[k] = make_double2(cospi_frac(k, L), -sinpi_frac(k, L));
+    int rc;
+    if ((rc = p->alloc(&t.fwd, L / 2)) || (rc = p->alloc(&t.inv, L / 2)) || (rc = p->alloc(&t.half, L + 1)))
+        return rc;
+    IDP_CK(cudaMemcpy(t.fwd, fw.data(), sizeof(Tw) * (L / 2), cudaMemcpyHostToDevice));
+    IDP_CK(cudaMemcpy(t.inv, iv.data(), sizeof(Tw) * (L / 2), cudaMemcpyHostToDevice));
+    IDP_CK(cudaMemcpy(t.half, hf.data(), sizeof(double2) * (L + 1), cudaMemcpyHostToDevice));
+    p->fft[L] = t;
+    *out = t.view(L);
+    return IDP_OK;
+}
+
+int get_sin2(idp_plan p, int M, const double **out)
+{
+    auto it = p->sin2.find(M);
+    if (it != p->sin2.end()) {
+        *out = it->second;
+        return IDP_OK;
+    }
+    std::vector<double> s(M / 2 + 1);
+    for (int j = 0; j <= M / 2; ++j) s[j] = 2.0 * sinpi_frac(j, M);
+    double *d;
+    int rc = p->alloc(&d, M / 2 + 1);
+    if (rc) return rc;
+    IDP_CK(cudaMemcpy(d, s.data(), sizeof(double) * (M / 2 + 1), cudaMemcpyHostToDevice));
+    p->sin2[M] = d;
+    *out = d;
+    return IDP_OK;
+}
+
+View3 node_interior(idp_plan p, const double *base)
+{
+    int64_t off = 0;
+    for (int s = 0; s < 3; ++s)
+        if (p->act[s]) off += p->ns[s];
+    return View3{const_cast<double *>(base) + off, p->ns[0], p->ns[1], p->ns[2]};
+}
+View3 dense(idp_plan p, const double *base) { return View3{const_cast<double *>(base), p->is[0], p->is[1], p->is[2]}; }
+
+// one full sine transform (all active axes); `first` pass reads `in`, the
+// last pass applies the epilogue (tab, add) and writes `out`; intermediate
+// passes run in place on `work`.
+int transform(idp_plan p, View3 in, double *work, View3 out, const double *tab, View3 add, bool forward,
+              cudaStream_t st)
+{
+    int axes[3], na = 0;
+    if (forward) {
+        for (int s = 2; s >= 0; --s)
+            if (p->act[s]) axes[na++] = s;
+    } else {
+        for (int s = 0; s < 3; ++s)
+            if (p->act[s]) axes[na++] = s;
+    }
+    for (int q = 0; q < na; ++q) {
+        const int s = axes[q];
+        DstPass a{};
+        a.in = (q == 0) ? in : dense(p, work);
+        a.out = (q == na - 1) ? out : dense(p, work);
+        a.add = (q == na - 1) ? add : View3{nullptr, 0, 0, 0};
+        a.tab = (q == na - 1) ? tab : nullptr;
+        a.n0 = p->ni[0]; a.n1 = p->ni[1]; a.n2 = p->ni[2];
+        a.axis = s;
+        a.M = p->M[s];
+        FftTables t;
+        int rc = get_fft(p, p->M[s] / 2, &t);
+        if (rc) return rc;
+        a.tw = t.fwd;
+        a.half = t.half;
+        if ((rc = get_sin2(p, p->M[s], &a.sin2))) return rc;
+        Mark mk(p, IDP_KERNEL_DST, st);
+        IDP_CK(launch_dst_pass(a, st));
+    }
+    return IDP_OK;
+}
+
+// boundary values g into the boundary nodes of dst0 (and dst1 if not null)
+int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStream_t st)
+{
+    const View3 r = node_interior(p, rho);
+    int rc;
+    FftTables t;
+    // stage 1a: along axis 2 -> T0[i0][i1][m2]
+    {
+        RfftPass a{};
+        a.in = r.p; a.is0 = r.s0; a.is1 = r.s1; a.is2 = r.s2;
+        a.out = p->T0;
+        a.os2 = 1; a.os1 = p->M[2] + 1; a.os0 = (int64_t)p->ni[1] * (p->M[2] + 1);
+        a.n0 = p->ni[0]; a.n1 = p->ni[1]; a.n2 = p->ni[2];
+        a.axis = 2; a.M = p->M[2];
+        if ((rc = get_fft(p, p->M[2], &t))) return rc;
+        a.t = t;
+        Mark mk(p, IDP_KERNEL_RFFT, st);
+        IDP_CK(launch_rfft_pass(a, st));
+    }
+    // stage 1b: along axis 1 -> T1[i0][i2][m1]
+    {
+        RfftPass a{};
+        a.in = r.p; a.is0 = r.s0; a.is1 = r.s1; a.is2 = r.s2;
+        a.out = p->T1;
+        a.os1 = 1; a.os2 = p->M[1] + 1; a.os0 = (int64_t)p->ni[2] * (p->M[1] + 1);
+        a.n0 = p->ni[0]; a.n1 = p->ni[1]; a.n2 = p->ni[2];
+        a.axis = 1; a.M = p->M[1];
+        if ((rc = get_fft(p, p->M[1], &t))) return rc;
+        a.t = t;
+        Mark mk(p, IDP_KERNEL_RFFT, st);
+        IDP_CK(launch_rfft_pass(a, st));
+    }
+    if (p->d == 2) {
+        // faces of axis 1 (rows i1 = 0, M1; data along axis 2) and of axis 2
+        for (int face = 1; face <= 2; ++face) {
+            FacePass2D a{};
+            const int other = face == 1 ? 2 : 1;
+            if (face == 1) { a.T = p->T0; a.sp = p->M[2] + 1; a.sm = 1; }
+            else { a.T = p->T1; a.sp = p->M[1] + 1; a.sm = 1; }
+            a.np = p->ni[face];
+            a.nm = p->M[other] + 1;
+            a.khat = p->khat[face];
+            a.acc = p->F;
+            {
+                Mark mk(p, IDP_KERNEL_FACE, st);
+                IDP_CK(launch_face_pass_2d(a, st));
+            }
+            FaceC2R c{};
+            c.in = p->F; c.nrows = 1; c.Mc = p->M[other];
+            c.dst0 = dst0; c.dst1 = dst1;
+            c.base[0] = 0; c.base[1] = (int64_t)p->M[face] * p->ns[face];
+            c.row_stride = 0; c.col_stride = p->ns[other];
+            c.skip_row_edges = 0; c.skip_col_edges = (face == 2);
+            if ((rc = get_fft(p, p->M[other], &t))) return rc;
+            c.t = t;
+            Mark mk(p, IDP_KERNEL_FACE_C2R, st);
+            IDP_CK(launch_face_c2r(c, st));
+        }
+        return IDP_OK;
+    }
+    // 3-D: faces of axis a; b < c the other axes; data and strides per face
+    for (int a_ = 0; a_ < 3; ++a_) {
+        const int b = a_ == 0 ? 1 : 0;
+        const int c = a_ == 2 ? 1 : 2;
+        FacePass f{};
+        if (a_ == 0) { f.D = p->T0; f.sp = (int64_t)p->ni[1] * (p->M[2] + 1); f.sb = p->M[2] + 1; f.sc = 1; }
+        else if (a_ == 1) { f.D = p->T0; f.sp = p->M[2] + 1; f.sb = (int64_t)p->ni[1] * (p->M[2] + 1); f.sc = 1; }
+        else { f.D = p->T1; f.sp = p->M[1] + 1; f.sb = (int64_t)p->ni[2] * (p->M[1] + 1); f.sc = 1; }
+        f.np = p->ni[a_];
+        f.Mb = p->M[b];
+        f.nc = p->M[c] + 1;
+        f.khat = p->khat[a_];
+        f.part = p->part;
+        f.pchunk = p->pchunk[a_];
+        if ((rc = get_fft(p, 2 * p->M[b], &t))) return rc;
+        f.t = t;
+        {
+            Mark mk(p, IDP_KERNEL_FACE, st);
+            IDP_CK(launch_face_pass(f, p->nchunk[a_], st));
+        }
+        FaceInvB ib{};
+        ib.part = p->part; ib.nchunk = p->nchunk[a_];
+        ib.Mb = p->M[b]; ib.nc = f.nc; ib.out = p->F; ib.t = t;
+        {
+            Mark mk(p, IDP_KERNEL_FACE_INVB, st);
+            IDP_CK(launch_face_inv_b(ib, st));
+        }
+        FaceC2R cr{};
+        cr.in = p->F; cr.nrows = p->M[b] + 1; cr.Mc = p->M[c];
+        cr.dst0 = dst0; cr.dst1 = dst1;
+        cr.base[0] = 0; cr.base[1] = (int64_t)p->M[a_] * p->ns[a_];
+        cr.row_stride = p->ns[b]; cr.col_stride = p->ns[c];
+        cr.skip_row_edges = (a_ >= 1);
+        cr.skip_col_edges = (a_ == 2);
+        if ((rc = get_fft(p, p->M[c], &t))) return rc;
+        cr.t = t;
+        Mark mk(p, IDP_KERNEL_FACE_C2R, st);
+        IDP_CK(launch_face_c2r(cr, st));
+    }
+    return IDP_OK;
+}
+
+enum { RUN_PHI = 0 };
+
+// Queue the stages of one solve.  stop: 0 = full solve into phi; otherwise an
+// IDP_STAGE_* value whose result is written to `out`.
+int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t st)
+{
+    int rc;
+    const View3 none{nullptr, 0, 0, 0};
+    const size_t node_bytes = sizeof(double) * p->nodes, int_bytes = sizeof(double) * p->nint;
+    if (stop == IDP_STAGE_BOUNDARY) {
+        IDP_CK(cudaMemsetAsync(phi, 0, node_bytes, st));
+        return boundary(p, rho, phi, nullptr, st);
+    }
+    if (stop == IDP_STAGE_PHISTAR) {
+        IDP_CK(cudaMemsetAsync(phi, 0, node_bytes, st));
+        if ((rc = transform(p, node_interior(p, rho), p->A, dense(p, p->A), p->tabc, none, true, st))) return rc;
+        return transform(p, dense(p, p->A), p->A, node_interior(p, phi), nullptr, none, false, st);
+    }
+    // 1. boundary values: phi boundary and U boundary
+    if ((rc = boundary(p, rho, stop == 0 ? phi : p->U, stop == 0 ? p->U : nullptr, st))) return rc;
+    // 2. gtilde -> B
+    {
+        Mark mk(p, IDP_KERNEL_GTILDE, st);
+        IDP_CK(launch_gtilde(p->grid, p->coef, p->U, p->B, st));
+    }
+    if (stop == IDP_STAGE_GTILDE) {
+        IDP_CK(cudaMemcpyAsync(phi, p->B, int_bytes, cudaMemcpyDeviceToDevice, st));
+        return IDP_OK;
+    }
+    // 3. forward transform of rho, scaled by 1/lambda_c -> A
+    if (stop == 0 || p->order == 6) {
+        if ((rc = transform(p, node_interior(p, rho), p->A, dense(p, p->A), p->tabc, none, true, st))) return rc;
+    }
+    if (p->order == 4 && stop == 0) {
+        // A += tab4 * S gtilde; phi = S A inside
+        if ((rc = transform(p, dense(p, p->B), p->B, dense(p, p->A), p->tab4, dense(p, p->A), true, st))) return rc;
+        return transform(p, dense(p, p->A), p->A, node_interior(p, phi), nullptr, none, false, st);
+    }
+    // 4. u1 = S (tab4 * S gtilde) -> U interior
+    if ((rc = transform(p, dense(p, p->B), p->B, dense(p, p->B), p->tab4, none, true, st))) return rc;
+    if ((rc = transform(p, dense(p, p->B), p->B, node_interior(p, p->U), nullptr, none, false, st))) return rc;
+    if (stop == IDP_STAGE_U1) {
+        IDP_CK(cudaMemcpyAsync(phi, p->U, node_bytes, cudaMemcpyDeviceToDevice, st));
+        return IDP_OK;
+    }
+    // 5. R(u1) with extrapolation -> C
+    {
+        Mark mk(p, IDP_KERNEL_RHS6_W, st);
+        IDP_CK(launch_rhs6_w(p->grid, p->coef, p->U, p->W, st));
+    }
+    {
+        Mark mk(p, IDP_KERNEL_RHS6_CORE, st);
+        IDP_CK(launch_rhs6_core(p->grid, p->W, p->C, st));
+    }
+    {
+        Mark mk(p, IDP_KERNEL_RHS6_EXTRAP, st);
+        IDP_CK(launch_rhs6_extrap(p->grid, p->C, st));
+    }
+    if (stop == IDP_STAGE_R) {
+        IDP_CK(cudaMemcpyAsync(phi, p->C, int_bytes, cudaMemcpyDeviceToDevice, st));
+        return IDP_OK;
+    }
+    // 6. C = A + tab4 * S R;  phi = S C + u1 inside
+    if ((rc = transform(p, dense(p, p->C), p->C, dense(p, p->C), p->tab4, dense(p, p->A), true, st))) return rc;
+    return transform(p, dense(p, p->C), p->C, node_interior(p, phi), nullptr, node_interior(p, p->U), false, st);
+}
+
+int plan_setup(idp_plan p)
+{
+    int rc;
+    // every table a solve uses is created here, so that solves (and their
+    // graph capture) never allocate
+    for (int s = 0; s < 3; ++s) {
+        if (!p->act[s]) continue;
+        FftTables t;
+        const double *sn;
+        if ((rc = get_fft(p, p->M[s] / 2, &t)) || (rc = get_fft(p, p->M[s], &t)) ||
+            (rc = get_fft(p, 2 * p->M[s], &t)) || (rc = get_sin2(p, p->M[s], &sn)))
+            return rc;
+    }
+    // workspace
+    if ((rc = p->alloc(&p->A, p->nint)) || (rc = p->alloc(&p->B, p->nint)) || (rc = p->alloc(&p->C, p->nint)) ||
+        (rc = p->alloc(&p->U, p->nodes)) || (rc = p->alloc(&p->W, 3 * p->nodes)) ||
+        (rc = p->alloc(&p->tabc, p->nint)) || (rc = p->alloc(&p->tab4, p->nint)))
+        return rc;
+    if ((rc = p->alloc(&p->T0, (int64_t)p->ni[0] * p->ni[1] * (p->M[2] + 1))) ||
+        (rc = p->alloc(&p->T1, (int64_t)p->ni[0] * p->ni[2] * (p->M[1] + 1))))
+        return rc;
+    IDP_CK(cudaMemset(p->U, 0, sizeof(double) * p->nodes));
+    IDP_CK(cudaMemset(p->W, 0, sizeof(double) * 3 * p->nodes));
+
+    // eigenvalue tables (sections 3 and 5)
+    {
+        std::vector<double> lc, ld;
+        int64_t off[3] = {0, 0, 0};
+        for (int s = 0; s < 3; ++s) {
+            off[s] = (int64_t)lc.size();
+            if (!p->act[s]) { lc.push_back(0.0); ld.push_back(0.0); continue; }
+            const double L = p->M[s] * p->h[s];
+            for (int k = 1; k < p->M[s]; ++k) {
+                lc.push_back(-(M_PI * M_PI) * (double)k * k / (L * L));
+                const double sn = sinpi_frac(k, 2 * p->M[s]);
+                ld.push_back(-(4.0 / (p->h[s] * p->h[s])) * sn * sn);
+            }
+        }
+        double *dlc, *dld;
+        if ((rc = p->alloc(&dlc, (int64_t)lc.size())) || (rc = p->alloc(&dld, (int64_t)ld.size()))) return rc;
+        IDP_CK(cudaMemcpy(dlc, lc.data(), sizeof(double) * lc.size(), cudaMemcpyHostToDevice));
+        IDP_CK(cudaMemcpy(dld, ld.data(), sizeof(double) * ld.size(), cudaMemcpyHostToDevice));
+        double sc = 1.0;
+        int da = 0;
+        for (int s = 0; s < 3; ++s)
+            if (p->act[s]) { sc *= 2.0 / p->M[s]; ++da; }
+        for (int q = 0; q < 2 * da; ++q) sc *= 0.25;   // each sine pass returns 4 S x
+        IDP_CK(launch_eigen_tables(p->grid, dlc, dld, off[1], off[2], sc, p->tabc, p->tab4, 0));
+    }
+
+    // kernel spectra of the boundary convolutions (section 4)
+    if (p->d == 2) {
+        int64_t fmax = 0;
+        for (int face = 1; face <= 2; ++face) {
+            const int other = face == 1 ? 2 : 1;
+            const int Mb = p->M[other];
+            const int np = p->ni[face];
+            if ((rc = p->alloc(&p->khat[face], (int64_t)np * (Mb + 1)))) return rc;
+            double *kb, *tb;
+            if ((rc = p->alloc(&kb, (int64_t)np * (Mb + 1))) || (rc = p->alloc(&tb, (int64_t)(Mb + 1) * (Mb + 1))))
+                return rc;
+            KernelFill kf{kb, 2, np, Mb, 0, p->h[face], p->h[other], 0.0, 0};
+            IDP_CK(launch_kernel_fill(kf, 0));
+            // DCT-I table Cb[t][m] = w_t cos(pi m t / Mb) * h_a h_b / (4 Mb)
+            std::vector<double> cb((size_t)(Mb + 1) * (Mb + 1));
+            const double sc = p->h[face] * p->h[other] / (4.0 * Mb);
+            for (int tt = 0; tt <= Mb; ++tt)
+                for (int m = 0; m <= Mb; ++m)
+                    cb[(size_t)tt * (Mb + 1) + m] = ((tt == 0 || tt == Mb) ? 1.0 : 2.0) *
+                                                    cospi_frac((int64_t)m * tt, Mb) * sc;
+            IDP_CK(cudaMemcpy(tb, cb.data(), sizeof(double) * cb.size(), cudaMemcpyHostToDevice));
+            IDP_CK(launch_gemm_batched(np, Mb + 1, Mb + 1, kb, Mb + 1, 0, tb, Mb + 1, 0, p->khat[face], Mb + 1, 0,
+                                       1, 0));
+            fmax = std::max<int64_t>(fmax, 2 * (Mb + 1));
+        }
+        if ((rc = p->alloc(&p->F, fmax))) return rc;
+    } else {
+        int64_t pmax = 0, fmax = 0;
+        for (int a_ = 0; a_ < 3; ++a_) {
+            const int b = a_ == 0 ? 1 : 0;
+            const int c = a_ == 2 ? 1 : 2;
+            const int Mb = p->M[b], Mc = p->M[c], np = p->ni[a_];
+            const int L = 2 * Mb;
+            const int TC = face_columns_per_block(L);
+            const int tiles = (Mc + 1 + TC - 1) / TC;
+            // about one wave of resident blocks (2 per SM); fewer chunks = fewer partial sums
+            int nsm = 152;
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->dev);
+            int nch = std::max(1, std::min(np, (2 * nsm) / tiles));
+            int pch = (np + nch - 1) / nch;
+            nch = (np + pch - 1) / pch;
+            p->nchunk[a_] = nch;
+            p->pchunk[a_] = pch;
+            pmax = std::max<int64_t>(pmax, (int64_t)nch * 2 * L * (Mc + 1));
+            fmax = std::max<int64_t>(fmax, (int64_t)2 * (Mb + 1) * (Mc + 1));
+            const int64_t per = (int64_t)(Mb + 1) * (Mc + 1);
+            if ((rc = p->alloc(&p->khat[a_], (int64_t)np * per))) return rc;
+            // build in slabs of slices to bound the temporaries
+            const int slab = std::max(1, (int)std::min<int64_t>(np, (int64_t)(64 << 20) / (per * 8)));
+            double *kb, *yb, *tcb, *tbb;
+            if ((rc = p->alloc(&kb, (int64_t)slab * per)) || (rc = p->alloc(&yb, (int64_t)slab * per)) ||
+                (rc = p->alloc(&tcb, (int64_t)(Mc + 1) * (Mc + 1))) || (rc = p->alloc(&tbb, (int64_t)(Mb + 1) * (Mb + 1))))
+                return rc;
+            std::vector<double> cc((size_t)(Mc + 1) * (Mc + 1)), cbm((size_t)(Mb + 1) * (Mb + 1));
+            const double sc = p->h[0] * p->h[1] * p->h[2] / (8.0 * Mb * Mc);
+            for (int tt = 0; tt <= Mc; ++tt)     // Cc[t][m] = w_t cos(pi m t / Mc) * sc
+                for (int m = 0; m <= Mc; ++m)
+                    cc[(size_t)tt * (Mc + 1) + m] = ((tt == 0 || tt == Mc) ? 1.0 : 2.0) *
+                                                    cospi_frac((int64_t)m * tt, Mc) * sc;
+            for (int m = 0; m <= Mb; ++m)        // Cb[m][t] = w_t cos(pi m t / Mb)
+                for (int tt = 0; tt <= Mb; ++tt)
+                    cbm[(size_t)m * (Mb + 1) + tt] = ((tt == 0 || tt == Mb) ? 1.0 : 2.0) *
+                                                     cospi_frac((int64_t)m * tt, Mb);
+            IDP_CK(cudaMemcpy(tcb, cc.data(), sizeof(double) * cc.size(), cudaMemcpyHostToDevice));
+            IDP_CK(cudaMemcpy(tbb, cbm.data(), sizeof(double) * cbm.size(), cudaMemcpyHostToDevice));
+            for (int p0 = 0; p0 < np; p0 += slab) {
+                const int cnt = std::min(slab, np - p0);
+                KernelFill kf{kb, 3, cnt, Mb, Mc, p->h[a_], p->h[b], p->h[c], p0};
+                IDP_CK(launch_kernel_fill(kf, 0));
+                // rows (t_b) x cols (t_c) times Cc -> Y
+                IDP_CK(launch_gemm_batched(Mb + 1, Mc + 1, Mc + 1, kb, Mc + 1, per, tcb, Mc + 1, 0, yb, Mc + 1, per,
+                                           cnt, 0));
+                IDP_CK(launch_gemm_batched(Mb + 1, Mc + 1, Mb + 1, tbb, Mb + 1, 0, yb, Mc + 1, per,
+                                           p->khat[a_] + (int64_t)p0 * per, Mc + 1, per, cnt, 0));
+            }
+        }
+        if ((rc = p->alloc(&p->part, pmax)) || (rc = p->alloc(&p->F, fmax))) return rc;
+    }
+    IDP_CK(cudaDeviceSynchronize());
+    return IDP_OK;
+}
+
+bool overlap(const void *a, size_t na, const void *b, size_t nb)
+{
+    const char *x = (const char *)a, *y = (const char *)b;
+    return x < y + nb && y < x + na;
+}
+
+int run_solve(idp_plan p, const double *rho, double *phi, cudaStream_t st)
+{
+    p->last = st;
+    p->last_valid = 1;
+    if (!p->use_graph) {
+        p->launches = 0;
+        return enqueue(p, rho, phi, 0, st);
+    }
+    if (!p->gexec || p->g_rho != rho || p->g_phi != phi) {
+        if (!p->cap) IDP_CK(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
+        IDP_CK(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+        p->launches = 0;
+        int rc = enqueue(p, rho, phi, 0, p->cap);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(p->cap, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        if (p->gexec) {
+            cudaGraphExecDestroy(p->gexec);
+            p->gexec = nullptr;
+        }
+        e = cudaGraphInstantiate(&p->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        p->g_rho = rho;
+        p->g_phi = phi;
+    }
+    IDP_CK(cudaGraphLaunch(p->gexec, st));
+    return IDP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int idp_create_plan(idp_plan *out, int d, const int64_t n[], const double h[], int order)
+{
+    if (!out || !n || !h) return IDP_EINVAL;
+    *out = nullptr;
+    if (d != 2 && d != 3) return IDP_EINVAL;
+    if (order != 4 && order != 6) return IDP_EINVAL;
+    for (int s = 0; s < d; ++s) {
+        if (!(h[s] > 0.0) || !std::isfinite(h[s])) return IDP_EINVAL;
+        if (n[s] < 3) return IDP_EINVAL;
+        const int64_t M = n[s] - 1;
+        if (!is_pow2(M) || M < 16 || M > 512) return IDP_ESUPPORT;
+    }
+    idp_plan p = new (std::nothrow) idp_plan_s();
+    if (!p) return IDP_ENOMEM;
+    p->d = d;
+    p->order = order;
+    const int o = 3 - d;
+    for (int s = 0; s < d; ++s) {
+        p->n[s + o] = (int)n[s];
+        p->h[s + o] = h[s];
+        p->act[s + o] = 1;
+    }
+    for (int s = 0; s < 3; ++s) {
+        p->M[s] = p->n[s] - 1;
+        p->ni[s] = p->act[s] ? p->n[s] - 2 : 1;
+    }
+    p->ns[2] = 1; p->ns[1] = p->n[2]; p->ns[0] = (int64_t)p->n[1] * p->n[2];
+    p->is[2] = 1; p->is[1] = p->ni[2]; p->is[0] = (int64_t)p->ni[1] * p->ni[2];
+    p->nodes = (int64_t)p->n[0] * p->n[1] * p->n[2];
+    p->nint = (int64_t)p->ni[0] * p->ni[1] * p->ni[2];
+    p->grid = Grid3{d, p->n[0], p->n[1], p->n[2], p->h[0], p->h[1], p->h[2]};
+    p->coef = make_stencil_coef(p->grid);
+    int rc;
+    cudaError_t e = cudaGetDevice(&p->dev);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaGetDevice");
+    else if (!(rc = ensure_attributes(p->dev))) rc = plan_setup(p);
+    if (rc) {
+        idp_destroy_plan(p);
+        return rc;
+    }
+    *out = p;
+    return IDP_OK;
+}
+
+int idp_plan_set(idp_plan p, int key, int64_t value)
+{
+    if (!p) return IDP_EINVAL;
+    if (key == IDP_KEY_USE_GRAPH) {
+        p->use_graph = value ? 1 : 0;
+        return IDP_OK;
+    }
+    return IDP_EINVAL;
+}
+
+int idp_solve(idp_plan p, const double *rho, double *phi, void *stream)
+{
+    if (!p || !rho || !phi) return IDP_EINVAL;
+    const size_t b = sizeof(double) * p->nodes;
+    if (overlap(rho, b, phi, b)) return IDP_EALIAS;
+    return run_solve(p, rho, phi, (cudaStream_t)stream);
+}
+
+int idp_solve_host(idp_plan p, const double *rho_host, double *phi_host, void *stream)
+{
+    if (!p || !rho_host || !phi_host) return IDP_EINVAL;
+    const size_t b = sizeof(double) * p->nodes;
+    if (overlap(rho_host, b, phi_host, b)) return IDP_EALIAS;
+    int rc;
+    if (!p->h_rho && ((rc = p->alloc(&p->h_rho, p->nodes)) || (rc = p->alloc(&p->h_phi, p->nodes)))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    IDP_CK(cudaMemcpyAsync(p->h_rho, rho_host, b, cudaMemcpyHostToDevice, st));
+    if ((rc = run_solve(p, p->h_rho, p->h_phi, st))) return rc;
+    IDP_CK(cudaMemcpyAsync(phi_host, p->h_phi, b, cudaMemcpyDeviceToHost, st));
+    IDP_CK(cudaStreamSynchronize(st));
+    return IDP_OK;
+}
+
+int idp_solve_batched(int count, const idp_plan plans[], const double *const rho[], double *const phi[],
+                      void *stream)
+{
+    if (count < 0 || (count > 0 && (!plans || !rho || !phi))) return IDP_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i] || !rho[i] || !phi[i]) return IDP_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) return IDP_EINVAL;
+        const size_t b = sizeof(double) * plans[i]->nodes;
+        if (overlap(rho[i], b, phi[i], b)) return IDP_EALIAS;
+    }
+    for (int i = 0; i < count; ++i) {
+        int rc = run_solve(plans[i], rho[i], phi[i], (cudaStream_t)stream);
+        if (rc) return rc;
+    }
+    return IDP_OK;
+}
+
+int idp_solve_stage(idp_plan p, int stage, const double *rho, double *out, void *stream)
+{
+    if (!p || !rho || !out) return IDP_EINVAL;
+    if (stage < IDP_STAGE_BOUNDARY || stage > IDP_STAGE_PHI) return IDP_EINVAL;
+    if (stage == IDP_STAGE_R && p->order != 6) return IDP_EINVAL;
+    const size_t b = sizeof(double) * p->nodes;
+    if (overlap(rho, b, out, b)) return IDP_EALIAS;
+    p->last = (cudaStream_t)stream;
+    p->last_valid = 1;
+    return enqueue(p, rho, out, stage == IDP_STAGE_PHI ? 0 : stage, (cudaStream_t)stream);
+}
+
+int idp_plan_status(idp_plan p)
+{
+    if (!p) return IDP_EINVAL;
+    if (p->last_valid) IDP_CK(cudaStreamSynchronize(p->last));
+    IDP_CK(cudaGetLastError());
+    return IDP_OK;
+}
+
+int idp_profile_solve(idp_plan p, const double *rho, double *phi, void *stream, int capacity, int *kinds,
+                      float *ms)
+{
+    if (!p || !rho || !phi || capacity < 0 || (capacity > 0 && (!kinds || !ms))) return IDP_EINVAL;
+    const size_t b = sizeof(double) * p->nodes;
+    if (overlap(rho, b, phi, b)) return IDP_EALIAS;
+    cudaStream_t st = (cudaStream_t)stream;
+    while ((int)p->ev.size() < 2 * capacity) {
+        cudaEvent_t e;
+        IDP_CK(cudaEventCreate(&e));
+        p->ev.push_back(e);
+    }
+    p->profiling = 1;
+    p->ev_used = 0;
+    p->ev_kind.clear();
+    p->launches = 0;
+    p->last = st;
+    p->last_valid = 1;
+    const int rc = enqueue(p, rho, phi, 0, st);
+    p->profiling = 0;
+    if (rc) return rc;
+    IDP_CK(cudaStreamSynchronize(st));
+    const int n = (int)p->ev_kind.size();
+    for (int i = 0; i < n; ++i) {
+        kinds[i] = p->ev_kind[i];
+        IDP_CK(cudaEventElapsedTime(&ms[i], p->ev[2 * i], p->ev[2 * i + 1]));
+    }
+    return n;
+}
+
+int idp_plan_info(idp_plan p, int64_t *nodes, int64_t *interior, int64_t *workspace_bytes)
+{
+    if (!p) return IDP_EINVAL;
+    if (nodes) *nodes = p->nodes;
+    if (interior) *interior = p->nint;
+    if (workspace_bytes) *workspace_bytes = p->bytes;
+    return IDP_OK;
+}
+
+int idp_destroy_plan(idp_plan p)
+{
+    if (!p) return IDP_EINVAL;
+    cudaDeviceSynchronize();
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->cap) cudaStreamDestroy(p->cap);
+    for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+    for (void *q : p->allocs) cudaFree(q);
+    delete p;
+    return IDP_OK;
+}
+
+const char *idp_strerror(int code)
+{
+    switch (code) {
+    case IDP_OK: return "ok";
+    case IDP_EINVAL: return "invalid argument";
+    case IDP_ENOMEM: return "out of memory";
+    case IDP_ECUDA: return "CUDA error";
+    case IDP_EALIAS: return "input and output overlap";
+    case IDP_ESUPPORT: return "size or option not supported (panel counts must be powers of two in [16, 512])";
+    default: return "unknown error";
+    }
+}
+
+const char *idp_last_cuda_error(void) { return g_cuda_err; }
+
+int idp_plan_launches(idp_plan p, int64_t *launches)
+{
+    if (!p || !launches) return IDP_EINVAL;
+    *launches = p->launches;
+    return IDP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,46 @@
+"""The C ABI library loads and exports what include/idp.h declares (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "idp.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(idp_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2108_11871_gb300 import build
+    return ctypes.CDLL(build.build())
+
+
+def test_header_declares_the_boundary_calls():
+    names = _declared()
+    for n in ("idp_create_plan", "idp_solve", "idp_solve_batched", "idp_destroy_plan",
+              "idp_plan_status", "idp_strerror"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_argument_errors_need_no_gpu():
+    import paper_2108_11871_gb300 as idp
+    lib = idp.library()
+    out = ctypes.c_void_p()
+    n = (ctypes.c_int64 * 3)(33, 33, 33)
+    h = (ctypes.c_double * 3)(0.1, 0.1, 0.1)
+    assert lib.idp_create_plan(ctypes.byref(out), 4, n, h, 6) == idp.IDP_EINVAL
+    assert lib.idp_create_plan(ctypes.byref(out), 3, n, h, 5) == idp.IDP_EINVAL
+    bad = (ctypes.c_int64 * 3)(33, 34, 33)
+    assert lib.idp_create_plan(ctypes.byref(out), 3, bad, h, 6) == idp.IDP_ESUPPORT
+    assert lib.idp_solve(None, None, None, None) == idp.IDP_EINVAL
+    assert idp.strerror(idp.IDP_EALIAS) == "input and output overlap"
