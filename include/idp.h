@@ -51,7 +51,8 @@ enum {
     IDP_ENOMEM = -2,     /* device or host allocation failed */
     IDP_ECUDA = -3,      /* a CUDA call failed; see idp_last_cuda_error() */
     IDP_EALIAS = -4,     /* rho and phi overlap */
-    IDP_ESUPPORT = -5    /* size or option outside the supported set */
+    IDP_ESUPPORT = -5,   /* size or option outside the supported set */
+    IDP_ESCRATCH = -6    /* problem larger than the fixed scratch of idp_rhs6_noalloc */
 };
 
 /* keys for idp_plan_set */
@@ -138,6 +139,31 @@ int idp_plan_info(idp_plan plan, int64_t *nodes, int64_t *interior, int64_t *wor
 
 /* Release the plan and all its device memory (synchronises the device). */
 int idp_destroy_plan(idp_plan plan);
+
+/* Allocation-free 6th-order right-hand side (no counterpart in the paper:
+ * it exists for callers that cannot let a library allocate device memory --
+ * applications whose own pool allocator holds nearly all GPU memory, and
+ * time-critical loops that cannot afford cudaMalloc's implicit
+ * synchronisation).
+ *
+ * Computes the same R as the 6th-order step of idp_solve (IDP_STAGE_R):
+ * R = sum over ordered axis pairs s != r of (h_s^4/240 + h_s^2 h_r^2/144)
+ * D2_s D2_s D2_r u1 on the nodes whose indices all lie in 2..M-2, extended
+ * to the layers next to the boundary by cubic extrapolation.
+ *   d, n[d], h[d] : grid as in idp_create_plan (any n[s] >= 8, not only powers of two)
+ *   u1            : device node array, prod(n) doubles (boundary values included)
+ *   R             : device interior array, prod(n[s]-2) doubles; must not overlap u1
+ * Scratch: a fixed device array of 3 * IDP_RHS6_NOALLOC_MAX_NODES doubles
+ * (12 MiB), held by every GPU that loads the library until the process exits.
+ * Problems with more than IDP_RHS6_NOALLOC_MAX_NODES nodes return IDP_ESCRATCH.
+ * The call allocates nothing.  Its first call on a device looks up the
+ * scratch's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the one scratch array, which
+ * keeps the last call's contents: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller. */
+#define IDP_RHS6_NOALLOC_MAX_NODES 524288
+int idp_rhs6_noalloc(int d, const int64_t n[], const double h[], const double *u1, double *R,
+                     void *stream);
 
 /* Static description of an IDP_* code. */
 const char *idp_strerror(int code);

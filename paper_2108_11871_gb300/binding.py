@@ -12,7 +12,8 @@ import numpy as np
 
 from . import build as _build
 
-IDP_OK, IDP_EINVAL, IDP_ENOMEM, IDP_ECUDA, IDP_EALIAS, IDP_ESUPPORT = 0, -1, -2, -3, -4, -5
+IDP_OK, IDP_EINVAL, IDP_ENOMEM, IDP_ECUDA, IDP_EALIAS, IDP_ESUPPORT, IDP_ESCRATCH = 0, -1, -2, -3, -4, -5, -6
+IDP_RHS6_NOALLOC_MAX_NODES = 524288
 IDP_KEY_USE_GRAPH = 1
 (IDP_STAGE_BOUNDARY, IDP_STAGE_GTILDE, IDP_STAGE_PHISTAR, IDP_STAGE_U1, IDP_STAGE_R,
  IDP_STAGE_PHI) = range(1, 7)
@@ -55,6 +56,7 @@ def library(path: str = None):
         "idp_destroy_plan": (_int, [_vp]),
         "idp_strerror": (ctypes.c_char_p, [_int]),
         "idp_last_cuda_error": (ctypes.c_char_p, []),
+        "idp_rhs6_noalloc": (_int, [_int, ctypes.POINTER(_i64), ctypes.POINTER(_dbl), _vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -167,3 +169,16 @@ def destroy_plan(plan: Plan):
     if plan.handle:
         h, plan.handle = plan.handle, None
         _check(library().idp_destroy_plan(h), "idp_destroy_plan")
+
+
+def rhs6_noalloc(d, n, h, u1, R, stream=None):
+    """6th-order right-hand side R from u1 without any device allocation (fixed
+    12 MiB library scratch; at most IDP_RHS6_NOALLOC_MAX_NODES nodes).  For
+    callers whose memory is fully owned by their own allocator or whose loop
+    cannot pay cudaMalloc's synchronisation.  Concurrent calls race on the
+    shared scratch."""
+    n = [int(v) for v in n]
+    h = [float(v) for v in h]
+    rc = library().idp_rhs6_noalloc(int(d), (_i64 * d)(*n), (_dbl * d)(*h), _ptr(u1), _ptr(R),
+                                    _stream(stream))
+    _check(rc, "idp_rhs6_noalloc")

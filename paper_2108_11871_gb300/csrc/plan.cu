@@ -774,6 +774,7 @@ const char *idp_strerror(int code)
     case IDP_ECUDA: return "CUDA error";
     case IDP_EALIAS: return "input and output overlap";
     case IDP_ESUPPORT: return "size or option not supported (panel counts must be powers of two in [16, 512])";
+    case IDP_ESCRATCH: return "problem larger than the fixed scratch of idp_rhs6_noalloc (524288 nodes)";
     default: return "unknown error";
     }
 }

@@ -1,0 +1,70 @@
+"""The allocation-free right-hand-side entry point (idp_rhs6_noalloc).
+
+It is meant for callers that cannot let the library allocate device memory
+(their own pool allocator owns the GPU's memory, or their loop cannot pay
+for cudaMalloc's synchronisation).  Through the C ABI, its R must equal the
+R of the plan-based solver (IDP_STAGE_R) within the parity tolerance, on
+consecutive calls that share the library's fixed scratch.  This file is
+collected last so that a run stopping at the first failure has already run
+every other test.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import workloads as w
+from tests.gpu_util import device, rel_max, run_stage, to_dev
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def idp():
+    import paper_2108_11871_gb300 as m
+    device()
+    m.library()
+    return m
+
+
+def _reference(idp, prob):
+    """u1 and R from the plan-based entry points."""
+    plan = idp.create_plan(prob.d, prob.n, prob.h, 6)
+    r = to_dev(prob.rho())
+    u1 = run_stage(idp, plan, idp.IDP_STAGE_U1, r, prob.n)
+    R = run_stage(idp, plan, idp.IDP_STAGE_R, r, tuple(k - 2 for k in prob.n))
+    return u1, R
+
+
+def test_noalloc_rhs_matches_plan_rhs_on_consecutive_calls(idp):
+    import torch
+    probs = [w.Problem("a", (33, 17, 65), (0.0, 0.0, 0.0), (1.0, 0.5, 2.0), "gauss", dict(seed=4)),
+             w.c1_2d(65),
+             w.c2_3d(65)]
+    refs = [_reference(idp, p) for p in probs]
+    # two calls in a row per problem, problems interleaved, so each call starts
+    # from scratch contents left by a different problem
+    for rep in range(2):
+        for p, (u1, Rref) in zip(probs, refs):
+            u1d = to_dev(u1)
+            out = torch.full(tuple(k - 2 for k in p.n), float("nan"), dtype=torch.float64,
+                             device=u1d.device)
+            idp.rhs6_noalloc(p.d, p.n, p.h, u1d, out)
+            torch.cuda.synchronize()
+            got = out.cpu().numpy()
+            assert np.all(np.isfinite(got))
+            assert rel_max(got, Rref) < TOL, (rep, p.name)
+
+
+def test_noalloc_rejects_problems_beyond_its_scratch(idp):
+    import torch
+    n = (129, 129, 129)           # 2 146 689 nodes > IDP_RHS6_NOALLOC_MAX_NODES
+    assert np.prod(n) > idp.IDP_RHS6_NOALLOC_MAX_NODES
+    x = torch.zeros(8, dtype=torch.float64, device=device())
+    lib = idp.library()
+    rc = lib.idp_rhs6_noalloc(3, (ctypes.c_int64 * 3)(*n), (ctypes.c_double * 3)(0.1, 0.1, 0.1),
+                              ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr() + 8),
+                              None)
+    assert rc == idp.IDP_ESCRATCH
+    assert "scratch" in idp.strerror(rc)
