@@ -116,14 +116,16 @@ enum {
     IDP_KERNEL_FACE = 3,         /* boundary stage 2: per-slice FFT x kernel spectrum, summed over slices */
     IDP_KERNEL_FACE_INVB = 4,    /* boundary stage 3a: inverse FFT across the face */
     IDP_KERNEL_FACE_C2R = 5,     /* boundary stage 3b: inverse real FFT and scatter to the face nodes */
-    IDP_KERNEL_GTILDE = 6,       /* gtilde stencil (eq. harmonic4thOrderNH2D) */
+    IDP_KERNEL_GTILDE = 6,       /* gtilde stencil on the boundary-adjacent layers (eq. harmonic4thOrderNH2D) */
     IDP_KERNEL_RHS6_W = 7,       /* 6th-order RHS, second differences (eqs. 6thOrderRelation2D/3D) */
     IDP_KERNEL_RHS6_CORE = 8,    /* 6th-order RHS on the core */
-    IDP_KERNEL_RHS6_EXTRAP = 9   /* cubic extrapolation next to the boundary */
+    IDP_KERNEL_RHS6_EXTRAP = 9,  /* cubic extrapolation next to the boundary */
+    IDP_KERNEL_GTILDE_EXPAND = 10, /* sine transform of gtilde assembled from its transformed layers */
+    IDP_KERNEL_DST_PARTS = 11    /* sine passes over the boundary-adjacent layers of gtilde */
 };
 
-/* Run one solve (as idp_solve, but with plain launches) and time every kernel
- * launch with CUDA events recorded on `stream`.  kinds[i] receives the
+/* Run one solve (as idp_solve, but with plain launches, all on `stream`, none
+ * overlapped) and time every kernel launch with CUDA events recorded on `stream`.  kinds[i] receives the
  * IDP_KERNEL_* family and ms[i] the duration of launch i, for at most
  * `capacity` launches.  Synchronises the stream.  Returns the number of
  * launches timed (>= 0) or a negative IDP_E* code. */

@@ -360,6 +360,16 @@ int face_columns_per_block(int L)
     IDP_LEN_SWITCH(L, return FaceCfg<L>::TC;)
 }
 
+int face_blocks_per_sm(int L)
+{
+    int nb = 1;
+    IDP_LEN_SWITCH(L, {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, face_kernel<L>, NT, smem_face<L>()) != cudaSuccess)
+            nb = 1;
+        return nb > 0 ? nb : 1;
+    })
+}
+
 cudaError_t launch_rfft_pass(const RfftPass &a, cudaStream_t st)
 {
     int nu, nv;

@@ -21,8 +21,10 @@ template <int K>
 struct DstCfg {
     static constexpr int M = 2 * K;
     static constexpr int N = M - 1;
-    // lines per block: shared memory = 2 buffers x LB x M doubles <= 64 KB
-    static constexpr int LB = (4096 / M) > 32 ? 32 : (4096 / M);
+    // lines per block: 2 buffers x LB x M doubles (32 KB for M >= 128), at
+    // least 8 lines so that the scan groups fit a warp
+    static constexpr int LB0 = (2048 / M) > 32 ? 32 : (2048 / M);
+    static constexpr int LB = LB0 < 8 ? 8 : LB0;
     static constexpr int G = NT / LB;             // threads per line in the scan
     static constexpr int C = (K / G) > 0 ? K / G : 1;  // scan elements per thread
 };

@@ -79,6 +79,7 @@ struct FacePass {
 };
 cudaError_t launch_face_pass(const FacePass &a, int nchunk, cudaStream_t st);
 int face_columns_per_block(int L);   // frequencies c per block of the face pass
+int face_blocks_per_sm(int L);       // resident blocks per SM of the face pass
 
 // 2-D contraction: part[0/1][m] = sum_p khat[p or np-1-p][m] * T[p][m]
 struct FacePass2D {
@@ -143,8 +144,15 @@ struct StencilCoef {
     double a[3][3];
 };
 StencilCoef make_stencil_coef(const Grid3 &g);
-// gtilde = -L4(g extended by 0) on interior nodes; reads boundary of `U`, writes dense interior `out`.
-cudaError_t launch_gtilde(const Grid3 &g, const StencilCoef &c, const double *U, double *out, cudaStream_t st);
+// gtilde on the boundary-adjacent layers, split into parts Q0 (3-D), Q1, Q2 (see stencil.cu)
+cudaError_t launch_gtilde_planes(const Grid3 &g, const StencilCoef &c, const double *U, double *Q0, double *Q1,
+                                 double *Q2, cudaStream_t st);
+// out = tab * (4^d S gtilde) (+ add) from the transformed parts
+cudaError_t launch_gtilde_expand(const Grid3 &g, const double *Q0, const double *Q1, const double *Q2,
+                                 const double *sin4, const double *tab, const double *add, double *out,
+                                 cudaStream_t st);
+cudaError_t launch_gtilde_scatter(const Grid3 &g, const double *Q0, const double *Q1, const double *Q2,
+                                  double *out, cudaStream_t st);
 // W_s = sum_{r != s} a_sr (u(+e_r) + u(-e_r) - 2u) on nodes; W is 3 node arrays (2 for d = 2).
 cudaError_t launch_rhs6_w(const Grid3 &g, const StencilCoef &c, const double *U, double *W, cudaStream_t st);
 // R on the core (indices 2..M-2) into dense interior `R`, then extrapolation to the layers 1, M-1.

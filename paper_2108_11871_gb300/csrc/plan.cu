@@ -100,6 +100,7 @@ struct idp_plan_s {
 
     double *A = nullptr, *B = nullptr, *C = nullptr, *U = nullptr, *W = nullptr;
     double *tabc = nullptr, *tab4 = nullptr;
+    double *Q0 = nullptr, *Q1 = nullptr, *Q2 = nullptr, *sin4 = nullptr;   // gtilde parts
     double2 *T0 = nullptr, *T1 = nullptr, *part = nullptr, *F = nullptr;
     double *khat[3] = {nullptr, nullptr, nullptr};
     int nchunk[3] = {1, 1, 1}, pchunk[3] = {1, 1, 1};
@@ -117,6 +118,8 @@ struct idp_plan_s {
     // CUDA graph of one solve for a fixed (rho, phi)
     int use_graph = 1;
     cudaStream_t cap = nullptr;
+    cudaStream_t side = nullptr;          // second stream of a solve (forward transform of rho)
+    cudaEvent_t fork = nullptr, join = nullptr;
     cudaGraphExec_t gexec = nullptr;
     const double *g_rho = nullptr;
     double *g_phi = nullptr;
@@ -254,6 +257,56 @@ int transform(idp_plan p, View3 in, double *work, View3 out, const double *tab, 
     return IDP_OK;
 }
 
+// in-place sine passes over a dense box b0 x b1 x b2 along axis 2, then axis 1
+// (if M1 > 0), with panel counts M2 / M1
+int dst_box(idp_plan p, double *x, int b0, int b1, int b2, int M2, int M1, cudaStream_t st)
+{
+    const int axes[2] = {2, 1};
+    const int Ms[2] = {M2, M1};
+    for (int q = 0; q < 2; ++q) {
+        if (Ms[q] <= 0) continue;
+        DstPass a{};
+        const View3 v{x, (int64_t)b1 * b2, b2, 1};
+        a.in = v; a.out = v; a.add = View3{nullptr, 0, 0, 0}; a.tab = nullptr;
+        a.n0 = b0; a.n1 = b1; a.n2 = b2;
+        a.axis = axes[q];
+        a.M = Ms[q];
+        FftTables t;
+        int rc = get_fft(p, Ms[q] / 2, &t);
+        if (rc) return rc;
+        a.tw = t.fwd;
+        a.half = t.half;
+        if ((rc = get_sin2(p, Ms[q], &a.sin2))) return rc;
+        Mark mk(p, IDP_KERNEL_DST_PARTS, st);
+        IDP_CK(launch_dst_pass(a, st));
+    }
+    return IDP_OK;
+}
+
+// gtilde parts Q0, Q1, Q2 and their (d-1)-dimensional sine transforms
+int gtilde_parts(idp_plan p, bool transform_parts, cudaStream_t st)
+{
+    {
+        Mark mk(p, IDP_KERNEL_GTILDE, st);
+        IDP_CK(launch_gtilde_planes(p->grid, p->coef, p->U, p->Q0, p->Q1, p->Q2, st));
+    }
+    if (!transform_parts) return IDP_OK;
+    int rc;
+    const int n0 = p->ni[0], n1 = p->ni[1], n2 = p->ni[2];
+    if (p->d == 3 && n0 == n1 && n1 == n2) {
+        // equal shapes: the three parts form one box of 6 layers
+        if ((rc = dst_box(p, p->Q0, 6, n1, n2, p->M[2], p->M[1], st))) return rc;
+    } else if (p->d == 3) {
+        if ((rc = dst_box(p, p->Q0, 2, n1, n2, p->M[2], p->M[1], st))) return rc;
+        if ((rc = dst_box(p, p->Q1, 2, n0, n2, p->M[2], p->M[0], st))) return rc;
+        if ((rc = dst_box(p, p->Q2, 2, n0, n1, p->M[1], p->M[0], st))) return rc;
+    } else {
+        if ((rc = dst_box(p, p->Q1, 2, 1, n2, p->M[2], 0, st))) return rc;
+        if ((rc = dst_box(p, p->Q2, 2, 1, n1, p->M[1], 0, st))) return rc;
+    }
+    return IDP_OK;
+}
+
 // boundary values g into the boundary nodes of dst0 (and dst1 if not null)
 int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStream_t st)
 {
@@ -374,28 +427,44 @@ int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t s
         if ((rc = transform(p, node_interior(p, rho), p->A, dense(p, p->A), p->tabc, none, true, st))) return rc;
         return transform(p, dense(p, p->A), p->A, node_interior(p, phi), nullptr, none, false, st);
     }
+    // 0. the forward transform of rho does not depend on the boundary values:
+    //    queue it on the side stream so it overlaps the boundary convolutions
+    // (profiling keeps one stream so that every launch is timed on its own)
+    const bool overlap_rho = (stop == 0) && !p->profiling;
+    if (overlap_rho) {
+        IDP_CK(cudaEventRecord(p->fork, st));
+        IDP_CK(cudaStreamWaitEvent(p->side, p->fork, 0));
+        if ((rc = transform(p, node_interior(p, rho), p->A, dense(p, p->A), p->tabc, none, true, p->side)))
+            return rc;
+        IDP_CK(cudaEventRecord(p->join, p->side));
+    }
     // 1. boundary values: phi boundary and U boundary
     if ((rc = boundary(p, rho, stop == 0 ? phi : p->U, stop == 0 ? p->U : nullptr, st))) return rc;
-    // 2. gtilde -> B
-    {
-        Mark mk(p, IDP_KERNEL_GTILDE, st);
-        IDP_CK(launch_gtilde(p->grid, p->coef, p->U, p->B, st));
-    }
+    // 2. gtilde on the boundary-adjacent layers, and the transforms of its parts
+    if ((rc = gtilde_parts(p, stop != IDP_STAGE_GTILDE, st))) return rc;
     if (stop == IDP_STAGE_GTILDE) {
-        IDP_CK(cudaMemcpyAsync(phi, p->B, int_bytes, cudaMemcpyDeviceToDevice, st));
+        IDP_CK(launch_gtilde_scatter(p->grid, p->Q0, p->Q1, p->Q2, phi, st));
         return IDP_OK;
     }
-    // 3. forward transform of rho, scaled by 1/lambda_c -> A
-    if (stop == 0 || p->order == 6) {
+    // 3. the forward transform of rho, scaled by 1/lambda_c (on the side stream
+    //    in a full solve, joined before A is first used)
+    if (stop == 0 && !overlap_rho) {
         if ((rc = transform(p, node_interior(p, rho), p->A, dense(p, p->A), p->tabc, none, true, st))) return rc;
     }
     if (p->order == 4 && stop == 0) {
+        if (overlap_rho) IDP_CK(cudaStreamWaitEvent(st, p->join, 0));
         // A += tab4 * S gtilde; phi = S A inside
-        if ((rc = transform(p, dense(p, p->B), p->B, dense(p, p->A), p->tab4, dense(p, p->A), true, st))) return rc;
+        {
+            Mark mk(p, IDP_KERNEL_GTILDE_EXPAND, st);
+            IDP_CK(launch_gtilde_expand(p->grid, p->Q0, p->Q1, p->Q2, p->sin4, p->tab4, p->A, p->A, st));
+        }
         return transform(p, dense(p, p->A), p->A, node_interior(p, phi), nullptr, none, false, st);
     }
     // 4. u1 = S (tab4 * S gtilde) -> U interior
-    if ((rc = transform(p, dense(p, p->B), p->B, dense(p, p->B), p->tab4, none, true, st))) return rc;
+    {
+        Mark mk(p, IDP_KERNEL_GTILDE_EXPAND, st);
+        IDP_CK(launch_gtilde_expand(p->grid, p->Q0, p->Q1, p->Q2, p->sin4, p->tab4, nullptr, p->B, st));
+    }
     if ((rc = transform(p, dense(p, p->B), p->B, node_interior(p, p->U), nullptr, none, false, st))) return rc;
     if (stop == IDP_STAGE_U1) {
         IDP_CK(cudaMemcpyAsync(phi, p->U, node_bytes, cudaMemcpyDeviceToDevice, st));
@@ -419,6 +488,7 @@ int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t s
         return IDP_OK;
     }
     // 6. C = A + tab4 * S R;  phi = S C + u1 inside
+    if (overlap_rho) IDP_CK(cudaStreamWaitEvent(st, p->join, 0));
     if ((rc = transform(p, dense(p, p->C), p->C, dense(p, p->C), p->tab4, dense(p, p->A), true, st))) return rc;
     return transform(p, dense(p, p->C), p->C, node_interior(p, phi), nullptr, node_interior(p, p->U), false, st);
 }
@@ -444,6 +514,25 @@ int plan_setup(idp_plan p)
     if ((rc = p->alloc(&p->T0, (int64_t)p->ni[0] * p->ni[1] * (p->M[2] + 1))) ||
         (rc = p->alloc(&p->T1, (int64_t)p->ni[0] * p->ni[2] * (p->M[1] + 1))))
         return rc;
+    {
+        const int64_t q0 = 2 * (int64_t)p->ni[1] * p->ni[2], q1 = 2 * (int64_t)p->ni[0] * p->ni[2],
+                      q2 = 2 * (int64_t)p->ni[0] * p->ni[1];
+        if ((rc = p->alloc(&p->Q0, q0 + q1 + q2))) return rc;
+        p->Q1 = p->Q0 + q0;
+        p->Q2 = p->Q1 + q1;
+    }
+    IDP_CK(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+    IDP_CK(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming));
+    IDP_CK(cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming));
+    {
+        std::vector<double> s4;
+        for (int s = 0; s < 3; ++s) {
+            if (!p->act[s]) continue;
+            for (int k = 0; k < p->ni[s]; ++k) s4.push_back(4.0 * sinpi_frac(k + 1, p->M[s]));
+        }
+        if ((rc = p->alloc(&p->sin4, (int64_t)s4.size()))) return rc;
+        IDP_CK(cudaMemcpy(p->sin4, s4.data(), sizeof(double) * s4.size(), cudaMemcpyHostToDevice));
+    }
     IDP_CK(cudaMemset(p->U, 0, sizeof(double) * p->nodes));
     IDP_CK(cudaMemset(p->W, 0, sizeof(double) * 3 * p->nodes));
 
@@ -508,10 +597,11 @@ int plan_setup(idp_plan p)
             const int L = 2 * Mb;
             const int TC = face_columns_per_block(L);
             const int tiles = (Mc + 1 + TC - 1) / TC;
-            // about one wave of resident blocks (2 per SM); fewer chunks = fewer partial sums
+            // one wave of resident blocks; fewer chunks = fewer partial sums
             int nsm = 152;
             cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->dev);
-            int nch = std::max(1, std::min(np, (2 * nsm) / tiles));
+            const int slots = nsm * face_blocks_per_sm(L);
+            int nch = std::max(1, std::min(np, slots / tiles));
             int pch = (np + nch - 1) / nch;
             nch = (np + pch - 1) / pch;
             p->nchunk[a_] = nch;
@@ -759,6 +849,9 @@ int idp_destroy_plan(idp_plan p)
     cudaDeviceSynchronize();
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->cap) cudaStreamDestroy(p->cap);
+    if (p->side) cudaStreamDestroy(p->side);
+    if (p->fork) cudaEventDestroy(p->fork);
+    if (p->join) cudaEventDestroy(p->join);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
     for (void *q : p->allocs) cudaFree(q);
     delete p;

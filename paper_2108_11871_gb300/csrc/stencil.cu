@@ -38,40 +38,121 @@ __device__ __forceinline__ bool on_boundary(const Geo &g, const int j[3])
     return false;
 }
 
-// gtilde = -L4(ghat) at interior nodes, ghat = U on boundary nodes, 0 inside
+// gtilde = -L4(ghat) at interior node i, ghat = U on boundary nodes and 0 inside
 // (eq. harmonic4thOrderNH2D).  L4 weights (host-computed in c): face +-e_s:
 // 1/h_s^2 - 2 sum_r c_sr/(h_s^2 h_r^2); edge +-e_s +-e_r: c_sr/(h_s^2 h_r^2),
-// c_sr = (h_s^2 + h_r^2)/12.  Grid: x = interior index 2, y = index 1, z = index 0.
-__global__ void gtilde_kernel(const Grid3 gg, const StencilCoef c, const double *__restrict__ U,
-                              double *__restrict__ out)
+// c_sr = (h_s^2 + h_r^2)/12.
+__device__ __forceinline__ double gtilde_at(const Geo &g, const StencilCoef &c, const double *__restrict__ U,
+                                            const int i[3])
+{
+    double acc = 0.0;
+    for (int d0 = -1; d0 <= 1; ++d0) {
+        if (d0 != 0 && !g.act[0]) continue;
+        for (int d1 = -1; d1 <= 1; ++d1)
+            for (int d2 = -1; d2 <= 1; ++d2) {
+                const int nz = (d0 != 0) + (d1 != 0) + (d2 != 0);
+                if (nz == 0 || nz == 3) continue;
+                const int j[3] = {i[0] + d0, i[1] + d1, i[2] + d2};
+                if (!on_boundary(g, j)) continue;
+                double wgt;
+                if (nz == 1) wgt = c.wf[d0 != 0 ? 0 : (d1 != 0 ? 1 : 2)];
+                else wgt = c.we[d0 != 0 ? 0 : 1][d2 != 0 ? 2 : 1];
+                acc = fma(wgt, U[j[0] * g.ns[0] + j[1] * g.ns[1] + j[2] * g.ns[2]], acc);
+            }
+    }
+    return -acc;
+}
+
+// gtilde on the layers next to the boundary, as planes (3-D) or lines (2-D).
+// The shell is split by the first axis s whose index is 0 or n_s-1:
+//   Q0[side][i1][i2]  (3-D only)      nodes i0 = side ? n0-1 : 0
+//   Q1[side][i0][i2]                  i1 = side ? n1-1 : 0, i0 not on the i0 layers
+//   Q2[side][i0][i1]                  i2 = side ? n2-1 : 0, i0, i1 not on their layers
+// (2-D: axis 0 is inactive, Q1[side][i2] and Q2[side][i1]).  Entries outside a
+// part are zero.  Interior indices i_s = node index - 1.
+__global__ void gtilde_planes_kernel(const Grid3 gg, const StencilCoef c, const double *__restrict__ U,
+                                     double *__restrict__ Q0, double *__restrict__ Q1, double *__restrict__ Q2)
+{
+    const Geo g = make_geo(gg);
+    const int n0 = g.ni[0], n1 = g.ni[1], n2 = g.ni[2];
+    const int s0 = g.act[0] ? 2 * n1 * n2 : 0, s1 = 2 * n0 * n2, s2 = 2 * n0 * n1;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < s0 + s1 + s2; t += gridDim.x * blockDim.x) {
+        int part, side, a, b;
+        double *dst;
+        if (t < s0) {
+            part = 0; const int q = t; side = q / (n1 * n2); const int r = q - side * n1 * n2;
+            a = r / n2; b = r - a * n2; dst = Q0 + q;
+        } else if (t < s0 + s1) {
+            part = 1; const int q = t - s0; side = q / (n0 * n2); const int r = q - side * n0 * n2;
+            a = r / n2; b = r - a * n2; dst = Q1 + q;
+        } else {
+            part = 2; const int q = t - s0 - s1; side = q / (n0 * n1); const int r = q - side * n0 * n1;
+            a = r / n1; b = r - a * n1; dst = Q2 + q;
+        }
+        int k[3];   // interior indices
+        if (part == 0) { k[0] = side ? n0 - 1 : 0; k[1] = a; k[2] = b; }
+        else if (part == 1) { k[0] = a; k[1] = side ? n1 - 1 : 0; k[2] = b; }
+        else { k[0] = a; k[1] = b; k[2] = side ? n2 - 1 : 0; }
+        bool keep = true;
+        if (part >= 1 && g.act[0] && (k[0] == 0 || k[0] == n0 - 1)) keep = false;
+        if (part == 2 && (k[1] == 0 || k[1] == n1 - 1)) keep = false;
+        double v = 0.0;
+        if (keep) {
+            const int i[3] = {g.act[0] ? k[0] + 1 : 0, k[1] + 1, k[2] + 1};
+            v = gtilde_at(g, c, U, i);
+        }
+        *dst = v;
+    }
+}
+
+// Forward sine transform of gtilde from the transformed parts (U = 4^d S gtilde):
+//   val(k) = sum_s sin4_s(k_s) (Qs[0](k_other) + (-1)^{k_s} Qs[1](k_other)),
+// sin4_s(k) = 4 sin(pi (k+1)/M_s); Qs holds the (d-1)-dimensional transforms of
+// the parts (4^{d-1} S).  out = tab * val (+ add).
+__global__ void gtilde_expand_kernel(const Grid3 gg, const double *__restrict__ Q0, const double *__restrict__ Q1,
+                                     const double *__restrict__ Q2, const double *__restrict__ sin4,
+                                     const double *__restrict__ tab, const double *add, double *out)
 {
     const Geo g = make_geo(gg);
     const int k2 = blockIdx.x * blockDim.x + threadIdx.x;
     const int k1 = blockIdx.y * blockDim.y + threadIdx.y;
     const int k0 = blockIdx.z;
     if (k2 >= g.ni[2] || k1 >= g.ni[1]) return;
-    const int i[3] = {g.act[0] ? k0 + 1 : 0, k1 + 1, k2 + 1};
-    bool shell = false;
-    for (int s = 0; s < 3; ++s)
-        if (g.act[s] && (i[s] == 1 || i[s] == g.M[s] - 1)) shell = true;
-    double acc = 0.0;
-    if (shell) {
-        for (int d0 = -1; d0 <= 1; ++d0) {
-            if (d0 != 0 && !g.act[0]) continue;
-            for (int d1 = -1; d1 <= 1; ++d1)
-                for (int d2 = -1; d2 <= 1; ++d2) {
-                    const int nz = (d0 != 0) + (d1 != 0) + (d2 != 0);
-                    if (nz == 0 || nz == 3) continue;
-                    const int j[3] = {i[0] + d0, i[1] + d1, i[2] + d2};
-                    if (!on_boundary(g, j)) continue;
-                    double wgt;
-                    if (nz == 1) wgt = c.wf[d0 != 0 ? 0 : (d1 != 0 ? 1 : 2)];
-                    else wgt = c.we[d0 != 0 ? 0 : 1][d2 != 0 ? 2 : 1];
-                    acc = fma(wgt, U[j[0] * g.ns[0] + j[1] * g.ns[1] + j[2] * g.ns[2]], acc);
-                }
-        }
+    const int n0 = g.ni[0], n1 = g.ni[1], n2 = g.ni[2];
+    const double *sn0 = sin4, *sn1 = sin4 + (g.act[0] ? n0 : 0), *sn2 = sn1 + n1;
+    double v;
+    {
+        const double a = Q1[(int64_t)k0 * n2 + k2], b = Q1[(int64_t)(n0 + k0) * n2 + k2];
+        v = sn1[k1] * ((k1 & 1) ? a - b : a + b);
     }
-    out[k0 * g.is[0] + (int64_t)k1 * g.is[1] + k2] = -acc;
+    {
+        const double a = Q2[(int64_t)k0 * n1 + k1], b = Q2[(int64_t)(n0 + k0) * n1 + k1];
+        v = fma(sn2[k2], (k2 & 1) ? a - b : a + b, v);
+    }
+    if (g.act[0]) {
+        const int64_t o = (int64_t)k1 * n2 + k2;
+        const double a = Q0[o], b = Q0[(int64_t)n1 * n2 + o];
+        v = fma(sn0[k0], (k0 & 1) ? a - b : a + b, v);
+    }
+    const int64_t t = k0 * g.is[0] + (int64_t)k1 * g.is[1] + k2;
+    out[t] = add ? fma(tab[t], v, add[t]) : tab[t] * v;
+}
+
+// gtilde as a dense interior array from its parts (for the stage output).
+__global__ void gtilde_scatter_kernel(const Grid3 gg, const double *__restrict__ Q0, const double *__restrict__ Q1,
+                                      const double *__restrict__ Q2, double *__restrict__ out)
+{
+    const Geo g = make_geo(gg);
+    const int k2 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k1 = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k0 = blockIdx.z;
+    if (k2 >= g.ni[2] || k1 >= g.ni[1]) return;
+    const int n0 = g.ni[0], n1 = g.ni[1], n2 = g.ni[2];
+    double v = 0.0;
+    if (g.act[0] && (k0 == 0 || k0 == n0 - 1)) v = Q0[((int64_t)(k0 ? 1 : 0) * n1 + k1) * n2 + k2];
+    else if (k1 == 0 || k1 == n1 - 1) v = Q1[((int64_t)(k1 ? 1 : 0) * n0 + k0) * n2 + k2];
+    else if (k2 == 0 || k2 == n2 - 1) v = Q2[((int64_t)(k2 ? 1 : 0) * n0 + k0) * n1 + k1];
+    out[k0 * g.is[0] + (int64_t)k1 * g.is[1] + k2] = v;
 }
 
 // W_s(j) = sum_{r != s} a_sr (U(j+e_r) + U(j-e_r) - 2 U(j)),
@@ -237,9 +318,29 @@ StencilCoef make_stencil_coef(const Grid3 &g)
 
 dim3 grid3(int x, int y, int z) { return dim3((x + 31) / 32, (y + 7) / 8, z); }
 
-cudaError_t launch_gtilde(const Grid3 &g, const StencilCoef &c, const double *U, double *out, cudaStream_t st)
+cudaError_t launch_gtilde_planes(const Grid3 &g, const StencilCoef &c, const double *U, double *Q0, double *Q1,
+                                 double *Q2, cudaStream_t st)
 {
-    gtilde_kernel<<<grid3(g.n2 - 2, g.n1 - 2, g.d == 3 ? g.n0 - 2 : 1), dim3(32, 8), 0, st>>>(g, c, U, out);
+    const int64_t n0 = g.d == 3 ? g.n0 - 2 : 1, n1 = g.n1 - 2, n2 = g.n2 - 2;
+    const int64_t total = (g.d == 3 ? 2 * n1 * n2 : 0) + 2 * n0 * n2 + 2 * n0 * n1;
+    gtilde_planes_kernel<<<grid_for(total), 256, 0, st>>>(g, c, U, Q0, Q1, Q2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gtilde_expand(const Grid3 &g, const double *Q0, const double *Q1, const double *Q2,
+                                 const double *sin4, const double *tab, const double *add, double *out,
+                                 cudaStream_t st)
+{
+    gtilde_expand_kernel<<<grid3(g.n2 - 2, g.n1 - 2, g.d == 3 ? g.n0 - 2 : 1), dim3(32, 8), 0, st>>>(
+        g, Q0, Q1, Q2, sin4, tab, add, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gtilde_scatter(const Grid3 &g, const double *Q0, const double *Q1, const double *Q2,
+                                  double *out, cudaStream_t st)
+{
+    gtilde_scatter_kernel<<<grid3(g.n2 - 2, g.n1 - 2, g.d == 3 ? g.n0 - 2 : 1), dim3(32, 8), 0, st>>>(
+        g, Q0, Q1, Q2, out);
     return cudaGetLastError();
 }
 
