@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=129)
     ap.add_argument("--order", type=int, default=6)
+    ap.add_argument("--fp64-only", action="store_true", help="skip the mixed-precision variant")
     return ap.parse_args()
 
 
@@ -217,7 +218,7 @@ def run_ours(args, rank, world):
         for j in range(n):
             per_kind.setdefault(kinds[j], []).append(ms[j])
     names = {1: "dst_pass", 2: "rfft", 3: "face", 4: "face_invb", 5: "face_c2r", 6: "gtilde_layers",
-             7: "rhs6_w", 8: "rhs6_core", 9: "rhs6_extrap", 10: "gtilde_expand", 11: "dst_pass_layers"}
+             7: "rhs6_w", 8: "rhs6_core", 9: "rhs6_extrap", 10: "gtilde_expand", 11: "dst_pass_layers", 12: "mixed_pass"}
     prof_steps = max(3, min(args.steps, 10))
     shares = {names[k]: sum(v) / prof_steps for k, v in per_kind.items()}
     dom = max(per_kind, key=lambda k: sum(per_kind[k]))
@@ -238,6 +239,32 @@ def run_ours(args, rank, world):
     e2e = {"value": world * prob.points / e2e_t, "unit": UNIT,
            "h2d_bytes_per_step": 8 * prob.points, "d2h_bytes_per_step": 8 * prob.points}
 
+    # mixed-precision variant (tensor-core sine transforms), same workload and timing rules
+    mixed = None
+    if not args.fp64_only:
+        mplan = idp.create_plan(3, prob.n, prob.h, args.order)
+        idp.plan_set(mplan, idp.IDP_KEY_PRECISION, idp.IDP_PRECISION_MIXED_BF16X3)
+        phi_m = torch.empty_like(rho)
+        for _ in range(args.warmup):
+            idp.solve(mplan, rho, phi_m, stream)
+        torch.cuda.synchronize()
+        idp.plan_status(mplan)
+        ms_m = []
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            idp.solve(mplan, rho, phi_m, stream)
+            s1.record(stream)
+            ms_m.append((s0, s1))
+        torch.cuda.synchronize()
+        idp.plan_status(mplan)
+        t_m = sum(a.elapsed_time(b) for a, b in ms_m)
+        diff = (phi_m - phi).abs().max().item() / phi.abs().max().item()
+        mixed = {"variant": "bf16x3 pieces, fp32 accumulate, tcgen05 (rho, R and final transforms)",
+                 "value": world * prob.points * args.steps / (t_m / 1e3), "unit": UNIT,
+                 "ms_per_step": t_m / args.steps, "max_rel_error_vs_fp64": diff}
+
     if rank != 0:
         return
     out = phi.cpu().numpy()
@@ -249,6 +276,7 @@ def run_ours(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(prob, args.order, {"parallelism": "replicas" if world > 1 else "single"}),
             "precision": {"variant": "fp64", "max_rel_error_vs_exact_potential": err_exact},
+            "mixed_precision": mixed,
             "e2e": e2e,
             "gpu_launches": int(launches.value) * args.steps,
             "roofline": {"bound": "alu", "kernel": "dst_pass (FP64 sine-transform pass)",

@@ -52,12 +52,26 @@ enum {
     IDP_ECUDA = -3,      /* a CUDA call failed; see idp_last_cuda_error() */
     IDP_EALIAS = -4,     /* rho and phi overlap */
     IDP_ESUPPORT = -5,   /* size or option outside the supported set */
-    IDP_ESCRATCH = -6    /* problem larger than the fixed scratch of idp_rhs6_noalloc */
+    IDP_ESCRATCH = -6,   /* problem larger than the fixed scratch of idp_rhs6_noalloc */
+    IDP_ETIMEOUT = -7    /* a device-side wait exceeded its iteration limit */
 };
 
 /* keys for idp_plan_set */
 enum {
-    IDP_KEY_USE_GRAPH = 1   /* 1 (default): replay solves from a CUDA graph; 0: plain launches */
+    IDP_KEY_USE_GRAPH = 1,  /* 1 (default): replay solves from a CUDA graph; 0: plain launches */
+    IDP_KEY_PRECISION = 2   /* IDP_PRECISION_*: arithmetic of the four full-volume sine transforms */
+};
+
+/* values of IDP_KEY_PRECISION */
+enum {
+    IDP_PRECISION_FP64 = 0,        /* FP64 FFT-based sine transforms (default) */
+    IDP_PRECISION_MIXED_BF16X3 = 1 /* the sine transforms of rho, of R and the final inverse become
+                                      dense sine-matrix products on the tensor cores: operands split
+                                      into three BF16 pieces, six products, FP32 accumulation
+                                      (relative error of phi ~1e-5 or better); the eigenvalue division,
+                                      the boundary values, the stencils and the transform that produces
+                                      u1 (whose sixth differences form R) stay FP64.  Setting it
+                                      allocates the pieces of the sine matrices and FP32 temporaries. */
 };
 
 /* stages for idp_solve_stage */
@@ -105,8 +119,9 @@ int idp_solve_batched(int count, const idp_plan plans[], const double *const rho
  * the components against a reference. */
 int idp_solve_stage(idp_plan plan, int stage, const double *rho, double *out, void *stream);
 
-/* Device-side status of the plan's last queued work: IDP_OK or IDP_ECUDA if a
- * launch or asynchronous error was recorded.  Synchronises the plan's last stream. */
+/* Device-side status of the plan's last queued work: IDP_OK, IDP_ECUDA if a
+ * launch or asynchronous error was recorded, or IDP_ETIMEOUT if a bounded
+ * device-side wait gave up.  Synchronises the plan's last stream. */
 int idp_plan_status(idp_plan plan);
 
 /* kernel families reported by idp_profile_solve */
@@ -121,7 +136,8 @@ enum {
     IDP_KERNEL_RHS6_CORE = 8,    /* 6th-order RHS on the core */
     IDP_KERNEL_RHS6_EXTRAP = 9,  /* cubic extrapolation next to the boundary */
     IDP_KERNEL_GTILDE_EXPAND = 10, /* sine transform of gtilde assembled from its transformed layers */
-    IDP_KERNEL_DST_PARTS = 11    /* sine passes over the boundary-adjacent layers of gtilde */
+    IDP_KERNEL_DST_PARTS = 11,   /* sine passes over the boundary-adjacent layers of gtilde */
+    IDP_KERNEL_MIXED = 12        /* tensor-core sine-matrix pass (IDP_PRECISION_MIXED_BF16X3) */
 };
 
 /* Run one solve (as idp_solve, but with plain launches, all on `stream`, none

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libidp.so")
-SOURCES = ["dst.cu", "boundary.cu", "stencil.cu", "plan.cu", "noalloc.cu"]
+SOURCES = ["dst.cu", "boundary.cu", "stencil.cu", "plan.cu", "noalloc.cu", "mixed.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

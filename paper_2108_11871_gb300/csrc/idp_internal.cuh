@@ -51,6 +51,24 @@ cudaError_t launch_dst_pass(const DstPass &a, cudaStream_t st);
 cudaError_t dst_set_attributes();
 cudaError_t boundary_set_attributes();
 
+// ---- mixed-precision sine pass on the tensor cores (mixed.cu) ---------------
+// Y[m][p][q] = 4 sum_k S[m][k] X[p][q][k] for every line (p, q), S_{m,k} =
+// sin(pi (m+1)(k+1)/M), k, m < n = M-1.  Input/output elements are FP64 or
+// FP32; on FP64 output the epilogue out = tab * Y (+ add) is applied in FP64.
+struct MpPass {
+    const void *in; int in_f64;
+    int64_t is_p, is_q, is_k;
+    void *out; int out_f64;
+    int64_t os_m, os_p, os_q;
+    int P, Q, n;
+    const void *bimg;           // BF16 pieces of S: [ntile][kblock][3][128 x 64 tile]
+    const double *tab; int64_t ts_m, ts_p, ts_q;
+    const double *add; int64_t as_m, as_p, as_q;
+    int *err;                   // set to 1 if a wait on the tensor cores timed out
+};
+cudaError_t launch_mp_pass(const MpPass &a, cudaStream_t st);
+cudaError_t mp_set_attributes();
+
 // ---- boundary values (section 4) ------------------------------------------
 
 // Stage 1: real FFT of length 2M of each zero-padded line of interior data along

@@ -1,0 +1,245 @@
+// Mixed-precision sine-transform pass on the 5th-generation tensor cores.
+//
+// One pass transforms every line of an array along its contiguous axis:
+//     Y[m][L] = 4 * sum_k S[m][k] X[L][k],   S[m][k] = sin(pi (m+1)(k+1) / M),
+// with lines L = p*Q + q read from a strided view and the result written with
+// the transformed axis outermost (the pass rotates the axes; three passes of
+// a 3-D transform, two of a 2-D one, return to the original layout).
+//
+// Precision: X and S are split into three BF16 pieces each (x = x0 + x1 + x2,
+// |x_i| ~ 2^-8i |x|); the six products with i + j <= 2 are accumulated by
+// tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) in one TMEM accumulator.
+// The dropped products are below 2^-24 relative, so the error is set by the
+// FP32 accumulation.  The eigenvalue scaling and the additions of the last
+// pass are done in FP64.
+//
+// Block: 128 threads, a tile of 128 lines x 128 modes, K in blocks of 64.
+// Operands live in shared memory in the canonical K-major layout without
+// swizzle: 8 x 16-byte core matrices, core matrices adjacent along K are
+// LBO = 2048 bytes apart, adjacent along M/N SBO = 128 bytes apart.
+#include <cuda_bf16.h>
+
+#include "idp_internal.cuh"
+
+namespace idp {
+
+namespace {
+
+constexpr int MT = 128;            // lines per tile (MMA M)
+constexpr int NTILE = 128;         // modes per tile (MMA N)
+constexpr int KB = 64;             // K per shared-memory block
+constexpr int PIECES = 3;
+constexpr int TILE_BYTES = MT * KB * 2;                 // 16 KB per operand piece
+constexpr int SMEM_A = 0;
+constexpr int SMEM_B = PIECES * TILE_BYTES;
+constexpr int SMEM_BAR = 2 * PIECES * TILE_BYTES;       // mbarrier (8 B) + TMEM address (4 B)
+constexpr int SMEM_TOTAL = SMEM_BAR + 64;
+constexpr uint32_t LBO = 2048, SBO = 128;
+constexpr long long WAIT_CYCLES = 2000000000ll;       // bounded mbarrier polling (~1 s)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// byte offset of element (row r, k) of a 128 x 64 BF16 tile
+__device__ __forceinline__ uint32_t tile_off(int r, int k)
+{
+    return (uint32_t)((k >> 3) * LBO + (r >> 3) * SBO + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// shared-memory matrix descriptor: start, LBO, SBO (>> 4), version 1, no swizzle
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)((LBO >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((SBO >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// instruction descriptor: kind::f16, A = B = BF16, D = F32, K-major, M = 128, N = 128
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NTILE >> 3) << 17) |
+                           ((uint32_t)(MT >> 4) << 24);
+
+__device__ __forceinline__ void split3(double x, __nv_bfloat16 &a, __nv_bfloat16 &b, __nv_bfloat16 &c)
+{
+    a = __float2bfloat16_rn((float)x);
+    const double r1 = x - (double)__bfloat162float(a);
+    b = __float2bfloat16_rn((float)r1);
+    const double r2 = r1 - (double)__bfloat162float(b);
+    c = __float2bfloat16_rn((float)r2);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (clock64() - t0 < WAIT_CYCLES) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(128) mp_pass_kernel(const MpPass a)
+{
+    extern __shared__ __align__(128) unsigned char sm[];
+    const int t = threadIdx.x;
+    const int warp = t >> 5, lane = t & 31;
+    const int64_t nlines = (int64_t)a.P * a.Q;
+    const int64_t L0 = (int64_t)blockIdx.x * MT;
+    const int m0 = blockIdx.y * NTILE;
+    const int nkb = (a.n + KB - 1) / KB;
+    const uint32_t bar = smem_u32(sm + SMEM_BAR);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + SMEM_BAR + 8);
+    __shared__ int s_fail;
+
+    if (t == 0) {
+        s_fail = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(NTILE)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    for (int kb = 0; kb < nkb; ++kb) {
+        // A pieces: 128 lines x 64 k of the input, split into BF16 pieces
+        for (int e = t; e < MT * KB; e += 128) {
+            const int r = e >> 6, k = e & 63;
+            const int64_t L = L0 + r;
+            const int kg = kb * KB + k;
+            double x = 0.0;
+            if (L < nlines && kg < a.n) {
+                const int64_t p = L / a.Q, q = L - p * a.Q;
+                const int64_t off = p * a.is_p + q * a.is_q + (int64_t)kg * a.is_k;
+                x = a.in_f64 ? reinterpret_cast<const double *>(a.in)[off]
+                             : (double)reinterpret_cast<const float *>(a.in)[off];
+            }
+            __nv_bfloat16 x0, x1, x2;
+            split3(x, x0, x1, x2);
+            const uint32_t o = tile_off(r, k);
+            *reinterpret_cast<__nv_bfloat16 *>(sm + SMEM_A + 0 * TILE_BYTES + o) = x0;
+            *reinterpret_cast<__nv_bfloat16 *>(sm + SMEM_A + 1 * TILE_BYTES + o) = x1;
+            *reinterpret_cast<__nv_bfloat16 *>(sm + SMEM_A + 2 * TILE_BYTES + o) = x2;
+        }
+        // B pieces: pre-split sine-matrix images, copied as 16-byte vectors
+        {
+            const int4 *src = reinterpret_cast<const int4 *>(a.bimg) +
+                              ((int64_t)blockIdx.y * nkb + kb) * (PIECES * TILE_BYTES / 16);
+            int4 *dst = reinterpret_cast<int4 *>(sm + SMEM_B);
+            for (int e = t; e < PIECES * TILE_BYTES / 16; e += 128) dst[e] = src[e];
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            // products (i, j) with i + j <= 2
+            const int pa[6] = {0, 0, 1, 0, 1, 2};
+            const int pb[6] = {0, 1, 0, 2, 1, 0};
+            for (int pr = 0; pr < 6; ++pr) {
+                for (int ks = 0; ks < KB / 16; ++ks) {
+                    const uint64_t ad = make_desc(smem_u32(sm + SMEM_A + pa[pr] * TILE_BYTES) + ks * 2 * LBO);
+                    const uint64_t bd = make_desc(smem_u32(sm + SMEM_B + pb[pr] * TILE_BYTES) + ks * 2 * LBO);
+                    const uint32_t acc = (kb > 0 || pr > 0 || ks > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
+                        : "memory");
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             bar)
+                         : "memory");
+        }
+        // every thread waits for the products (they read the shared memory we refill next)
+        if (!mbar_wait(bar, (uint32_t)(kb & 1))) s_fail = 1;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        __syncthreads();
+        if (s_fail) break;
+    }
+
+    if (!s_fail) {
+        // epilogue: lane quadrant of this warp = lines 32*warp .. 32*warp+31
+        const int64_t L = L0 + 32 * warp + lane;
+        const bool live = L < nlines;
+        int64_t p = 0, q = 0;
+        if (live) { p = L / a.Q; q = L - p * a.Q; }
+        for (int c0 = 0; c0 < NTILE; c0 += 32) {
+            uint32_t v[32];
+            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                  "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                  "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+                  "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+                  "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            if (!live) continue;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int m = m0 + c0 + j;
+                if (m >= a.n) break;
+                const double y = 4.0 * (double)__uint_as_float(v[j]);
+                const int64_t oo = (int64_t)m * a.os_m + p * a.os_p + q * a.os_q;
+                if (a.out_f64) {
+                    double r = y;
+                    if (a.tab) {
+                        const double tv = a.tab[(int64_t)m * a.ts_m + p * a.ts_p + q * a.ts_q];
+                        r = a.add ? fma(tv, y, a.add[(int64_t)m * a.as_m + p * a.as_p + q * a.as_q]) : tv * y;
+                    } else if (a.add) {
+                        r = y + a.add[(int64_t)m * a.as_m + p * a.as_p + q * a.as_q];
+                    }
+                    reinterpret_cast<double *>(a.out)[oo] = r;
+                } else {
+                    reinterpret_cast<float *>(a.out)[oo] = (float)y;
+                }
+            }
+        }
+    } else if (t == 0 && a.err) {
+        atomicExch(a.err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(NTILE)
+                     : "memory");
+    }
+}
+
+}  // namespace
+
+size_t mp_smem_bytes() { return SMEM_TOTAL; }
+
+cudaError_t mp_set_attributes()
+{
+    return cudaFuncSetAttribute(mp_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL);
+}
+
+cudaError_t launch_mp_pass(const MpPass &a, cudaStream_t st)
+{
+    const int64_t lines = (int64_t)a.P * a.Q;
+    dim3 grid((unsigned)((lines + MT - 1) / MT), (unsigned)((a.n + NTILE - 1) / NTILE));
+    mp_pass_kernel<<<grid, 128, SMEM_TOTAL, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace idp

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -65,6 +66,7 @@ struct DevFft {
 };
 
 std::mutex g_attr_mu;
+std::atomic<uint64_t> g_serial{1};
 std::vector<int> g_attr_done;
 
 int ensure_attributes(int dev)
@@ -74,14 +76,28 @@ int ensure_attributes(int dev)
         if (d == dev) return IDP_OK;
     IDP_CK(dst_set_attributes());
     IDP_CK(boundary_set_attributes());
+    IDP_CK(mp_set_attributes());
     g_attr_done.push_back(dev);
     return IDP_OK;
 }
 
 }  // namespace
 
+struct BatchCache {
+    std::vector<uint64_t> serials;
+    std::vector<const double *> rho;
+    std::vector<double *> phi;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
+};
+
 struct idp_plan_s {
     int d = 0, order = 0, dev = 0;
+    uint64_t serial = 0;                 // unique per plan (keys the batch graph cache)
+    uint64_t version = 0;                // bumped when an option changes the queued work
+    cudaStream_t bst = nullptr;          // this plan's branch stream in a batched graph
+    BatchCache *batch = nullptr;         // batched graph owned by this plan (first of its batch)
     int n[3] = {1, 1, 1};      // internal node counts (2-D: n[0] = 1)
     int M[3] = {0, 0, 0};
     int ni[3] = {1, 1, 1};     // interior extents
@@ -104,6 +120,12 @@ struct idp_plan_s {
     double2 *T0 = nullptr, *T1 = nullptr, *part = nullptr, *F = nullptr;
     double *khat[3] = {nullptr, nullptr, nullptr};
     int nchunk[3] = {1, 1, 1}, pchunk[3] = {1, 1, 1};
+
+    // mixed precision (IDP_KEY_PRECISION = 1): sine passes on the tensor cores
+    int mixed = 0;
+    std::map<int, void *> mp_img;     // by M: BF16 pieces of the sine matrix
+    float *t32[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [stream][ping/pong]
+    int *d_err = nullptr;
 
     // per-launch timing (idp_profile_solve)
     int profiling = 0;
@@ -221,12 +243,116 @@ View3 node_interior(idp_plan p, const double *base)
 }
 View3 dense(idp_plan p, const double *base) { return View3{const_cast<double *>(base), p->is[0], p->is[1], p->is[2]}; }
 
+uint16_t bf16_bits(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);   // round to nearest even (finite values)
+    return (uint16_t)(u >> 16);
+}
+double bf16_value(uint16_t b)
+{
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+// BF16 pieces of S_{m,k} = sin(pi (m+1)(k+1)/M), laid out as the kernel's
+// shared-memory tiles: [ntile][kblock][piece][128 rows m x 64 k], element
+// (r, c) at byte (c/8)*2048 + (r/8)*128 + (r%8)*16 + (c%8)*2.
+int get_mp_image(idp_plan p, int M, const void **out)
+{
+    auto it = p->mp_img.find(M);
+    if (it != p->mp_img.end()) {
+        *out = it->second;
+        return IDP_OK;
+    }
+    const int n = M - 1, nt = (n + 127) / 128, nkb = (n + 63) / 64;
+    const size_t tile = 128 * 64;
+    std::vector<uint16_t> img((size_t)nt * nkb * 3 * tile, 0);
+    for (int t = 0; t < nt; ++t)
+        for (int kb = 0; kb < nkb; ++kb)
+            for (int r = 0; r < 128; ++r)
+                for (int c = 0; c < 64; ++c) {
+                    const int m = t * 128 + r, k = kb * 64 + c;
+                    const double s = (m < n && k < n) ? sinpi_frac((int64_t)(m + 1) * (k + 1), M) : 0.0;
+                    const uint16_t a = bf16_bits((float)s);
+                    const double r1 = s - bf16_value(a);
+                    const uint16_t b = bf16_bits((float)r1);
+                    const double r2 = r1 - bf16_value(b);
+                    const uint16_t cc = bf16_bits((float)r2);
+                    const size_t off = ((size_t)(c / 8) * 2048 + (r / 8) * 128 + (r % 8) * 16 + (c % 8) * 2) / 2;
+                    const size_t base = (((size_t)t * nkb + kb) * 3) * tile;
+                    img[base + off] = a;
+                    img[base + tile + off] = b;
+                    img[base + 2 * tile + off] = cc;
+                }
+    uint16_t *d;
+    int rc = p->alloc(&d, (int64_t)img.size());
+    if (rc) return rc;
+    IDP_CK(cudaMemcpy(d, img.data(), img.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    p->mp_img[M] = d;
+    *out = d;
+    return IDP_OK;
+}
+
+// Sine transform of all active axes with the tensor-core pass (mixed.cu).
+// The passes rotate the axes: (a,b,c) -> (c',a,b) -> (b',c',a) -> (a',b',c').
+int transform_mixed(idp_plan p, View3 in, View3 out, const double *tab, View3 add, int sidx, cudaStream_t st)
+{
+    const int n0 = p->ni[0], n1 = p->ni[1], n2 = p->ni[2];
+    float *ta = p->t32[sidx][0], *tb = p->t32[sidx][1];
+    std::vector<MpPass> ps;
+    MpPass a{};
+    a.err = p->d_err;
+    if (p->d == 3) {
+        a.in = in.p; a.in_f64 = 1; a.is_p = in.s0; a.is_q = in.s1; a.is_k = in.s2;
+        a.out = ta; a.out_f64 = 0; a.os_m = (int64_t)n0 * n1; a.os_p = n1; a.os_q = 1;
+        a.P = n0; a.Q = n1; a.n = n2;
+        ps.push_back(a);
+        a.in = ta; a.in_f64 = 0; a.is_p = (int64_t)n0 * n1; a.is_q = n1; a.is_k = 1;
+        a.out = tb; a.os_m = (int64_t)n2 * n0; a.os_p = n0; a.os_q = 1;
+        a.P = n2; a.Q = n0; a.n = n1;
+        ps.push_back(a);
+        a.in = tb; a.is_p = (int64_t)n2 * n0; a.is_q = n0; a.is_k = 1;
+        a.P = n1; a.Q = n2; a.n = n0;
+    } else {
+        a.in = in.p; a.in_f64 = 1; a.is_p = 0; a.is_q = in.s1; a.is_k = in.s2;
+        a.out = ta; a.out_f64 = 0; a.os_m = n1; a.os_p = 0; a.os_q = 1;
+        a.P = 1; a.Q = n1; a.n = n2;
+        ps.push_back(a);
+        a.in = ta; a.in_f64 = 0; a.is_p = 0; a.is_q = n1; a.is_k = 1;
+        a.P = 1; a.Q = n2; a.n = n1;
+    }
+    // last pass: FP64 output in the original layout with the epilogue
+    const int s0 = p->d == 3 ? 0 : 1;   // output axis of the modes
+    const int64_t os[3] = {out.s0, out.s1, out.s2}, as[3] = {add.s0, add.s1, add.s2};
+    const int64_t ts[3] = {p->is[0], p->is[1], p->is[2]};
+    a.out = out.p; a.out_f64 = 1;
+    a.os_m = os[s0]; a.os_p = p->d == 3 ? os[1] : 0; a.os_q = os[2];
+    a.tab = tab; a.ts_m = ts[s0]; a.ts_p = p->d == 3 ? ts[1] : 0; a.ts_q = ts[2];
+    a.add = add.p; a.as_m = as[s0]; a.as_p = p->d == 3 ? as[1] : 0; a.as_q = as[2];
+    ps.push_back(a);
+    // pass i transforms axis 2, 1, 0 (3-D) / 2, 1 (2-D) of the original array
+    const int axes3[3] = {2, 1, 0}, axes2[2] = {2, 1};
+    for (size_t i = 0; i < ps.size(); ++i) {
+        const int ax = p->d == 3 ? axes3[i] : axes2[i];
+        int rc = get_mp_image(p, p->M[ax], &ps[i].bimg);
+        if (rc) return rc;
+        Mark mk(p, IDP_KERNEL_MIXED, st);
+        IDP_CK(launch_mp_pass(ps[i], st));
+    }
+    return IDP_OK;
+}
+
 // one full sine transform (all active axes); `first` pass reads `in`, the
 // last pass applies the epilogue (tab, add) and writes `out`; intermediate
 // passes run in place on `work`.
 int transform(idp_plan p, View3 in, double *work, View3 out, const double *tab, View3 add, bool forward,
-              cudaStream_t st)
+              cudaStream_t st, bool allow_mixed = true)
 {
+    if (p->mixed && allow_mixed) return transform_mixed(p, in, out, tab, add, st == p->side ? 1 : 0, st);
     int axes[3], na = 0;
     if (forward) {
         for (int s = 2; s >= 0; --s)
@@ -465,7 +591,10 @@ int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t s
         Mark mk(p, IDP_KERNEL_GTILDE_EXPAND, st);
         IDP_CK(launch_gtilde_expand(p->grid, p->Q0, p->Q1, p->Q2, p->sin4, p->tab4, nullptr, p->B, st));
     }
-    if ((rc = transform(p, dense(p, p->B), p->B, node_interior(p, p->U), nullptr, none, false, st))) return rc;
+    // u1 feeds the sixth differences of R, which amplify its rounding: this
+    // inverse transform stays FP64 in every precision mode
+    if ((rc = transform(p, dense(p, p->B), p->B, node_interior(p, p->U), nullptr, none, false, st, false)))
+        return rc;
     if (stop == IDP_STAGE_U1) {
         IDP_CK(cudaMemcpyAsync(phi, p->U, node_bytes, cudaMemcpyDeviceToDevice, st));
         return IDP_OK;
@@ -522,6 +651,8 @@ int plan_setup(idp_plan p)
         p->Q2 = p->Q1 + q1;
     }
     IDP_CK(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+    IDP_CK(cudaStreamCreateWithFlags(&p->bst, cudaStreamNonBlocking));
+    if (!p->cap) IDP_CK(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
     IDP_CK(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming));
     IDP_CK(cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming));
     {
@@ -705,6 +836,7 @@ int idp_create_plan(idp_plan *out, int d, const int64_t n[], const double h[], i
     if (!p) return IDP_ENOMEM;
     p->d = d;
     p->order = order;
+    p->serial = g_serial.fetch_add(1);
     const int o = 3 - d;
     for (int s = 0; s < d; ++s) {
         p->n[s + o] = (int)n[s];
@@ -738,6 +870,32 @@ int idp_plan_set(idp_plan p, int key, int64_t value)
     if (!p) return IDP_EINVAL;
     if (key == IDP_KEY_USE_GRAPH) {
         p->use_graph = value ? 1 : 0;
+        return IDP_OK;
+    }
+    if (key == IDP_KEY_PRECISION) {
+        if (value != IDP_PRECISION_FP64 && value != IDP_PRECISION_MIXED_BF16X3) return IDP_EINVAL;
+        if (value == IDP_PRECISION_MIXED_BF16X3) {
+            int rc;
+            if (!p->d_err) {
+                if ((rc = p->alloc(&p->d_err, 1))) return rc;
+                IDP_CK(cudaMemset(p->d_err, 0, sizeof(int)));
+            }
+            for (int s = 0; s < 2; ++s)
+                for (int q = 0; q < 2; ++q)
+                    if (!p->t32[s][q] && (rc = p->alloc(&p->t32[s][q], p->nint))) return rc;
+            for (int s = 0; s < 3; ++s) {
+                const void *img;
+                if (p->act[s] && (rc = get_mp_image(p, p->M[s], &img))) return rc;
+            }
+        }
+        if (p->mixed != (int)value) {
+            p->mixed = (int)value;
+            ++p->version;
+            if (p->gexec) {
+                cudaGraphExecDestroy(p->gexec);
+                p->gexec = nullptr;
+            }
+        }
         return IDP_OK;
     }
     return IDP_EINVAL;
@@ -777,10 +935,71 @@ int idp_solve_batched(int count, const idp_plan plans[], const double *const rho
         const size_t b = sizeof(double) * plans[i]->nodes;
         if (overlap(rho[i], b, phi[i], b)) return IDP_EALIAS;
     }
-    for (int i = 0; i < count; ++i) {
-        int rc = run_solve(plans[i], rho[i], phi[i], (cudaStream_t)stream);
-        if (rc) return rc;
+    if (count == 0) return IDP_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    idp_plan p0 = plans[0];
+    bool graphs = true;
+    for (int i = 0; i < count; ++i) graphs = graphs && plans[i]->use_graph && plans[i]->dev == p0->dev;
+    if (!graphs) {
+        for (int i = 0; i < count; ++i) {
+            int rc = run_solve(plans[i], rho[i], phi[i], st);
+            if (rc) return rc;
+        }
+        return IDP_OK;
     }
+    // one CUDA graph: a branch per problem (each with its own two streams), all
+    // forked from and joined into the launch stream, so that independent
+    // problems of different sizes run concurrently
+    BatchCache *bc = p0->batch;
+    bool hit = bc && (int)bc->serials.size() == count;
+    for (int i = 0; hit && i < count; ++i)
+        hit = bc->serials[i] == (plans[i]->serial << 16 ^ plans[i]->version) && bc->rho[i] == rho[i] &&
+              bc->phi[i] == phi[i];
+    if (!hit) {
+        if (!bc) bc = p0->batch = new BatchCache();
+        if (bc->exec) {
+            cudaGraphExecDestroy(bc->exec);
+            bc->exec = nullptr;
+        }
+        if (!bc->fork) IDP_CK(cudaEventCreateWithFlags(&bc->fork, cudaEventDisableTiming));
+        while ((int)bc->joins.size() < count) {
+            cudaEvent_t e;
+            IDP_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            bc->joins.push_back(e);
+        }
+        cudaStream_t origin = p0->cap;
+        IDP_CK(cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal));
+        int rc = IDP_OK;
+        cudaError_t e = cudaEventRecord(bc->fork, origin);
+        for (int i = 0; i < count && !rc && e == cudaSuccess; ++i) {
+            idp_plan q = plans[i];
+            e = cudaStreamWaitEvent(q->bst, bc->fork, 0);
+            if (e != cudaSuccess) break;
+            q->launches = 0;
+            rc = enqueue(q, rho[i], phi[i], 0, q->bst);
+            if (!rc) e = cudaEventRecord(bc->joins[i], q->bst);
+            if (!rc && e == cudaSuccess) e = cudaStreamWaitEvent(origin, bc->joins[i], 0);
+        }
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(origin, &g);
+        if (rc || e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            if (rc) return rc;
+            return cuda_fail(e != cudaSuccess ? e : e2, "batched capture");
+        }
+        e = cudaGraphInstantiate(&bc->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        bc->serials.assign(count, 0);
+        bc->rho.assign(rho, rho + count);
+        bc->phi.assign(phi, phi + count);
+        for (int i = 0; i < count; ++i) bc->serials[i] = plans[i]->serial << 16 ^ plans[i]->version;
+    }
+    for (int i = 0; i < count; ++i) {
+        plans[i]->last = st;
+        plans[i]->last_valid = 1;
+    }
+    IDP_CK(cudaGraphLaunch(bc->exec, st));
     return IDP_OK;
 }
 
@@ -801,6 +1020,11 @@ int idp_plan_status(idp_plan p)
     if (!p) return IDP_EINVAL;
     if (p->last_valid) IDP_CK(cudaStreamSynchronize(p->last));
     IDP_CK(cudaGetLastError());
+    if (p->d_err) {
+        int e = 0;
+        IDP_CK(cudaMemcpy(&e, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e) return IDP_ETIMEOUT;
+    }
     return IDP_OK;
 }
 
@@ -850,6 +1074,13 @@ int idp_destroy_plan(idp_plan p)
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->cap) cudaStreamDestroy(p->cap);
     if (p->side) cudaStreamDestroy(p->side);
+    if (p->bst) cudaStreamDestroy(p->bst);
+    if (p->batch) {
+        if (p->batch->exec) cudaGraphExecDestroy(p->batch->exec);
+        for (cudaEvent_t e : p->batch->joins) cudaEventDestroy(e);
+        if (p->batch->fork) cudaEventDestroy(p->batch->fork);
+        delete p->batch;
+    }
     if (p->fork) cudaEventDestroy(p->fork);
     if (p->join) cudaEventDestroy(p->join);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
@@ -867,6 +1098,7 @@ const char *idp_strerror(int code)
     case IDP_ECUDA: return "CUDA error";
     case IDP_EALIAS: return "input and output overlap";
     case IDP_ESUPPORT: return "size or option not supported (panel counts must be powers of two in [16, 512])";
+    case IDP_ETIMEOUT: return "a device-side wait exceeded its iteration limit";
     case IDP_ESCRATCH: return "problem larger than the fixed scratch of idp_rhs6_noalloc (524288 nodes)";
     default: return "unknown error";
     }

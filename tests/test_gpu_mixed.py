@@ -1,0 +1,89 @@
+"""Tensor-core (mixed-precision) sine transforms against the FP64 oracle.
+
+IDP_PRECISION_MIXED_BF16X3 replaces the sine transforms of rho, of R and the
+final inverse by dense sine-matrix products on the tensor cores: operands
+split into three BF16 pieces, the six products with piece indices i + j <= 2,
+FP32 accumulation.  The transform producing u1 stays FP64 because R is a
+sixth difference of u1 (section 5) and would amplify its rounding.  The dropped products are below 2^-24 relative; the FP32
+accumulation of n terms gives a relative error of order sqrt(n) 2^-24 per
+pass.  Stated accuracy (checked here): max-norm error relative to max|phi|
+below 1e-5 for the full solve, and below 1e-5 for phi*.
+"""
+import numpy as np
+import pytest
+
+import workloads as w
+from oracle import dst as odst, solve as osolve
+from tests.gpu_util import device, rel_max, run_stage, to_dev
+
+pytestmark = pytest.mark.gpu
+MIXED_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def idp():
+    import paper_2108_11871_gb300 as m
+    device()
+    m.library()
+    return m
+
+
+def _plan(idp, prob, order=6):
+    plan = idp.create_plan(prob.d, prob.n, prob.h, order)
+    idp.plan_set(plan, idp.IDP_KEY_PRECISION, idp.IDP_PRECISION_MIXED_BF16X3)
+    return plan
+
+
+def test_mixed_phistar_of_a_sine_mode(idp):
+    n = (33, 65, 129)
+    box = ((0.0, 1.0), (0.0, 0.7), (-1.0, 1.5))
+    coords = [np.linspace(a, b, k) for (a, b), k in zip(box, n)]
+    h = [c[1] - c[0] for c in coords]
+    X = np.meshgrid(*coords, indexing="ij")
+    modes = (3, 7, 40)
+    rho = np.ones(n)
+    lam = 0.0
+    for s in range(3):
+        L = box[s][1] - box[s][0]
+        rho = rho * np.sin(modes[s] * np.pi * (X[s] - box[s][0]) / L)
+        lam += (modes[s] * np.pi / L) ** 2
+    plan = idp.create_plan(3, n, h, 4)
+    idp.plan_set(plan, idp.IDP_KEY_PRECISION, idp.IDP_PRECISION_MIXED_BF16X3)
+    ps = run_stage(idp, plan, idp.IDP_STAGE_PHISTAR, to_dev(rho), n)
+    assert rel_max(ps, -rho / lam) < MIXED_TOL
+
+
+@pytest.mark.parametrize("prob", [w.c2_3d(33), w.c1_2d(65),
+                                  w.Problem("g", (65, 33, 129), (0.0,) * 3, (1.0, 1.0, 2.0), "gauss",
+                                            dict(seed=2108)),
+                                  w.c2_3d(129)], ids=["3d_33", "2d_65", "3d_65x33x129", "3d_129"])
+def test_mixed_solve_against_oracle(idp, prob):
+    rho = prob.rho()
+    plan = _plan(idp, prob)
+    r = to_dev(rho)
+    ps = run_stage(idp, plan, idp.IDP_STAGE_PHISTAR, r, prob.n)
+    assert rel_max(ps, odst.phi_star(rho, prob.h)) < MIXED_TOL
+    phi = to_dev(np.zeros(prob.n))
+    idp.solve(plan, r, phi)
+    idp.plan_status(plan)
+    ref = osolve.solve(rho, prob.h, 6, boundary="convolution")
+    err = rel_max(phi.cpu().numpy(), ref)
+    assert err < MIXED_TOL, err
+
+
+def test_switching_precision_back_to_fp64_restores_fp64_results(idp):
+    prob = w.c2_3d(33)
+    rho = to_dev(prob.rho())
+    plan = idp.create_plan(3, prob.n, prob.h, 6)
+    a = to_dev(np.zeros(prob.n))
+    idp.solve(plan, rho, a)
+    idp.plan_set(plan, idp.IDP_KEY_PRECISION, idp.IDP_PRECISION_MIXED_BF16X3)
+    b = to_dev(np.zeros(prob.n))
+    idp.solve(plan, rho, b)
+    idp.plan_set(plan, idp.IDP_KEY_PRECISION, idp.IDP_PRECISION_FP64)
+    c = to_dev(np.zeros(prob.n))
+    idp.solve(plan, rho, c)
+    idp.plan_status(plan)
+    a, b, c = a.cpu().numpy(), b.cpu().numpy(), c.cpu().numpy()
+    assert np.array_equal(a, c)
+    assert 0 < rel_max(b, a) < MIXED_TOL

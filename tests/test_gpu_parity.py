@@ -181,6 +181,33 @@ def test_batched_equals_single(idp):
         assert np.array_equal(single.cpu().numpy(), o.cpu().numpy())
 
 
+def test_batched_graph_uneven_sizes_cache_and_recapture(idp):
+    # several problems of different sizes in one graph launch; a second launch
+    # replays the cached graph, a changed output pointer recaptures it
+    sizes = [(17, 33, 65), (65, 17, 33), (33, 33, 33), (17, 17, 129), (65, 65, 17)]
+    probs = [w.Problem("b%d" % i, n, (0.0,) * 3, (1.0,) * 3, "gauss", dict(seed=100 + i))
+             for i, n in enumerate(sizes)]
+    plans = [idp.create_plan(3, p.n, p.h, 6) for p in probs]
+    rhos = [to_dev(p.rho()) for p in probs]
+    singles = []
+    for pl, r, p in zip(plans, rhos, probs):
+        o = to_dev(np.zeros(p.n))
+        idp.solve(pl, r, o)
+        idp.plan_status(pl)
+        singles.append(o.cpu().numpy())
+    outs = [to_dev(np.full(p.n, np.nan)) for p in probs]
+    for _ in range(2):
+        idp.solve_batched(plans, rhos, outs)
+        for pl in plans:
+            idp.plan_status(pl)
+        for o, s in zip(outs, singles):
+            assert np.array_equal(o.cpu().numpy(), s)
+    outs[2] = to_dev(np.zeros(probs[2].n))
+    idp.solve_batched(plans, rhos, outs)
+    idp.plan_status(plans[0])
+    assert np.array_equal(outs[2].cpu().numpy(), singles[2])
+
+
 def test_alias_and_bad_arguments_are_rejected(idp):
     prob = w.c2_3d(33)
     plan = idp.create_plan(3, prob.n, prob.h, 6)
