@@ -13,7 +13,7 @@
 // FP32 accumulation.  The eigenvalue scaling and the additions of the last
 // pass are done in FP64.
 //
-// Block: 128 threads, a tile of 128 lines x 128 modes, K in blocks of 64.
+// Block: 256 threads, a tile of 128 lines x 128 modes, K in blocks of 64.
 // Operands live in shared memory in the canonical K-major layout without
 // swizzle: 8 x 16-byte core matrices, core matrices adjacent along K are
 // LBO = 2048 bytes apart, adjacent along M/N SBO = 128 bytes apart.
@@ -63,13 +63,19 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr)
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NTILE >> 3) << 17) |
                            ((uint32_t)(MT >> 4) << 24);
 
-__device__ __forceinline__ void split3(double x, __nv_bfloat16 &a, __nv_bfloat16 &b, __nv_bfloat16 &c)
+// x = hi + lo (two floats, |lo| <= 2^-24 |hi|) -> three BF16 pieces.  The
+// residuals hi - a and r1 - b are exact in FP32; lo enters below 2^-16 |x|.
+__device__ __forceinline__ void split3(float hi, float lo, unsigned short &a, unsigned short &b,
+                                       unsigned short &c)
 {
-    a = __float2bfloat16_rn((float)x);
-    const double r1 = x - (double)__bfloat162float(a);
-    b = __float2bfloat16_rn((float)r1);
-    const double r2 = r1 - (double)__bfloat162float(b);
-    c = __float2bfloat16_rn((float)r2);
+    const __nv_bfloat16 ba = __float2bfloat16_rn(hi);
+    const float r1 = (hi - __bfloat162float(ba)) + lo;
+    const __nv_bfloat16 bb = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(bb);
+    const __nv_bfloat16 bc = __float2bfloat16_rn(r2);
+    a = __bfloat16_as_ushort(ba);
+    b = __bfloat16_as_ushort(bb);
+    c = __bfloat16_as_ushort(bc);
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
@@ -87,7 +93,9 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     return false;
 }
 
-__global__ void __launch_bounds__(128) mp_pass_kernel(const MpPass a)
+constexpr int NTHR = 256;
+
+__global__ void __launch_bounds__(NTHR) mp_pass_kernel(const MpPass a)
 {
     extern __shared__ __align__(128) unsigned char sm[];
     const int t = threadIdx.x;
@@ -118,31 +126,53 @@ __global__ void __launch_bounds__(128) mp_pass_kernel(const MpPass a)
     const uint32_t tmem = *tmem_slot;
 
     for (int kb = 0; kb < nkb; ++kb) {
-        // A pieces: 128 lines x 64 k of the input, split into BF16 pieces
-        for (int e = t; e < MT * KB; e += 128) {
-            const int r = e >> 6, k = e & 63;
+        // A pieces: 128 lines x 64 k of the input, split into BF16 pieces; a
+        // thread takes 8 consecutive k of one line (one 16-byte core-matrix row)
+        for (int e = t; e < MT * (KB / 8); e += NTHR) {
+            const int r = e >> 3, g8 = e & 7;
             const int64_t L = L0 + r;
-            const int kg = kb * KB + k;
-            double x = 0.0;
-            if (L < nlines && kg < a.n) {
+            const int kg0 = kb * KB + g8 * 8;
+            unsigned short pa[8], pb[8], pc[8];
+            const bool row_ok = L < nlines;
+            int64_t base = 0;
+            if (row_ok) {
                 const int64_t p = L / a.Q, q = L - p * a.Q;
-                const int64_t off = p * a.is_p + q * a.is_q + (int64_t)kg * a.is_k;
-                x = a.in_f64 ? reinterpret_cast<const double *>(a.in)[off]
-                             : (double)reinterpret_cast<const float *>(a.in)[off];
+                base = p * a.is_p + q * a.is_q;
             }
-            __nv_bfloat16 x0, x1, x2;
-            split3(x, x0, x1, x2);
-            const uint32_t o = tile_off(r, k);
-            *reinterpret_cast<__nv_bfloat16 *>(sm + SMEM_A + 0 * TILE_BYTES + o) = x0;
-            *reinterpret_cast<__nv_bfloat16 *>(sm + SMEM_A + 1 * TILE_BYTES + o) = x1;
-            *reinterpret_cast<__nv_bfloat16 *>(sm + SMEM_A + 2 * TILE_BYTES + o) = x2;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int kg = kg0 + j;
+                float hi = 0.f, lo = 0.f;
+                if (row_ok && kg < a.n) {
+                    const int64_t off = base + (int64_t)kg * a.is_k;
+                    if (a.in_f64) {
+                        const double x = reinterpret_cast<const double *>(a.in)[off];
+                        hi = (float)x;
+                        lo = (float)(x - (double)hi);
+                    } else {
+                        hi = reinterpret_cast<const float *>(a.in)[off];
+                    }
+                }
+                split3(hi, lo, pa[j], pb[j], pc[j]);
+            }
+            const uint32_t o = tile_off(r, g8 * 8);
+            uint4 va, vb, vc;
+            va.x = pa[0] | ((uint32_t)pa[1] << 16); va.y = pa[2] | ((uint32_t)pa[3] << 16);
+            va.z = pa[4] | ((uint32_t)pa[5] << 16); va.w = pa[6] | ((uint32_t)pa[7] << 16);
+            vb.x = pb[0] | ((uint32_t)pb[1] << 16); vb.y = pb[2] | ((uint32_t)pb[3] << 16);
+            vb.z = pb[4] | ((uint32_t)pb[5] << 16); vb.w = pb[6] | ((uint32_t)pb[7] << 16);
+            vc.x = pc[0] | ((uint32_t)pc[1] << 16); vc.y = pc[2] | ((uint32_t)pc[3] << 16);
+            vc.z = pc[4] | ((uint32_t)pc[5] << 16); vc.w = pc[6] | ((uint32_t)pc[7] << 16);
+            *reinterpret_cast<uint4 *>(sm + SMEM_A + 0 * TILE_BYTES + o) = va;
+            *reinterpret_cast<uint4 *>(sm + SMEM_A + 1 * TILE_BYTES + o) = vb;
+            *reinterpret_cast<uint4 *>(sm + SMEM_A + 2 * TILE_BYTES + o) = vc;
         }
         // B pieces: pre-split sine-matrix images, copied as 16-byte vectors
         {
             const int4 *src = reinterpret_cast<const int4 *>(a.bimg) +
                               ((int64_t)blockIdx.y * nkb + kb) * (PIECES * TILE_BYTES / 16);
             int4 *dst = reinterpret_cast<int4 *>(sm + SMEM_B);
-            for (int e = t; e < PIECES * TILE_BYTES / 16; e += 128) dst[e] = src[e];
+            for (int e = t; e < PIECES * TILE_BYTES / 16; e += NTHR) dst[e] = src[e];
         }
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
@@ -175,14 +205,16 @@ __global__ void __launch_bounds__(128) mp_pass_kernel(const MpPass a)
     }
 
     if (!s_fail) {
-        // epilogue: lane quadrant of this warp = lines 32*warp .. 32*warp+31
-        const int64_t L = L0 + 32 * warp + lane;
+        // epilogue: warp w reads TMEM lane quadrant w % 4 (lines 32*(w%4) ..),
+        // columns [64 * (w / 4), 64 * (w / 4) + 64)
+        const int quad = warp & 3;
+        const int64_t L = L0 + 32 * quad + lane;
         const bool live = L < nlines;
         int64_t p = 0, q = 0;
         if (live) { p = L / a.Q; q = L - p * a.Q; }
-        for (int c0 = 0; c0 < NTILE; c0 += 32) {
+        for (int c0 = 64 * (warp >> 2); c0 < 64 * (warp >> 2) + 64; c0 += 32) {
             uint32_t v[32];
-            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+            const uint32_t taddr = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)c0;
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
@@ -238,7 +270,7 @@ cudaError_t launch_mp_pass(const MpPass &a, cudaStream_t st)
 {
     const int64_t lines = (int64_t)a.P * a.Q;
     dim3 grid((unsigned)((lines + MT - 1) / MT), (unsigned)((a.n + NTILE - 1) / NTILE));
-    mp_pass_kernel<<<grid, 128, SMEM_TOTAL, st>>>(a);
+    mp_pass_kernel<<<grid, NTHR, SMEM_TOTAL, st>>>(a);
     return cudaGetLastError();
 }
 
