@@ -181,10 +181,17 @@ __global__ void face2d_kernel(const FacePass2D a)
 }
 
 // ---------------------------------------------------------------- stage 3a
+// small lines-per-block for the two inverse stages: they are short and need
+// many blocks to fill the GPU
+template <int L>
+struct SmallCfg {
+    static constexpr int LB = (512 / L) > 32 ? 32 : ((512 / L) < 1 ? 1 : 512 / L);
+};
+
 template <int L>
 __global__ void __launch_bounds__(NT) face_invb_kernel(const FaceInvB a)
 {
-    constexpr int TC = LineCfg<L>::LB;
+    constexpr int TC = SmallCfg<L>::LB;
     constexpr int Mb = L / 2;
     extern __shared__ double2 smem[];
     double2 *bufA = smem, *bufB = smem + TC * L;
@@ -216,7 +223,7 @@ __global__ void __launch_bounds__(NT) face_invb_kernel(const FaceInvB a)
 template <int L>
 __global__ void __launch_bounds__(NT) face_c2r_kernel(const FaceC2R a)
 {
-    constexpr int LB = LineCfg<L>::LB;
+    constexpr int LB = SmallCfg<L>::LB;
     extern __shared__ double2 smem[];
     double2 *bufA = smem, *bufB = smem + LB * L;
     const int face = blockIdx.y;
@@ -315,6 +322,8 @@ template <int L>
 size_t smem_lines() { return 2 * sizeof(double2) * LineCfg<L>::LB * L; }
 template <int L>
 size_t smem_face() { return 2 * sizeof(double2) * FaceCfg<L>::TC * L; }
+template <int L>
+size_t smem_small() { return 2 * sizeof(double2) * SmallCfg<L>::LB * L; }
 
 template <int L>
 cudaError_t attrs_len()
@@ -325,8 +334,11 @@ cudaError_t attrs_len()
     if ((e = cudaFuncSetAttribute(face_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem_face<L>())))
         return e;
-    if ((e = cudaFuncSetAttribute(face_invb_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
-    return cudaFuncSetAttribute(face_c2r_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if ((e = cudaFuncSetAttribute(face_invb_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_small<L>())))
+        return e;
+    return cudaFuncSetAttribute(face_c2r_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_small<L>());
 }
 
 #define IDP_LEN_SWITCH(LEN, ...)              \
@@ -401,8 +413,8 @@ cudaError_t launch_face_pass_2d(const FacePass2D &a, cudaStream_t st)
 cudaError_t launch_face_inv_b(const FaceInvB &a, cudaStream_t st)
 {
     IDP_LEN_SWITCH(2 * a.Mb, {
-        dim3 grid((a.nc + LineCfg<L>::LB - 1) / LineCfg<L>::LB, 2);
-        face_invb_kernel<L><<<grid, NT, smem_lines<L>(), st>>>(a);
+        dim3 grid((a.nc + SmallCfg<L>::LB - 1) / SmallCfg<L>::LB, 2);
+        face_invb_kernel<L><<<grid, NT, smem_small<L>(), st>>>(a);
         return cudaGetLastError();
     })
 }
@@ -410,8 +422,8 @@ cudaError_t launch_face_inv_b(const FaceInvB &a, cudaStream_t st)
 cudaError_t launch_face_c2r(const FaceC2R &a, cudaStream_t st)
 {
     IDP_LEN_SWITCH(a.Mc, {
-        dim3 grid((a.nrows + LineCfg<L>::LB - 1) / LineCfg<L>::LB, 2);
-        face_c2r_kernel<L><<<grid, NT, smem_lines<L>(), st>>>(a);
+        dim3 grid((a.nrows + SmallCfg<L>::LB - 1) / SmallCfg<L>::LB, 2);
+        face_c2r_kernel<L><<<grid, NT, smem_small<L>(), st>>>(a);
         return cudaGetLastError();
     })
 }
