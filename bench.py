@@ -275,6 +275,42 @@ def run_ours(args, rank, world):
                  "kernel_ms_per_step": {k: sum(v) / 3 for k, v in mk.items()},
                  "mixed_pass_avg_ms": statistics.mean(mk["mixed_pass"]) if "mixed_pass" in mk else None}
 
+    # double-float variant (FFT butterflies on the FP32 pipe, FP64-level accuracy)
+    df32 = None
+    if not args.fp64_only:
+        dplan = idp.create_plan(3, prob.n, prob.h, args.order)
+        idp.plan_set(dplan, idp.IDP_KEY_PRECISION, idp.IDP_PRECISION_DF32)
+        phi_d = torch.empty_like(rho)
+        for _ in range(args.warmup):
+            idp.solve(dplan, rho, phi_d, stream)
+        torch.cuda.synchronize()
+        idp.plan_status(dplan)
+        ev = []
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            idp.solve(dplan, rho, phi_d, stream)
+            s1.record(stream)
+            ev.append((s0, s1))
+        torch.cuda.synchronize()
+        idp.plan_status(dplan)
+        t_d = sum(x.elapsed_time(y) for x, y in ev)
+        dk = {}
+        for i in range(3):
+            flush.fill_(float(i))
+            n = idp.library().idp_profile_solve(dplan.handle, ctypes.c_void_p(rho.data_ptr()),
+                                                ctypes.c_void_p(phi_d.data_ptr()),
+                                                ctypes.c_void_p(stream.cuda_stream), cap, kinds, ms)
+            for j in range(max(n, 0)):
+                dk.setdefault(names.get(kinds[j], str(kinds[j])), []).append(ms[j])
+        df32 = {"variant": "double-float (FP32 pairs) FFT arithmetic",
+                "value": world * prob.points * args.steps / (t_d / 1e3), "unit": UNIT,
+                "ms_per_step": t_d / args.steps,
+                "max_rel_error_vs_fp64": (phi_d - phi).abs().max().item() / phi.abs().max().item(),
+                "kernel_ms_per_step": {k: sum(v) / 3 for k, v in dk.items()},
+                "dst_pass_avg_ms": statistics.mean(dk["dst_pass"]) if "dst_pass" in dk else None}
+
     if rank != 0:
         return
     out = phi.cpu().numpy()
@@ -287,6 +323,7 @@ def run_ours(args, rank, world):
             "config": config_of(prob, args.order, {"parallelism": "replicas" if world > 1 else "single"}),
             "precision": {"variant": "fp64", "max_rel_error_vs_exact_potential": err_exact},
             "mixed_precision": mixed,
+            "df32": df32,
             "e2e": e2e,
             "gpu_launches": int(launches.value) * args.steps,
             "roofline": {"bound": "alu", "kernel": "dst_pass (FP64 sine-transform pass)",

@@ -65,13 +65,19 @@ enum {
 /* values of IDP_KEY_PRECISION */
 enum {
     IDP_PRECISION_FP64 = 0,        /* FP64 FFT-based sine transforms (default) */
-    IDP_PRECISION_MIXED_BF16X3 = 1 /* the sine transforms of rho, of R and the final inverse become
+    IDP_PRECISION_MIXED_BF16X3 = 1, /* the sine transforms of rho, of R and the final inverse become
                                       dense sine-matrix products on the tensor cores: operands split
                                       into three BF16 pieces, six products, FP32 accumulation
                                       (relative error of phi ~1e-5 or better); the eigenvalue division,
                                       the boundary values, the stencils and the transform that produces
                                       u1 (whose sixth differences form R) stay FP64.  Setting it
                                       allocates the pieces of the sine matrices and FP32 temporaries. */
+    IDP_PRECISION_DF32 = 2         /* the FFT-based transforms (sine transforms of rho, R and the final
+                                      inverse, and the 3-D boundary convolutions) in double-float
+                                      arithmetic (a value is a pair of FP32 numbers, ~48 significant
+                                      bits) on the FP32 pipe, FP64 arrays in and out; the transform
+                                      producing u1 and all stencils stay FP64.  Results agree with
+                                      FP64 to a few 1e-13 relative. */
 };
 
 /* stages for idp_solve_stage */

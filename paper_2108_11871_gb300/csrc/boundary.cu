@@ -27,12 +27,46 @@ struct LineCfg {
 // ---------------------------------------------------------------- stage 1
 // L = M: complex FFT length; input line has M-1 reals at positions 1..M-1 of
 // a zero-padded sequence of length 2M; output X'_m = 2 X_m, m = 0..M.
-template <int L>
+template <class R>
+__device__ __forceinline__ R ld_real(const double *p, int64_t i);
+template <>
+__device__ __forceinline__ double ld_real<double>(const double *p, int64_t i) { return p[i]; }
+template <>
+__device__ __forceinline__ ddr ld_real<ddr>(const double *p, int64_t i) { return dd_from_bits(p[i]); }
+template <class R>
+__device__ __forceinline__ void st_real(double *p, int64_t i, R v);
+template <>
+__device__ __forceinline__ void st_real<double>(double *p, int64_t i, double v) { p[i] = v; }
+template <>
+__device__ __forceinline__ void st_real<ddr>(double *p, int64_t i, ddr v) { p[i] = dd_to_bits(v); }
+
+template <class R>
+__device__ __forceinline__ const typename Ar<R>::T *fwd_tw(const FftTables &t);
+template <>
+__device__ __forceinline__ const Tw *fwd_tw<double>(const FftTables &t) { return t.fwd; }
+template <>
+__device__ __forceinline__ const TwD *fwd_tw<ddr>(const FftTables &t) { return t.fwdd; }
+template <class R>
+__device__ __forceinline__ const typename Ar<R>::T *inv_tw(const FftTables &t);
+template <>
+__device__ __forceinline__ const Tw *inv_tw<double>(const FftTables &t) { return t.inv; }
+template <>
+__device__ __forceinline__ const TwD *inv_tw<ddr>(const FftTables &t) { return t.invd; }
+template <class R>
+__device__ __forceinline__ typename Ar<R>::C half_tw(const FftTables &t, int k);
+template <>
+__device__ __forceinline__ double2 half_tw<double>(const FftTables &t, int k) { return t.half[k]; }
+template <>
+__device__ __forceinline__ ddc half_tw<ddr>(const FftTables &t, int k) { return t.halfd[k]; }
+
+template <class R, int L>
 __global__ void __launch_bounds__(NT) rfft_kernel(const RfftPass a)
 {
+    using A = Ar<R>;
+    using Cx = typename A::C;
     constexpr int M = L, N = M - 1, LB = LineCfg<L>::LB;
-    extern __shared__ double2 smem[];
-    double2 *bufA = smem, *bufB = smem + LB * L;
+    extern __shared__ double2 smem_raw[];
+    Cx *bufA = reinterpret_cast<Cx *>(smem_raw), *bufB = bufA + LB * L;
     int nu, nv;
     int64_t isu, isv, ise, osu, osv, ose;
     if (a.axis == 2) {
@@ -48,41 +82,41 @@ __global__ void __launch_bounds__(NT) rfft_kernel(const RfftPass a)
     const int u = blockIdx.y, v0 = blockIdx.x * LB;
     const int nl = min(LB, nv - v0);
     const bool contig = (ise == 1);
-    double *zf = reinterpret_cast<double *>(bufA);   // [LB][2L] reals
-    const double *inb = a.in + (int64_t)u * isu + (int64_t)v0 * isv;
+    R *zf = reinterpret_cast<R *>(bufA);   // [LB][2L] reals
+    const int64_t inb = (int64_t)u * isu + (int64_t)v0 * isv;
     for (int f = threadIdx.x; f < LB * 2 * L; f += NT) {
         const int l = f / (2 * L), q = f - l * 2 * L;
-        if (q == 0 || q >= M) zf[f] = 0.0;
+        if (q == 0 || q >= M) zf[f] = A::zero();
     }
     for (int f = threadIdx.x; f < LB * N; f += NT) {
         int l, e;
         if (contig) { l = f / N; e = f - l * N; }
         else { e = f / LB; l = f - e * LB; }
-        double x = 0.0;
-        if (l < nl) x = inb[(int64_t)l * isv + (int64_t)e * ise];
+        R x = A::zero();
+        if (l < nl) x = ld_real<R>(a.in, inb + (int64_t)l * isv + (int64_t)e * ise);
         zf[l * 2 * L + e + 1] = x;
     }
     __syncthreads();
-    double2 *Z = cta_fft<L, LB, NT, false>(bufA, bufB, a.t.fwd, true);
-    double2 *outb = a.out + (int64_t)u * osu + (int64_t)v0 * osv;
+    Cx *Z = cta_fft_t<R, L, LB, NT, false>(bufA, bufB, fwd_tw<R>(a.t), true);
+    Cx *outb = reinterpret_cast<Cx *>(a.out) + (int64_t)u * osu + (int64_t)v0 * osv;
     for (int f = threadIdx.x; f < LB * (L / 2); f += NT) {
         const int l = f / (L / 2);
         const int m = f - l * (L / 2) + 1;   // 1..L/2
         if (l >= nl) continue;
-        const double2 *zl = Z + l * L;
-        const double2 zm = zl[m], zc = zl[L - m];
-        const double Er = zm.x + zc.x, Ei = zm.y - zc.y;
-        const double Or = zm.x - zc.x, Oi = zm.y + zc.y;
-        const double2 w = a.t.half[m];
-        const double Pr = fma(w.x, Or, -w.y * Oi);
-        const double Pi = fma(w.x, Oi, w.y * Or);
-        double2 *ol = outb + (int64_t)l * osv;
-        ol[(int64_t)m * ose] = make_double2(Er + Pi, Ei - Pr);
-        ol[(int64_t)(M - m) * ose] = make_double2(Er - Pi, -(Ei + Pr));
+        const Cx *zl = Z + l * L;
+        const Cx zm = zl[m], zc = zl[L - m];
+        const R Er = A::add(A::re(zm), A::re(zc)), Ei = A::sub(A::im(zm), A::im(zc));
+        const R Or = A::sub(A::re(zm), A::re(zc)), Oi = A::add(A::im(zm), A::im(zc));
+        const Cx w = half_tw<R>(a.t, m);
+        const R Pr = A::mul_sub(A::re(w), Or, A::im(w), Oi);
+        const R Pi = A::mul_add(A::re(w), Oi, A::im(w), Or);
+        Cx *ol = outb + (int64_t)l * osv;
+        ol[(int64_t)m * ose] = A::cmake(A::add(Er, Pi), A::sub(Ei, Pr));
+        ol[(int64_t)(M - m) * ose] = A::cmake(A::sub(Er, Pi), A::neg(A::add(Ei, Pr)));
         if (m == 1) {
-            const double2 z0 = zl[0];
-            ol[0] = make_double2(2.0 * (z0.x + z0.y), 0.0);
-            ol[(int64_t)M * ose] = make_double2(2.0 * (z0.x - z0.y), 0.0);
+            const Cx z0 = zl[0];
+            ol[0] = A::cmake(A::times2(A::add(A::re(z0), A::im(z0))), A::zero());
+            ol[(int64_t)M * ose] = A::cmake(A::times2(A::sub(A::re(z0), A::im(z0))), A::zero());
         }
     }
 }
@@ -95,39 +129,49 @@ struct FaceCfg {
 };
 
 // L = 2 Mb.  Block: TC consecutive frequencies c, one chunk of slices p.
-template <int L>
+template <class R>
+__device__ __forceinline__ R ld_khat(const FacePass &a, int64_t i);
+template <>
+__device__ __forceinline__ double ld_khat<double>(const FacePass &a, int64_t i) { return a.khat[i]; }
+template <>
+__device__ __forceinline__ ddr ld_khat<ddr>(const FacePass &a, int64_t i) { return a.khatd[i]; }
+
+template <class R, int L>
 __global__ void __launch_bounds__(NT) face_kernel(const FacePass a)
 {
+    using A = Ar<R>;
+    using Cx = typename A::C;
     constexpr int TC = FaceCfg<L>::TC;
     constexpr int Mb = L / 2;
     constexpr int OPT = (TC * L + NT - 1) / NT;   // outputs per thread
-    extern __shared__ double2 smem[];
-    double2 *bufA = smem, *bufB = smem + TC * L;
+    extern __shared__ double2 smem_raw[];
+    Cx *bufA = reinterpret_cast<Cx *>(smem_raw), *bufB = bufA + TC * L;
     const int c0 = blockIdx.x * TC;
     const int ncl = min(TC, a.nc - c0);
     const int chunk = blockIdx.y;
     const int p0 = chunk * a.pchunk;
     const int p1 = min(a.np, p0 + a.pchunk);
-    double2 acc_lo[OPT], acc_hi[OPT];
+    Cx acc_lo[OPT], acc_hi[OPT];
 #pragma unroll
     for (int r = 0; r < OPT; ++r) {
-        acc_lo[r] = make_double2(0.0, 0.0);
-        acc_hi[r] = make_double2(0.0, 0.0);
+        acc_lo[r] = A::cmake(A::zero(), A::zero());
+        acc_hi[r] = A::cmake(A::zero(), A::zero());
     }
     const int64_t kstride = (int64_t)(Mb + 1) * a.nc;
+    const Cx *D = reinterpret_cast<const Cx *>(a.D);
     for (int p = p0; p < p1; ++p) {
         // load TC columns: positions 1..Mb-1 (interior index 0..Mb-2), rest zero
-        const double2 *Dp = a.D + (int64_t)p * a.sp + (int64_t)c0 * a.sc;
+        const Cx *Dp = D + (int64_t)p * a.sp + (int64_t)c0 * a.sc;
         for (int f = threadIdx.x; f < TC * L; f += NT) {
             const int q = f / TC, t = f - q * TC;
-            double2 x = make_double2(0.0, 0.0);
+            Cx x = A::cmake(A::zero(), A::zero());
             if (q >= 1 && q <= Mb - 1 && t < ncl) x = Dp[(int64_t)(q - 1) * a.sb + (int64_t)t * a.sc];
             bufA[t * L + q] = x;
         }
         __syncthreads();
-        const double2 *Z = cta_fft<L, TC, NT, false>(bufA, bufB, a.t.fwd, true);
-        const double *klo = a.khat + (int64_t)p * kstride + c0;
-        const double *khi = a.khat + (int64_t)(a.np - 1 - p) * kstride + c0;
+        const Cx *Z = cta_fft_t<R, L, TC, NT, false>(bufA, bufB, fwd_tw<R>(a.t), true);
+        const int64_t klo = (int64_t)p * kstride + c0;
+        const int64_t khi = (int64_t)(a.np - 1 - p) * kstride + c0;
 #pragma unroll
         for (int r = 0; r < OPT; ++r) {
             const int o = threadIdx.x + r * NT;
@@ -135,21 +179,20 @@ __global__ void __launch_bounds__(NT) face_kernel(const FacePass a)
                 const int m = o / TC, t = o - m * TC;
                 if (t < ncl) {
                     const int mm = m <= Mb ? m : L - m;
-                    const double2 X = Z[t * L + m];
-                    const double kl = klo[(int64_t)mm * a.nc + t];
-                    const double kh = khi[(int64_t)mm * a.nc + t];
-                    acc_lo[r].x = fma(kl, X.x, acc_lo[r].x);
-                    acc_lo[r].y = fma(kl, X.y, acc_lo[r].y);
-                    acc_hi[r].x = fma(kh, X.x, acc_hi[r].x);
-                    acc_hi[r].y = fma(kh, X.y, acc_hi[r].y);
+                    const Cx X = Z[t * L + m];
+                    const R kl = ld_khat<R>(a, klo + (int64_t)mm * a.nc + t);
+                    const R kh = ld_khat<R>(a, khi + (int64_t)mm * a.nc + t);
+                    acc_lo[r] = A::cmake(A::fma(kl, A::re(X), A::re(acc_lo[r])), A::fma(kl, A::im(X), A::im(acc_lo[r])));
+                    acc_hi[r] = A::cmake(A::fma(kh, A::re(X), A::re(acc_hi[r])), A::fma(kh, A::im(X), A::im(acc_hi[r])));
                 }
             }
         }
         __syncthreads();
     }
     // partial sums: part[chunk][face][m][c]
-    double2 *plo = a.part + ((int64_t)chunk * 2 + 0) * L * a.nc + c0;
-    double2 *phi = a.part + ((int64_t)chunk * 2 + 1) * L * a.nc + c0;
+    Cx *part = reinterpret_cast<Cx *>(a.part);
+    Cx *plo = part + ((int64_t)chunk * 2 + 0) * L * a.nc + c0;
+    Cx *phi = part + ((int64_t)chunk * 2 + 1) * L * a.nc + c0;
 #pragma unroll
     for (int r = 0; r < OPT; ++r) {
         const int o = threadIdx.x + r * NT;
@@ -188,78 +231,84 @@ struct SmallCfg {
     static constexpr int LB = (512 / L) > 32 ? 32 : ((512 / L) < 1 ? 1 : 512 / L);
 };
 
-template <int L>
+template <class R, int L>
 __global__ void __launch_bounds__(NT) face_invb_kernel(const FaceInvB a)
 {
+    using A = Ar<R>;
+    using Cx = typename A::C;
     constexpr int TC = SmallCfg<L>::LB;
     constexpr int Mb = L / 2;
-    extern __shared__ double2 smem[];
-    double2 *bufA = smem, *bufB = smem + TC * L;
+    extern __shared__ double2 smem_raw[];
+    Cx *bufA = reinterpret_cast<Cx *>(smem_raw), *bufB = bufA + TC * L;
     const int c0 = blockIdx.x * TC;
     const int face = blockIdx.y;
     const int ncl = min(TC, a.nc - c0);
+    const Cx *part = reinterpret_cast<const Cx *>(a.part);
     for (int f = threadIdx.x; f < TC * L; f += NT) {
         const int m = f / TC, t = f - m * TC;
-        double2 s = make_double2(0.0, 0.0);
+        R sr = A::zero(), si = A::zero();
         if (t < ncl) {
             for (int ch = 0; ch < a.nchunk; ++ch) {
-                const double2 v = a.part[(((int64_t)ch * 2 + face) * L + m) * a.nc + c0 + t];
-                s.x += v.x;
-                s.y += v.y;
+                const Cx v = part[(((int64_t)ch * 2 + face) * L + m) * a.nc + c0 + t];
+                sr = A::add(sr, A::re(v));
+                si = A::add(si, A::im(v));
             }
         }
-        bufA[t * L + m] = s;
+        bufA[t * L + m] = A::cmake(sr, si);
     }
     __syncthreads();
-    const double2 *Z = cta_fft<L, TC, NT, true>(bufA, bufB, a.t.inv, false);
+    const Cx *Z = cta_fft_t<R, L, TC, NT, true>(bufA, bufB, inv_tw<R>(a.t), false);
+    Cx *out = reinterpret_cast<Cx *>(a.out);
     for (int f = threadIdx.x; f < TC * (Mb + 1); f += NT) {
         const int j = f / TC, t = f - j * TC;
-        if (t < ncl) a.out[((int64_t)face * (Mb + 1) + j) * a.nc + c0 + t] = Z[t * L + j];
+        if (t < ncl) out[((int64_t)face * (Mb + 1) + j) * a.nc + c0 + t] = Z[t * L + j];
     }
 }
 
 // ---------------------------------------------------------------- stage 3b
 // L = Mc.  One line = one row of one face.
-template <int L>
+template <class R, int L>
 __global__ void __launch_bounds__(NT) face_c2r_kernel(const FaceC2R a)
 {
+    using A = Ar<R>;
+    using Cx = typename A::C;
     constexpr int LB = SmallCfg<L>::LB;
-    extern __shared__ double2 smem[];
-    double2 *bufA = smem, *bufB = smem + LB * L;
+    extern __shared__ double2 smem_raw[];
+    Cx *bufA = reinterpret_cast<Cx *>(smem_raw), *bufB = bufA + LB * L;
     const int face = blockIdx.y;
     const int r0 = blockIdx.x * LB;
     const int64_t fbase = face ? a.base[1] : a.base[0];
     const int nl = min(LB, a.nrows - r0);
-    const double2 *inb = a.in + ((int64_t)face * a.nrows + r0) * (L + 1);
+    const Cx *inb = reinterpret_cast<const Cx *>(a.in) + ((int64_t)face * a.nrows + r0) * (L + 1);
     for (int f = threadIdx.x; f < LB * L; f += NT) {
         const int l = f / L, k = f - l * L;
-        double2 z = make_double2(0.0, 0.0);
+        Cx z = A::cmake(A::zero(), A::zero());
         if (l < nl) {
-            const double2 xk = inb[(int64_t)l * (L + 1) + k];
-            const double2 xc = inb[(int64_t)l * (L + 1) + (L - k)];
+            const Cx xk = inb[(int64_t)l * (L + 1) + k];
+            const Cx xc = inb[(int64_t)l * (L + 1) + (L - k)];
             // A = X_k + conj X_{L-k};  B = e^{+i pi k/L} (X_k - conj X_{L-k});  Z' = A + i B
-            const double Ar = xk.x + xc.x, Ai = xk.y - xc.y;
-            const double Dr = xk.x - xc.x, Di = xk.y + xc.y;
-            const double2 w = a.t.half[k];   // (cos, -sin)
-            const double Br = fma(w.x, Dr, w.y * Di);     // cos*Dr + sin*Di
-            const double Bi = fma(w.x, Di, -w.y * Dr);    // cos*Di - sin*Dr
-            z = make_double2(Ar - Bi, Ai + Br);
+            const R Arr = A::add(A::re(xk), A::re(xc)), Ai = A::sub(A::im(xk), A::im(xc));
+            const R Dr = A::sub(A::re(xk), A::re(xc)), Di = A::add(A::im(xk), A::im(xc));
+            const Cx w = half_tw<R>(a.t, k);   // (cos, -sin)
+            const R Br = A::mul_add(A::re(w), Dr, A::im(w), Di);   // cos*Dr + sin*Di
+            const R Bi = A::mul_sub(A::re(w), Di, A::im(w), Dr);   // cos*Di - sin*Dr
+            z = A::cmake(A::sub(Arr, Bi), A::add(Ai, Br));
         }
         bufA[l * L + k] = z;
     }
     __syncthreads();
-    const double2 *Z = cta_fft<L, LB, NT, true>(bufA, bufB, a.t.inv, false);
+    const Cx *Z = cta_fft_t<R, L, LB, NT, true>(bufA, bufB, inv_tw<R>(a.t), false);
     for (int f = threadIdx.x; f < LB * (L + 1); f += NT) {
         const int l = f / (L + 1), t = f - l * (L + 1);
         if (l >= nl) continue;
         const int row = r0 + l;
         if (a.skip_row_edges && (row == 0 || row == a.nrows - 1)) continue;
         if (a.skip_col_edges && (t == 0 || t == L)) continue;
-        const double2 z = Z[l * L + ((t >> 1) & (L - 1))];
-        const double v = (t & 1) ? z.y : z.x;
+        const Cx z = Z[l * L + ((t >> 1) & (L - 1))];
+        const R v = (t & 1) ? A::im(z) : A::re(z);
         const int64_t node = fbase + (int64_t)row * a.row_stride + (int64_t)t * a.col_stride;
-        a.dst0[node] = v;
-        if (a.dst1) a.dst1[node] = v;
+        st_real<R>(a.dst0, node, v);
+        if (a.dst1) st_real<R>(a.dst1, node, v);
     }
 }
 
@@ -325,20 +374,27 @@ size_t smem_face() { return 2 * sizeof(double2) * FaceCfg<L>::TC * L; }
 template <int L>
 size_t smem_small() { return 2 * sizeof(double2) * SmallCfg<L>::LB * L; }
 
-template <int L>
-cudaError_t attrs_len()
+template <class R, int L>
+cudaError_t attrs_len_r()
 {
     cudaError_t e;
     const int sm = (int)smem_lines<L>();
-    if ((e = cudaFuncSetAttribute(rfft_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
-    if ((e = cudaFuncSetAttribute(face_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(rfft_kernel<R, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
+    if ((e = cudaFuncSetAttribute(face_kernel<R, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem_face<L>())))
         return e;
-    if ((e = cudaFuncSetAttribute(face_invb_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(face_invb_kernel<R, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem_small<L>())))
         return e;
-    return cudaFuncSetAttribute(face_c2r_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(face_c2r_kernel<R, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem_small<L>());
+}
+template <int L>
+cudaError_t attrs_len()
+{
+    cudaError_t e = attrs_len_r<double, L>();
+    if (e) return e;
+    return attrs_len_r<ddr, L>();
 }
 
 #define IDP_LEN_SWITCH(LEN, ...)              \
@@ -376,7 +432,8 @@ int face_blocks_per_sm(int L)
 {
     int nb = 1;
     IDP_LEN_SWITCH(L, {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, face_kernel<L>, NT, smem_face<L>()) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, face_kernel<double, L>, NT, smem_face<L>()) !=
+            cudaSuccess)
             nb = 1;
         return nb > 0 ? nb : 1;
     })
@@ -390,7 +447,8 @@ cudaError_t launch_rfft_pass(const RfftPass &a, cudaStream_t st)
     else { nu = a.n1; nv = a.n2; }
     IDP_LEN_SWITCH(a.M, {
         dim3 grid((nv + LineCfg<L>::LB - 1) / LineCfg<L>::LB, nu);
-        rfft_kernel<L><<<grid, NT, smem_lines<L>(), st>>>(a);
+        if (a.dd) rfft_kernel<ddr, L><<<grid, NT, smem_lines<L>(), st>>>(a);
+        else rfft_kernel<double, L><<<grid, NT, smem_lines<L>(), st>>>(a);
         return cudaGetLastError();
     })
 }
@@ -399,7 +457,8 @@ cudaError_t launch_face_pass(const FacePass &a, int nchunk, cudaStream_t st)
 {
     IDP_LEN_SWITCH(2 * a.Mb, {
         dim3 grid((a.nc + FaceCfg<L>::TC - 1) / FaceCfg<L>::TC, nchunk);
-        face_kernel<L><<<grid, NT, smem_face<L>(), st>>>(a);
+        if (a.dd) face_kernel<ddr, L><<<grid, NT, smem_face<L>(), st>>>(a);
+        else face_kernel<double, L><<<grid, NT, smem_face<L>(), st>>>(a);
         return cudaGetLastError();
     })
 }
@@ -414,7 +473,8 @@ cudaError_t launch_face_inv_b(const FaceInvB &a, cudaStream_t st)
 {
     IDP_LEN_SWITCH(2 * a.Mb, {
         dim3 grid((a.nc + SmallCfg<L>::LB - 1) / SmallCfg<L>::LB, 2);
-        face_invb_kernel<L><<<grid, NT, smem_small<L>(), st>>>(a);
+        if (a.dd) face_invb_kernel<ddr, L><<<grid, NT, smem_small<L>(), st>>>(a);
+        else face_invb_kernel<double, L><<<grid, NT, smem_small<L>(), st>>>(a);
         return cudaGetLastError();
     })
 }
@@ -423,7 +483,8 @@ cudaError_t launch_face_c2r(const FaceC2R &a, cudaStream_t st)
 {
     IDP_LEN_SWITCH(a.Mc, {
         dim3 grid((a.nrows + SmallCfg<L>::LB - 1) / SmallCfg<L>::LB, 2);
-        face_c2r_kernel<L><<<grid, NT, smem_small<L>(), st>>>(a);
+        if (a.dd) face_c2r_kernel<ddr, L><<<grid, NT, smem_small<L>(), st>>>(a);
+        else face_c2r_kernel<double, L><<<grid, NT, smem_small<L>(), st>>>(a);
         return cudaGetLastError();
     })
 }

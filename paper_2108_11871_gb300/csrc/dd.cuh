@@ -14,10 +14,10 @@
 
 namespace idp {
 
-struct ddr {
+struct __align__(8) ddr {
     float hi, lo;
 };
-struct ddc {
+struct __align__(16) ddc {
     ddr re, im;
 };
 
@@ -86,5 +86,54 @@ struct TwD {
     ddr r, mre, mim;
     int swap, pad;
 };
+
+}  // namespace idp
+
+namespace idp {
+
+// FP64 <-> double-float conversions with integer operations only (the FP64
+// pipe is the scarce unit, and conversions F2F run on it).
+//   hi = x with the low 29 mantissa bits cleared (exact as FP32 if the
+//        exponent is in FP32 range), lo = the cleared bits as FP32 (rounded to
+//        24 bits).  |x| < 2^-126 gives (0, 0); lo underflows gracefully for
+//        |x| < 2^-74.  Relative error at most 2^-48.
+__device__ __forceinline__ ddr dd_from_bits(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int hiw = (unsigned int)(b >> 32), low = (unsigned int)b;
+    const int e = (int)((hiw >> 20) & 0x7FF) - 1023;
+    if (e < -126) return dd_make(0.f, 0.f);
+    const unsigned int sign = hiw & 0x80000000u;
+    // top 23 mantissa bits: 20 from the high word, 3 from the low word
+    const unsigned int m23 = ((hiw & 0xFFFFFu) << 3) | (low >> 29);
+    const float hi = __int_as_float((int)(sign | ((unsigned int)(e + 127) << 23) | m23));
+    // remaining 29 bits, value rest * 2^(e-52)
+    const unsigned int rest = low & 0x1FFFFFFFu;
+    // exact FP32 of the two parts of rest (magic-number conversion), then one rounding
+    const float r_lo = __fsub_rn(__int_as_float(0x4B000000 | (rest & 0x7FFFFFu)), 8388608.0f);
+    const float r_hi = __fsub_rn(__int_as_float(0x4B000000 | (rest >> 23)), 8388608.0f);
+    const float rf = __fmaf_rn(r_hi, 8388608.0f, r_lo);
+    const int se = e - 52 + 127;
+    float lo = 0.f;
+    if (se > 0) lo = __fmul_rn(rf, __int_as_float(se << 23));
+    else if (se > -23) lo = __fmul_rn(__fmul_rn(rf, __int_as_float((se + 24) << 23)), 5.9604645e-8f);  // 2^-24
+    lo = sign ? -lo : lo;
+    return dd_make(hi, lo);
+}
+
+// FP32 -> FP64 by bits (normal or zero inputs; FP32 denormals flush to 0)
+__device__ __forceinline__ double f2d_bits(float f)
+{
+    const unsigned int u = (unsigned int)__float_as_int(f);
+    const unsigned int ex = (u >> 23) & 0xFF;
+    if (ex == 0) return 0.0;
+    const unsigned int sign = u & 0x80000000u;
+    const unsigned int hiw = sign | ((ex - 127 + 1023) << 20) | ((u & 0x7FFFFFu) >> 3);
+    const unsigned int low = (u & 7u) << 29;
+    return __hiloint2double((int)hiw, (int)low);
+}
+
+// hi + lo as FP64: two bit conversions and one FP64 addition
+__device__ __forceinline__ double dd_to_bits(ddr a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
 
 }  // namespace idp

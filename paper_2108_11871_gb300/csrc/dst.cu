@@ -21,7 +21,7 @@ template <int K>
 struct DstCfg {
     static constexpr int M = 2 * K;
     static constexpr int N = M - 1;
-    // lines per block: 2 buffers x LB x M doubles (32 KB for M >= 128), at
+    // lines per block: 2 buffers x LB x M reals (32 KB for M >= 128), at
     // least 8 lines so that the scan groups fit a warp
     static constexpr int LB0 = (2048 / M) > 32 ? 32 : (2048 / M);
     static constexpr int LB = LB0 < 8 ? 8 : LB0;
@@ -29,14 +29,54 @@ struct DstCfg {
     static constexpr int C = (K / G) > 0 ? K / G : 1;  // scan elements per thread
 };
 
-template <int K>
+// element access for the two storage forms of a real value: FP64, or a
+// double-float pair (the DD kernels keep intermediates in that form)
+template <class R>
+struct Io;
+template <>
+struct Io<double> {
+    static __device__ __forceinline__ double ld(const void *p, int64_t i, int) { return reinterpret_cast<const double *>(p)[i]; }
+    static __device__ __forceinline__ void st(void *p, int64_t i, double v, int) { reinterpret_cast<double *>(p)[i] = v; }
+};
+template <>
+struct Io<ddr> {
+    static __device__ __forceinline__ ddr ld(const void *p, int64_t i, int dd)
+    {
+        if (dd) return reinterpret_cast<const ddr *>(p)[i];
+        return dd_from_bits(reinterpret_cast<const double *>(p)[i]);
+    }
+    static __device__ __forceinline__ void st(void *p, int64_t i, ddr v, int dd)
+    {
+        if (dd) reinterpret_cast<ddr *>(p)[i] = v;
+        else reinterpret_cast<double *>(p)[i] = dd_to_bits(v);
+    }
+};
+
+template <class R>
+struct Tabs;
+template <>
+struct Tabs<double> {
+    static __device__ __forceinline__ const Tw *tw(const DstPass &a) { return a.tw; }
+    static __device__ __forceinline__ double2 half(const DstPass &a, int k) { return a.half[k]; }
+    static __device__ __forceinline__ double sin2(const DstPass &a, int j) { return a.sin2[j]; }
+};
+template <>
+struct Tabs<ddr> {
+    static __device__ __forceinline__ const TwD *tw(const DstPass &a) { return a.twd; }
+    static __device__ __forceinline__ ddc half(const DstPass &a, int k) { return a.halfd[k]; }
+    static __device__ __forceinline__ ddr sin2(const DstPass &a, int j) { return a.sin2d[j]; }
+};
+
+template <class R, int K>
 __global__ void __launch_bounds__(NT) dst_pass_kernel(const DstPass a)
 {
     using Cfg = DstCfg<K>;
+    using A = Ar<R>;
+    using Cx = typename A::C;
     constexpr int M = Cfg::M, N = Cfg::N, LB = Cfg::LB;
-    extern __shared__ double2 smem[];
-    double2 *bufA = smem;            // LB * K complex
-    double2 *bufB = smem + LB * K;   // LB * K complex
+    extern __shared__ double2 smem_raw[];
+    Cx *bufA = reinterpret_cast<Cx *>(smem_raw);   // LB * K complex
+    Cx *bufB = bufA + LB * K;                      // LB * K complex
 
     // line (u, v) coordinates: the two non-transform axes, v fastest
     int nv, nu;
@@ -66,60 +106,60 @@ __global__ void __launch_bounds__(NT) dst_pass_kernel(const DstPass a)
     const int nl = min(LB, nv - v0);
     const bool contig = (a.axis == 2);
 
-    // 1. load raw lines into bufB viewed as double[LB][M] (entries 0..N-1)
-    double *raw = reinterpret_cast<double *>(bufB);
-    const double *inb = a.in.p + (int64_t)u * isu + (int64_t)v0 * isv;
+    // 1. load raw lines into bufB viewed as R[LB][M] (entries 0..N-1)
+    R *raw = reinterpret_cast<R *>(bufB);
+    const int64_t inb = (int64_t)u * isu + (int64_t)v0 * isv;
     for (int f = threadIdx.x; f < LB * N; f += NT) {
         int l, e;
         if (contig) { l = f / N; e = f - l * N; }
         else { e = f / LB; l = f - e * LB; }
-        double x = 0.0;
-        if (l < nl) x = inb[(int64_t)l * isv + (int64_t)e * ise];
+        R x = A::zero();
+        if (l < nl) x = Io<R>::ld(a.in.p, inb + (int64_t)l * isv + (int64_t)e * ise, a.in_dd);
         raw[l * M + e] = x;
     }
     __syncthreads();
 
-    // 2. pre-processing into bufA viewed as double[LB][M] (zf[j] = y'_j)
-    double *zf = reinterpret_cast<double *>(bufA);
+    // 2. pre-processing into bufA viewed as R[LB][M] (zf[j] = y'_j)
+    R *zf = reinterpret_cast<R *>(bufA);
     for (int f = threadIdx.x; f < LB * K; f += NT) {
         const int l = f / K;
         const int j = f - l * K;
-        const double *xl = raw + l * M;   // x_i at xl[i-1]
-        double *zl = zf + l * M;
+        const R *xl = raw + l * M;   // x_i at xl[i-1]
+        R *zl = zf + l * M;
         if (j == 0) {
-            zl[0] = 0.0;
-            zl[K] = 4.0 * xl[K - 1];
+            zl[0] = A::zero();
+            zl[K] = A::times4(xl[K - 1]);
         } else {
-            const double xa = xl[j - 1], xb = xl[M - j - 1];
-            const double s = a.sin2[j];
-            const double p = xa + xb, m = xa - xb;
-            zl[j] = fma(s, p, m);
-            zl[M - j] = fma(s, p, -m);
+            const R xa = xl[j - 1], xb = xl[M - j - 1];
+            const R s = Tabs<R>::sin2(a, j);
+            const R p = A::add(xa, xb), m = A::sub(xa, xb);
+            zl[j] = A::fma(s, p, m);
+            zl[M - j] = A::fma(s, p, A::neg(m));
         }
     }
     __syncthreads();
 
     // 3. complex FFT of length K
-    double2 *Z = cta_fft<K, LB, NT, false>(bufA, bufB, a.tw, false);
-    double *o = reinterpret_cast<double *>(Z == bufA ? bufB : bufA);   // double[LB][M]
+    Cx *Z = cta_fft_t<R, K, LB, NT, false>(bufA, bufB, Tabs<R>::tw(a), false);
+    R *o = reinterpret_cast<R *>(Z == bufA ? bufB : bufA);   // R[LB][M]
 
     // 4. post-processing: even outputs final, odd slots get Re T_k
     for (int f = threadIdx.x; f < LB * (K / 2); f += NT) {
         const int l = f / (K / 2);
         const int k = f - l * (K / 2) + 1;      // 1..K/2
-        const double2 *zl = Z + l * K;
-        double *ol = o + l * M;
-        const double2 zk = zl[k], zc = zl[K - k];
-        const double Er = zk.x + zc.x, Ei = zk.y - zc.y;
-        const double Or = zk.x - zc.x, Oi = zk.y + zc.y;
-        const double2 w = a.half[k];
-        const double Pr = fma(w.x, Or, -w.y * Oi);
-        const double Pi = fma(w.x, Oi, w.y * Or);
-        ol[2 * k - 1] = Pr - Ei;
-        ol[2 * (K - k) - 1] = Ei + Pr;
-        ol[2 * k] = Er + Pi;
-        ol[2 * (K - k)] = Er - Pi;
-        if (k == 1) ol[0] = zl[0].x + zl[0].y;
+        const Cx *zl = Z + l * K;
+        R *ol = o + l * M;
+        const Cx zk = zl[k], zc = zl[K - k];
+        const R Er = A::add(A::re(zk), A::re(zc)), Ei = A::sub(A::im(zk), A::im(zc));
+        const R Or = A::sub(A::re(zk), A::re(zc)), Oi = A::add(A::im(zk), A::im(zc));
+        const Cx w = Tabs<R>::half(a, k);
+        const R Pr = A::mul_sub(A::re(w), Or, A::im(w), Oi);
+        const R Pi = A::mul_add(A::re(w), Oi, A::im(w), Or);
+        ol[2 * k - 1] = A::sub(Pr, Ei);
+        ol[2 * (K - k) - 1] = A::add(Ei, Pr);
+        ol[2 * k] = A::add(Er, Pi);
+        ol[2 * (K - k)] = A::sub(Er, Pi);
+        if (k == 1) ol[0] = A::add(A::re(zl[0]), A::im(zl[0]));
     }
     __syncthreads();
 
@@ -128,52 +168,55 @@ __global__ void __launch_bounds__(NT) dst_pass_kernel(const DstPass a)
         constexpr int G = Cfg::G, C = Cfg::C;
         const int l = threadIdx.x / G;
         const int g = threadIdx.x - l * G;
-        double vals[C];
-        double run = 0.0;
+        R vals[C];
+        R run = A::zero();
         if (g * C < K) {
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                run += o[l * M + 2 * (g * C + c)];
+                run = A::add(run, o[l * M + 2 * (g * C + c)]);
                 vals[c] = run;
             }
         }
         // inclusive scan of the group totals (groups of G consecutive lanes)
-        double incl = run;
+        R incl = run;
 #pragma unroll
         for (int dd = 1; dd < G; dd <<= 1) {
-            const double nb = __shfl_up_sync(0xffffffffu, incl, dd, G);
-            if (g >= dd) incl += nb;
+            const R nb = A::shfl_up(incl, dd, G);
+            if (g >= dd) incl = A::add(incl, nb);
         }
-        const double off = incl - run;
+        const R off = A::sub(incl, run);
         if (g * C < K) {
 #pragma unroll
-            for (int c = 0; c < C; ++c) o[l * M + 2 * (g * C + c)] = vals[c] + off;
+            for (int c = 0; c < C; ++c) o[l * M + 2 * (g * C + c)] = A::add(vals[c], off);
         }
     }
     __syncthreads();
 
     // 6. epilogue and store
-    double *outb = a.out.p + (int64_t)u * osu + (int64_t)v0 * osv;
-    const double *tabb = a.tab ? a.tab + (int64_t)u * tsu + (int64_t)v0 * tsv : nullptr;
-    const double *addb = a.add.p ? a.add.p + (int64_t)u * asu + (int64_t)v0 * asv : nullptr;
+    const int64_t outb = (int64_t)u * osu + (int64_t)v0 * osv;
+    const int64_t tabb = (int64_t)u * tsu + (int64_t)v0 * tsv;
+    const int64_t addb = (int64_t)u * asu + (int64_t)v0 * asv;
+    const bool has_tab = a.tab || a.tabd;
     for (int f = threadIdx.x; f < LB * N; f += NT) {
         int l, e;
         if (contig) { l = f / N; e = f - l * N; }
         else { e = f / LB; l = f - e * LB; }
         if (l >= nl) continue;
-        double y = o[l * M + e];
-        if (tabb) {
-            const double t = tabb[(int64_t)l * tsv + (int64_t)e * tse];
-            if (addb) y = fma(t, y, addb[(int64_t)l * asv + (int64_t)e * ase]);
-            else y = t * y;
-        } else if (addb) {
-            y += addb[(int64_t)l * asv + (int64_t)e * ase];
+        R y = o[l * M + e];
+        const int64_t ti = tabb + (int64_t)l * tsv + (int64_t)e * tse;
+        const int64_t ai = addb + (int64_t)l * asv + (int64_t)e * ase;
+        if (has_tab) {
+            const R t = Io<R>::ld(a.tabd ? (const void *)a.tabd : (const void *)a.tab, ti, a.tabd != nullptr);
+            if (a.add.p) y = A::fma(t, y, Io<R>::ld(a.add.p, ai, a.add_dd));
+            else y = A::mul(t, y);
+        } else if (a.add.p) {
+            y = A::add(y, Io<R>::ld(a.add.p, ai, a.add_dd));
         }
-        outb[(int64_t)l * osv + (int64_t)e * ose] = y;
+        Io<R>::st(a.out.p, outb + (int64_t)l * osv + (int64_t)e * ose, y, a.out_dd);
     }
 }
 
-template <int K>
+template <class R, int K>
 cudaError_t launch_k(const DstPass &a, cudaStream_t st)
 {
     using Cfg = DstCfg<K>;
@@ -185,42 +228,56 @@ cudaError_t launch_k(const DstPass &a, cudaStream_t st)
     else if (a.axis == 1) { nu = a.n0; nv = a.n2; }
     else { nu = a.n1; nv = a.n2; }
     dim3 grid((nv + Cfg::LB - 1) / Cfg::LB, nu);
-    dst_pass_kernel<K><<<grid, NT, sm, st>>>(a);
+    dst_pass_kernel<R, K><<<grid, NT, sm, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int K>
+template <class R, int K>
 cudaError_t attr_k()
 {
     using Cfg = DstCfg<K>;
     const int sm = (int)(2 * sizeof(double2) * Cfg::LB * K);
-    return cudaFuncSetAttribute(dst_pass_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    return cudaFuncSetAttribute(dst_pass_kernel<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+}
+
+template <class R>
+cudaError_t attrs()
+{
+    cudaError_t e;
+    if ((e = attr_k<R, 8>()) != cudaSuccess) return e;
+    if ((e = attr_k<R, 16>()) != cudaSuccess) return e;
+    if ((e = attr_k<R, 32>()) != cudaSuccess) return e;
+    if ((e = attr_k<R, 64>()) != cudaSuccess) return e;
+    if ((e = attr_k<R, 128>()) != cudaSuccess) return e;
+    return attr_k<R, 256>();
+}
+
+template <class R>
+cudaError_t launch_r(const DstPass &a, cudaStream_t st)
+{
+    switch (a.M) {
+    case 16: return launch_k<R, 8>(a, st);
+    case 32: return launch_k<R, 16>(a, st);
+    case 64: return launch_k<R, 32>(a, st);
+    case 128: return launch_k<R, 64>(a, st);
+    case 256: return launch_k<R, 128>(a, st);
+    case 512: return launch_k<R, 256>(a, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
 
 cudaError_t dst_set_attributes()
 {
-    cudaError_t e;
-    if ((e = attr_k<8>()) != cudaSuccess) return e;
-    if ((e = attr_k<16>()) != cudaSuccess) return e;
-    if ((e = attr_k<32>()) != cudaSuccess) return e;
-    if ((e = attr_k<64>()) != cudaSuccess) return e;
-    if ((e = attr_k<128>()) != cudaSuccess) return e;
-    return attr_k<256>();
+    cudaError_t e = attrs<double>();
+    if (e != cudaSuccess) return e;
+    return attrs<ddr>();
 }
 
 cudaError_t launch_dst_pass(const DstPass &a, cudaStream_t st)
 {
-    switch (a.M) {
-    case 16: return launch_k<8>(a, st);
-    case 32: return launch_k<16>(a, st);
-    case 64: return launch_k<32>(a, st);
-    case 128: return launch_k<64>(a, st);
-    case 256: return launch_k<128>(a, st);
-    case 512: return launch_k<256>(a, st);
-    default: return cudaErrorInvalidValue;
-    }
+    return a.dd ? launch_r<ddr>(a, st) : launch_r<double>(a, st);
 }
 
 }  // namespace idp

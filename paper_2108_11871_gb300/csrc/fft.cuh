@@ -1,10 +1,12 @@
-// CTA-cooperative FP64 complex FFT in shared memory (radix-2 Stockham,
-// natural order in and out).  FP64 arithmetic is the scarce resource on
-// GB300 (about 1/60 of the FP32 rate), so the butterfly uses the ratio
-// ("tangent") form of the twiddle: 6 FP64 instructions per butterfly
-// instead of 8, and the first two stages use no multiplications.
+// CTA-cooperative complex FFT in shared memory (radix-2 Stockham, natural
+// order in and out), for FP64 (double2) or double-float (ddc) elements.
+// FP64 arithmetic is the scarce resource on GB300 (about 1/60 of the FP32
+// rate), so the FP64 butterfly uses the ratio ("tangent") form of the
+// twiddle: 6 FP64 instructions per butterfly instead of 8, and the first two
+// stages use no multiplications.  The double-float butterfly runs the same
+// schedule on the FP32 pipe.
 #pragma once
-#include "idp_internal.cuh"
+#include "arith.cuh"
 
 namespace idp {
 
@@ -16,62 +18,59 @@ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_doub
 // INV selects e^{+2 pi i jk/L} (unnormalised).  If zero_half, the second
 // half of every input line is known to be zero (saves the first stage).
 // All NT threads of the block must call it; it ends with __syncthreads().
-template <int L, int LB, int NT, bool INV>
-__device__ __forceinline__ double2 *cta_fft(double2 *X, double2 *Y, const Tw *__restrict__ tw,
-                                            bool zero_half)
+template <class R, int L, int LB, int NT, bool INV>
+__device__ __forceinline__ typename Ar<R>::C *cta_fft_t(typename Ar<R>::C *X, typename Ar<R>::C *Y,
+                                                        const typename Ar<R>::T *__restrict__ tw, bool zero_half)
 {
+    using C = typename Ar<R>::C;
     constexpr int H = L / 2;
 #pragma unroll 1
     for (int Ns = 1; Ns < L; Ns <<= 1) {
+#pragma unroll
         for (int b = threadIdx.x; b < LB * H; b += NT) {
             const int line = b / H;
             const int j = b - line * H;
-            const double2 *x = X + line * L;
-            double2 *y = Y + line * L;
+            const C *x = X + line * L;
+            C *y = Y + line * L;
             const int k = j & (Ns - 1);
             const int o = ((j - k) << 1) + k;
-            const double2 a = x[j];
-            double2 A, B;
+            const C a = x[j];
+            C A, B;
             if (Ns == 1) {
                 if (zero_half) {
                     A = a;
                     B = a;
                 } else {
-                    const double2 c = x[j + H];
-                    A = cadd(a, c);
-                    B = csub(a, c);
+                    const C c = x[j + H];
+                    A = Ar<R>::cadd(a, c);
+                    B = Ar<R>::csub(a, c);
                 }
             } else if (Ns == 2) {
-                const double2 c = x[j + H];
+                const C c = x[j + H];
                 // w = 1 (k = 0) or -i (forward) / +i (inverse) (k = 1)
-                double2 t;
-                if (INV)
-                    t = k ? make_double2(-c.y, c.x) : c;
-                else
-                    t = k ? make_double2(c.y, -c.x) : c;
-                A = cadd(a, t);
-                B = csub(a, t);
+                const C t = k ? (INV ? mul_pi(c) : mul_mi(c)) : c;
+                A = Ar<R>::cadd(a, t);
+                B = Ar<R>::csub(a, t);
             } else {
-                const double2 c = x[j + H];
-                const Tw w = tw[k * (L / (2 * Ns))];
-                const double P = w.swap ? c.y : c.x;
-                const double Q = w.swap ? c.x : c.y;
-                const double u = fma(-w.r, Q, P);
-                const double v = fma(w.r, P, Q);
-                A.x = fma(w.mre, u, a.x);
-                B.x = fma(-w.mre, u, a.x);
-                A.y = fma(w.mim, v, a.y);
-                B.y = fma(-w.mim, v, a.y);
+                const C c = x[j + H];
+                Ar<R>::bfly(a, c, tw[k * (L / (2 * Ns))], A, B);
             }
             y[o] = A;
             y[o + Ns] = B;
         }
         __syncthreads();
-        double2 *t = X;
+        C *t = X;
         X = Y;
         Y = t;
     }
     return X;
+}
+
+// FP64 form used by the boundary kernels
+template <int L, int LB, int NT, bool INV>
+__device__ __forceinline__ double2 *cta_fft(double2 *X, double2 *Y, const Tw *__restrict__ tw, bool zero_half)
+{
+    return cta_fft_t<double, L, LB, NT, INV>(X, Y, tw, zero_half);
 }
 
 }  // namespace idp

@@ -18,11 +18,17 @@ struct Tw {
 // Tables for one complex FFT length L (power of two): forward and inverse
 // twiddles e^{-+2 pi i j / L}, j < L/2, and the real-transform post/pre
 // twiddles e^{-i pi k / L}, k <= L (cos, sin pairs).
+struct TwD;
+struct ddc;
+struct ddr;
 struct FftTables {
     int L;
     const Tw *fwd;      // device, L/2 entries
     const Tw *inv;      // device, L/2 entries
     const double2 *half; // device, L+1 entries: (cos(pi k/L), -sin(pi k/L))
+    const TwD *fwdd;    // double-float forms of the three tables
+    const TwD *invd;
+    const ddc *halfd;
 };
 
 // Strided 3-D view in units of elements: element (i0,i1,i2) at base + i0*s0 + i1*s1 + i2*s2.
@@ -45,6 +51,14 @@ struct DstPass {
     const Tw *tw;          // twiddles for the complex FFT of length M/2
     const double2 *half;   // half-step twiddles for length M/2 (e^{-i pi k/(M/2)})
     const double *sin2;    // 2 sin(pi j / M), j = 0..M/2
+    // double-float variant (dd = 1): arithmetic on the FP32 pipe; in/out/add
+    // may hold FP64 values or double-float pairs (in_dd / out_dd / add_dd)
+    int dd;
+    int in_dd, out_dd, add_dd;
+    const ddr *tabd;       // tab as double-float pairs (if not null, used instead of tab)
+    const TwD *twd;
+    const ddc *halfd;
+    const ddr *sin2d;
 };
 
 cudaError_t launch_dst_pass(const DstPass &a, cudaStream_t st);
@@ -79,6 +93,7 @@ struct RfftPass {
     int n0, n1, n2;                               // interior box (extent along axis = M-1)
     int axis, M;
     FftTables t;                                  // tables for complex length M
+    int dd;                                       // 1: double-float arithmetic, output as pairs
 };
 cudaError_t launch_rfft_pass(const RfftPass &a, cudaStream_t st);
 
@@ -94,6 +109,8 @@ struct FacePass {
     double2 *part;             // partial sums [nchunk][2][2Mb][nc]
     int pchunk;                // slices per chunk
     FftTables t;               // tables for complex length 2Mb
+    int dd;                    // 1: double-float (D, part as pairs; khatd used)
+    const ddr *khatd;          // kernel spectra as double-float pairs
 };
 cudaError_t launch_face_pass(const FacePass &a, int nchunk, cudaStream_t st);
 int face_columns_per_block(int L);   // frequencies c per block of the face pass
@@ -114,6 +131,7 @@ struct FaceInvB {
     int Mb, nc;
     double2 *out;              // [2][Mb+1][nc]
     FftTables t;               // length 2Mb
+    int dd;
 };
 cudaError_t launch_face_inv_b(const FaceInvB &a, cudaStream_t st);
 
@@ -131,6 +149,7 @@ struct FaceC2R {
     // lower face axis) and columns with col in {0, Mc} if skip_cols is set.
     int skip_row_edges, skip_col_edges;
     FftTables t;               // length Mc
+    int dd;
 };
 cudaError_t launch_face_c2r(const FaceC2R &a, cudaStream_t st);
 
@@ -178,6 +197,8 @@ cudaError_t launch_rhs6_core(const Grid3 &g, const double *W, double *R, cudaStr
 cudaError_t launch_rhs6_extrap(const Grid3 &g, double *R, cudaStream_t st);
 // tabc = sc / lambda_c(k) and tab4 = sc / Lambda4(k) on the dense mode grid;
 // lc / ld hold the per-axis 1-D eigenvalues, axis s at offset off_s (axis 0 at 0).
+// y = double-float pairs of x (set-up only)
+cudaError_t launch_to_dd(const double *x, ddr *y, int64_t n, cudaStream_t st);
 cudaError_t launch_eigen_tables(const Grid3 &g, const double *lc, const double *ld, int64_t off1,
                                 int64_t off2, double sc, double *tabc, double *tab4, cudaStream_t st);
 

@@ -9,6 +9,7 @@
 #include <new>
 #include <vector>
 
+#include "dd.cuh"
 #include "idp_internal.cuh"
 #include "../../include/idp.h"
 
@@ -62,8 +63,29 @@ Tw make_tw(double c, double s)
 struct DevFft {
     Tw *fwd = nullptr, *inv = nullptr;
     double2 *half = nullptr;
-    FftTables view(int L) const { return FftTables{L, fwd, inv, half}; }
+    TwD *fwdd = nullptr, *invd = nullptr;   // double-float forms
+    ddc *halfd = nullptr;
+    FftTables view(int L) const { return FftTables{L, fwd, inv, half, fwdd, invd, halfd}; }
 };
+
+// double-float pair of a double (host): hi = nearest float, lo = nearest float of the rest
+ddr host_dd(double x)
+{
+    ddr r;
+    r.hi = (float)x;
+    r.lo = (float)(x - (double)r.hi);
+    return r;
+}
+TwD make_twd(const Tw &t)
+{
+    TwD d;
+    d.r = host_dd(t.r);
+    d.mre = host_dd(t.mre);
+    d.mim = host_dd(t.mim);
+    d.swap = t.swap;
+    d.pad = 0;
+    return d;
+}
 
 std::mutex g_attr_mu;
 std::atomic<uint64_t> g_serial{1};
@@ -111,6 +133,7 @@ struct idp_plan_s {
 
     std::map<int, DevFft> fft;        // by complex length
     std::map<int, double *> sin2;     // by M: 2 sin(pi j / M), j = 0..M/2
+    std::map<int, ddr *> sin2d;       // double-float form
     std::vector<void *> allocs;
     int64_t bytes = 0;
 
@@ -119,6 +142,8 @@ struct idp_plan_s {
     double *Q0 = nullptr, *Q1 = nullptr, *Q2 = nullptr, *sin4 = nullptr;   // gtilde parts
     double2 *T0 = nullptr, *T1 = nullptr, *part = nullptr, *F = nullptr;
     double *khat[3] = {nullptr, nullptr, nullptr};
+    ddr *khatd[3] = {nullptr, nullptr, nullptr};   // double-float copies (precision DF32)
+    int64_t khat_n[3] = {0, 0, 0};
     int nchunk[3] = {1, 1, 1}, pchunk[3] = {1, 1, 1};
 
     // mixed precision (IDP_KEY_PRECISION = 1): sine passes on the tensor cores
@@ -205,12 +230,26 @@ int get_fft(idp_plan p, int L, FftTables *out)
     }
     std::vector<double2> hf(L + 1);
     for (int k = 0; k <= L; ++k) hf[k] = make_double2(cospi_frac(k, L), -sinpi_frac(k, L));
+    std::vector<TwD> fwd2(L / 2), ivd2(L / 2);
+    std::vector<ddc> hfd(L + 1);
+    for (int j = 0; j < L / 2; ++j) {
+        fwd2[j] = make_twd(fw[j]);
+        ivd2[j] = make_twd(iv[j]);
+    }
+    for (int k = 0; k <= L; ++k) {
+        hfd[k].re = host_dd(hf[k].x);
+        hfd[k].im = host_dd(hf[k].y);
+    }
     int rc;
-    if ((rc = p->alloc(&t.fwd, L / 2)) || (rc = p->alloc(&t.inv, L / 2)) || (rc = p->alloc(&t.half, L + 1)))
+    if ((rc = p->alloc(&t.fwd, L / 2)) || (rc = p->alloc(&t.inv, L / 2)) || (rc = p->alloc(&t.half, L + 1)) ||
+        (rc = p->alloc(&t.fwdd, L / 2)) || (rc = p->alloc(&t.invd, L / 2)) || (rc = p->alloc(&t.halfd, L + 1)))
         return rc;
     IDP_CK(cudaMemcpy(t.fwd, fw.data(), sizeof(Tw) * (L / 2), cudaMemcpyHostToDevice));
     IDP_CK(cudaMemcpy(t.inv, iv.data(), sizeof(Tw) * (L / 2), cudaMemcpyHostToDevice));
     IDP_CK(cudaMemcpy(t.half, hf.data(), sizeof(double2) * (L + 1), cudaMemcpyHostToDevice));
+    IDP_CK(cudaMemcpy(t.fwdd, fwd2.data(), sizeof(TwD) * (L / 2), cudaMemcpyHostToDevice));
+    IDP_CK(cudaMemcpy(t.invd, ivd2.data(), sizeof(TwD) * (L / 2), cudaMemcpyHostToDevice));
+    IDP_CK(cudaMemcpy(t.halfd, hfd.data(), sizeof(ddc) * (L + 1), cudaMemcpyHostToDevice));
     p->fft[L] = t;
     *out = t.view(L);
     return IDP_OK;
@@ -224,12 +263,19 @@ int get_sin2(idp_plan p, int M, const double **out)
         return IDP_OK;
     }
     std::vector<double> s(M / 2 + 1);
-    for (int j = 0; j <= M / 2; ++j) s[j] = 2.0 * sinpi_frac(j, M);
+    std::vector<ddr> sd(M / 2 + 1);
+    for (int j = 0; j <= M / 2; ++j) {
+        s[j] = 2.0 * sinpi_frac(j, M);
+        sd[j] = host_dd(s[j]);
+    }
     double *d;
-    int rc = p->alloc(&d, M / 2 + 1);
-    if (rc) return rc;
+    ddr *dd;
+    int rc;
+    if ((rc = p->alloc(&d, M / 2 + 1)) || (rc = p->alloc(&dd, M / 2 + 1))) return rc;
     IDP_CK(cudaMemcpy(d, s.data(), sizeof(double) * (M / 2 + 1), cudaMemcpyHostToDevice));
+    IDP_CK(cudaMemcpy(dd, sd.data(), sizeof(ddr) * (M / 2 + 1), cudaMemcpyHostToDevice));
     p->sin2[M] = d;
+    p->sin2d[M] = dd;
     *out = d;
     return IDP_OK;
 }
@@ -350,9 +396,11 @@ int transform_mixed(idp_plan p, View3 in, View3 out, const double *tab, View3 ad
 // last pass applies the epilogue (tab, add) and writes `out`; intermediate
 // passes run in place on `work`.
 int transform(idp_plan p, View3 in, double *work, View3 out, const double *tab, View3 add, bool forward,
-              cudaStream_t st, bool allow_mixed = true)
+              cudaStream_t st, bool allow_reduced = true)
 {
-    if (p->mixed && allow_mixed) return transform_mixed(p, in, out, tab, add, st == p->side ? 1 : 0, st);
+    if (p->mixed == IDP_PRECISION_MIXED_BF16X3 && allow_reduced)
+        return transform_mixed(p, in, out, tab, add, st == p->side ? 1 : 0, st);
+    const bool dd = (p->mixed == IDP_PRECISION_DF32) && allow_reduced;
     int axes[3], na = 0;
     if (forward) {
         for (int s = 2; s >= 0; --s)
@@ -377,6 +425,16 @@ int transform(idp_plan p, View3 in, double *work, View3 out, const double *tab, 
         a.tw = t.fwd;
         a.half = t.half;
         if ((rc = get_sin2(p, p->M[s], &a.sin2))) return rc;
+        if (dd) {
+            // double-float arithmetic; intermediate passes keep double-float pairs
+            a.dd = 1;
+            a.in_dd = (q == 0) ? 0 : 1;
+            a.out_dd = (q == na - 1) ? 0 : 1;
+            a.add_dd = 0;
+            a.twd = t.fwdd;
+            a.halfd = t.halfd;
+            a.sin2d = p->sin2d[p->M[s]];
+        }
         Mark mk(p, IDP_KERNEL_DST, st);
         IDP_CK(launch_dst_pass(a, st));
     }
@@ -403,6 +461,12 @@ int dst_box(idp_plan p, double *x, int b0, int b1, int b2, int M2, int M1, cudaS
         a.tw = t.fwd;
         a.half = t.half;
         if ((rc = get_sin2(p, Ms[q], &a.sin2))) return rc;
+        if (p->mixed == IDP_PRECISION_DF32) {
+            a.dd = 1;
+            a.twd = t.fwdd;
+            a.halfd = t.halfd;
+            a.sin2d = p->sin2d[Ms[q]];
+        }
         Mark mk(p, IDP_KERNEL_DST_PARTS, st);
         IDP_CK(launch_dst_pass(a, st));
     }
@@ -439,6 +503,8 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
     const View3 r = node_interior(p, rho);
     int rc;
     FftTables t;
+    // double-float arithmetic for the 3-D convolutions in precision DF32
+    const int dd = (p->mixed == IDP_PRECISION_DF32 && p->d == 3) ? 1 : 0;
     // stage 1a: along axis 2 -> T0[i0][i1][m2]
     {
         RfftPass a{};
@@ -449,6 +515,7 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
         a.axis = 2; a.M = p->M[2];
         if ((rc = get_fft(p, p->M[2], &t))) return rc;
         a.t = t;
+        a.dd = dd;
         Mark mk(p, IDP_KERNEL_RFFT, st);
         IDP_CK(launch_rfft_pass(a, st));
     }
@@ -462,6 +529,7 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
         a.axis = 1; a.M = p->M[1];
         if ((rc = get_fft(p, p->M[1], &t))) return rc;
         a.t = t;
+        a.dd = dd;
         Mark mk(p, IDP_KERNEL_RFFT, st);
         IDP_CK(launch_rfft_pass(a, st));
     }
@@ -509,6 +577,8 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
         f.pchunk = p->pchunk[a_];
         if ((rc = get_fft(p, 2 * p->M[b], &t))) return rc;
         f.t = t;
+        f.dd = dd;
+        f.khatd = p->khatd[a_];
         {
             Mark mk(p, IDP_KERNEL_FACE, st);
             IDP_CK(launch_face_pass(f, p->nchunk[a_], st));
@@ -516,6 +586,7 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
         FaceInvB ib{};
         ib.part = p->part; ib.nchunk = p->nchunk[a_];
         ib.Mb = p->M[b]; ib.nc = f.nc; ib.out = p->F; ib.t = t;
+        ib.dd = dd;
         {
             Mark mk(p, IDP_KERNEL_FACE_INVB, st);
             IDP_CK(launch_face_inv_b(ib, st));
@@ -529,6 +600,7 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
         cr.skip_col_edges = (a_ == 2);
         if ((rc = get_fft(p, p->M[c], &t))) return rc;
         cr.t = t;
+        cr.dd = dd;
         Mark mk(p, IDP_KERNEL_FACE_C2R, st);
         IDP_CK(launch_face_c2r(cr, st));
     }
@@ -591,8 +663,8 @@ int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t s
         Mark mk(p, IDP_KERNEL_GTILDE_EXPAND, st);
         IDP_CK(launch_gtilde_expand(p->grid, p->Q0, p->Q1, p->Q2, p->sin4, p->tab4, nullptr, p->B, st));
     }
-    // u1 feeds the sixth differences of R, which amplify its rounding: this
-    // inverse transform stays FP64 in every precision mode
+    // u1 feeds the sixth differences of R, which amplify its rounding by ~1e4-1e7:
+    // this inverse transform stays FP64 in every precision mode
     if ((rc = transform(p, dense(p, p->B), p->B, node_interior(p, p->U), nullptr, none, false, st, false)))
         return rc;
     if (stop == IDP_STAGE_U1) {
@@ -741,6 +813,7 @@ int plan_setup(idp_plan p)
             fmax = std::max<int64_t>(fmax, (int64_t)2 * (Mb + 1) * (Mc + 1));
             const int64_t per = (int64_t)(Mb + 1) * (Mc + 1);
             if ((rc = p->alloc(&p->khat[a_], (int64_t)np * per))) return rc;
+            p->khat_n[a_] = (int64_t)np * per;
             // build in slabs of slices to bound the temporaries
             const int slab = std::max(1, (int)std::min<int64_t>(np, (int64_t)(64 << 20) / (per * 8)));
             double *kb, *yb, *tcb, *tbb;
@@ -873,7 +946,8 @@ int idp_plan_set(idp_plan p, int key, int64_t value)
         return IDP_OK;
     }
     if (key == IDP_KEY_PRECISION) {
-        if (value != IDP_PRECISION_FP64 && value != IDP_PRECISION_MIXED_BF16X3) return IDP_EINVAL;
+        if (value != IDP_PRECISION_FP64 && value != IDP_PRECISION_MIXED_BF16X3 && value != IDP_PRECISION_DF32)
+            return IDP_EINVAL;
         if (value == IDP_PRECISION_MIXED_BF16X3) {
             int rc;
             if (!p->d_err) {
@@ -887,6 +961,14 @@ int idp_plan_set(idp_plan p, int key, int64_t value)
                 const void *img;
                 if (p->act[s] && (rc = get_mp_image(p, p->M[s], &img))) return rc;
             }
+        }
+        if (value == IDP_PRECISION_DF32 && p->d == 3 && !p->khatd[0]) {
+            int rc;
+            for (int a_ = 0; a_ < 3; ++a_) {
+                if ((rc = p->alloc(&p->khatd[a_], p->khat_n[a_]))) return rc;
+                IDP_CK(launch_to_dd(p->khat[a_], p->khatd[a_], p->khat_n[a_], 0));
+            }
+            IDP_CK(cudaDeviceSynchronize());
         }
         if (p->mixed != (int)value) {
             p->mixed = (int)value;

@@ -3,6 +3,7 @@
 //
 // Node arrays are n0 x n1 x n2 (C order); 2-D grids use n0 = 1 and the
 // axes 1, 2.  Interior arrays are dense over the interior nodes.
+#include "dd.cuh"
 #include "idp_internal.cuh"
 
 namespace idp {
@@ -359,6 +360,20 @@ cudaError_t launch_rhs6_core(const Grid3 &g, const double *W, double *R, cudaStr
 cudaError_t launch_rhs6_extrap(const Grid3 &g, double *R, cudaStream_t st)
 {
     rhs6_extrap_kernel<<<grid3(g.n2 - 2, g.n1 - 2, g.d == 3 ? g.n0 - 2 : 1), dim3(32, 8), 0, st>>>(g, R);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void to_dd_kernel(const double *x, ddr *y, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = dd_from(x[i]);
+}
+}  // namespace
+
+cudaError_t launch_to_dd(const double *x, ddr *y, int64_t n, cudaStream_t st)
+{
+    to_dd_kernel<<<grid_for(n), 256, 0, st>>>(x, y, n);
     return cudaGetLastError();
 }
 

@@ -63,12 +63,17 @@ def _oracle_parts(prob, order):
     return parts
 
 
+@pytest.mark.parametrize("precision", ["fp64", "df32"])
 @pytest.mark.parametrize("order", [4, 6])
 @pytest.mark.parametrize("name,prob", CASES, ids=[c[0] for c in CASES])
-def test_components_match_oracle(idp, name, prob, order):
+def test_components_match_oracle(idp, name, prob, order, precision):
+    # fp64: FP64 transforms; df32: double-float transforms on the FP32 pipe,
+    # held to the same 1e-12 target
     rho = prob.rho()
     ref = _oracle_parts(prob, order)
     plan = idp.create_plan(prob.d, prob.n, prob.h, order)
+    if precision == "df32":
+        idp.plan_set(plan, idp.IDP_KEY_PRECISION, idp.IDP_PRECISION_DF32)
     r = to_dev(rho)
     nshape = prob.n
     ishape = tuple(k - 2 for k in prob.n)
@@ -118,12 +123,15 @@ def test_single_sine_transform_pass_against_library_dst(idp):
     assert rel_max(ps, -rho / lam) < TOL
 
 
-def test_129_cube_sampled_against_direct_sum_and_full_oracle(idp):
+@pytest.mark.parametrize("precision", ["fp64", "df32"])
+def test_129_cube_sampled_against_direct_sum_and_full_oracle(idp, precision):
     # the bench workload (129^3 bump, order 6): g at sampled boundary nodes
     # against the direct trapezoid sum, and phi against the oracle everywhere
     prob = w.c2_3d(129)
     rho = prob.rho()
     plan = idp.create_plan(3, prob.n, prob.h, 6)
+    if precision == "df32":
+        idp.plan_set(plan, idp.IDP_KEY_PRECISION, idp.IDP_PRECISION_DF32)
     r = to_dev(rho)
     g = run_stage(idp, plan, idp.IDP_STAGE_BOUNDARY, r, prob.n)
     idx = ogreens.boundary_indices(prob.n)
