@@ -226,3 +226,45 @@ def test_alias_and_bad_arguments_are_rejected(idp):
     with pytest.raises(idp.IdpError) as e:
         idp.solve_stage(plan, 99, r, to_dev(np.zeros(prob.n)))
     assert e.value.code == idp.IDP_EINVAL
+
+
+def test_513_cube_large_grid(idp):
+    # the largest supported grid (513^3, M = 512: 256-point sine FFTs and
+    # 1024-point face FFTs): a sine mode through all three precision modes
+    # (closed form), the boundary sum at sampled nodes (direct sum), and phi
+    # of a bump against its exact potential (discretisation error ~1e-13 here)
+    import torch
+    n = (513, 513, 513)
+    prob = w.scaled_bump(n, p=10)
+    plan = idp.create_plan(3, n, prob.h, 6)
+    x = [torch.linspace(-1, 1, 513, dtype=torch.float64, device=device())] * 3
+    # low modes: the inverse Laplacian amplifies rounding in low modes by
+    # lambda_mode / lambda_min, so a high mode would test conditioning, not the code
+    rho = (torch.sin(3 * np.pi * (x[0][:, None, None] + 1) / 2) * torch.sin(5 * np.pi * (x[1][None, :, None] + 1) / 2)
+           * torch.sin(7 * np.pi * (x[2][None, None, :] + 1) / 2))
+    lam = (np.pi / 2) ** 2 * (9 + 25 + 49)
+    out = torch.empty_like(rho)
+    for prec, tol in ((idp.IDP_PRECISION_FP64, TOL), (idp.IDP_PRECISION_DF32, TOL),
+                      (idp.IDP_PRECISION_MIXED_BF16X3, 1e-5)):
+        idp.plan_set(plan, idp.IDP_KEY_PRECISION, prec)
+        idp.solve_stage(plan, idp.IDP_STAGE_PHISTAR, rho, out)
+        idp.plan_status(plan)
+        err = ((out + rho / lam).abs().max() / (rho / lam).abs().max()).item()
+        assert err < tol, (prec, err)
+    del rho
+    idp.plan_set(plan, idp.IDP_KEY_PRECISION, idp.IDP_PRECISION_FP64)
+    rho_h = prob.rho()
+    r = to_dev(rho_h)
+    idp.solve_stage(plan, idp.IDP_STAGE_BOUNDARY, r, out)
+    idp.plan_status(plan)
+    idx = ogreens.boundary_indices(n)
+    pick = idx[np.random.default_rng(9).choice(len(idx), 48, replace=False)]
+    g = out.cpu().numpy()[tuple(pick.T)]
+    assert rel_max(g, ogreens.boundary_direct(rho_h, prob.h, pick)) < TOL
+    idp.solve(plan, r, out)
+    idp.plan_status(plan)
+    from oracle import closed_form
+    # exact potential on every 4th node (129^3 points of the 513^3 grid)
+    sub = w.scaled_bump((129, 129, 129), p=10)
+    exact = closed_form.bump_potential_on_grid(sub)
+    assert rel_max(out[::4, ::4, ::4].cpu().numpy(), exact) < 1e-11
