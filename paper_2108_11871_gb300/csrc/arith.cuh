@@ -32,6 +32,19 @@ struct Ar<double> {
     static __device__ __forceinline__ double im(double2 c) { return c.y; }
     static __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
     static __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+    // 3-point DFT: y0 = a0 + t, y1,2 = a0 - t/2 -+ i s3 (a1 - a2) (forward; +- for inverse),
+    // t = a1 + a2, s3 = sqrt(3)/2
+    static __device__ __forceinline__ void radix3(double2 a0, double2 a1, double2 a2, bool inv, double2 &y0,
+                                                  double2 &y1, double2 &y2)
+    {
+        const double s3 = inv ? -0.86602540378443864676 : 0.86602540378443864676;
+        const double tr = a1.x + a2.x, ti = a1.y + a2.y;
+        const double dr = a1.x - a2.x, di = a1.y - a2.y;
+        y0 = make_double2(a0.x + tr, a0.y + ti);
+        const double mr = ::fma(-0.5, tr, a0.x), mi = ::fma(-0.5, ti, a0.y);
+        y1 = make_double2(::fma(s3, di, mr), ::fma(-s3, dr, mi));
+        y2 = make_double2(::fma(-s3, di, mr), ::fma(s3, dr, mi));
+    }
     // A = a + w c, B = a - w c with w in ratio form
     static __device__ __forceinline__ void bfly(double2 a, double2 c, const Tw &w, double2 &A, double2 &B)
     {
@@ -75,6 +88,22 @@ struct Ar<ddr> {
     static __device__ __forceinline__ ddr im(ddc c) { return c.im; }
     static __device__ __forceinline__ ddc cadd(ddc a, ddc b) { return ddc_add(a, b); }
     static __device__ __forceinline__ ddc csub(ddc a, ddc b) { return ddc_sub(a, b); }
+    static __device__ __forceinline__ void radix3(ddc a0, ddc a1, ddc a2, bool inv, ddc &y0, ddc &y1, ddc &y2)
+    {
+        // sqrt(3)/2 as a double-float pair
+        const ddr s3 = inv ? dd_make(-0.866025388240814208984375f, -1.5543625e-08f)
+                           : dd_make(0.866025388240814208984375f, 1.5543625e-08f);
+        const ddr tr = dd_add(a1.re, a2.re), ti = dd_add(a1.im, a2.im);
+        const ddr dr = dd_sub(a1.re, a2.re), di = dd_sub(a1.im, a2.im);
+        y0.re = dd_add(a0.re, tr);
+        y0.im = dd_add(a0.im, ti);
+        const ddr mr = dd_sub(a0.re, dd_scale2(tr, 0.5f)), mi = dd_sub(a0.im, dd_scale2(ti, 0.5f));
+        const ddr pr = dd_mul_raw(s3, di), pi = dd_mul_raw(s3, dr);
+        y1.re = dd_add_raw(mr, pr);
+        y1.im = dd_sub_raw(mi, pi);
+        y2.re = dd_sub_raw(mr, pr);
+        y2.im = dd_add_raw(mi, pi);
+    }
     static __device__ __forceinline__ void bfly(ddc a, ddc c, const TwD &w, ddc &A, ddc &B)
     {
         const ddr P = w.swap ? c.im : c.re;

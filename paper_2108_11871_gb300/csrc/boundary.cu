@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(NT) face_c2r_kernel(const FaceC2R a)
         const int row = r0 + l;
         if (a.skip_row_edges && (row == 0 || row == a.nrows - 1)) continue;
         if (a.skip_col_edges && (t == 0 || t == L)) continue;
-        const Cx z = Z[l * L + ((t >> 1) & (L - 1))];
+        const Cx z = Z[l * L + (t >> 1)];   // t <= L, so t/2 < L
         const R v = (t & 1) ? A::im(z) : A::re(z);
         const int64_t node = fbase + (int64_t)row * a.row_stride + (int64_t)t * a.col_stride;
         st_real<R>(a.dst0, node, v);
@@ -401,10 +401,15 @@ cudaError_t attrs_len()
     switch (LEN) {                             \
     case 16: { constexpr int L = 16; __VA_ARGS__; }   \
     case 32: { constexpr int L = 32; __VA_ARGS__; }   \
+    case 48: { constexpr int L = 48; __VA_ARGS__; }   \
     case 64: { constexpr int L = 64; __VA_ARGS__; }   \
+    case 96: { constexpr int L = 96; __VA_ARGS__; }   \
     case 128: { constexpr int L = 128; __VA_ARGS__; } \
+    case 192: { constexpr int L = 192; __VA_ARGS__; } \
     case 256: { constexpr int L = 256; __VA_ARGS__; } \
+    case 384: { constexpr int L = 384; __VA_ARGS__; } \
     case 512: { constexpr int L = 512; __VA_ARGS__; } \
+    case 768: { constexpr int L = 768; __VA_ARGS__; } \
     case 1024: { constexpr int L = 1024; __VA_ARGS__; } \
     default: return cudaErrorInvalidValue;     \
     }
@@ -416,10 +421,15 @@ cudaError_t boundary_set_attributes()
     cudaError_t e;
     if ((e = attrs_len<16>())) return e;
     if ((e = attrs_len<32>())) return e;
+    if ((e = attrs_len<48>())) return e;
     if ((e = attrs_len<64>())) return e;
+    if ((e = attrs_len<96>())) return e;
     if ((e = attrs_len<128>())) return e;
+    if ((e = attrs_len<192>())) return e;
     if ((e = attrs_len<256>())) return e;
+    if ((e = attrs_len<384>())) return e;
     if ((e = attrs_len<512>())) return e;
+    if ((e = attrs_len<768>())) return e;
     return attrs_len<1024>();
 }
 

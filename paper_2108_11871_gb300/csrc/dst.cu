@@ -23,7 +23,9 @@ struct DstCfg {
     static constexpr int N = M - 1;
     // lines per block: 2 buffers x LB x M reals (32 KB for M >= 128), at
     // least 8 lines so that the scan groups fit a warp
-    static constexpr int LB0 = (2048 / M) > 32 ? 32 : (2048 / M);
+    static constexpr int LBr = (2048 / M) > 32 ? 32 : (2048 / M);
+    // a power of two (so that LB * G = 256)
+    static constexpr int LB0 = LBr >= 32 ? 32 : LBr >= 16 ? 16 : LBr >= 8 ? 8 : 4;
     static constexpr int LB = LB0 < 8 ? 8 : LB0;
     static constexpr int G = NT / LB;             // threads per line in the scan
     static constexpr int C = (K / G) > 0 ? K / G : 1;  // scan elements per thread
@@ -246,9 +248,13 @@ cudaError_t attrs()
     cudaError_t e;
     if ((e = attr_k<R, 8>()) != cudaSuccess) return e;
     if ((e = attr_k<R, 16>()) != cudaSuccess) return e;
+    if ((e = attr_k<R, 24>()) != cudaSuccess) return e;
     if ((e = attr_k<R, 32>()) != cudaSuccess) return e;
+    if ((e = attr_k<R, 48>()) != cudaSuccess) return e;
     if ((e = attr_k<R, 64>()) != cudaSuccess) return e;
+    if ((e = attr_k<R, 96>()) != cudaSuccess) return e;
     if ((e = attr_k<R, 128>()) != cudaSuccess) return e;
+    if ((e = attr_k<R, 192>()) != cudaSuccess) return e;
     return attr_k<R, 256>();
 }
 
@@ -258,9 +264,13 @@ cudaError_t launch_r(const DstPass &a, cudaStream_t st)
     switch (a.M) {
     case 16: return launch_k<R, 8>(a, st);
     case 32: return launch_k<R, 16>(a, st);
+    case 48: return launch_k<R, 24>(a, st);
     case 64: return launch_k<R, 32>(a, st);
+    case 96: return launch_k<R, 48>(a, st);
     case 128: return launch_k<R, 64>(a, st);
+    case 192: return launch_k<R, 96>(a, st);
     case 256: return launch_k<R, 128>(a, st);
+    case 384: return launch_k<R, 192>(a, st);
     case 512: return launch_k<R, 256>(a, st);
     default: return cudaErrorInvalidValue;
     }

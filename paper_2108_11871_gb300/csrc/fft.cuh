@@ -1,5 +1,6 @@
-// CTA-cooperative complex FFT in shared memory (radix-2 Stockham, natural
-// order in and out), for FP64 (double2) or double-float (ddc) elements.
+// CTA-cooperative complex FFT in shared memory (Stockham, natural order in and
+// out; one radix-3 stage first when the length is 3 * 2^m, radix-2 stages
+// otherwise), for FP64 (double2) or double-float (ddc) elements.
 // FP64 arithmetic is the scarce resource on GB300 (about 1/60 of the FP32
 // rate), so the FP64 butterfly uses the ratio ("tangent") form of the
 // twiddle: 6 FP64 instructions per butterfly instead of 8, and the first two
@@ -24,15 +25,34 @@ __device__ __forceinline__ typename Ar<R>::C *cta_fft_t(typename Ar<R>::C *X, ty
 {
     using C = typename Ar<R>::C;
     constexpr int H = L / 2;
+    constexpr bool P2 = (L & (L - 1)) == 0;
+    int first = 1;
+    if (!P2) {
+        // radix-3 stage (lengths 3 * 2^m): y[3j + r] = sum_q x[j + q L/3] w3^{qr}
+        constexpr int T = L / 3;
+        for (int b = threadIdx.x; b < LB * T; b += NT) {
+            const int line = b / T;
+            const int j = b - line * T;
+            const C *x = X + line * L;
+            C *y = Y + line * L;
+            Ar<R>::radix3(x[j], x[j + T], x[j + 2 * T], INV, y[3 * j], y[3 * j + 1], y[3 * j + 2]);
+        }
+        __syncthreads();
+        C *t = X;
+        X = Y;
+        Y = t;
+        first = 3;
+        zero_half = false;
+    }
 #pragma unroll 1
-    for (int Ns = 1; Ns < L; Ns <<= 1) {
+    for (int Ns = first; Ns < L; Ns <<= 1) {
 #pragma unroll
         for (int b = threadIdx.x; b < LB * H; b += NT) {
             const int line = b / H;
             const int j = b - line * H;
             const C *x = X + line * L;
             C *y = Y + line * L;
-            const int k = j & (Ns - 1);
+            const int k = P2 ? (j & (Ns - 1)) : (j % Ns);
             const int o = ((j - k) << 1) + k;
             const C a = x[j];
             C A, B;

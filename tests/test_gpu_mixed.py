@@ -6,8 +6,9 @@ split into three BF16 pieces, the six products with piece indices i + j <= 2,
 FP32 accumulation.  The transform producing u1 stays FP64 because R is a
 sixth difference of u1 (section 5) and would amplify its rounding.  The dropped products are below 2^-24 relative; the FP32
 accumulation of n terms gives a relative error of order sqrt(n) 2^-24 per
-pass.  Stated accuracy (checked here): max-norm error relative to max|phi|
-below 1e-5 for the full solve, and below 1e-5 for phi*.
+pass.  Stated accuracy (checked here and at 513^3 in test_gpu_parity.py):
+max-norm error relative to max|phi| below 1e-6 * sqrt(n_max) for phi* and the
+full solve, n_max the longest line (1.1e-5 for the 129^3 grid).
 """
 import numpy as np
 import pytest
@@ -17,7 +18,7 @@ from oracle import dst as odst, solve as osolve
 from tests.gpu_util import device, rel_max, run_stage, to_dev
 
 pytestmark = pytest.mark.gpu
-MIXED_TOL = 1e-5
+MIXED_TOL = 1e-6 * np.sqrt(127)
 
 
 @pytest.fixture(scope="module")

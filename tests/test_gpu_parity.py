@@ -33,6 +33,11 @@ CASES = [
     ("3d_33", w.c2_3d(33)),
     ("3d_65x33x129", w.Problem("c", (65, 33, 129), (0.0, 0.0, 0.0), (1.0, 1.0, 2.0), "gauss",
                                dict(seed=2108))),
+    # panel counts 3 * 2^a (radix-3 FFT stage): 48, 96, 32 and 96, 48
+    ("3d_49x97x33", w.Problem("d", (49, 97, 33), (0.0, 0.0, 0.0), (1.0, 1.5, 0.8), "gauss",
+                              dict(seed=7))),
+    ("2d_97x49", w.Problem("e", (97, 49), (-1.0, -0.7), (1.0, 0.8), "bump",
+                           dict(centre=(0.05, 0.0), eps=0.6, p=8))),
 ]
 
 
@@ -216,6 +221,21 @@ def test_batched_graph_uneven_sizes_cache_and_recapture(idp):
     assert np.array_equal(outs[2].cpu().numpy(), singles[2])
 
 
+def test_batched_sizes_of_the_batched_workload(idp):
+    # the first problems of the 96-problem batched workload (per-axis nodes from
+    # {33, 65, 97, 129, 193, 257}), solved in one graph launch, against the oracle
+    probs = [p for p in w.c5_batch() if max(p.n) <= 129][:4]
+    plans = [idp.create_plan(3, p.n, p.h, 6) for p in probs]
+    rhos = [to_dev(p.rho()) for p in probs]
+    outs = [to_dev(np.zeros(p.n)) for p in probs]
+    idp.solve_batched(plans, rhos, outs)
+    for pl in plans:
+        idp.plan_status(pl)
+    for p, o in zip(probs, outs):
+        ref = osolve.solve(p.rho(), p.h, 6, boundary="convolution")
+        assert rel_max(o.cpu().numpy(), ref) < TOL, p.n
+
+
 def test_alias_and_bad_arguments_are_rejected(idp):
     prob = w.c2_3d(33)
     plan = idp.create_plan(3, prob.n, prob.h, 6)
@@ -244,8 +264,10 @@ def test_513_cube_large_grid(idp):
            * torch.sin(7 * np.pi * (x[2][None, None, :] + 1) / 2))
     lam = (np.pi / 2) ** 2 * (9 + 25 + 49)
     out = torch.empty_like(rho)
+    # mixed precision: FP32 accumulation of n = 511 terms per pass, stated
+    # accuracy 1e-6 * sqrt(n_max) (see test_gpu_mixed.py)
     for prec, tol in ((idp.IDP_PRECISION_FP64, TOL), (idp.IDP_PRECISION_DF32, TOL),
-                      (idp.IDP_PRECISION_MIXED_BF16X3, 1e-5)):
+                      (idp.IDP_PRECISION_MIXED_BF16X3, 1e-6 * np.sqrt(511))):
         idp.plan_set(plan, idp.IDP_KEY_PRECISION, prec)
         idp.solve_stage(plan, idp.IDP_STAGE_PHISTAR, rho, out)
         idp.plan_status(plan)
