@@ -59,7 +59,11 @@ enum {
 /* keys for idp_plan_set */
 enum {
     IDP_KEY_USE_GRAPH = 1,  /* 1 (default): replay solves from a CUDA graph; 0: plain launches */
-    IDP_KEY_PRECISION = 2   /* IDP_PRECISION_*: arithmetic of the four full-volume sine transforms */
+    IDP_KEY_PRECISION = 2,  /* IDP_PRECISION_*: arithmetic of the four full-volume sine transforms */
+    IDP_KEY_STALL_TEST = 3  /* test hook for failure handling (mixed precision only): the next
+                               tensor-core pass issues no products, so its bounded wait expires
+                               (after ~5 ms); the kernel records the failure, frees its tensor
+                               memory and returns, and idp_plan_status reports IDP_ETIMEOUT */
 };
 
 /* values of IDP_KEY_PRECISION */
@@ -127,7 +131,8 @@ int idp_solve_stage(idp_plan plan, int stage, const double *rho, double *out, vo
 
 /* Device-side status of the plan's last queued work: IDP_OK, IDP_ECUDA if a
  * launch or asynchronous error was recorded, or IDP_ETIMEOUT if a bounded
- * device-side wait gave up.  Synchronises the plan's last stream. */
+ * device-side wait gave up (reported once; the outputs of that solve are
+ * invalid, the plan stays usable).  Synchronises the plan's last stream. */
 int idp_plan_status(idp_plan plan);
 
 /* kernel families reported by idp_profile_solve */

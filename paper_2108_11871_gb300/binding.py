@@ -16,6 +16,7 @@ IDP_OK, IDP_EINVAL, IDP_ENOMEM, IDP_ECUDA, IDP_EALIAS, IDP_ESUPPORT, IDP_ESCRATC
 IDP_RHS6_NOALLOC_MAX_NODES = 524288
 IDP_KEY_USE_GRAPH = 1
 IDP_KEY_PRECISION = 2
+IDP_KEY_STALL_TEST = 3
 IDP_PRECISION_FP64, IDP_PRECISION_MIXED_BF16X3, IDP_PRECISION_DF32 = 0, 1, 2
 IDP_ETIMEOUT = -7
 (IDP_STAGE_BOUNDARY, IDP_STAGE_GTILDE, IDP_STAGE_PHISTAR, IDP_STAGE_U1, IDP_STAGE_R,

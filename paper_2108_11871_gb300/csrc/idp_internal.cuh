@@ -79,6 +79,7 @@ struct MpPass {
     const double *tab; int64_t ts_m, ts_p, ts_q;
     const double *add; int64_t as_m, as_p, as_q;
     int *err;                   // set to 1 if a wait on the tensor cores timed out
+    int stall_test;             // test hook: issue no products, so the bounded wait expires
 };
 cudaError_t launch_mp_pass(const MpPass &a, cudaStream_t st);
 cudaError_t mp_set_attributes();

@@ -78,10 +78,10 @@ __device__ __forceinline__ void split3(float hi, float lo, unsigned short &a, un
     c = __bfloat16_as_ushort(bc);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit)
 {
     const long long t0 = clock64();
-    while (clock64() - t0 < WAIT_CYCLES) {
+    while (clock64() - t0 < limit) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(NTHR) mp_pass_kernel(const MpPass a)
         }
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
-        if (t == 0) {
+        if (t == 0 && !a.stall_test) {
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             // products (i, j) with i + j <= 2
             const int pa[6] = {0, 0, 1, 0, 1, 2};
@@ -198,7 +198,8 @@ __global__ void __launch_bounds__(NTHR) mp_pass_kernel(const MpPass a)
                          : "memory");
         }
         // every thread waits for the products (they read the shared memory we refill next)
-        if (!mbar_wait(bar, (uint32_t)(kb & 1))) s_fail = 1;
+        // (stall_test: no products were issued, so this wait runs out on purpose)
+        if (!mbar_wait(bar, (uint32_t)(kb & 1), a.stall_test ? WAIT_CYCLES / 400 : WAIT_CYCLES)) s_fail = 1;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         __syncthreads();
         if (s_fail) break;

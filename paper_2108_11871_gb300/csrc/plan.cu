@@ -150,6 +150,7 @@ struct idp_plan_s {
 
     // mixed precision (IDP_KEY_PRECISION = 1): sine passes on the tensor cores
     int mixed = 0;
+    int stall_test = 0;               // IDP_KEY_STALL_TEST: next tensor-core pass waits in vain
     std::map<int, void *> mp_img;     // by M: BF16 pieces of the sine matrix
     float *t32[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [stream][ping/pong]
     int *d_err = nullptr;
@@ -384,6 +385,10 @@ int transform_mixed(idp_plan p, View3 in, View3 out, const double *tab, View3 ad
     ps.push_back(a);
     // pass i transforms axis 2, 1, 0 (3-D) / 2, 1 (2-D) of the original array
     const int axes3[3] = {2, 1, 0}, axes2[2] = {2, 1};
+    if (p->stall_test) {
+        ps[0].stall_test = 1;
+        p->stall_test = 0;
+    }
     for (size_t i = 0; i < ps.size(); ++i) {
         const int ax = p->d == 3 ? axes3[i] : axes2[i];
         int rc = get_mp_image(p, p->M[ax], &ps[i].bimg);
@@ -861,7 +866,7 @@ int run_solve(idp_plan p, const double *rho, double *phi, cudaStream_t st)
 {
     p->last = st;
     p->last_valid = 1;
-    if (!p->use_graph) {
+    if (!p->use_graph || p->stall_test) {   // a stall test is never baked into a graph
         p->launches = 0;
         return enqueue(p, rho, phi, 0, st);
     }
@@ -945,6 +950,16 @@ int idp_plan_set(idp_plan p, int key, int64_t value)
     if (!p) return IDP_EINVAL;
     if (key == IDP_KEY_USE_GRAPH) {
         p->use_graph = value ? 1 : 0;
+        return IDP_OK;
+    }
+    if (key == IDP_KEY_STALL_TEST) {
+        if (p->mixed != IDP_PRECISION_MIXED_BF16X3) return IDP_EINVAL;
+        p->stall_test = value ? 1 : 0;
+        ++p->version;
+        if (p->gexec) {
+            cudaGraphExecDestroy(p->gexec);
+            p->gexec = nullptr;
+        }
         return IDP_OK;
     }
     if (key == IDP_KEY_PRECISION) {
@@ -1107,7 +1122,10 @@ int idp_plan_status(idp_plan p)
     if (p->d_err) {
         int e = 0;
         IDP_CK(cudaMemcpy(&e, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-        if (e) return IDP_ETIMEOUT;
+        if (e) {
+            IDP_CK(cudaMemset(p->d_err, 0, sizeof(int)));   // reported once
+            return IDP_ETIMEOUT;
+        }
     }
     return IDP_OK;
 }

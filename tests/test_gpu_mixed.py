@@ -88,3 +88,23 @@ def test_switching_precision_back_to_fp64_restores_fp64_results(idp):
     a, b, c = a.cpu().numpy(), b.cpu().numpy(), c.cpu().numpy()
     assert np.array_equal(a, c)
     assert 0 < rel_max(b, a) < MIXED_TOL
+
+
+def test_bounded_wait_expires_into_a_status_not_a_hang(idp):
+    # failure handling without a GPU fault: the stall-test hook makes one
+    # tensor-core pass issue no products, so its mbarrier wait runs out after
+    # its bound; the kernel records it, frees its tensor memory and returns
+    prob = w.c2_3d(33)
+    rho = to_dev(prob.rho())
+    plan = _plan(idp, prob)
+    out = to_dev(np.zeros(prob.n))
+    idp.plan_set(plan, idp.IDP_KEY_STALL_TEST, 1)
+    idp.solve(plan, rho, out)
+    with pytest.raises(idp.IdpError) as e:
+        idp.plan_status(plan)
+    assert e.value.code == idp.IDP_ETIMEOUT
+    # the context and the plan remain usable
+    idp.solve(plan, rho, out)
+    idp.plan_status(plan)
+    ref = osolve.solve(prob.rho(), prob.h, 6, boundary="convolution")
+    assert rel_max(out.cpu().numpy(), ref) < MIXED_TOL
