@@ -62,6 +62,23 @@ def config_of(prob, order, extra=None):
     return c
 
 
+# ----------------------------------------------------------------------------- multi-rank helpers
+def shard(items, rank, world):
+    """Problems of rank `rank` (round robin; the batched workload needs no collective)."""
+    return items[rank::world]
+
+
+def max_over_ranks(value, world, device=None):
+    """Largest `value` over all ranks (the job time is the slowest rank's)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -203,10 +220,7 @@ def run_ours(args, rank, world):
     total_ms = sum(step_ms)
     launches = ctypes.c_int64()
     idp.library().idp_plan_launches(plan.handle, ctypes.byref(launches))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     value = world * prob.points * args.steps / (total_ms / 1e3)
 
     # per-kernel durations (plain launches, events on the launch stream)
@@ -358,7 +372,7 @@ def run_batched(args, rank, world):
     import paper_2108_11871_gb300 as idp
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     probs = w.c5_batch()
-    mine = probs[rank::world]
+    mine = shard(probs, rank, world)
     total = sum(p.points for p in mine)
     t0 = time.perf_counter()
     plans = [idp.create_plan(3, p.n, p.h, args.order) for p in mine]
@@ -386,7 +400,7 @@ def run_batched(args, rank, world):
         torch.cuda.synchronize()
         for pl in plans:
             idp.plan_status(pl)
-        t = sum(x.elapsed_time(y) for x, y in ev) / args.steps
+        t = max_over_ranks(sum(x.elapsed_time(y) for x, y in ev) / args.steps, world, dev)
         # the same problems one after another (separate graph launches)
         for i in range(2):
             flush.fill_(float(i))
