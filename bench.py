@@ -188,6 +188,7 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", local)
     prob = workload(args.n)
     plan = idp.create_plan(3, prob.n, prob.h, args.order)
+    idp.plan_set(plan, idp.IDP_KEY_AUTOTUNE, 1)
     rho_h = prob.rho()
     rho = torch.from_numpy(rho_h).to(dev)
     phi = torch.empty_like(rho)
@@ -264,6 +265,7 @@ def run_ours(args, rank, world):
     if not args.fp64_only:
         mplan = idp.create_plan(3, prob.n, prob.h, args.order)
         idp.plan_set(mplan, idp.IDP_KEY_PRECISION, idp.IDP_PRECISION_MIXED_BF16X3)
+        idp.plan_set(mplan, idp.IDP_KEY_AUTOTUNE, 1)
         phi_m = torch.empty_like(rho)
         for _ in range(args.warmup):
             idp.solve(mplan, rho, phi_m, stream)
@@ -290,6 +292,7 @@ def run_ours(args, rank, world):
             for j in range(max(n, 0)):
                 mk.setdefault(names.get(kinds[j], str(kinds[j])), []).append(ms[j])
         mixed = {"variant": "bf16x3 pieces, fp32 accumulate, tcgen05 (rho, R and final transforms)",
+                 "tuning": idp.plan_tuning(mplan),
                  "value": world * prob.points * args.steps / (t_m / 1e3), "unit": UNIT,
                  "ms_per_step": t_m / args.steps, "max_rel_error_vs_fp64": diff,
                  "kernel_ms_per_step": {k: sum(v) / 3 for k, v in mk.items()},
@@ -300,6 +303,7 @@ def run_ours(args, rank, world):
     if not args.fp64_only:
         dplan = idp.create_plan(3, prob.n, prob.h, args.order)
         idp.plan_set(dplan, idp.IDP_KEY_PRECISION, idp.IDP_PRECISION_DF32)
+        idp.plan_set(dplan, idp.IDP_KEY_AUTOTUNE, 1)
         phi_d = torch.empty_like(rho)
         for _ in range(args.warmup):
             idp.solve(dplan, rho, phi_d, stream)
@@ -358,7 +362,7 @@ def run_ours(args, rank, world):
                                       "FMA-chain probe measured %.3f" % FP64_PROBE_TFLOPS,
                          "traffic": None, "avg_launch_ms": dst_ms,
                          "flops_per_launch": dst_flops_per_launch(prob)},
-            "kernel_ms_per_step": shares, "dominant_kernel": names[dom],
+            "kernel_ms_per_step": shares, "dominant_kernel": names[dom], "tuning": idp.plan_tuning(plan),
             "clocks": clk.summary()}
     if world == 1:
         line["cpu_baseline"] = cpu_baseline(prob, args.order)
@@ -376,6 +380,8 @@ def run_batched(args, rank, world):
     total = sum(p.points for p in mine)
     t0 = time.perf_counter()
     plans = [idp.create_plan(3, p.n, p.h, args.order) for p in mine]
+    for pl in plans:
+        idp.plan_set(pl, idp.IDP_KEY_AUTOTUNE, 1)
     setup_s = time.perf_counter() - t0
     rhos = [torch.from_numpy(p.rho()).to(dev) for p in mine]
     phis = [torch.empty_like(r) for r in rhos]
@@ -386,6 +392,8 @@ def run_batched(args, rank, world):
                         ("mixed_bf16x3", idp.IDP_PRECISION_MIXED_BF16X3)):
         for pl in plans:
             idp.plan_set(pl, idp.IDP_KEY_PRECISION, prec)
+            if prec == idp.IDP_PRECISION_MIXED_BF16X3:
+                idp.plan_set(pl, idp.IDP_KEY_AUTOTUNE, 1)
         for _ in range(args.warmup):
             idp.solve_batched(plans, rhos, phis, stream)
         torch.cuda.synchronize()

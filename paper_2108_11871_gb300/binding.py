@@ -17,6 +17,7 @@ IDP_RHS6_NOALLOC_MAX_NODES = 524288
 IDP_KEY_USE_GRAPH = 1
 IDP_KEY_PRECISION = 2
 IDP_KEY_STALL_TEST = 3
+IDP_KEY_AUTOTUNE = 4
 IDP_PRECISION_FP64, IDP_PRECISION_MIXED_BF16X3, IDP_PRECISION_DF32 = 0, 1, 2
 IDP_ETIMEOUT = -7
 (IDP_STAGE_BOUNDARY, IDP_STAGE_GTILDE, IDP_STAGE_PHISTAR, IDP_STAGE_U1, IDP_STAGE_R,
@@ -60,6 +61,9 @@ def library(path: str = None):
         "idp_destroy_plan": (_int, [_vp]),
         "idp_strerror": (ctypes.c_char_p, [_int]),
         "idp_last_cuda_error": (ctypes.c_char_p, []),
+        "idp_plan_tuning": (_int, [_vp, ctypes.POINTER(_i64)]),
+        "idp_profile_solve": (_int, [_vp, _vp, _vp, _vp, _int, ctypes.POINTER(_int), ctypes.POINTER(ctypes.c_float)]),
+        "idp_plan_launches": (_int, [_vp, ctypes.POINTER(_i64)]),
         "idp_rhs6_noalloc": (_int, [_int, ctypes.POINTER(_i64), ctypes.POINTER(_dbl), _vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
@@ -167,6 +171,13 @@ def plan_info(plan: Plan):
     _check(library().idp_plan_info(plan.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
            "idp_plan_info")
     return dict(nodes=a.value, interior=b.value, workspace_bytes=c.value)
+
+
+def plan_tuning(plan: Plan):
+    out = (_i64 * 8)()
+    _check(library().idp_plan_tuning(plan.handle, out), "idp_plan_tuning")
+    return dict(tuned=bool(out[0]), mixed_path=("df32_fft" if out[1] else "tensor_matrix"),
+                face_chunks=list(out[2:5]), slices_per_chunk=list(out[5:8]))
 
 
 def destroy_plan(plan: Plan):

@@ -151,6 +151,9 @@ struct idp_plan_s {
     // mixed precision (IDP_KEY_PRECISION = 1): sine passes on the tensor cores
     int mixed = 0;
     int stall_test = 0;               // IDP_KEY_STALL_TEST: next tensor-core pass waits in vain
+    int mixed_path = 0;               // mixed precision: 0 = tensor-core matrix pass, 1 = df32 FFT pass
+    int64_t part_cap = 0;             // capacity (complex) of the partial face sums
+    int tuned = 0;
     std::map<int, void *> mp_img;     // by M: BF16 pieces of the sine matrix
     float *t32[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [stream][ping/pong]
     int *d_err = nullptr;
@@ -405,9 +408,12 @@ int transform_mixed(idp_plan p, View3 in, View3 out, const double *tab, View3 ad
 int transform(idp_plan p, View3 in, double *work, View3 out, const double *tab, View3 add, bool forward,
               cudaStream_t st, bool allow_reduced = true)
 {
-    if (p->mixed == IDP_PRECISION_MIXED_BF16X3 && allow_reduced)
+    if (p->mixed == IDP_PRECISION_MIXED_BF16X3 && allow_reduced && p->mixed_path == 0)
         return transform_mixed(p, in, out, tab, add, st == p->side ? 1 : 0, st);
-    const bool dd = (p->mixed == IDP_PRECISION_DF32) && allow_reduced;
+    // df32 passes: precision DF32, or precision MIXED when the autotuner found the
+    // double-float FFT faster than the matrix pass (it is also more accurate)
+    const bool dd = (p->mixed == IDP_PRECISION_DF32 ||
+                     (p->mixed == IDP_PRECISION_MIXED_BF16X3 && p->mixed_path == 1)) && allow_reduced;
     int axes[3], na = 0;
     if (forward) {
         for (int s = 2; s >= 0; --s)
@@ -851,9 +857,92 @@ int plan_setup(idp_plan p)
             }
         }
         if ((rc = p->alloc(&p->part, pmax)) || (rc = p->alloc(&p->F, fmax))) return rc;
+        p->part_cap = pmax;
     }
     IDP_CK(cudaDeviceSynchronize());
     return IDP_OK;
+}
+
+// Times candidate settings on the plan's own buffers and keeps the fastest:
+// the slice chunking of each 3-D face pass, and (precision MIXED) the
+// tensor-core matrix pass versus the df32 FFT pass for the reduced-precision
+// transforms.  Results depend only on timing, not on the data.
+int autotune(idp_plan p)
+{
+    cudaStream_t st = p->cap;
+    cudaEvent_t e0, e1;
+    IDP_CK(cudaEventCreate(&e0));
+    IDP_CK(cudaEventCreate(&e1));
+    int rc = IDP_OK;
+    auto timed = [&](auto &&fn) -> float {
+        float best = 1e30f;
+        for (int r = 0; r < 4 && !rc; ++r) {
+            cudaEventRecord(e0, st);
+            rc = fn();
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r > 0 && ms < best) best = ms;   // first run warms up
+        }
+        return best;
+    };
+    if (p->d == 3) {
+        for (int a_ = 0; a_ < 3 && !rc; ++a_) {
+            const int b = a_ == 0 ? 1 : 0, c = a_ == 2 ? 1 : 2;
+            const int np = p->ni[a_], L = 2 * p->M[b], nc = p->M[c] + 1;
+            const int n0 = p->nchunk[a_];
+            int cands[4] = {std::max(1, n0 / 2), n0, std::min(np, 2 * n0), std::min(np, 4 * n0)};
+            int best_n = n0, best_p = p->pchunk[a_];
+            float best_t = 1e30f;
+            for (int ci = 0; ci < 4 && !rc; ++ci) {
+                const int pch = (np + cands[ci] - 1) / cands[ci];
+                const int nch = (np + pch - 1) / pch;
+                if ((int64_t)nch * 2 * L * nc > p->part_cap) {
+                    double2 *np_part;
+                    if ((rc = p->alloc(&np_part, (int64_t)nch * 2 * L * nc))) break;
+                    p->part = np_part;
+                    p->part_cap = (int64_t)nch * 2 * L * nc;
+                }
+                FacePass f{};
+                if (a_ == 0) { f.D = p->T0; f.sp = (int64_t)p->ni[1] * (p->M[2] + 1); f.sb = p->M[2] + 1; f.sc = 1; }
+                else if (a_ == 1) { f.D = p->T0; f.sp = p->M[2] + 1; f.sb = (int64_t)p->ni[1] * (p->M[2] + 1); f.sc = 1; }
+                else { f.D = p->T1; f.sp = p->M[1] + 1; f.sb = (int64_t)p->ni[2] * (p->M[1] + 1); f.sc = 1; }
+                f.np = np; f.Mb = p->M[b]; f.nc = nc; f.khat = p->khat[a_]; f.part = p->part; f.pchunk = pch;
+                FftTables t;
+                if ((rc = get_fft(p, L, &t))) break;
+                f.t = t;
+                const float ms = timed([&]() -> int {
+                    cudaError_t e = launch_face_pass(f, nch, st);
+                    return e == cudaSuccess ? IDP_OK : cuda_fail(e, "face pass (autotune)");
+                });
+                if (ms < best_t) { best_t = ms; best_n = nch; best_p = pch; }
+            }
+            p->nchunk[a_] = best_n;
+            p->pchunk[a_] = best_p;
+        }
+    }
+    if (!rc && p->mixed == IDP_PRECISION_MIXED_BF16X3) {
+        const View3 none{nullptr, 0, 0, 0};
+        float tm[2];
+        for (int path = 0; path < 2 && !rc; ++path) {
+            p->mixed_path = path;
+            tm[path] = timed([&]() -> int {
+                return transform(p, dense(p, p->C), p->C, dense(p, p->C), nullptr, none, false, st);
+            });
+        }
+        p->mixed_path = (tm[1] < tm[0]) ? 1 : 0;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    IDP_CK(cudaStreamSynchronize(st));
+    p->tuned = 1;
+    ++p->version;
+    if (p->gexec) {
+        cudaGraphExecDestroy(p->gexec);
+        p->gexec = nullptr;
+    }
+    return rc;
 }
 
 bool overlap(const void *a, size_t na, const void *b, size_t nb)
@@ -952,6 +1041,10 @@ int idp_plan_set(idp_plan p, int key, int64_t value)
         p->use_graph = value ? 1 : 0;
         return IDP_OK;
     }
+    if (key == IDP_KEY_AUTOTUNE) {
+        if (!value) return IDP_OK;
+        return autotune(p);
+    }
     if (key == IDP_KEY_STALL_TEST) {
         if (p->mixed != IDP_PRECISION_MIXED_BF16X3) return IDP_EINVAL;
         p->stall_test = value ? 1 : 0;
@@ -989,6 +1082,7 @@ int idp_plan_set(idp_plan p, int key, int64_t value)
         }
         if (p->mixed != (int)value) {
             p->mixed = (int)value;
+            p->mixed_path = 0;
             ++p->version;
             if (p->gexec) {
                 cudaGraphExecDestroy(p->gexec);
@@ -1207,6 +1301,18 @@ const char *idp_strerror(int code)
 }
 
 const char *idp_last_cuda_error(void) { return g_cuda_err; }
+
+int idp_plan_tuning(idp_plan p, int64_t out[8])
+{
+    if (!p || !out) return IDP_EINVAL;
+    out[0] = p->tuned;
+    out[1] = p->mixed_path;
+    for (int a = 0; a < 3; ++a) {
+        out[2 + a] = p->nchunk[a];
+        out[5 + a] = p->pchunk[a];
+    }
+    return IDP_OK;
+}
 
 int idp_plan_launches(idp_plan p, int64_t *launches)
 {

@@ -236,6 +236,27 @@ def test_batched_sizes_of_the_batched_workload(idp):
         assert rel_max(o.cpu().numpy(), ref) < TOL, p.n
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autotuned_plan_still_matches_oracle(idp, precision):
+    prob = w.Problem("t", (65, 33, 129), (0.0, 0.0, 0.0), (1.0, 1.0, 2.0), "gauss", dict(seed=3))
+    rho = prob.rho()
+    plan = idp.create_plan(3, prob.n, prob.h, 6)
+    tol = TOL
+    if precision == "mixed":
+        idp.plan_set(plan, idp.IDP_KEY_PRECISION, idp.IDP_PRECISION_MIXED_BF16X3)
+        tol = 1e-6 * np.sqrt(127)
+    idp.plan_set(plan, idp.IDP_KEY_AUTOTUNE, 1)
+    info = idp.plan_tuning(plan)
+    assert info["tuned"]
+    for nch, pch, np_ in zip(info["face_chunks"], info["slices_per_chunk"], (63, 31, 127)):
+        assert 1 <= nch <= np_ and nch * pch >= np_ and (nch - 1) * pch < np_
+    out = to_dev(np.zeros(prob.n))
+    idp.solve(plan, to_dev(rho), out)
+    idp.plan_status(plan)
+    ref = osolve.solve(rho, prob.h, 6, boundary="convolution")
+    assert rel_max(out.cpu().numpy(), ref) < tol
+
+
 def test_alias_and_bad_arguments_are_rejected(idp):
     prob = w.c2_3d(33)
     plan = idp.create_plan(3, prob.n, prob.h, 6)
