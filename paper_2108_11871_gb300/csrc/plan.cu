@@ -141,6 +141,7 @@ struct idp_plan_s {
 
     double *A = nullptr, *B = nullptr, *C = nullptr, *U = nullptr, *W = nullptr;
     double *tabc = nullptr, *tab4 = nullptr;
+    double *tabc2 = nullptr;   // -2 * tabc (forward transform of rho continued from T0)
     double *Q0 = nullptr, *Q1 = nullptr, *Q2 = nullptr, *sin4 = nullptr;   // gtilde parts
     double2 *T0 = nullptr, *T1 = nullptr, *part = nullptr, *F = nullptr;
     double *khat[3] = {nullptr, nullptr, nullptr};
@@ -406,7 +407,7 @@ int transform_mixed(idp_plan p, View3 in, View3 out, const double *tab, View3 ad
 // last pass applies the epilogue (tab, add) and writes `out`; intermediate
 // passes run in place on `work`.
 int transform(idp_plan p, View3 in, double *work, View3 out, const double *tab, View3 add, bool forward,
-              cudaStream_t st, bool allow_reduced = true)
+              cudaStream_t st, bool allow_reduced = true, bool skip_axis2 = false, int in_dd0 = 0)
 {
     if (p->mixed == IDP_PRECISION_MIXED_BF16X3 && allow_reduced && p->mixed_path == 0)
         return transform_mixed(p, in, out, tab, add, st == p->side ? 1 : 0, st);
@@ -416,7 +417,7 @@ int transform(idp_plan p, View3 in, double *work, View3 out, const double *tab, 
                      (p->mixed == IDP_PRECISION_MIXED_BF16X3 && p->mixed_path == 1)) && allow_reduced;
     int axes[3], na = 0;
     if (forward) {
-        for (int s = 2; s >= 0; --s)
+        for (int s = skip_axis2 ? 1 : 2; s >= 0; --s)
             if (p->act[s]) axes[na++] = s;
     } else {
         for (int s = 0; s < 3; ++s)
@@ -441,7 +442,7 @@ int transform(idp_plan p, View3 in, double *work, View3 out, const double *tab, 
         if (dd) {
             // double-float arithmetic; intermediate passes keep double-float pairs
             a.dd = 1;
-            a.in_dd = (q == 0) ? 0 : 1;
+            a.in_dd = (q == 0) ? in_dd0 : 1;
             a.out_dd = (q == na - 1) ? 0 : 1;
             a.add_dd = 0;
             a.twd = t.fwdd;
@@ -510,8 +511,23 @@ int gtilde_parts(idp_plan p, bool transform_parts, cudaStream_t st)
     return IDP_OK;
 }
 
+// Forward transform of rho scaled by 1/lambda_c into A, starting from the
+// boundary stage 1a output: T0 = 2 * (real FFT of the zero-padded rows along
+// axis 2), whose imaginary part at m = 1..M2-1 is -2 times the sine sums of
+// the rows, i.e. -1/2 of the first sine pass (4 S).  The remaining passes run
+// on that data and the factor -2 is in tabc2.
+int transform_rho_from_T0(idp_plan p, cudaStream_t st)
+{
+    const View3 none{nullptr, 0, 0, 0};
+    const int64_t row = 2 * (int64_t)(p->M[2] + 1);   // doubles per T0 row
+    const View3 im{reinterpret_cast<double *>(p->T0) + 3, (int64_t)p->ni[1] * row, row, 2};
+    const int dd = (p->mixed == IDP_PRECISION_DF32 && p->d == 3) ? 1 : 0;   // T0 holds pairs
+    return transform(p, im, p->A, dense(p, p->A), p->tabc2, none, true, st, true, true, dd);
+}
+
 // boundary values g into the boundary nodes of dst0 (and dst1 if not null)
-int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStream_t st)
+int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStream_t st,
+             bool fork_rho = false)
 {
     const View3 r = node_interior(p, rho);
     int rc;
@@ -531,6 +547,13 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
         a.dd = dd;
         Mark mk(p, IDP_KERNEL_RFFT, st);
         IDP_CK(launch_rfft_pass(a, st));
+    }
+    if (fork_rho) {
+        // the rest of the forward transform of rho runs beside the boundary stages
+        IDP_CK(cudaEventRecord(p->fork, st));
+        IDP_CK(cudaStreamWaitEvent(p->side, p->fork, 0));
+        if ((rc = transform_rho_from_T0(p, p->side))) return rc;
+        IDP_CK(cudaEventRecord(p->join, p->side));
     }
     // stage 1b: along axis 1 -> T1[i0][i2][m1]
     {
@@ -642,7 +665,10 @@ int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t s
     //    queue it on the side stream so it overlaps the boundary convolutions
     // (profiling keeps one stream so that every launch is timed on its own)
     const bool overlap_rho = (stop == 0) && !p->profiling;
-    if (overlap_rho) {
+    // FP64 / df32 transforms: the first pass of the forward transform of rho is
+    // the imaginary part of the boundary's first real FFT (see transform_rho_from_T0)
+    const bool rho_from_T0 = (stop == 0) && !(p->mixed == IDP_PRECISION_MIXED_BF16X3 && p->mixed_path == 0);
+    if (overlap_rho && !rho_from_T0) {
         IDP_CK(cudaEventRecord(p->fork, st));
         IDP_CK(cudaStreamWaitEvent(p->side, p->fork, 0));
         if ((rc = transform(p, node_interior(p, rho), p->A, dense(p, p->A), p->tabc, none, true, p->side)))
@@ -650,7 +676,9 @@ int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t s
         IDP_CK(cudaEventRecord(p->join, p->side));
     }
     // 1. boundary values: phi boundary and U boundary
-    if ((rc = boundary(p, rho, stop == 0 ? phi : p->U, stop == 0 ? p->U : nullptr, st))) return rc;
+    if ((rc = boundary(p, rho, stop == 0 ? phi : p->U, stop == 0 ? p->U : nullptr, st,
+                       overlap_rho && rho_from_T0)))
+        return rc;
     // 2. gtilde on the boundary-adjacent layers, and the transforms of its parts
     if ((rc = gtilde_parts(p, stop != IDP_STAGE_GTILDE, st))) return rc;
     if (stop == IDP_STAGE_GTILDE) {
@@ -660,7 +688,11 @@ int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t s
     // 3. the forward transform of rho, scaled by 1/lambda_c (on the side stream
     //    in a full solve, joined before A is first used)
     if (stop == 0 && !overlap_rho) {
-        if ((rc = transform(p, node_interior(p, rho), p->A, dense(p, p->A), p->tabc, none, true, st))) return rc;
+        if (rho_from_T0) {
+            if ((rc = transform_rho_from_T0(p, st))) return rc;
+        } else if ((rc = transform(p, node_interior(p, rho), p->A, dense(p, p->A), p->tabc, none, true, st))) {
+            return rc;
+        }
     }
     if (p->order == 4 && stop == 0) {
         if (overlap_rho) IDP_CK(cudaStreamWaitEvent(st, p->join, 0));
@@ -723,7 +755,8 @@ int plan_setup(idp_plan p)
     // workspace
     if ((rc = p->alloc(&p->A, p->nint)) || (rc = p->alloc(&p->B, p->nint)) || (rc = p->alloc(&p->C, p->nint)) ||
         (rc = p->alloc(&p->U, p->nodes)) || (rc = p->alloc(&p->W, 3 * p->nodes)) ||
-        (rc = p->alloc(&p->tabc, p->nint)) || (rc = p->alloc(&p->tab4, p->nint)))
+        (rc = p->alloc(&p->tabc, p->nint)) || (rc = p->alloc(&p->tab4, p->nint)) ||
+        (rc = p->alloc(&p->tabc2, p->nint)))
         return rc;
     if ((rc = p->alloc(&p->T0, (int64_t)p->ni[0] * p->ni[1] * (p->M[2] + 1))) ||
         (rc = p->alloc(&p->T1, (int64_t)p->ni[0] * p->ni[2] * (p->M[1] + 1))))
@@ -776,6 +809,7 @@ int plan_setup(idp_plan p)
             if (p->act[s]) { sc *= 2.0 / p->M[s]; ++da; }
         for (int q = 0; q < 2 * da; ++q) sc *= 0.25;   // each sine pass returns 4 S x
         IDP_CK(launch_eigen_tables(p->grid, dlc, dld, off[1], off[2], sc, p->tabc, p->tab4, 0));
+        IDP_CK(launch_eigen_tables(p->grid, dlc, dld, off[1], off[2], -2.0 * sc, p->tabc2, p->B, 0));
     }
 
     // kernel spectra of the boundary convolutions (section 4)
@@ -912,8 +946,13 @@ int autotune(idp_plan p)
                 FftTables t;
                 if ((rc = get_fft(p, L, &t))) break;
                 f.t = t;
+                // the chunk count sets the work of the face pass and of the
+                // partial-sum reduction that follows it: time both
+                FaceInvB ib{};
+                ib.part = p->part; ib.nchunk = nch; ib.Mb = p->M[b]; ib.nc = nc; ib.out = p->F; ib.t = t;
                 const float ms = timed([&]() -> int {
                     cudaError_t e = launch_face_pass(f, nch, st);
+                    if (e == cudaSuccess) e = launch_face_inv_b(ib, st);
                     return e == cudaSuccess ? IDP_OK : cuda_fail(e, "face pass (autotune)");
                 });
                 if (ms < best_t) { best_t = ms; best_n = nch; best_p = pch; }
