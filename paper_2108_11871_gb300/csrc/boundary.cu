@@ -11,6 +11,8 @@
 //   stage 3  inverse FFT along b, inverse real FFT along c, scatter to nodes.
 // The kernel spectra are real and even (the cyclic kernel is even), so only
 // frequencies 0..M are stored; they are computed once per plan.
+#include <type_traits>
+
 #include "fft.cuh"
 
 namespace idp {
@@ -107,12 +109,21 @@ __global__ void __launch_bounds__(NT) rfft_kernel(const RfftPass a)
         const Cx zm = zl[m], zc = zl[L - m];
         const R Er = A::add(A::re(zm), A::re(zc)), Ei = A::sub(A::im(zm), A::im(zc));
         const R Or = A::sub(A::re(zm), A::re(zc)), Oi = A::add(A::im(zm), A::im(zc));
-        const Cx w = half_tw<R>(a.t, m);
-        const R Pr = A::mul_sub(A::re(w), Or, A::im(w), Oi);
-        const R Pi = A::mul_add(A::re(w), Oi, A::im(w), Or);
         Cx *ol = outb + (int64_t)l * osv;
-        ol[(int64_t)m * ose] = A::cmake(A::add(Er, Pi), A::sub(Ei, Pr));
-        ol[(int64_t)(M - m) * ose] = A::cmake(A::sub(Er, Pi), A::neg(A::add(Ei, Pr)));
+        if constexpr (std::is_same<R, double>::value) {
+            // P = W O in ratio form (10 FP64 ops per pair of outputs)
+            const Tw w = a.t.halfr[m];
+            const double Pp = w.swap ? Oi : Or, Qq = w.swap ? Or : Oi;
+            const double u = fma(-w.r, Qq, Pp), v = fma(w.r, Pp, Qq);
+            ol[(int64_t)m * ose] = make_double2(fma(w.mim, v, Er), fma(-w.mre, u, Ei));
+            ol[(int64_t)(M - m) * ose] = make_double2(fma(-w.mim, v, Er), -fma(w.mre, u, Ei));
+        } else {
+            const Cx w = half_tw<R>(a.t, m);
+            const R Pr = A::mul_sub(A::re(w), Or, A::im(w), Oi);
+            const R Pi = A::mul_add(A::re(w), Oi, A::im(w), Or);
+            ol[(int64_t)m * ose] = A::cmake(A::add(Er, Pi), A::sub(Ei, Pr));
+            ol[(int64_t)(M - m) * ose] = A::cmake(A::sub(Er, Pi), A::neg(A::add(Ei, Pr)));
+        }
         if (m == 1) {
             const Cx z0 = zl[0];
             ol[0] = A::cmake(A::times2(A::add(A::re(z0), A::im(z0))), A::zero());

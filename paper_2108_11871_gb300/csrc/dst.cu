@@ -9,6 +9,8 @@
 //   T_k  = (Z_k + conj Z_{K-k}) - i e^{-2 pi i k/M} (Z_k - conj Z_{K-k})
 //   U_{2k} = -Im T_k,   U_{2k+1} = U_{2k-1} + Re T_k,   U_1 = Re Z_0 + Im Z_0
 // (the real-FFT form of the DST-I; T = 4 Y where Y is the real FFT of y).
+#include <type_traits>
+
 #include "fft.cuh"
 
 namespace idp {
@@ -154,19 +156,41 @@ __global__ void __launch_bounds__(NT) dst_pass_kernel(const DstPass a)
         const Cx zk = zl[k], zc = zl[K - k];
         const R Er = A::add(A::re(zk), A::re(zc)), Ei = A::sub(A::im(zk), A::im(zc));
         const R Or = A::sub(A::re(zk), A::re(zc)), Oi = A::add(A::im(zk), A::im(zc));
-        const Cx w = Tabs<R>::half(a, k);
-        const R Pr = A::mul_sub(A::re(w), Or, A::im(w), Oi);
-        const R Pi = A::mul_add(A::re(w), Oi, A::im(w), Or);
-        ol[2 * k - 1] = A::sub(Pr, Ei);
-        ol[2 * (K - k) - 1] = A::add(Ei, Pr);
-        ol[2 * k] = A::add(Er, Pi);
-        ol[2 * (K - k)] = A::sub(Er, Pi);
+        if constexpr (std::is_same<R, double>::value) {
+            // P = W O with W in ratio form: P_re = mre u, P_im = mim v (10 FP64 ops per pair)
+            const Tw w = a.halfr[k];
+            const double Pp = w.swap ? Oi : Or, Qq = w.swap ? Or : Oi;
+            const double u = fma(-w.r, Qq, Pp), v = fma(w.r, Pp, Qq);
+            ol[2 * k - 1] = fma(w.mre, u, -Ei);
+            ol[2 * (K - k) - 1] = fma(w.mre, u, Ei);
+            ol[2 * k] = fma(w.mim, v, Er);
+            ol[2 * (K - k)] = fma(-w.mim, v, Er);
+        } else {
+            const Cx w = Tabs<R>::half(a, k);
+            const R Pr = A::mul_sub(A::re(w), Or, A::im(w), Oi);
+            const R Pi = A::mul_add(A::re(w), Oi, A::im(w), Or);
+            ol[2 * k - 1] = A::sub(Pr, Ei);
+            ol[2 * (K - k) - 1] = A::add(Ei, Pr);
+            ol[2 * k] = A::add(Er, Pi);
+            ol[2 * (K - k)] = A::sub(Er, Pi);
+        }
         if (k == 1) ol[0] = A::add(A::re(zl[0]), A::im(zl[0]));
     }
     __syncthreads();
 
     // 5. prefix sum over the odd slots o[2k], k = 0..K-1
-    {
+    if constexpr (std::is_same<R, double>::value) {
+        // one thread per line, K-1 additions: the fewest FP64 operations
+        if (threadIdx.x < LB) {
+            double *ol = o + threadIdx.x * M;
+            double run = ol[0];
+#pragma unroll 8
+            for (int k = 1; k < K; ++k) {
+                run += ol[2 * k];
+                ol[2 * k] = run;
+            }
+        }
+    } else {
         constexpr int G = Cfg::G, C = Cfg::C;
         const int l = threadIdx.x / G;
         const int g = threadIdx.x - l * G;

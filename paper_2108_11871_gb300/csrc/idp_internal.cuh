@@ -26,6 +26,7 @@ struct FftTables {
     const Tw *fwd;      // device, L/2 entries
     const Tw *inv;      // device, L/2 entries
     const double2 *half; // device, L+1 entries: (cos(pi k/L), -sin(pi k/L))
+    const Tw *halfr;     // device, L+1 entries: the same in ratio form
     const TwD *fwdd;    // double-float forms of the three tables
     const TwD *invd;
     const ddc *halfd;
@@ -50,6 +51,7 @@ struct DstPass {
     int M;
     const Tw *tw;          // twiddles for the complex FFT of length M/2
     const double2 *half;   // half-step twiddles for length M/2 (e^{-i pi k/(M/2)})
+    const Tw *halfr;       // the same in ratio form
     const double *sin2;    // 2 sin(pi j / M), j = 0..M/2
     // double-float variant (dd = 1): arithmetic on the FP32 pipe; in/out/add
     // may hold FP64 values or double-float pairs (in_dd / out_dd / add_dd)

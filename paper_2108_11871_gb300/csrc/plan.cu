@@ -65,9 +65,10 @@ Tw make_tw(double c, double s)
 struct DevFft {
     Tw *fwd = nullptr, *inv = nullptr;
     double2 *half = nullptr;
+    Tw *halfr = nullptr;
     TwD *fwdd = nullptr, *invd = nullptr;   // double-float forms
     ddc *halfd = nullptr;
-    FftTables view(int L) const { return FftTables{L, fwd, inv, half, fwdd, invd, halfd}; }
+    FftTables view(int L) const { return FftTables{L, fwd, inv, half, halfr, fwdd, invd, halfd}; }
 };
 
 // double-float pair of a double (host): hi = nearest float, lo = nearest float of the rest
@@ -236,7 +237,11 @@ int get_fft(idp_plan p, int L, FftTables *out)
         iv[j] = make_tw(c, s);
     }
     std::vector<double2> hf(L + 1);
-    for (int k = 0; k <= L; ++k) hf[k] = make_double2(cospi_frac(k, L), -sinpi_frac(k, L));
+    std::vector<Tw> hr(L + 1);
+    for (int k = 0; k <= L; ++k) {
+        hf[k] = make_double2(cospi_frac(k, L), -sinpi_frac(k, L));
+        hr[k] = make_tw(hf[k].x, hf[k].y);
+    }
     std::vector<TwD> fwd2(L / 2), ivd2(L / 2);
     std::vector<ddc> hfd(L + 1);
     for (int j = 0; j < L / 2; ++j) {
@@ -249,11 +254,13 @@ int get_fft(idp_plan p, int L, FftTables *out)
     }
     int rc;
     if ((rc = p->alloc(&t.fwd, L / 2)) || (rc = p->alloc(&t.inv, L / 2)) || (rc = p->alloc(&t.half, L + 1)) ||
+        (rc = p->alloc(&t.halfr, L + 1)) ||
         (rc = p->alloc(&t.fwdd, L / 2)) || (rc = p->alloc(&t.invd, L / 2)) || (rc = p->alloc(&t.halfd, L + 1)))
         return rc;
     IDP_CK(cudaMemcpy(t.fwd, fw.data(), sizeof(Tw) * (L / 2), cudaMemcpyHostToDevice));
     IDP_CK(cudaMemcpy(t.inv, iv.data(), sizeof(Tw) * (L / 2), cudaMemcpyHostToDevice));
     IDP_CK(cudaMemcpy(t.half, hf.data(), sizeof(double2) * (L + 1), cudaMemcpyHostToDevice));
+    IDP_CK(cudaMemcpy(t.halfr, hr.data(), sizeof(Tw) * (L + 1), cudaMemcpyHostToDevice));
     IDP_CK(cudaMemcpy(t.fwdd, fwd2.data(), sizeof(TwD) * (L / 2), cudaMemcpyHostToDevice));
     IDP_CK(cudaMemcpy(t.invd, ivd2.data(), sizeof(TwD) * (L / 2), cudaMemcpyHostToDevice));
     IDP_CK(cudaMemcpy(t.halfd, hfd.data(), sizeof(ddc) * (L + 1), cudaMemcpyHostToDevice));
@@ -438,6 +445,7 @@ int transform(idp_plan p, View3 in, double *work, View3 out, const double *tab, 
         if (rc) return rc;
         a.tw = t.fwd;
         a.half = t.half;
+        a.halfr = t.halfr;
         if ((rc = get_sin2(p, p->M[s], &a.sin2))) return rc;
         if (dd) {
             // double-float arithmetic; intermediate passes keep double-float pairs
@@ -474,6 +482,7 @@ int dst_box(idp_plan p, double *x, int b0, int b1, int b2, int M2, int M1, cudaS
         if (rc) return rc;
         a.tw = t.fwd;
         a.half = t.half;
+        a.halfr = t.halfr;
         if ((rc = get_sin2(p, Ms[q], &a.sin2))) return rc;
         if (p->mixed == IDP_PRECISION_DF32) {
             a.dd = 1;
