@@ -1,6 +1,7 @@
 // CTA-cooperative complex FFT in shared memory (Stockham, natural order in and
-// out; one radix-3 stage first when the length is 3 * 2^m, radix-2 stages
-// otherwise), for FP64 (double2) or double-float (ddc) elements.
+// out; one radix-3 stage first when the length is 3 * 2^m, then radix-4
+// passes and at most one radix-2 pass), for FP64 (double2) or double-float
+// (ddc) elements.
 // FP64 arithmetic is the scarce resource on GB300 (about 1/60 of the FP32
 // rate), so the FP64 butterfly uses the ratio ("tangent") form of the
 // twiddle: 6 FP64 instructions per butterfly instead of 8, and the first two
@@ -44,8 +45,58 @@ __device__ __forceinline__ typename Ar<R>::C *cta_fft_t(typename Ar<R>::C *X, ty
         first = 3;
         zero_half = false;
     }
+    // radix-4 passes: two radix-2 stages fused in registers, four ratio-form
+    // butterflies per four points (the FP64 operation count of the radix-2 form),
+    // half the shared-memory round trips and barriers
+    int Ns = first;
+    constexpr int Q = L / 4;
 #pragma unroll 1
-    for (int Ns = first; Ns < L; Ns <<= 1) {
+    for (; Ns * 4 <= L; Ns <<= 2) {
+#pragma unroll
+        for (int b = threadIdx.x; b < LB * Q; b += NT) {
+            const int line = b / Q;
+            const int j = b - line * Q;
+            const C *x = X + line * L;
+            C *y = Y + line * L;
+            const int k = P2 ? (j & (Ns - 1)) : (j % Ns);
+            const C a0 = x[j], a1 = x[j + Q];
+            C y0, y1, y2, y3;
+            if (Ns == 1) {
+                C c0, c1, e0, e1;
+                if (zero_half) {
+                    c0 = a0; c1 = a0; e0 = a1; e1 = a1;
+                } else {
+                    const C a2 = x[j + 2 * Q], a3 = x[j + 3 * Q];
+                    c0 = Ar<R>::cadd(a0, a2); c1 = Ar<R>::csub(a0, a2);
+                    e0 = Ar<R>::cadd(a1, a3); e1 = Ar<R>::csub(a1, a3);
+                }
+                y0 = Ar<R>::cadd(c0, e0);
+                y2 = Ar<R>::csub(c0, e0);
+                const C t = INV ? mul_pi(e1) : mul_mi(e1);
+                y1 = Ar<R>::cadd(c1, t);
+                y3 = Ar<R>::csub(c1, t);
+            } else {
+                const C a2 = x[j + 2 * Q], a3 = x[j + 3 * Q];
+                const int s1 = L / (4 * Ns);
+                C c0, c1, e0, e1;
+                Ar<R>::bfly(a0, a2, tw[2 * k * s1], c0, c1);       // w^2k
+                Ar<R>::bfly(a1, a3, tw[2 * k * s1], e0, e1);
+                Ar<R>::bfly(c0, e0, tw[k * s1], y0, y2);           // w^k
+                Ar<R>::bfly(c1, e1, tw[(k + Ns) * s1], y1, y3);    // -+ i w^k
+            }
+            const int base = ((j - k) << 2) + k;
+            y[base] = y0;
+            y[base + Ns] = y1;
+            y[base + 2 * Ns] = y2;
+            y[base + 3 * Ns] = y3;
+        }
+        __syncthreads();
+        C *t = X;
+        X = Y;
+        Y = t;
+        zero_half = false;
+    }
+    if (Ns < L) {   // one radix-2 stage left
 #pragma unroll
         for (int b = threadIdx.x; b < LB * H; b += NT) {
             const int line = b / H;
@@ -65,15 +116,8 @@ __device__ __forceinline__ typename Ar<R>::C *cta_fft_t(typename Ar<R>::C *X, ty
                     A = Ar<R>::cadd(a, c);
                     B = Ar<R>::csub(a, c);
                 }
-            } else if (Ns == 2) {
-                const C c = x[j + H];
-                // w = 1 (k = 0) or -i (forward) / +i (inverse) (k = 1)
-                const C t = k ? (INV ? mul_pi(c) : mul_mi(c)) : c;
-                A = Ar<R>::cadd(a, t);
-                B = Ar<R>::csub(a, t);
             } else {
-                const C c = x[j + H];
-                Ar<R>::bfly(a, c, tw[k * (L / (2 * Ns))], A, B);
+                Ar<R>::bfly(a, x[j + H], tw[k * (L / (2 * Ns))], A, B);
             }
             y[o] = A;
             y[o + Ns] = B;
