@@ -223,39 +223,52 @@ __global__ void rhs6_core_kernel(const Grid3 gg, const double *__restrict__ W, d
 // layer M-1); applied as the tensor product over the axes.
 __global__ void rhs6_extrap_kernel(const Grid3 gg, double *R)
 {
+    // one thread per node of the layers next to the boundary (the shell of the
+    // interior box), enumerated like the gtilde parts: the slabs of axis 0, then
+    // those of axis 1 inside them, then those of axis 2
     const Geo g = make_geo(gg);
-    const int k2 = blockIdx.x * blockDim.x + threadIdx.x;
-    const int k1 = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k0 = blockIdx.z;
-    if (k2 >= g.ni[2] || k1 >= g.ni[1]) return;
-    const int i[3] = {g.act[0] ? k0 + 1 : 0, k1 + 1, k2 + 1};
-    bool shell = false;
-    for (int s = 0; s < 3; ++s)
-        if (g.act[s] && (i[s] == 1 || i[s] == g.M[s] - 1)) shell = true;
-    if (!shell) return;
-    // per axis: first tap index (interior coordinate), step and count
-    int first[3], step[3], ntap[3];
-    for (int s = 0; s < 3; ++s) {
-        const int k = g.act[s] ? i[s] - 1 : 0;
-        if (g.act[s] && i[s] == 1) { first[s] = 1; step[s] = 1; ntap[s] = 4; }
-        else if (g.act[s] && i[s] == g.M[s] - 1) { first[s] = g.M[s] - 3; step[s] = -1; ntap[s] = 4; }
-        else { first[s] = k; step[s] = 0; ntap[s] = 1; }
-    }
+    const int n0 = g.ni[0], n1 = g.ni[1], n2 = g.ni[2];
+    const int s0 = g.act[0] ? 2 * n1 * n2 : 0;
+    const int s1 = 2 * (g.act[0] ? n0 - 2 : 1) * n2;
+    const int s2 = 2 * (g.act[0] ? n0 - 2 : 1) * (n1 - 2);
     const double wts[4] = {4.0, -6.0, 4.0, -1.0};
-    double acc = 0.0;
-    for (int q0 = 0; q0 < ntap[0]; ++q0) {
-        const double w0 = ntap[0] == 4 ? wts[q0] : 1.0;
-        const int64_t c0 = (first[0] + q0 * step[0]) * g.is[0];
-        for (int q1 = 0; q1 < ntap[1]; ++q1) {
-            const double w1 = ntap[1] == 4 ? wts[q1] : 1.0;
-            const int64_t c1 = c0 + (int64_t)(first[1] + q1 * step[1]) * g.is[1];
-            for (int q2 = 0; q2 < ntap[2]; ++q2) {
-                const double w2 = ntap[2] == 4 ? wts[q2] : 1.0;
-                acc = fma(w0 * w1 * w2, R[c1 + first[2] + q2 * step[2]], acc);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < s0 + s1 + s2; t += gridDim.x * blockDim.x) {
+        int k[3];   // interior indices
+        if (t < s0) {
+            const int side = t / (n1 * n2), r = t - side * n1 * n2;
+            k[0] = side ? n0 - 1 : 0; k[1] = r / n2; k[2] = r - k[1] * n2;
+        } else if (t < s0 + s1) {
+            const int q = t - s0, m0 = g.act[0] ? n0 - 2 : 1;
+            const int side = q / (m0 * n2), r = q - side * m0 * n2;
+            k[0] = g.act[0] ? r / n2 + 1 : 0; k[1] = side ? n1 - 1 : 0; k[2] = r % n2;
+        } else {
+            const int q = t - s0 - s1, m0 = g.act[0] ? n0 - 2 : 1;
+            const int side = q / (m0 * (n1 - 2)), r = q - side * m0 * (n1 - 2);
+            k[0] = g.act[0] ? r / (n1 - 2) + 1 : 0; k[1] = r % (n1 - 2) + 1; k[2] = side ? n2 - 1 : 0;
+        }
+        const int i[3] = {g.act[0] ? k[0] + 1 : 0, k[1] + 1, k[2] + 1};
+        // per axis: first tap index (interior coordinate), step and count
+        int first[3], step[3], ntap[3];
+        for (int s = 0; s < 3; ++s) {
+            if (g.act[s] && i[s] == 1) { first[s] = 1; step[s] = 1; ntap[s] = 4; }
+            else if (g.act[s] && i[s] == g.M[s] - 1) { first[s] = g.M[s] - 3; step[s] = -1; ntap[s] = 4; }
+            else { first[s] = k[s]; step[s] = 0; ntap[s] = 1; }
+        }
+        double acc = 0.0;
+        for (int q0 = 0; q0 < ntap[0]; ++q0) {
+            const double w0 = ntap[0] == 4 ? wts[q0] : 1.0;
+            const int64_t c0 = (first[0] + q0 * step[0]) * g.is[0];
+            for (int q1 = 0; q1 < ntap[1]; ++q1) {
+                const double w1 = ntap[1] == 4 ? wts[q1] : 1.0;
+                const int64_t c1 = c0 + (int64_t)(first[1] + q1 * step[1]) * g.is[1];
+                for (int q2 = 0; q2 < ntap[2]; ++q2) {
+                    const double w2 = ntap[2] == 4 ? wts[q2] : 1.0;
+                    acc = fma(w0 * w1 * w2, R[c1 + first[2] + q2 * step[2]], acc);
+                }
             }
         }
+        R[k[0] * g.is[0] + (int64_t)k[1] * g.is[1] + k[2]] = acc;
     }
-    R[k0 * g.is[0] + (int64_t)k1 * g.is[1] + k2] = acc;
 }
 
 // tabc = sc / lambda_c, tab4 = sc / Lambda4 on the mode grid (dense interior).
@@ -359,7 +372,10 @@ cudaError_t launch_rhs6_core(const Grid3 &g, const double *W, double *R, cudaStr
 
 cudaError_t launch_rhs6_extrap(const Grid3 &g, double *R, cudaStream_t st)
 {
-    rhs6_extrap_kernel<<<grid3(g.n2 - 2, g.n1 - 2, g.d == 3 ? g.n0 - 2 : 1), dim3(32, 8), 0, st>>>(g, R);
+    const int64_t n0 = g.d == 3 ? g.n0 - 2 : 1, n1 = g.n1 - 2, n2 = g.n2 - 2;
+    const int64_t total = (g.d == 3 ? 2 * n1 * n2 : 0) + 2 * (g.d == 3 ? n0 - 2 : 1) * n2 +
+                          2 * (g.d == 3 ? n0 - 2 : 1) * (n1 - 2);
+    rhs6_extrap_kernel<<<grid_for(total), 256, 0, st>>>(g, R);
     return cudaGetLastError();
 }
 
