@@ -22,7 +22,8 @@
  *   - Grids: d in {2, 3}; n[s] = node count along array axis s INCLUDING the
  *     two boundary nodes (n[s] = M_s + 1, M_s panels); h[s] > 0 is the mesh
  *     width.  Arrays are FP64, C order, last axis contiguous, prod(n) entries.
- *   - Supported sizes: M_s = 2^a or 3 * 2^a with 16 <= M_s <= 512.
+ *   - Supported sizes: M_s = 2^a with 16 <= M_s <= 512, or M_s = 3 * 2^a with
+ *     48 <= M_s <= 384.
  *   - rho is read on interior nodes only; its boundary entries are ignored.
  *     The method assumes rho vanishes near the boundary (section 2); the
  *     library does not check it.

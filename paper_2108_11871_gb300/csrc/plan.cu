@@ -32,8 +32,11 @@ int cuda_fail(cudaError_t e, const char *what)
     } while (0)
 
 bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
-// panel counts with a transform kernel: 2^a or 3 * 2^a in [16, 512]
-bool supported_panels(int64_t M) { return M >= 16 && M <= 512 && (is_pow2(M) || (M % 3 == 0 && is_pow2(M / 3))); }
+// panel counts with a transform kernel: 2^a in [16, 512] or 3 * 2^a in [48, 384]
+bool supported_panels(int64_t M)
+{
+    return M >= 16 && M <= 512 && (is_pow2(M) || (M >= 48 && M % 3 == 0 && is_pow2(M / 3)));
+}
 
 // host tables ----------------------------------------------------------------
 // sin(pi m / L) and cos(pi m / L) with the integer argument reduced to [0, 2L).
@@ -1341,7 +1344,7 @@ const char *idp_strerror(int code)
     case IDP_ENOMEM: return "out of memory";
     case IDP_ECUDA: return "CUDA error";
     case IDP_EALIAS: return "input and output overlap";
-    case IDP_ESUPPORT: return "size or option not supported (panel counts must be 2^a or 3*2^a in [16, 512])";
+    case IDP_ESUPPORT: return "size or option not supported (panel counts must be 2^a in [16, 512] or 3*2^a in [48, 384])";
     case IDP_ETIMEOUT: return "a device-side wait exceeded its iteration limit";
     case IDP_ESCRATCH: return "problem larger than the fixed scratch of idp_rhs6_noalloc (524288 nodes)";
     default: return "unknown error";

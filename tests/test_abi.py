@@ -40,7 +40,8 @@ def test_argument_errors_need_no_gpu():
     h = (ctypes.c_double * 3)(0.1, 0.1, 0.1)
     assert lib.idp_create_plan(ctypes.byref(out), 4, n, h, 6) == idp.IDP_EINVAL
     assert lib.idp_create_plan(ctypes.byref(out), 3, n, h, 5) == idp.IDP_EINVAL
-    bad = (ctypes.c_int64 * 3)(33, 34, 33)
-    assert lib.idp_create_plan(ctypes.byref(out), 3, bad, h, 6) == idp.IDP_ESUPPORT
+    for bad_n in ((33, 34, 33), (25, 33, 33), (33, 33, 1025)):   # M = 33, 24, 1024
+        bad = (ctypes.c_int64 * 3)(*bad_n)
+        assert lib.idp_create_plan(ctypes.byref(out), 3, bad, h, 6) == idp.IDP_ESUPPORT
     assert lib.idp_solve(None, None, None, None) == idp.IDP_EINVAL
     assert idp.strerror(idp.IDP_EALIAS) == "input and output overlap"

@@ -1,0 +1,111 @@
+"""The paper's computational experiments (section 6) run on the GPU solver.
+
+Table 1: convergence rates of phi for rho = B_{eps,p}(x - a) on [-1,1]^3,
+eps = 0.4, a = (1/sqrt(31), 0.2, 0.1), rho (p-1)-times differentiable, against
+the exact potential.  The paper fits 4th-order rates over h in [0.01, 0.02]
+and 6th-order rates over h in [0.02, 0.1] with M = 20..200 panels; the
+supported panel counts here are 2^a and 3*2^a, so the fits use M = 128, 192
+(h = 0.0156, 0.0104) and M = 32, 48, 64, 96 (h = 0.0625 .. 0.021).
+
+Figure 2: the domain grows from [-1,1]^3 to [-D,D]^3 at fixed h for the C^6
+density; the 6th-order values on [-1,1]^3 change by little more than
+rounding (the paper: "up to essentially machine precision", except at the
+largest h).  Here h = 1/32 and D = 1, 1.5, 2 (M = 64, 96, 128).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as w
+from oracle import closed_form
+from tests.gpu_util import device, to_dev
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "table1_rates.txt")
+CENTRE = (1 / np.sqrt(31), 0.2, 0.1)
+
+
+@pytest.fixture(scope="module")
+def idp():
+    import paper_2108_11871_gb300 as m
+    device()
+    m.library()
+    return m
+
+
+def _solve(idp, prob, order):
+    import torch
+    plan = idp.create_plan(3, prob.n, prob.h, order)
+    r = to_dev(prob.rho())
+    out = torch.empty_like(r)
+    idp.solve(plan, r, out)
+    idp.plan_status(plan)
+    return out.cpu().numpy()
+
+
+def _rel_err(idp, M, p, order):
+    prob = w.scaled_bump((M + 1,) * 3, centre=CENTRE, eps=0.4, p=p)
+    phi = _solve(idp, prob, order)
+    ex = closed_form.bump_potential_on_grid(prob)
+    return float(np.abs(phi - ex).max() / np.abs(ex).max())
+
+
+def _golden():
+    rows = [l.split() for l in open(GOLDEN) if l.strip() and not l.startswith("#")]
+    return {int(r[0]): (float(r[1]), float(r[2])) for r in rows}
+
+
+def _rate(Ms, errs):
+    hs = [2.0 / M for M in Ms]
+    return float(np.polyfit(np.log(hs), np.log(errs), 1)[0])
+
+
+def test_table1_convergence_rates(idp):
+    gold = _golden()
+    report = []
+    for diff, p in ((0, 1), (2, 3), (4, 5), (6, 7), (8, 9)):
+        M6 = (32, 48, 64, 96)
+        r6 = _rate(M6, [_rel_err(idp, M, p, 6) for M in M6])
+        M4 = (128, 192)
+        r4 = _rate(M4, [_rel_err(idp, M, p, 4) for M in M4])
+        report.append((diff, r4, gold[diff][0], r6, gold[diff][1]))
+    print("\n  C^k   4th order (paper)   6th order (paper)")
+    for diff, r4, g4, r6, g6 in report:
+        print("  %d     %5.2f (%4.1f)        %5.2f (%4.1f)" % (diff, r4, g4, r6, g6))
+    for diff, r4, g4, r6, g6 in report:
+        # rates of the smooth densities: the 4th-order harmonic correction shows
+        # its order (paper 4.1), the 6th-order one far more (paper 9.8, 10.8)
+        if diff >= 6:
+            assert abs(r4 - g4) < 0.8, (diff, r4, g4)
+            assert r6 > 8.0, (diff, r6, g6)
+        # limited smoothness: both orders show the rate of the spectral part
+        # (the 4th-order fit has only two grids in the paper's window, where
+        # the 4th-order harmonic error and the spectral error mix: +-1.5)
+        else:
+            assert abs(r6 - g6) < 0.5, (diff, r6, g6)
+            assert abs(r4 - g4) < 1.5, (diff, r4, g4)
+
+
+def test_domain_size_invariance(idp):
+    # phi on [-1,1]^3 from domains [-D, D]^3, D = 1, 1.5, 2, h = 1/32, C^6 density
+    vals = {}
+    for D, M in ((1.0, 64), (1.5, 96), (2.0, 128)):
+        prob = w.scaled_bump((M + 1,) * 3, lo=(-D,) * 3, hi=(D,) * 3, centre=CENTRE, eps=0.4, p=7)
+        for order in (4, 6):
+            phi = _solve(idp, prob, order)
+            o = int(round((D - 1.0) * 32))
+            vals[D, order] = phi[o:o + 65, o:o + 65, o:o + 65]
+    ref = vals[1.0, 6]
+    scale = np.abs(ref).max()
+    d6 = max(np.abs(vals[D, 6] - ref).max() / scale for D in (1.5, 2.0))
+    d4 = max(np.abs(vals[D, 4] - vals[1.0, 4]).max() / scale for D in (1.5, 2.0))
+    # the approximation error of the 6th-order solution on [-1,1]^3 itself
+    exact = closed_form.bump_potential_on_grid(w.scaled_bump((65,) * 3, centre=CENTRE, eps=0.4, p=7))
+    e6 = np.abs(ref - exact).max() / np.abs(exact).max()
+    print("\n  domain-size variation on [-1,1]^3: order 6 %.2e, order 4 %.2e; 6th-order error %.2e"
+          % (d6, d4, e6))
+    # the paper: the variation is at most the size of the approximation error,
+    # and the 6th-order values vary far less than the 4th-order ones
+    assert d6 <= e6
+    assert d6 < 0.1 * d4
