@@ -148,12 +148,14 @@ enum {
     IDP_KERNEL_FACE_INVB = 4,    /* boundary stage 3a: inverse FFT across the face */
     IDP_KERNEL_FACE_C2R = 5,     /* boundary stage 3b: inverse real FFT and scatter to the face nodes */
     IDP_KERNEL_GTILDE = 6,       /* gtilde stencil on the boundary-adjacent layers (eq. harmonic4thOrderNH2D) */
-    IDP_KERNEL_RHS6_W = 7,       /* 6th-order RHS, second differences (eqs. 6thOrderRelation2D/3D) */
-    IDP_KERNEL_RHS6_CORE = 8,    /* 6th-order RHS on the core */
-    IDP_KERNEL_RHS6_EXTRAP = 9,  /* cubic extrapolation next to the boundary */
+    IDP_KERNEL_RHS6_W = 7,       /* 6th-order RHS: second differences of the odd continuation of u1 near the faces */
+    IDP_KERNEL_RHS6_CORE = 8,    /* 6th-order RHS at the taps of the cubic extrapolation */
+    IDP_KERNEL_RHS6_EXTRAP = 9,  /* layers of E = R - R_spec: cubic extrapolation and boundary terms */
     IDP_KERNEL_GTILDE_EXPAND = 10, /* sine transform of gtilde assembled from its transformed layers */
     IDP_KERNEL_DST_PARTS = 11,   /* sine passes over the boundary-adjacent layers of gtilde */
-    IDP_KERNEL_MIXED = 12        /* tensor-core sine-matrix pass (IDP_PRECISION_MIXED_BF16X3) */
+    IDP_KERNEL_MIXED = 12,       /* tensor-core sine-matrix pass (IDP_PRECISION_MIXED_BF16X3) */
+    IDP_KERNEL_SUPPORT = 13,     /* flags of the non-zero lines and slices of rho (zero ones skip stage 1 and 2) */
+    IDP_KERNEL_RHS6_EXPAND = 14  /* sine transform of the 6th-order layer correction from its layer transforms */
 };
 
 /* Run one solve (as idp_solve, but with plain launches, all on `stream`, none

@@ -84,6 +84,22 @@ __global__ void __launch_bounds__(NT) rfft_kernel(const RfftPass a)
     const int u = blockIdx.y, v0 = blockIdx.x * LB;
     const int nl = min(LB, nv - v0);
     const bool contig = (ise == 1);
+    if (a.lineflag) {
+        // lines that are all zero (rho vanishes near the boundary): write zero spectra
+        __shared__ int any_nz;
+        if (threadIdx.x == 0) any_nz = 0;
+        __syncthreads();
+        if (threadIdx.x < nl && a.lineflag[(int64_t)u * nv + v0 + threadIdx.x]) any_nz = 1;
+        __syncthreads();
+        if (!any_nz) {
+            Cx *outz = reinterpret_cast<Cx *>(a.out) + (int64_t)u * osu + (int64_t)v0 * osv;
+            for (int f = threadIdx.x; f < nl * (M + 1); f += NT) {
+                const int l = f / (M + 1), m = f - l * (M + 1);
+                outz[(int64_t)l * osv + (int64_t)m * ose] = A::cmake(A::zero(), A::zero());
+            }
+            return;
+        }
+    }
     R *zf = reinterpret_cast<R *>(bufA);   // [LB][2L] reals
     const int64_t inb = (int64_t)u * isu + (int64_t)v0 * isv;
     for (int f = threadIdx.x; f < LB * 2 * L; f += NT) {
@@ -171,6 +187,7 @@ __global__ void __launch_bounds__(NT) face_kernel(const FacePass a)
     const int64_t kstride = (int64_t)(Mb + 1) * a.nc;
     const Cx *D = reinterpret_cast<const Cx *>(a.D);
     for (int p = p0; p < p1; ++p) {
+        if (a.sliceflag && !a.sliceflag[p]) continue;   // slice of zeros: contributes nothing
         // load TC columns: positions 1..Mb-1 (interior index 0..Mb-2), rest zero
         const Cx *Dp = D + (int64_t)p * a.sp + (int64_t)c0 * a.sc;
         for (int f = threadIdx.x; f < TC * L; f += NT) {

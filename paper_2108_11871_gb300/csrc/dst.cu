@@ -19,18 +19,19 @@ namespace {
 
 constexpr int NT = 256;
 
-template <int K>
+template <int K, int LBO = 0>
 struct DstCfg {
     static constexpr int M = 2 * K;
     static constexpr int N = M - 1;
     // lines per block: 2 buffers x LB x M reals (32 KB for M >= 128), at
-    // least 8 lines so that the scan groups fit a warp
+    // least 8 lines so that the scan groups fit a warp; LBO = 8 gives the
+    // minimum (more blocks for small launches)
     static constexpr int LBr = (2048 / M) > 32 ? 32 : (2048 / M);
     // a power of two (so that LB * G = 256)
     static constexpr int LB0 = LBr >= 32 ? 32 : LBr >= 16 ? 16 : LBr >= 8 ? 8 : 4;
-    static constexpr int LB = LB0 < 8 ? 8 : LB0;
+    static constexpr int LB = LBO ? LBO : (LB0 < 8 ? 8 : LB0);
     static constexpr int G = NT / LB;             // threads per line in the scan
-    static constexpr int C = (K / G) > 0 ? K / G : 1;  // scan elements per thread
+    static constexpr int C = (K + G - 1) / G;     // scan elements per thread (the last ones guarded)
 };
 
 // element access for the two storage forms of a real value: FP64, or a
@@ -71,10 +72,10 @@ struct Tabs<ddr> {
     static __device__ __forceinline__ ddr sin2(const DstPass &a, int j) { return a.sin2d[j]; }
 };
 
-template <class R, int K>
+template <class R, int K, int LBO>
 __global__ void __launch_bounds__(NT) dst_pass_kernel(const DstPass a)
 {
-    using Cfg = DstCfg<K>;
+    using Cfg = DstCfg<K, LBO>;
     using A = Ar<R>;
     using Cx = typename A::C;
     constexpr int M = Cfg::M, N = Cfg::N, LB = Cfg::LB;
@@ -196,12 +197,10 @@ __global__ void __launch_bounds__(NT) dst_pass_kernel(const DstPass a)
         const int g = threadIdx.x - l * G;
         R vals[C];
         R run = A::zero();
-        if (g * C < K) {
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                run = A::add(run, o[l * M + 2 * (g * C + c)]);
-                vals[c] = run;
-            }
+        for (int c = 0; c < C; ++c) {
+            if (g * C + c < K) run = A::add(run, o[l * M + 2 * (g * C + c)]);
+            vals[c] = run;
         }
         // inclusive scan of the group totals (groups of G consecutive lanes)
         R incl = run;
@@ -211,10 +210,9 @@ __global__ void __launch_bounds__(NT) dst_pass_kernel(const DstPass a)
             if (g >= dd) incl = A::add(incl, nb);
         }
         const R off = A::sub(incl, run);
-        if (g * C < K) {
 #pragma unroll
-            for (int c = 0; c < C; ++c) o[l * M + 2 * (g * C + c)] = A::add(vals[c], off);
-        }
+        for (int c = 0; c < C; ++c)
+            if (g * C + c < K) o[l * M + 2 * (g * C + c)] = A::add(vals[c], off);
     }
     __syncthreads();
 
@@ -242,28 +240,49 @@ __global__ void __launch_bounds__(NT) dst_pass_kernel(const DstPass a)
     }
 }
 
-template <class R, int K>
-cudaError_t launch_k(const DstPass &a, cudaStream_t st)
+template <class R, int K, int LBO>
+cudaError_t launch_lb(const DstPass &a, int nu, int nv, cudaStream_t st)
 {
-    using Cfg = DstCfg<K>;
+    using Cfg = DstCfg<K, LBO>;
     static_assert(Cfg::G <= 32, "scan group must fit a warp");
     static_assert(Cfg::LB * Cfg::G == NT, "every thread belongs to one scan group");
     const size_t sm = 2 * sizeof(double2) * Cfg::LB * K;
+    dim3 grid((nv + Cfg::LB - 1) / Cfg::LB, nu);
+    dst_pass_kernel<R, K, LBO><<<grid, NT, sm, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <class R, int K>
+cudaError_t launch_k(const DstPass &a, cudaStream_t st)
+{
     int nu, nv;
     if (a.axis == 2) { nu = a.n0; nv = a.n1; }
     else if (a.axis == 1) { nu = a.n0; nv = a.n2; }
     else { nu = a.n1; nv = a.n2; }
-    dim3 grid((nv + Cfg::LB - 1) / Cfg::LB, nu);
-    dst_pass_kernel<R, K><<<grid, NT, sm, st>>>(a);
-    return cudaGetLastError();
+    if constexpr (DstCfg<K>::LB > 8) {
+        // a launch of less than two blocks per SM (the layer transforms) runs
+        // faster on more, smaller blocks
+        const int64_t blocks = (int64_t)nu * ((nv + DstCfg<K>::LB - 1) / DstCfg<K>::LB);
+        if (blocks < 2 * 152) return launch_lb<R, K, 8>(a, nu, nv, st);
+    }
+    return launch_lb<R, K, 0>(a, nu, nv, st);
+}
+
+template <class R, int K, int LBO>
+cudaError_t attr_lb()
+{
+    using Cfg = DstCfg<K, LBO>;
+    const int sm = (int)(2 * sizeof(double2) * Cfg::LB * K);
+    return cudaFuncSetAttribute(dst_pass_kernel<R, K, LBO>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
 template <class R, int K>
 cudaError_t attr_k()
 {
-    using Cfg = DstCfg<K>;
-    const int sm = (int)(2 * sizeof(double2) * Cfg::LB * K);
-    return cudaFuncSetAttribute(dst_pass_kernel<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaError_t e = attr_lb<R, K, 0>();
+    if (e != cudaSuccess) return e;
+    if constexpr (DstCfg<K>::LB > 8) e = attr_lb<R, K, 8>();
+    return e;
 }
 
 template <class R>

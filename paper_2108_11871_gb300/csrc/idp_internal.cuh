@@ -97,6 +97,7 @@ struct RfftPass {
     int axis, M;
     FftTables t;                                  // tables for complex length M
     int dd;                                       // 1: double-float arithmetic, output as pairs
+    const int *lineflag;   // optional: lineflag[u * nv + v] != 0 iff line (u, v) has a non-zero value
 };
 cudaError_t launch_rfft_pass(const RfftPass &a, cudaStream_t st);
 
@@ -114,6 +115,7 @@ struct FacePass {
     FftTables t;               // tables for complex length 2Mb
     int dd;                    // 1: double-float (D, part as pairs; khatd used)
     const ddr *khatd;          // kernel spectra as double-float pairs
+    const int *sliceflag;      // optional: sliceflag[p] != 0 iff slice p has a non-zero value
 };
 cudaError_t launch_face_pass(const FacePass &a, int nchunk, cudaStream_t st);
 int face_columns_per_block(int L);   // frequencies c per block of the face pass
@@ -187,10 +189,16 @@ StencilCoef make_stencil_coef(const Grid3 &g);
 // gtilde on the boundary-adjacent layers, split into parts Q0 (3-D), Q1, Q2 (see stencil.cu)
 cudaError_t launch_gtilde_planes(const Grid3 &g, const StencilCoef &c, const double *U, double *Q0, double *Q1,
                                  double *Q2, cudaStream_t st);
-// out = tab * (4^d S gtilde) (+ add) from the transformed parts
+// out = tab * (4^d S gtilde) (+ add) from the transformed, combined parts; if out2
+// is given, also out2 = (tab2 (+ tab if fold)) * (4^d S gtilde) + add2
 cudaError_t launch_gtilde_expand(const Grid3 &g, const double *Q0, const double *Q1, const double *Q2,
                                  const double *sin4, const double *tab, const double *add, double *out,
-                                 cudaStream_t st);
+                                 cudaStream_t st, const double *tab2 = nullptr, const double *add2 = nullptr,
+                                 double *out2 = nullptr, int fold = 0);
+// (a, b) -> (a + b, a - b) for the pairs of transformed layers at the two faces of
+// an axis: part i holds [2][nl][pl_i] (pl_i = 0: absent)
+cudaError_t launch_layers_combine(double *P0, int64_t pl0, double *P1, int64_t pl1, double *P2, int64_t pl2,
+                                  int nl, cudaStream_t st);
 cudaError_t launch_gtilde_scatter(const Grid3 &g, const double *Q0, const double *Q1, const double *Q2,
                                   double *out, cudaStream_t st);
 // W_s = sum_{r != s} a_sr (u(+e_r) + u(-e_r) - 2u) on nodes; W is 3 node arrays (2 for d = 2).
@@ -200,9 +208,32 @@ cudaError_t launch_rhs6_core(const Grid3 &g, const double *W, double *R, cudaStr
 cudaError_t launch_rhs6_extrap(const Grid3 &g, double *R, cudaStream_t st);
 // tabc = sc / lambda_c(k) and tab4 = sc / Lambda4(k) on the dense mode grid;
 // lc / ld hold the per-axis 1-D eigenvalues, axis s at offset off_s (axis 0 at 0).
+// Support flags of rho (interior view with node strides): row2[i0*n1+i1] for the
+// lines along axis 2, row1[i0*n2+i2] for the lines along axis 1, and the slice
+// flags sl0[i0], sl1[i1], sl2[i2]; each set to 1 where some value is non-zero
+// (the arrays must be zeroed before).
+cudaError_t launch_support_flags(const Grid3 &g, const double *rho_int, int64_t s0, int64_t s1, int64_t s2,
+                                 int *row2, int *row1, int *sl0, int *sl1, int *sl2, cudaStream_t st);
 // y = double-float pairs of x (set-up only)
 cudaError_t launch_to_dd(const double *x, ddr *y, int64_t n, cudaStream_t st);
+// tabR (optional) = tab4 * Lambda_R / Lambda4 with Lambda_R the symbol of the
+// 6th-order right-hand side.
 cudaError_t launch_eigen_tables(const Grid3 &g, const double *lc, const double *ld, int64_t off1,
-                                int64_t off2, double sc, double *tabc, double *tab4, cudaStream_t st);
+                                int64_t off2, double sc, double *tabc, double *tab4, double *tabR, cudaStream_t st);
+// The 6th-order right-hand side in spectral form (stencil.cu): kind 0: W of the
+// odd continuation of u1 on the nodes within 7 of a face; kind 1: R at the
+// extrapolation taps into the dense interior array Rt; kind 2: the layers of
+// E = R - R_spec (E0 [2][2][n1][n2] (3-D), E1 [2][2][n0][n2], E2 [2][2][n0][n1]).
+cudaError_t launch_rhs6_spectral(const Grid3 &g, const StencilCoef &c, const double *U, double *W, double *Rt,
+                                 double *E0, double *E1, double *E2, int kind, cudaStream_t st);
+// out += tab * (4^d S E) from the transformed layers of E
+cudaError_t launch_rhs6_e_expand(const Grid3 &g, const double *E0, const double *E1, const double *E2,
+                                 const double *sin4, const double *sin4b, const double *tab, double *out,
+                                 cudaStream_t st);
+// x *= Lambda_R (per mode) and out += E on its layers: the stage output of R
+cudaError_t launch_rhs6_symbol(const Grid3 &g, const double *ld, int64_t off1, int64_t off2, double *x,
+                               cudaStream_t st);
+cudaError_t launch_rhs6_e_scatter(const Grid3 &g, const double *E0, const double *E1, const double *E2,
+                                  double *out, cudaStream_t st);
 
 }  // namespace idp

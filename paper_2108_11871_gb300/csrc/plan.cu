@@ -147,6 +147,13 @@ struct idp_plan_s {
     double *tabc = nullptr, *tab4 = nullptr;
     double *tabc2 = nullptr;   // -2 * tabc (forward transform of rho continued from T0)
     double *Q0 = nullptr, *Q1 = nullptr, *Q2 = nullptr, *sin4 = nullptr;   // gtilde parts
+    double *tabR = nullptr;    // tab4 * Lambda_R / Lambda4 (6th-order right-hand side of R_spec)
+    double *E0 = nullptr, *E1 = nullptr, *E2 = nullptr, *sin4b = nullptr;   // layers of E = R - R_spec
+    double *ld = nullptr;      // per-axis eigenvalues of D2_s (axis s at ldoff[s])
+    int64_t ldoff[3] = {0, 0, 0};
+    int *flags = nullptr;        // support flags of rho: rows along axes 2 and 1, slices of axes 0, 1, 2
+    int64_t nflags = 0;
+    int *row2 = nullptr, *row1 = nullptr, *sl[3] = {nullptr, nullptr, nullptr};
     double2 *T0 = nullptr, *T1 = nullptr, *part = nullptr, *F = nullptr;
     double *khat[3] = {nullptr, nullptr, nullptr};
     ddr *khatd[3] = {nullptr, nullptr, nullptr};   // double-float copies (precision DF32)
@@ -520,6 +527,30 @@ int gtilde_parts(idp_plan p, bool transform_parts, cudaStream_t st)
         if ((rc = dst_box(p, p->Q1, 2, 1, n2, p->M[2], 0, st))) return rc;
         if ((rc = dst_box(p, p->Q2, 2, 1, n1, p->M[1], 0, st))) return rc;
     }
+    Mark mk(p, IDP_KERNEL_GTILDE, st);
+    IDP_CK(launch_layers_combine(p->Q0, p->d == 3 ? (int64_t)n1 * n2 : 0, p->Q1, (int64_t)n0 * n2, p->Q2,
+                                 (int64_t)n0 * n1, 1, st));
+    return IDP_OK;
+}
+
+// (d-1)-dimensional sine transforms of the layers of E (two per face)
+int e_layers(idp_plan p, cudaStream_t st)
+{
+    int rc;
+    const int n0 = p->ni[0], n1 = p->ni[1], n2 = p->ni[2];
+    if (p->d == 3 && n0 == n1 && n1 == n2) {
+        if ((rc = dst_box(p, p->E0, 12, n1, n2, p->M[2], p->M[1], st))) return rc;
+    } else if (p->d == 3) {
+        if ((rc = dst_box(p, p->E0, 4, n1, n2, p->M[2], p->M[1], st))) return rc;
+        if ((rc = dst_box(p, p->E1, 4, n0, n2, p->M[2], p->M[0], st))) return rc;
+        if ((rc = dst_box(p, p->E2, 4, n0, n1, p->M[1], p->M[0], st))) return rc;
+    } else {
+        if ((rc = dst_box(p, p->E1, 4, 1, n2, p->M[2], 0, st))) return rc;
+        if ((rc = dst_box(p, p->E2, 4, 1, n1, p->M[1], 0, st))) return rc;
+    }
+    Mark mk(p, IDP_KERNEL_RHS6_EXPAND, st);
+    IDP_CK(launch_layers_combine(p->E0, p->d == 3 ? (int64_t)n1 * n2 : 0, p->E1, (int64_t)n0 * n2, p->E2,
+                                 (int64_t)n0 * n1, 2, st));
     return IDP_OK;
 }
 
@@ -546,6 +577,14 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
     FftTables t;
     // double-float arithmetic for the 3-D convolutions in precision DF32
     const int dd = (p->mixed == IDP_PRECISION_DF32 && p->d == 3) ? 1 : 0;
+    // which rows and slices of rho are non-zero (zero ones are skipped below;
+    // their contributions are exactly zero)
+    IDP_CK(cudaMemsetAsync(p->flags, 0, sizeof(int) * p->nflags, st));
+    {
+        Mark mk(p, IDP_KERNEL_SUPPORT, st);
+        IDP_CK(launch_support_flags(p->grid, r.p, r.s0, r.s1, r.s2, p->row2, p->row1, p->sl[0], p->sl[1],
+                                    p->sl[2], st));
+    }
     // stage 1a: along axis 2 -> T0[i0][i1][m2]
     {
         RfftPass a{};
@@ -557,6 +596,7 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
         if ((rc = get_fft(p, p->M[2], &t))) return rc;
         a.t = t;
         a.dd = dd;
+        a.lineflag = p->row2;
         Mark mk(p, IDP_KERNEL_RFFT, st);
         IDP_CK(launch_rfft_pass(a, st));
     }
@@ -578,6 +618,7 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
         if ((rc = get_fft(p, p->M[1], &t))) return rc;
         a.t = t;
         a.dd = dd;
+        a.lineflag = p->row1;
         Mark mk(p, IDP_KERNEL_RFFT, st);
         IDP_CK(launch_rfft_pass(a, st));
     }
@@ -627,6 +668,7 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
         f.t = t;
         f.dd = dd;
         f.khatd = p->khatd[a_];
+        f.sliceflag = p->sl[a_];
         {
             Mark mk(p, IDP_KERNEL_FACE, st);
             IDP_CK(launch_face_pass(f, p->nchunk[a_], st));
@@ -715,10 +757,16 @@ int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t s
         }
         return transform(p, dense(p, p->A), p->A, node_interior(p, phi), nullptr, none, false, st);
     }
-    // 4. u1 = S (tab4 * S gtilde) -> U interior
+    // 4. u1 = S B, B = tab4 * S gtilde; in a full solve also C = A + tabR * S gtilde,
+    //    the solution coefficients less the layer correction (R_spec's share)
+    if (stop == 0 && overlap_rho) IDP_CK(cudaStreamWaitEvent(st, p->join, 0));
+    // FP64 / df32 final transforms take u1 in C (S C + S B = S (C + B)); the
+    // tensor-core one adds the FP64 u1 afterwards instead
+    const bool fold_u1 = !(p->mixed == IDP_PRECISION_MIXED_BF16X3 && p->mixed_path == 0);
     {
         Mark mk(p, IDP_KERNEL_GTILDE_EXPAND, st);
-        IDP_CK(launch_gtilde_expand(p->grid, p->Q0, p->Q1, p->Q2, p->sin4, p->tab4, nullptr, p->B, st));
+        IDP_CK(launch_gtilde_expand(p->grid, p->Q0, p->Q1, p->Q2, p->sin4, p->tab4, nullptr, p->B, st,
+                                    p->tabR, p->A, stop == 0 ? p->C : nullptr, fold_u1 ? 1 : 0));
     }
     // u1 feeds the sixth differences of R, which amplify its rounding by ~1e4-1e7:
     // this inverse transform stays FP64 in every precision mode
@@ -728,27 +776,40 @@ int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t s
         IDP_CK(cudaMemcpyAsync(phi, p->U, node_bytes, cudaMemcpyDeviceToDevice, st));
         return IDP_OK;
     }
-    // 5. R(u1) with extrapolation -> C
+    // 5. E = R - R_spec on the layers next to the faces: W of the odd continuation
+    //    near the faces, R at the extrapolation taps (into A, free now), E
     {
         Mark mk(p, IDP_KERNEL_RHS6_W, st);
-        IDP_CK(launch_rhs6_w(p->grid, p->coef, p->U, p->W, st));
+        IDP_CK(launch_rhs6_spectral(p->grid, p->coef, p->U, p->W, p->A, p->E0, p->E1, p->E2, 0, st));
     }
     {
         Mark mk(p, IDP_KERNEL_RHS6_CORE, st);
-        IDP_CK(launch_rhs6_core(p->grid, p->W, p->C, st));
+        IDP_CK(launch_rhs6_spectral(p->grid, p->coef, p->U, p->W, p->A, p->E0, p->E1, p->E2, 1, st));
     }
     {
         Mark mk(p, IDP_KERNEL_RHS6_EXTRAP, st);
-        IDP_CK(launch_rhs6_extrap(p->grid, p->C, st));
+        IDP_CK(launch_rhs6_spectral(p->grid, p->coef, p->U, p->W, p->A, p->E0, p->E1, p->E2, 2, st));
     }
     if (stop == IDP_STAGE_R) {
-        IDP_CK(cudaMemcpyAsync(phi, p->C, int_bytes, cudaMemcpyDeviceToDevice, st));
+        // R = S (Lambda_R b) + E with b the coefficients of u1 (recomputed), as a
+        // dense interior array
+        {
+            Mark mk(p, IDP_KERNEL_GTILDE_EXPAND, st);
+            IDP_CK(launch_gtilde_expand(p->grid, p->Q0, p->Q1, p->Q2, p->sin4, p->tab4, nullptr, p->C, st));
+        }
+        IDP_CK(launch_rhs6_symbol(p->grid, p->ld, p->ldoff[1], p->ldoff[2], p->C, st));
+        if ((rc = transform(p, dense(p, p->C), p->C, dense(p, phi), nullptr, none, false, st, false))) return rc;
+        IDP_CK(launch_rhs6_e_scatter(p->grid, p->E0, p->E1, p->E2, phi, st));
         return IDP_OK;
     }
-    // 6. C = A + tab4 * S R;  phi = S C + u1 inside
-    if (overlap_rho) IDP_CK(cudaStreamWaitEvent(st, p->join, 0));
-    if ((rc = transform(p, dense(p, p->C), p->C, dense(p, p->C), p->tab4, dense(p, p->A), true, st))) return rc;
-    return transform(p, dense(p, p->C), p->C, node_interior(p, phi), nullptr, node_interior(p, p->U), false, st);
+    // 6. the layer transforms of E; C += tab4 * S E;  phi = S C + u1 inside
+    if ((rc = e_layers(p, st))) return rc;
+    {
+        Mark mk(p, IDP_KERNEL_RHS6_EXPAND, st);
+        IDP_CK(launch_rhs6_e_expand(p->grid, p->E0, p->E1, p->E2, p->sin4, p->sin4b, p->tab4, p->C, st));
+    }
+    return transform(p, dense(p, p->C), p->C, node_interior(p, phi), nullptr,
+                     fold_u1 ? none : node_interior(p, p->U), false, st);
 }
 
 int plan_setup(idp_plan p)
@@ -780,6 +841,16 @@ int plan_setup(idp_plan p)
         p->Q1 = p->Q0 + q0;
         p->Q2 = p->Q1 + q1;
     }
+    {
+        const int64_t n0 = p->ni[0], n1 = p->ni[1], n2 = p->ni[2];
+        p->nflags = n0 * n1 + n0 * n2 + n0 + n1 + n2;
+        if ((rc = p->alloc(&p->flags, p->nflags))) return rc;
+        p->row2 = p->flags;
+        p->row1 = p->row2 + n0 * n1;
+        p->sl[0] = p->row1 + n0 * n2;
+        p->sl[1] = p->sl[0] + n0;
+        p->sl[2] = p->sl[1] + n1;
+    }
     IDP_CK(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
     IDP_CK(cudaStreamCreateWithFlags(&p->bst, cudaStreamNonBlocking));
     if (!p->cap) IDP_CK(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
@@ -793,6 +864,22 @@ int plan_setup(idp_plan p)
         }
         if ((rc = p->alloc(&p->sin4, (int64_t)s4.size()))) return rc;
         IDP_CK(cudaMemcpy(p->sin4, s4.data(), sizeof(double) * s4.size(), cudaMemcpyHostToDevice));
+        std::vector<double> s4b;
+        for (int s = 0; s < 3; ++s) {
+            if (!p->act[s]) continue;
+            for (int k = 0; k < p->ni[s]; ++k) s4b.push_back(4.0 * sinpi_frac(2 * (k + 1), p->M[s]));
+        }
+        if ((rc = p->alloc(&p->sin4b, (int64_t)s4b.size()))) return rc;
+        IDP_CK(cudaMemcpy(p->sin4b, s4b.data(), sizeof(double) * s4b.size(), cudaMemcpyHostToDevice));
+    }
+    {
+        // layers of E (two per face): E0 [2][2][n1][n2] (3-D), E1 [2][2][n0][n2], E2 [2][2][n0][n1]
+        const int64_t n0 = p->ni[0], n1 = p->ni[1], n2 = p->ni[2];
+        const int64_t e0 = p->d == 3 ? 4 * n1 * n2 : 0, e1 = 4 * n0 * n2, e2 = 4 * n0 * n1;
+        if ((rc = p->alloc(&p->E0, e0 + e1 + e2))) return rc;
+        p->E1 = p->E0 + e0;
+        p->E2 = p->E1 + e1;
+        if ((rc = p->alloc(&p->tabR, p->nint))) return rc;
     }
     IDP_CK(cudaMemset(p->U, 0, sizeof(double) * p->nodes));
     IDP_CK(cudaMemset(p->W, 0, sizeof(double) * 3 * p->nodes));
@@ -820,8 +907,10 @@ int plan_setup(idp_plan p)
         for (int s = 0; s < 3; ++s)
             if (p->act[s]) { sc *= 2.0 / p->M[s]; ++da; }
         for (int q = 0; q < 2 * da; ++q) sc *= 0.25;   // each sine pass returns 4 S x
-        IDP_CK(launch_eigen_tables(p->grid, dlc, dld, off[1], off[2], sc, p->tabc, p->tab4, 0));
-        IDP_CK(launch_eigen_tables(p->grid, dlc, dld, off[1], off[2], -2.0 * sc, p->tabc2, p->B, 0));
+        IDP_CK(launch_eigen_tables(p->grid, dlc, dld, off[1], off[2], sc, p->tabc, p->tab4, p->tabR, 0));
+        IDP_CK(launch_eigen_tables(p->grid, dlc, dld, off[1], off[2], -2.0 * sc, p->tabc2, p->B, nullptr, 0));
+        p->ld = dld;
+        for (int s = 0; s < 3; ++s) p->ldoff[s] = off[s];
     }
 
     // kernel spectra of the boundary convolutions (section 4)

@@ -39,6 +39,17 @@ __device__ __forceinline__ bool on_boundary(const Geo &g, const int j[3])
     return false;
 }
 
+// distance of node index j_s from the nearer face of axis s (large for an inactive axis)
+__device__ __forceinline__ int face_dist(const Geo &g, int s, int js)
+{
+    return g.act[s] ? min(js, g.M[s] - js) : (1 << 20);
+}
+
+__device__ __forceinline__ int min_dist(const Geo &g, const int j[3])
+{
+    return min(face_dist(g, 0, j[0]), min(face_dist(g, 1, j[1]), face_dist(g, 2, j[2])));
+}
+
 // gtilde = -L4(ghat) at interior node i, ghat = U on boundary nodes and 0 inside
 // (eq. harmonic4thOrderNH2D).  L4 weights (host-computed in c): face +-e_s:
 // 1/h_s^2 - 2 sum_r c_sr/(h_s^2 h_r^2); edge +-e_s +-e_r: c_sr/(h_s^2 h_r^2),
@@ -106,13 +117,15 @@ __global__ void gtilde_planes_kernel(const Grid3 gg, const StencilCoef c, const 
     }
 }
 
-// Forward sine transform of gtilde from the transformed parts (U = 4^d S gtilde):
-//   val(k) = sum_s sin4_s(k_s) (Qs[0](k_other) + (-1)^{k_s} Qs[1](k_other)),
-// sin4_s(k) = 4 sin(pi (k+1)/M_s); Qs holds the (d-1)-dimensional transforms of
-// the parts (4^{d-1} S).  out = tab * val (+ add).
+// Forward sine transform of gtilde from the transformed, combined parts
+// (4^{d-1} S of each part, then (a + b, a - b) per pair of faces):
+//   val(k) = sum_s sin4_s(k_s) Qs[k_s odd](k_other),  sin4_s(k) = 4 sin(pi (k+1)/M_s).
+// out = tab * val (+ add); if out2: out2 = (tab2 (+ tab if fold)) * val + add2.
 __global__ void gtilde_expand_kernel(const Grid3 gg, const double *__restrict__ Q0, const double *__restrict__ Q1,
                                      const double *__restrict__ Q2, const double *__restrict__ sin4,
-                                     const double *__restrict__ tab, const double *add, double *out)
+                                     const double *__restrict__ tab, const double *add, double *out,
+                                     const double *__restrict__ tab2, const double *__restrict__ add2,
+                                     double *__restrict__ out2, int fold)
 {
     const Geo g = make_geo(gg);
     const int k2 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -121,22 +134,13 @@ __global__ void gtilde_expand_kernel(const Grid3 gg, const double *__restrict__ 
     if (k2 >= g.ni[2] || k1 >= g.ni[1]) return;
     const int n0 = g.ni[0], n1 = g.ni[1], n2 = g.ni[2];
     const double *sn0 = sin4, *sn1 = sin4 + (g.act[0] ? n0 : 0), *sn2 = sn1 + n1;
-    double v;
-    {
-        const double a = Q1[(int64_t)k0 * n2 + k2], b = Q1[(int64_t)(n0 + k0) * n2 + k2];
-        v = sn1[k1] * ((k1 & 1) ? a - b : a + b);
-    }
-    {
-        const double a = Q2[(int64_t)k0 * n1 + k1], b = Q2[(int64_t)(n0 + k0) * n1 + k1];
-        v = fma(sn2[k2], (k2 & 1) ? a - b : a + b, v);
-    }
-    if (g.act[0]) {
-        const int64_t o = (int64_t)k1 * n2 + k2;
-        const double a = Q0[o], b = Q0[(int64_t)n1 * n2 + o];
-        v = fma(sn0[k0], (k0 & 1) ? a - b : a + b, v);
-    }
+    double v = sn1[k1] * Q1[(int64_t)((k1 & 1) ? n0 + k0 : k0) * n2 + k2];
+    v = fma(sn2[k2], Q2[(int64_t)((k2 & 1) ? n0 + k0 : k0) * n1 + k1], v);
+    if (g.act[0]) v = fma(sn0[k0], Q0[(int64_t)((k0 & 1) ? n1 + k1 : k1) * n2 + k2], v);
     const int64_t t = k0 * g.is[0] + (int64_t)k1 * g.is[1] + k2;
-    out[t] = add ? fma(tab[t], v, add[t]) : tab[t] * v;
+    const double tb = tab[t];
+    out[t] = add ? fma(tb, v, add[t]) : tb * v;
+    if (out2) out2[t] = fma(fold ? tab2[t] + tb : tab2[t], v, add2[t]);
 }
 
 // gtilde as a dense interior array from its parts (for the stage output).
@@ -160,7 +164,47 @@ __global__ void gtilde_scatter_kernel(const Grid3 gg, const double *__restrict__
 // a_sr = (h_s^4/240 + h_s^2 h_r^2/144) / (h_s^4 h_r^2) (host-computed), at nodes
 // with 1 <= j_r <= M_r-1 for r != s.  Then R = sum_s [1 -4 6 -4 1]_s W_s is the
 // right-hand side of eqs. 6thOrderRelation2D/3D, the sum over ordered pairs
-// of c_sr D2_s D2_s D2_r u.  Grid: x = node index 2, y = index 1, z = index 0.
+// of c_sr D2_s D2_s D2_r u.
+// odd = 1: u is taken as zero on the boundary nodes (the sine series of the
+// interior values, continued oddly).
+__device__ __forceinline__ void w_node(const Geo &g, const StencilCoef &c, const double *__restrict__ U,
+                                       double *__restrict__ W, const int j[3], bool odd)
+{
+    const int64_t nodes = (int64_t)g.n[0] * g.n[1] * g.n[2];
+    const int64_t t = j[0] * g.ns[0] + (int64_t)j[1] * g.ns[1] + j[2];
+    // odd: a node on a face reads as zero; the neighbours along r of a node off
+    // the faces lie on a face only through index r
+    const bool bnd = odd && on_boundary(g, j);
+    const double u0 = bnd ? 0.0 : U[t];
+    double e[3];
+    bool inner[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        inner[r] = !g.act[r] || (j[r] >= 1 && j[r] <= g.M[r] - 1);
+        e[r] = 0.0;
+        if (g.act[r] && inner[r] && !bnd) {
+            const double up = (odd && j[r] + 1 == g.M[r]) ? 0.0 : U[t + g.ns[r]];
+            const double um = (odd && j[r] - 1 == 0) ? 0.0 : U[t - g.ns[r]];
+            e[r] = fma(-2.0, u0, up + um);
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        if (!g.act[s]) continue;
+        bool ok = true;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            if (r != s && !inner[r]) ok = false;
+        if (!ok) continue;
+        double w = 0.0;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            if (r != s && g.act[r]) w = fma(c.a[s][r], e[r], w);
+        W[(int64_t)s * nodes + t] = w;
+    }
+}
+
+// all nodes; grid: x = node index 2, y = index 1, z = index 0
 __global__ void rhs6_w_kernel(const Grid3 gg, const StencilCoef c, const double *__restrict__ U,
                               double *__restrict__ W)
 {
@@ -170,26 +214,79 @@ __global__ void rhs6_w_kernel(const Grid3 gg, const StencilCoef c, const double 
     const int j0 = blockIdx.z;
     if (j2 >= g.n[2] || j1 >= g.n[1]) return;
     const int j[3] = {j0, j1, j2};
-    const int64_t nodes = (int64_t)g.n[0] * g.n[1] * g.n[2];
-    const int64_t t = j0 * g.ns[0] + (int64_t)j1 * g.ns[1] + j2;
-    const double u0 = U[t];
-    double e[3];
-    bool inner[3];
-    for (int r = 0; r < 3; ++r) {
-        inner[r] = !g.act[r] || (j[r] >= 1 && j[r] <= g.M[r] - 1);
-        e[r] = 0.0;
-        if (g.act[r] && inner[r]) e[r] = fma(-2.0, u0, U[t + g.ns[r]] + U[t - g.ns[r]]);
-    }
+    w_node(g, c, U, W, j, false);
+}
+
+// The nodes of a box (node indices lo_s .. lo_s + ext_s - 1 on the active axes)
+// that lie within tau - 1 of its faces, enumerated as the slabs of axis 0, then
+// those of axis 1 between them, then those of axis 2 (axis 2 fastest in each).
+// Requires ext_s >= 2 tau on the active axes.
+struct Shell {
+    int lo[3], ext[3], tau, act0;
+    int64_t c0, c1, count;
+};
+
+inline Shell make_shell(const Grid3 &g, int lo, int shrink, int tau)
+{
+    Shell sh{};
+    const int n[3] = {g.n0, g.n1, g.n2};
+    sh.act0 = g.d == 3;
     for (int s = 0; s < 3; ++s) {
-        if (!g.act[s]) continue;
-        bool ok = true;
-        for (int r = 0; r < 3; ++r)
-            if (r != s && !inner[r]) ok = false;
-        if (!ok) continue;
-        double w = 0.0;
-        for (int r = 0; r < 3; ++r)
-            if (r != s && g.act[r]) w = fma(c.a[s][r], e[r], w);
-        W[(int64_t)s * nodes + t] = w;
+        const bool act = s > 0 || sh.act0;
+        sh.lo[s] = act ? lo : 0;
+        sh.ext[s] = act ? n[s] - shrink : 1;
+    }
+    sh.tau = tau;
+    const int m0 = sh.act0 ? sh.ext[0] - 2 * tau : 1;
+    sh.c0 = sh.act0 ? 2 * (int64_t)tau * sh.ext[1] * sh.ext[2] : 0;
+    sh.c1 = (int64_t)m0 * 2 * tau * sh.ext[2];
+    sh.count = sh.c0 + sh.c1 + (int64_t)m0 * (sh.ext[1] - 2 * tau) * 2 * tau;
+    return sh;
+}
+
+__device__ __forceinline__ void shell_node(const Shell &sh, int t, int j[3])
+{
+    // 32-bit index arithmetic: a shell has at most 513^3 < 2^31 nodes (M_s <= 512)
+    const int tau = sh.tau, e0 = sh.ext[0], e1 = sh.ext[1], e2 = sh.ext[2];
+    const int c0 = (int)sh.c0, c1 = (int)sh.c1;
+    if (t < c0) {
+        const int pl = e1 * e2;
+        const int q = t / pl, r = t - q * pl;
+        j[0] = sh.lo[0] + (q < tau ? q : e0 - 2 * tau + q);
+        j[1] = sh.lo[1] + r / e2;
+        j[2] = sh.lo[2] + r % e2;
+        return;
+    }
+    t -= c0;
+    const int l0 = sh.act0 ? sh.lo[0] + tau : sh.lo[0];
+    if (t < c1) {
+        const int pl = 2 * tau * e2;
+        const int q = t / pl, r = t - q * pl;
+        const int a = r / e2;
+        j[0] = l0 + q;
+        j[1] = sh.lo[1] + (a < tau ? a : e1 - 2 * tau + a);
+        j[2] = sh.lo[2] + r - a * e2;
+        return;
+    }
+    t -= c1;
+    const int pl = (e1 - 2 * tau) * 2 * tau;
+    const int q = t / pl, r = t - q * pl;
+    const int a = r / (2 * tau), bb = r - a * 2 * tau;
+    j[0] = l0 + q;
+    j[1] = sh.lo[1] + tau + a;
+    j[2] = sh.lo[2] + (bb < tau ? bb : e2 - 2 * tau + bb);
+}
+
+// W of the odd continuation on the nodes of a shell
+__global__ void rhs6_wband_kernel(const Grid3 gg, const Shell sh, const StencilCoef c,
+                                  const double *__restrict__ U, double *__restrict__ W)
+{
+    const Geo g = make_geo(gg);
+    const int cnt = (int)sh.count;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
+        int j[3];
+        shell_node(sh, t, j);
+        w_node(g, c, U, W, j, true);
     }
 }
 
@@ -271,9 +368,283 @@ __global__ void rhs6_extrap_kernel(const Grid3 gg, double *R)
     }
 }
 
+// ---------------------------------------------------------------------------
+// The 6th-order right-hand side in spectral form (section 5).
+//
+// Inside the grid u1 equals its sine series, so on the nodes whose stencil stays
+// off the faces R is R_spec = S(Lambda_R b) with b the sine coefficients of u1
+// and Lambda_R(k) = sum_{s != r} c_sr lam_s(k)^2 lam_r(k) the symbol of the
+// stencil (lam_s the eigenvalues of D2_s).  R_spec is the same stencil applied
+// to the odd continuation of the interior values of u1 (zero on the faces).
+// The difference E = R - R_spec lives on the nodes within 2 of a face:
+//   * distance 2 (and no axis at distance 1): the stencil's only tap on a face
+//     is [1 -4 6 -4 1]_s at offset -+2, so E = sum over those s of W_s at the
+//     face node, W_s from the boundary values g (the second differences of g
+//     along the face);
+//   * distance 1: R is the cubic extrapolation of the core values, so
+//     E = R_extrap - R_spec there.
+// So S R = Lambda_R (S S b) + S E, and the sine transform of E is assembled
+// from the (d-1)-dimensional transforms of its layers.
+
+// u-weights of the fourth difference
+__device__ __constant__ double kD4[5] = {1.0, -4.0, 6.0, -4.0, 1.0};
+
+// W of the odd continuation (band array `W`, odd = 1) at node j shifted by o
+// along s: reflected (with a sign change) through the faces of axis s.
+__device__ __forceinline__ double w_odd_at(const Geo &g, const double *__restrict__ W, int64_t nodes, int s,
+                                           const int j[3], int o)
+{
+    int q = j[s] + o;
+    double sg = 1.0;
+    if (q < 0) { q = -q; sg = -1.0; }
+    else if (q > g.M[s]) { q = 2 * g.M[s] - q; sg = -1.0; }
+    int jj[3] = {j[0], j[1], j[2]};
+    jj[s] = q;
+    return sg * W[(int64_t)s * nodes + jj[0] * g.ns[0] + (int64_t)jj[1] * g.ns[1] + jj[2]];
+}
+
+// W_s at the face node of axis s nearest to j (j at distance 2 from it), from
+// the boundary values in U
+__device__ __forceinline__ double w_face(const Geo &g, const StencilCoef &c, const double *__restrict__ U, int s,
+                                         const int j[3])
+{
+    int f[3] = {j[0], j[1], j[2]};
+    f[s] = j[s] <= g.M[s] / 2 ? 0 : g.M[s];
+    const int64_t t = f[0] * g.ns[0] + (int64_t)f[1] * g.ns[1] + f[2];
+    const double u0 = U[t];
+    double w = 0.0;
+    for (int r = 0; r < 3; ++r)
+        if (r != s && g.act[r]) w = fma(c.a[s][r], fma(-2.0, u0, U[t + g.ns[r]] + U[t - g.ns[r]]), w);
+    return w;
+}
+
+// R_spec at node j (any interior node) from the band array of W of the odd continuation
+__device__ __forceinline__ double r_spec_at(const Geo &g, const double *__restrict__ W, int64_t nodes,
+                                            const int j[3])
+{
+    double acc = 0.0;
+    for (int s = 0; s < 3; ++s) {
+        if (!g.act[s]) continue;
+        for (int o = -2; o <= 2; ++o) acc = fma(kD4[o + 2], w_odd_at(g, W, nodes, s, j, o), acc);
+    }
+    return acc;
+}
+
+// R (with the boundary values) at core node j (all active distances >= 2)
+__device__ __forceinline__ double r_core_at(const Geo &g, const StencilCoef &c, const double *__restrict__ U,
+                                            const double *__restrict__ W, int64_t nodes, const int j[3])
+{
+    double acc = r_spec_at(g, W, nodes, j);
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
+        if (face_dist(g, s, j[s]) == 2) acc += w_face(g, c, U, s, j);
+    return acc;
+}
+
+// R on the core nodes within 5 of a face (the taps of the cubic extrapolation),
+// enumerated as a shell; written to the dense interior array Rt.
+__global__ void rhs6_taps_kernel(const Grid3 gg, const Shell sh, const StencilCoef c,
+                                 const double *__restrict__ U, const double *__restrict__ W, double *__restrict__ Rt)
+{
+    const Geo g = make_geo(gg);
+    const int64_t nodes = (int64_t)g.n[0] * g.n[1] * g.n[2];
+    const int cnt = (int)sh.count;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
+        int j[3];
+        shell_node(sh, t, j);
+        const int64_t k0 = g.act[0] ? j[0] - 1 : 0;
+        Rt[k0 * g.is[0] + (int64_t)(j[1] - 1) * g.is[1] + (j[2] - 1)] = r_core_at(g, c, U, W, nodes, j);
+    }
+}
+
+// weight q (0..3) of the cubic extrapolation from the taps at distance 2..5
+__device__ __forceinline__ double extrap_w(int q) { return q == 0 ? 4.0 : q == 1 ? -6.0 : q == 2 ? 4.0 : -1.0; }
+
+// E on the layers at distance 1 and 2 from the faces, split like the gtilde parts
+// by the first axis s at distance <= 2:
+//   Es[side][l][a][b], l = distance - 1, (a, b) the interior indices of the other
+//   two axes in increasing order; entries that belong to a lower part are zero.
+// E0 (3-D only) is followed by E1 and E2 in memory.
+__global__ void rhs6_e_kernel(const Grid3 gg, const StencilCoef c, const double *__restrict__ U,
+                              const double *__restrict__ W, const double *__restrict__ Rt, double *__restrict__ E0,
+                              double *__restrict__ E1, double *__restrict__ E2)
+{
+    const Geo g = make_geo(gg);
+    const int n0 = g.ni[0], n1 = g.ni[1], n2 = g.ni[2];
+    // 32-bit index arithmetic: 4 (n1 n2 + n0 n2 + n0 n1) < 2^31 for n <= 511
+    const int s0 = g.act[0] ? 4 * n1 * n2 : 0, s1 = 4 * n0 * n2, s2 = 4 * n0 * n1;
+    const int64_t nodes = (int64_t)g.n[0] * g.n[1] * g.n[2];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < s0 + s1 + s2; t += gridDim.x * blockDim.x) {
+        int sl, a, b, j0, j1, j2;
+        bool lower;
+        double *dst;
+        if (t < s0) {
+            const int pl = n1 * n2;
+            sl = t / pl; const int r = t - sl * pl;
+            a = r / n2; b = r - a * n2; dst = E0 + t;
+            const int l = sl & 1;
+            j0 = (sl >> 1) ? g.M[0] - 1 - l : 1 + l; j1 = a + 1; j2 = b + 1;
+            lower = false;
+        } else if (t < s0 + s1) {
+            const int q = t - s0, pl = n0 * n2;
+            sl = q / pl; const int r = q - sl * pl;
+            a = r / n2; b = r - a * n2; dst = E1 + q;
+            const int l = sl & 1;
+            j0 = g.act[0] ? a + 1 : 0; j1 = (sl >> 1) ? g.M[1] - 1 - l : 1 + l; j2 = b + 1;
+            lower = face_dist(g, 0, j0) <= 2;
+        } else {
+            const int q = t - s0 - s1, pl = n0 * n1;
+            sl = q / pl; const int r = q - sl * pl;
+            a = r / n1; b = r - a * n1; dst = E2 + q;
+            const int l = sl & 1;
+            j0 = g.act[0] ? a + 1 : 0; j1 = b + 1; j2 = (sl >> 1) ? g.M[2] - 1 - l : 1 + l;
+            lower = face_dist(g, 0, j0) <= 2 || face_dist(g, 1, j1) <= 2;
+        }
+        double v = 0.0;
+        if (!lower) {
+            const int j[3] = {j0, j1, j2};
+            const int d0 = face_dist(g, 0, j0), d1 = face_dist(g, 1, j1), d2 = face_dist(g, 2, j2);
+            if (d0 == 1 || d1 == 1 || d2 == 1) {
+                // cubic extrapolation, the tensor product over the axes at distance 1
+                // (taps at interior index 1..4 from the low face, M-3..M-6 from the high one)
+                const int nt0 = d0 == 1 ? 4 : 1, nt1 = d1 == 1 ? 4 : 1, nt2 = d2 == 1 ? 4 : 1;
+                const int f0 = d0 == 1 ? (j0 == 1 ? 1 : g.M[0] - 3) : j0 - (g.act[0] ? 1 : 0);
+                const int f1 = d1 == 1 ? (j1 == 1 ? 1 : g.M[1] - 3) : j1 - 1;
+                const int f2 = d2 == 1 ? (j2 == 1 ? 1 : g.M[2] - 3) : j2 - 1;
+                const int st0 = j0 == 1 ? 1 : -1, st1 = j1 == 1 ? 1 : -1, st2 = j2 == 1 ? 1 : -1;
+                double acc = 0.0;
+                for (int q0 = 0; q0 < nt0; ++q0) {
+                    const double w0 = nt0 == 4 ? extrap_w(q0) : 1.0;
+                    const int64_t c0 = (int64_t)(f0 + q0 * st0) * g.is[0];
+                    for (int q1 = 0; q1 < nt1; ++q1) {
+                        const double w1 = nt1 == 4 ? w0 * extrap_w(q1) : w0;
+                        const int64_t c1 = c0 + (int64_t)(f1 + q1 * st1) * g.is[1];
+                        for (int q2 = 0; q2 < nt2; ++q2) {
+                            const double w2 = nt2 == 4 ? w1 * extrap_w(q2) : w1;
+                            acc = fma(w2, Rt[c1 + f2 + q2 * st2], acc);
+                        }
+                    }
+                }
+                v = acc - r_spec_at(g, W, nodes, j);
+            } else {
+                if (d0 == 2) v += w_face(g, c, U, 0, j);
+                if (d1 == 2) v += w_face(g, c, U, 1, j);
+                if (d2 == 2) v += w_face(g, c, U, 2, j);
+            }
+        }
+        *dst = v;
+    }
+}
+
+// In place, per pair of layers at the two faces of an axis (layers a at offset l*pl,
+// b at (nl + l)*pl of each part): (a, b) -> (a + b, a - b), the two sign patterns
+// of sin(pi m j / M) and sin(pi m (M - j) / M) = (-1)^(m+1) sin(pi m j / M).
+__global__ void layers_combine_kernel(double *__restrict__ P0, int pl0, double *__restrict__ P1, int pl1,
+                                      double *__restrict__ P2, int pl2, int nl)
+{
+    // 32-bit index arithmetic: at most 2 * 3 * 511^2 entries
+    const int tot = nl * (pl0 + pl1 + pl2);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
+        double *P;
+        int pl, q = t;
+        if (q < nl * pl0) { P = P0; pl = pl0; }
+        else if ((q -= nl * pl0) < nl * pl1) { P = P1; pl = pl1; }
+        else { q -= nl * pl1; P = P2; pl = pl2; }
+        const int l = q / pl;
+        const int x = q - l * pl;
+        const double av = P[l * pl + x], bv = P[(nl + l) * pl + x];
+        P[l * pl + x] = av + bv;
+        P[(nl + l) * pl + x] = av - bv;
+    }
+}
+
+// out(k) += tab(k) * (4^d S E)(k) from the transformed, combined layers
+// (4^{d-1} S of each, then (a + b, a - b) per pair):
+//   sum_s sum_l 4 sin(pi (k_s+1)(l+1)/M_s) Es[k_s odd][l](k_other).
+// sin4 / sin4b hold 4 sin(pi (k+1)/M_s) / 4 sin(2 pi (k+1)/M_s) per active axis.
+__global__ void rhs6_e_expand_kernel(const Grid3 gg, const double *__restrict__ E0, const double *__restrict__ E1,
+                                     const double *__restrict__ E2, const double *__restrict__ sin4,
+                                     const double *__restrict__ sin4b, const double *__restrict__ tab,
+                                     double *__restrict__ out)
+{
+    const Geo g = make_geo(gg);
+    const int k2 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k1 = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k0 = blockIdx.z;
+    if (k2 >= g.ni[2] || k1 >= g.ni[1]) return;
+    const int n0 = g.ni[0], n1 = g.ni[1], n2 = g.ni[2];
+    const int o1 = g.act[0] ? n0 : 0, o2 = o1 + n1;
+    double v;
+    {
+        const int64_t pl = (int64_t)n0 * n2, o = (int64_t)k0 * n2 + k2 + ((k1 & 1) ? 2 * pl : 0);
+        v = sin4[o1 + k1] * E1[o];
+        v = fma(sin4b[o1 + k1], E1[pl + o], v);
+    }
+    {
+        const int64_t pl = (int64_t)n0 * n1, o = (int64_t)k0 * n1 + k1 + ((k2 & 1) ? 2 * pl : 0);
+        v = fma(sin4[o2 + k2], E2[o], v);
+        v = fma(sin4b[o2 + k2], E2[pl + o], v);
+    }
+    if (g.act[0]) {
+        const int64_t pl = (int64_t)n1 * n2, o = (int64_t)k1 * n2 + k2 + ((k0 & 1) ? 2 * pl : 0);
+        v = fma(sin4[k0], E0[o], v);
+        v = fma(sin4b[k0], E0[pl + o], v);
+    }
+    const int64_t t = k0 * g.is[0] + (int64_t)k1 * g.is[1] + k2;
+    out[t] = fma(tab[t], v, out[t]);
+}
+
+// x(k) *= Lambda_R(k) (stage output only); ld: per-axis eigenvalues of D2_s,
+// axis s at offset off_s
+__global__ void rhs6_symbol_kernel(const Grid3 gg, const double *__restrict__ ld, int64_t off1, int64_t off2,
+                                   double *__restrict__ x)
+{
+    const Geo g = make_geo(gg);
+    const int k2 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k1 = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k0 = blockIdx.z;
+    if (k2 >= g.ni[2] || k1 >= g.ni[1]) return;
+    const int k[3] = {k0, k1, k2};
+    const int64_t off[3] = {0, off1, off2};
+    double lam[3];
+    for (int s = 0; s < 3; ++s) lam[s] = g.act[s] ? ld[off[s] + k[s]] : 0.0;
+    double sym = 0.0;
+    for (int s = 0; s < 3; ++s)
+        for (int r = 0; r < 3; ++r)
+            if (r != s && g.act[s] && g.act[r]) {
+                const double hs2 = g.h[s] * g.h[s], hr2 = g.h[r] * g.h[r];
+                sym += (hs2 * hs2 / 240.0 + hs2 * hr2 / 144.0) * lam[s] * lam[s] * lam[r];
+            }
+    x[k0 * g.is[0] + (int64_t)k1 * g.is[1] + k2] *= sym;
+}
+
+// out += E on the layers (stage output only)
+__global__ void rhs6_e_scatter_kernel(const Grid3 gg, const double *__restrict__ E0, const double *__restrict__ E1,
+                                      const double *__restrict__ E2, double *__restrict__ out)
+{
+    const Geo g = make_geo(gg);
+    const int k2 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k1 = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k0 = blockIdx.z;
+    if (k2 >= g.ni[2] || k1 >= g.ni[1]) return;
+    const int n0 = g.ni[0], n1 = g.ni[1], n2 = g.ni[2];
+    const int j[3] = {g.act[0] ? k0 + 1 : 0, k1 + 1, k2 + 1};
+    double v = 0.0;
+    for (int s = 0; s < 3; ++s) {
+        const int dd = face_dist(g, s, j[s]);
+        if (dd > 2) continue;
+        const int sl = (j[s] <= g.M[s] / 2 ? 0 : 2) + (dd - 1);
+        if (s == 0) v = E0[((int64_t)sl * n1 + k1) * n2 + k2];
+        else if (s == 1) v = E1[((int64_t)sl * n0 + k0) * n2 + k2];
+        else v = E2[((int64_t)sl * n0 + k0) * n1 + k1];
+        break;
+    }
+    out[k0 * g.is[0] + (int64_t)k1 * g.is[1] + k2] += v;
+}
+
 // tabc = sc / lambda_c, tab4 = sc / Lambda4 on the mode grid (dense interior).
 __global__ void eigen_tables_kernel(const Grid3 gg, const double *lc, const double *ld, int64_t off1,
-                                    int64_t off2, double sc, double *tabc, double *tab4)
+                                    int64_t off2, double sc, double *tabc, double *tab4, double *tabR)
 {
     const Geo g = make_geo(gg);
     const int64_t total = (int64_t)g.ni[0] * g.ni[1] * g.ni[2];
@@ -301,6 +672,18 @@ __global__ void eigen_tables_kernel(const Grid3 gg, const double *lc, const doub
                     d += (g.h[s] * g.h[s] + g.h[r] * g.h[r]) / 12.0 * lam[s] * lam[r];
         tabc[t] = sc / c;
         tab4[t] = sc / d;
+        if (tabR) {
+            // tab4 * Lambda_R / Lambda4: maps u1's coefficients (tab4 * 4^d S gtilde)
+            // to those of the smoothing solve of R_spec
+            double sym = 0.0;
+            for (int s = 0; s < 3; ++s)
+                for (int r = 0; r < 3; ++r)
+                    if (r != s && g.act[s] && g.act[r]) {
+                        const double hs2 = g.h[s] * g.h[s], hr2 = g.h[r] * g.h[r];
+                        sym += (hs2 * hs2 / 240.0 + hs2 * hr2 / 144.0) * lam[s] * lam[s] * lam[r];
+                    }
+            tabR[t] = sc * sym / (d * d);
+        }
     }
 }
 
@@ -343,10 +726,10 @@ cudaError_t launch_gtilde_planes(const Grid3 &g, const StencilCoef &c, const dou
 
 cudaError_t launch_gtilde_expand(const Grid3 &g, const double *Q0, const double *Q1, const double *Q2,
                                  const double *sin4, const double *tab, const double *add, double *out,
-                                 cudaStream_t st)
+                                 cudaStream_t st, const double *tab2, const double *add2, double *out2, int fold)
 {
     gtilde_expand_kernel<<<grid3(g.n2 - 2, g.n1 - 2, g.d == 3 ? g.n0 - 2 : 1), dim3(32, 8), 0, st>>>(
-        g, Q0, Q1, Q2, sin4, tab, add, out);
+        g, Q0, Q1, Q2, sin4, tab, add, out, tab2, add2, out2, fold);
     return cudaGetLastError();
 }
 
@@ -379,13 +762,113 @@ cudaError_t launch_rhs6_extrap(const Grid3 &g, double *R, cudaStream_t st)
     return cudaGetLastError();
 }
 
+cudaError_t launch_rhs6_spectral(const Grid3 &g, const StencilCoef &c, const double *U, double *W, double *Rt,
+                                 double *E0, double *E1, double *E2, int kind, cudaStream_t st)
+{
+    if (kind == 0) {
+        // W of the odd continuation on the nodes within 7 of a face
+        const Shell sh = make_shell(g, 0, 0, 8);
+        rhs6_wband_kernel<<<grid_for(sh.count), 256, 0, st>>>(g, sh, c, U, W);
+    } else if (kind == 1) {
+        // the core nodes (indices 2..M-2) within 3 of the core's faces
+        const Shell sh = make_shell(g, 2, 4, 4);
+        rhs6_taps_kernel<<<grid_for(sh.count), 256, 0, st>>>(g, sh, c, U, W, Rt);
+    } else {
+        const int64_t n0 = g.d == 3 ? g.n0 - 2 : 1, n1 = g.n1 - 2, n2 = g.n2 - 2;
+        const int64_t total = 4 * ((g.d == 3 ? n1 * n2 : 0) + n0 * n2 + n0 * n1);
+        rhs6_e_kernel<<<grid_for(total), 256, 0, st>>>(g, c, U, W, Rt, E0, E1, E2);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_layers_combine(double *P0, int64_t pl0, double *P1, int64_t pl1, double *P2, int64_t pl2,
+                                  int nl, cudaStream_t st)
+{
+    layers_combine_kernel<<<grid_for((int64_t)nl * (pl0 + pl1 + pl2)), 256, 0, st>>>(P0, (int)pl0, P1, (int)pl1, P2,
+                                                                                   (int)pl2, nl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rhs6_e_expand(const Grid3 &g, const double *E0, const double *E1, const double *E2,
+                                 const double *sin4, const double *sin4b, const double *tab, double *out,
+                                 cudaStream_t st)
+{
+    rhs6_e_expand_kernel<<<grid3(g.n2 - 2, g.n1 - 2, g.d == 3 ? g.n0 - 2 : 1), dim3(32, 8), 0, st>>>(
+        g, E0, E1, E2, sin4, sin4b, tab, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rhs6_symbol(const Grid3 &g, const double *ld, int64_t off1, int64_t off2, double *x,
+                               cudaStream_t st)
+{
+    rhs6_symbol_kernel<<<grid3(g.n2 - 2, g.n1 - 2, g.d == 3 ? g.n0 - 2 : 1), dim3(32, 8), 0, st>>>(
+        g, ld, off1, off2, x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rhs6_e_scatter(const Grid3 &g, const double *E0, const double *E1, const double *E2,
+                                  double *out, cudaStream_t st)
+{
+    rhs6_e_scatter_kernel<<<grid3(g.n2 - 2, g.n1 - 2, g.d == 3 ? g.n0 - 2 : 1), dim3(32, 8), 0, st>>>(
+        g, E0, E1, E2, out);
+    return cudaGetLastError();
+}
+
 namespace {
+// One block covers 32 consecutive nodes along axis 2 (one warp each) of 16 rows
+// (axis 1) of one slice (axis 0).  The flags are only ever set to 1, so the stores
+// may race; they are reduced within the block first so that few of them hit the
+// same cache lines.
+constexpr int SF_ROWS = 16;
+__global__ void __launch_bounds__(32 * SF_ROWS) support_flags_kernel(const Grid3 gg, const double *__restrict__ r,
+                                                                   int64_t s0, int64_t s1, int64_t s2, int *row2,
+                                                                   int *row1, int *sl0, int *sl1, int *sl2)
+{
+    __shared__ unsigned colmask[SF_ROWS];
+    __shared__ int rowany[SF_ROWS];
+    const Geo g = make_geo(gg);
+    const int lane = threadIdx.x, wy = threadIdx.y;
+    const int k2 = blockIdx.x * 32 + lane;
+    const int k1 = blockIdx.y * SF_ROWS + wy;
+    const int k0 = blockIdx.z;
+    bool nz = false;
+    if (k2 < g.ni[2] && k1 < g.ni[1]) nz = r[k0 * s0 + (int64_t)k1 * s1 + (int64_t)k2 * s2] != 0.0;
+    const unsigned m = __ballot_sync(0xffffffffu, nz);
+    if (lane == 0) {
+        colmask[wy] = m;
+        rowany[wy] = m != 0u;
+        if (m) row2[(int64_t)k0 * g.ni[1] + k1] = 1;
+    }
+    __syncthreads();
+    if (wy == 0) {
+        unsigned c = 0;
+        for (int j = 0; j < SF_ROWS; ++j) c |= colmask[j];
+        const bool col = (c >> lane) & 1u;
+        if (col) {
+            row1[(int64_t)k0 * g.ni[2] + k2] = 1;
+            sl2[k2] = 1;
+        }
+        const bool row = lane < SF_ROWS && rowany[lane];
+        if (row) sl1[blockIdx.y * SF_ROWS + lane] = 1;
+        if (lane == 0 && c) sl0[k0] = 1;
+    }
+}
+
 __global__ void to_dd_kernel(const double *x, ddr *y, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = dd_from(x[i]);
 }
 }  // namespace
+
+cudaError_t launch_support_flags(const Grid3 &g, const double *rho_int, int64_t s0, int64_t s1, int64_t s2,
+                                 int *row2, int *row1, int *sl0, int *sl1, int *sl2, cudaStream_t st)
+{
+    const dim3 grid((g.n2 - 2 + 31) / 32, (g.n1 - 2 + SF_ROWS - 1) / SF_ROWS, g.d == 3 ? g.n0 - 2 : 1);
+    support_flags_kernel<<<grid, dim3(32, SF_ROWS), 0, st>>>(
+        g, rho_int, s0, s1, s2, row2, row1, sl0, sl1, sl2);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_to_dd(const double *x, ddr *y, int64_t n, cudaStream_t st)
 {
@@ -394,10 +877,10 @@ cudaError_t launch_to_dd(const double *x, ddr *y, int64_t n, cudaStream_t st)
 }
 
 cudaError_t launch_eigen_tables(const Grid3 &g, const double *lc, const double *ld, int64_t off1,
-                                int64_t off2, double sc, double *tabc, double *tab4, cudaStream_t st)
+                                int64_t off2, double sc, double *tabc, double *tab4, double *tabR, cudaStream_t st)
 {
     const int64_t total = (int64_t)(g.d == 3 ? g.n0 - 2 : 1) * (g.n1 - 2) * (g.n2 - 2);
-    eigen_tables_kernel<<<grid_for(total), 256, 0, st>>>(g, lc, ld, off1, off2, sc, tabc, tab4);
+    eigen_tables_kernel<<<grid_for(total), 256, 0, st>>>(g, lc, ld, off1, off2, sc, tabc, tab4, tabR);
     return cudaGetLastError();
 }
 

@@ -18,7 +18,7 @@ import pytest
 
 import workloads as w
 from oracle import dst as odst, greens as ogreens, harmonic as oharm, solve as osolve
-from tests.gpu_util import device, rel_max, run_stage, to_dev
+from tests.gpu_util import device, r_amplification, rel_max, run_stage, to_dev
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
@@ -38,6 +38,12 @@ CASES = [
                               dict(seed=7))),
     ("2d_97x49", w.Problem("e", (97, 49), (-1.0, -0.7), (1.0, 0.8), "bump",
                            dict(centre=(0.05, 0.0), eps=0.6, p=8))),
+    # scattered point values: most lines / slices exactly zero, some blocks of
+    # lines partly zero (the zero-line and zero-slice skipping of section 4's stages)
+    ("3d_65x33x129_points", w.Problem("f", (65, 33, 129), (0.0, 0.0, 0.0), (1.0, 1.0, 2.0), "points",
+                                      dict(seed=11, count=9))),
+    ("2d_65x33_points", w.Problem("g", (65, 33), (0.0, 0.0), (1.0, 0.5), "points",
+                                  dict(seed=12, count=4))),
 ]
 
 
@@ -47,18 +53,6 @@ def idp():
     device()
     m.library()
     return m
-
-
-def _r_amplification(h):
-    """A = sum over ordered pairs s != r of c_sr * 64 / (h_s^4 h_r^2)."""
-    d = len(h)
-    a = 0.0
-    for s in range(d):
-        for r in range(d):
-            if r != s:
-                c = h[s] ** 4 / 240 + h[s] ** 2 * h[r] ** 2 / 144
-                a += c * 64 / (h[s] ** 4 * h[r] ** 2)
-    return a
 
 
 def _oracle_parts(prob, order):
@@ -95,7 +89,7 @@ def test_components_match_oracle(idp, name, prob, order, precision):
     du = np.abs(u1 - ref["u1"]).max() + 4 * np.finfo(np.float64).eps * np.abs(ref["u1"]).max()
     if order == 6:
         R = run_stage(idp, plan, idp.IDP_STAGE_R, r, ishape)
-        amp = _r_amplification(prob.h)
+        amp = r_amplification(prob.h)
         core = tuple(slice(1, -1) for _ in ishape)
         assert np.abs(R - ref["R"])[core].max() <= amp * du
         assert np.abs(R - ref["R"]).max() <= amp * 15 ** prob.d * du

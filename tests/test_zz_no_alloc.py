@@ -2,9 +2,12 @@
 
 It is meant for callers that cannot let the library allocate device memory
 (their own pool allocator owns the GPU's memory, or their loop cannot pay
-for cudaMalloc's synchronisation).  Through the C ABI, its R must equal the
-R of the plan-based solver (IDP_STAGE_R) within the parity tolerance, on
-consecutive calls that share the library's fixed scratch.  This file is
+for cudaMalloc's synchronisation).  Through the C ABI, on the u1 of the
+plan-based solver (IDP_STAGE_U1), its R must equal the oracle's stencil R of
+the same u1 within the rounding of a sixth difference (the propagation bound of
+the parity tests with du = 4 eps max|u1|), and consecutive calls that share the
+library's fixed scratch must give the same bits.  (The plan's own R, computed
+in spectral form, is held to the oracle in test_gpu_parity.py.)  This file is
 collected last so that a run stopping at the first failure has already run
 every other test.
 """
@@ -14,10 +17,10 @@ import numpy as np
 import pytest
 
 import workloads as w
-from tests.gpu_util import device, rel_max, run_stage, to_dev
+from oracle import harmonic as oharm
+from tests.gpu_util import device, r_amplification, run_stage, to_dev
 
 pytestmark = pytest.mark.gpu
-TOL = 1e-12
 
 
 @pytest.fixture(scope="module")
@@ -29,12 +32,11 @@ def idp():
 
 
 def _reference(idp, prob):
-    """u1 and R from the plan-based entry points."""
+    """u1 from the plan-based entry point and the oracle's R of that u1."""
     plan = idp.create_plan(prob.d, prob.n, prob.h, 6)
     r = to_dev(prob.rho())
     u1 = run_stage(idp, plan, idp.IDP_STAGE_U1, r, prob.n)
-    R = run_stage(idp, plan, idp.IDP_STAGE_R, r, tuple(k - 2 for k in prob.n))
-    return u1, R
+    return u1, oharm.rhs6(u1, prob.h)
 
 
 def test_noalloc_rhs_matches_plan_rhs_on_consecutive_calls(idp):
@@ -43,6 +45,7 @@ def test_noalloc_rhs_matches_plan_rhs_on_consecutive_calls(idp):
              w.c1_2d(65),
              w.c2_3d(65)]
     refs = [_reference(idp, p) for p in probs]
+    first = {}
     # two calls in a row per problem, problems interleaved, so each call starts
     # from scratch contents left by a different problem
     for rep in range(2):
@@ -54,7 +57,15 @@ def test_noalloc_rhs_matches_plan_rhs_on_consecutive_calls(idp):
             torch.cuda.synchronize()
             got = out.cpu().numpy()
             assert np.all(np.isfinite(got))
-            assert rel_max(got, Rref) < TOL, (rep, p.name)
+            du = 4 * np.finfo(np.float64).eps * np.abs(u1).max()
+            amp = r_amplification(p.h)
+            core = tuple(slice(1, -1) for _ in got.shape)
+            assert np.abs(got - Rref)[core].max() <= amp * du, (rep, p.name)
+            assert np.abs(got - Rref).max() <= amp * 15 ** p.d * du, (rep, p.name)
+            if rep == 0:
+                first[p.name] = got
+            else:
+                assert np.array_equal(got, first[p.name]), p.name
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch(idp):

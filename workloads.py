@@ -17,6 +17,10 @@ Densities:
     that vanishes within 0.15 of every box edge (a smooth, mixed-sign density
     whose support keeps the distance from the boundary the method assumes,
     section 2).
+  * ``points``: seeded random values on a few scattered interior nodes, zero
+    elsewhere (most lines and slices of the array are then exactly zero, some
+    are not: the case the solver's zero-line and zero-slice skipping must
+    get right).
 """
 from __future__ import annotations
 
@@ -38,7 +42,7 @@ class Problem:
     n: tuple            # node counts per array axis (includes boundary nodes)
     lo: tuple           # lower box corner per axis
     hi: tuple           # upper box corner per axis
-    density: str        # "bump" or "gauss"
+    density: str        # "bump", "gauss", "random" or "points"
     params: dict        # density parameters
 
     @property
@@ -69,6 +73,8 @@ class Problem:
             r = gauss_sum(self.coords(), self.lo, self.hi, **self.params)
         elif self.density == "random":
             r = random_interior(self.n, **self.params)
+        elif self.density == "points":
+            r = point_sources(self.n, **self.params)
         else:
             raise ValueError(self.density)
         return np.ascontiguousarray(r, dtype=np.float64)
@@ -151,6 +157,15 @@ def random_interior(n, seed, margin=0):
     out = np.zeros(n, dtype=np.float64)
     sl = tuple(slice(1 + margin, k - 1 - margin) for k in n)
     out[sl] = rng.uniform(-1.0, 1.0, size=out[sl].shape)
+    return out
+
+
+def point_sources(n, seed, count):
+    """``count`` seeded uniform(-1, 1) values at seeded random interior nodes."""
+    rng = np.random.default_rng(seed)
+    out = np.zeros(n, dtype=np.float64)
+    idx = tuple(rng.integers(1, k - 1, size=count) for k in n)
+    out[idx] = rng.uniform(-1.0, 1.0, size=count)
     return out
 
 
