@@ -168,8 +168,9 @@ int idp_profile_solve(idp_plan plan, const double *rho, double *phi, void *strea
 
 /* Settings chosen by IDP_KEY_AUTOTUNE (or the defaults): out[0] = 1 if tuned,
  * out[1] = mixed path (0 tensor-core matrix, 1 double-float FFT), out[2..4] =
- * slice chunks of the face passes of axes 0..2, out[5..7] = slices per chunk. */
-int idp_plan_tuning(idp_plan plan, int64_t out[8]);
+ * slice chunks of the face passes of axes 0..2, out[5..7] = slices per chunk,
+ * out[8] = lines per block of the full-volume sine passes (0 = by size). */
+int idp_plan_tuning(idp_plan plan, int64_t out[9]);
 
 /* Number of kernel launches one solve of this plan queues (valid after the
  * first solve). */

@@ -174,10 +174,10 @@ def plan_info(plan: Plan):
 
 
 def plan_tuning(plan: Plan):
-    out = (_i64 * 8)()
+    out = (_i64 * 9)()
     _check(library().idp_plan_tuning(plan.handle, out), "idp_plan_tuning")
     return dict(tuned=bool(out[0]), mixed_path=("df32_fft" if out[1] else "tensor_matrix"),
-                face_chunks=list(out[2:5]), slices_per_chunk=list(out[5:8]))
+                face_chunks=list(out[2:5]), slices_per_chunk=list(out[5:8]), dst_lines=int(out[8]))
 
 
 def destroy_plan(plan: Plan):

@@ -72,6 +72,15 @@ struct Tabs<ddr> {
     static __device__ __forceinline__ ddr sin2(const DstPass &a, int j) { return a.sin2d[j]; }
 };
 
+// strides of a view along the line (u, v) coordinates and the element index e
+// of a pass along `axis` (u, v = the other two axes in order)
+__device__ __forceinline__ void view_strides(const View3 &w, int axis, int64_t &su, int64_t &sv, int64_t &se)
+{
+    if (axis == 2) { su = w.s0; sv = w.s1; se = w.s2; }
+    else if (axis == 1) { su = w.s0; sv = w.s2; se = w.s1; }
+    else { su = w.s1; sv = w.s2; se = w.s0; }
+}
+
 template <class R, int K, int LBO>
 __global__ void __launch_bounds__(NT) dst_pass_kernel(const DstPass a)
 {
@@ -83,29 +92,10 @@ __global__ void __launch_bounds__(NT) dst_pass_kernel(const DstPass a)
     Cx *bufA = reinterpret_cast<Cx *>(smem_raw);   // LB * K complex
     Cx *bufB = bufA + LB * K;                      // LB * K complex
 
-    // line (u, v) coordinates: the two non-transform axes, v fastest
-    int nv, nu;
-    int64_t isu, isv, ise, osu, osv, ose, asu = 0, asv = 0, ase = 0, tsu, tsv, tse;
-    const int64_t t0 = (int64_t)a.n1 * a.n2, t1 = a.n2;
-    if (a.axis == 2) {
-        nu = a.n0; nv = a.n1;
-        isu = a.in.s0; isv = a.in.s1; ise = a.in.s2;
-        osu = a.out.s0; osv = a.out.s1; ose = a.out.s2;
-        asu = a.add.s0; asv = a.add.s1; ase = a.add.s2;
-        tsu = t0; tsv = t1; tse = 1;
-    } else if (a.axis == 1) {
-        nu = a.n0; nv = a.n2;
-        isu = a.in.s0; isv = a.in.s2; ise = a.in.s1;
-        osu = a.out.s0; osv = a.out.s2; ose = a.out.s1;
-        asu = a.add.s0; asv = a.add.s2; ase = a.add.s1;
-        tsu = t0; tsv = 1; tse = t1;
-    } else {
-        nu = a.n1; nv = a.n2;
-        isu = a.in.s1; isv = a.in.s2; ise = a.in.s0;
-        osu = a.out.s1; osv = a.out.s2; ose = a.out.s0;
-        asu = a.add.s1; asv = a.add.s2; ase = a.add.s0;
-        tsu = t1; tsv = 1; tse = t0;
-    }
+    // line (u, v) coordinates: the two non-transform axes, v fastest.  The
+    // strides are taken from the parameters where they are used, so that none
+    // of them stays live across the FFT.
+    const int nv = a.axis == 2 ? a.n1 : a.n2;
     const int u = blockIdx.y;
     const int v0 = blockIdx.x * LB;
     const int nl = min(LB, nv - v0);
@@ -113,6 +103,8 @@ __global__ void __launch_bounds__(NT) dst_pass_kernel(const DstPass a)
 
     // 1. load raw lines into bufB viewed as R[LB][M] (entries 0..N-1)
     R *raw = reinterpret_cast<R *>(bufB);
+    int64_t isu, isv, ise;
+    view_strides(a.in, a.axis, isu, isv, ise);
     const int64_t inb = (int64_t)u * isu + (int64_t)v0 * isv;
     for (int f = threadIdx.x; f < LB * N; f += NT) {
         int l, e;
@@ -217,6 +209,14 @@ __global__ void __launch_bounds__(NT) dst_pass_kernel(const DstPass a)
     __syncthreads();
 
     // 6. epilogue and store
+    int64_t osu, osv, ose, asu, asv, ase, tsu, tsv, tse;
+    view_strides(a.out, a.axis, osu, osv, ose);
+    view_strides(a.add, a.axis, asu, asv, ase);
+    {
+        // the tables are dense interior arrays n0 x n1 x n2
+        const View3 tv{nullptr, (int64_t)a.n1 * a.n2, a.n2, 1};
+        view_strides(tv, a.axis, tsu, tsv, tse);
+    }
     const int64_t outb = (int64_t)u * osu + (int64_t)v0 * osv;
     const int64_t tabb = (int64_t)u * tsu + (int64_t)v0 * tsv;
     const int64_t addb = (int64_t)u * asu + (int64_t)v0 * asv;
@@ -263,7 +263,7 @@ cudaError_t launch_k(const DstPass &a, cudaStream_t st)
         // a launch of less than two blocks per SM (the layer transforms) runs
         // faster on more, smaller blocks
         const int64_t blocks = (int64_t)nu * ((nv + DstCfg<K>::LB - 1) / DstCfg<K>::LB);
-        if (blocks < 2 * 152) return launch_lb<R, K, 8>(a, nu, nv, st);
+        if (a.lines == 8 || blocks < 2 * 152) return launch_lb<R, K, 8>(a, nu, nv, st);
     }
     return launch_lb<R, K, 0>(a, nu, nv, st);
 }

@@ -61,6 +61,7 @@ struct DstPass {
     const TwD *twd;
     const ddc *halfd;
     const ddr *sin2d;
+    int lines;   // lines per block: 0 = by size (8 for launches of < 2 blocks per SM), 8 = always 8
 };
 
 cudaError_t launch_dst_pass(const DstPass &a, cudaStream_t st);
@@ -190,7 +191,7 @@ StencilCoef make_stencil_coef(const Grid3 &g);
 cudaError_t launch_gtilde_planes(const Grid3 &g, const StencilCoef &c, const double *U, double *Q0, double *Q1,
                                  double *Q2, cudaStream_t st);
 // out = tab * (4^d S gtilde) (+ add) from the transformed, combined parts; if out2
-// is given, also out2 = (tab2 (+ tab if fold)) * (4^d S gtilde) + add2
+// is given, also out2 = (tab2 (- tab unless fold)) * (4^d S gtilde) + add2
 cudaError_t launch_gtilde_expand(const Grid3 &g, const double *Q0, const double *Q1, const double *Q2,
                                  const double *sin4, const double *tab, const double *add, double *out,
                                  cudaStream_t st, const double *tab2 = nullptr, const double *add2 = nullptr,
@@ -216,8 +217,8 @@ cudaError_t launch_support_flags(const Grid3 &g, const double *rho_int, int64_t 
                                  int *row2, int *row1, int *sl0, int *sl1, int *sl2, cudaStream_t st);
 // y = double-float pairs of x (set-up only)
 cudaError_t launch_to_dd(const double *x, ddr *y, int64_t n, cudaStream_t st);
-// tabR (optional) = tab4 * Lambda_R / Lambda4 with Lambda_R the symbol of the
-// 6th-order right-hand side.
+// tabR (optional) = tab4 * Lambda_R / Lambda4 + tab4 with Lambda_R the symbol of
+// the 6th-order right-hand side.
 cudaError_t launch_eigen_tables(const Grid3 &g, const double *lc, const double *ld, int64_t off1,
                                 int64_t off2, double sc, double *tabc, double *tab4, double *tabR, cudaStream_t st);
 // The 6th-order right-hand side in spectral form (stencil.cu): kind 0: W of the

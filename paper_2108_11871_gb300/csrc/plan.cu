@@ -147,7 +147,7 @@ struct idp_plan_s {
     double *tabc = nullptr, *tab4 = nullptr;
     double *tabc2 = nullptr;   // -2 * tabc (forward transform of rho continued from T0)
     double *Q0 = nullptr, *Q1 = nullptr, *Q2 = nullptr, *sin4 = nullptr;   // gtilde parts
-    double *tabR = nullptr;    // tab4 * Lambda_R / Lambda4 (6th-order right-hand side of R_spec)
+    double *tabR = nullptr;    // tab4 * Lambda_R / Lambda4 + tab4 (R_spec's smoothing solve plus u1)
     double *E0 = nullptr, *E1 = nullptr, *E2 = nullptr, *sin4b = nullptr;   // layers of E = R - R_spec
     double *ld = nullptr;      // per-axis eigenvalues of D2_s (axis s at ldoff[s])
     int64_t ldoff[3] = {0, 0, 0};
@@ -159,6 +159,7 @@ struct idp_plan_s {
     ddr *khatd[3] = {nullptr, nullptr, nullptr};   // double-float copies (precision DF32)
     int64_t khat_n[3] = {0, 0, 0};
     int nchunk[3] = {1, 1, 1}, pchunk[3] = {1, 1, 1};
+    int dst_lines = 0;                // lines per block of the full-volume sine passes (0 = default)
 
     // mixed precision (IDP_KEY_PRECISION = 1): sine passes on the tensor cores
     int mixed = 0;
@@ -443,6 +444,7 @@ int transform(idp_plan p, View3 in, double *work, View3 out, const double *tab, 
     for (int q = 0; q < na; ++q) {
         const int s = axes[q];
         DstPass a{};
+        a.lines = p->dst_lines;
         a.in = (q == 0) ? in : dense(p, work);
         a.out = (q == na - 1) ? out : dense(p, work);
         a.add = (q == na - 1) ? add : View3{nullptr, 0, 0, 0};
@@ -1062,6 +1064,21 @@ int autotune(idp_plan p)
             p->pchunk[a_] = best_p;
         }
     }
+    if (!rc) {
+        // lines per block of the full-volume sine passes: the default (up to 32
+        // lines, one wave of large blocks) or 8 (more, smaller blocks whose load,
+        // FFT and store phases overlap)
+        const View3 none{nullptr, 0, 0, 0};
+        float tl[2];
+        const int opts[2] = {0, 8};
+        for (int i = 0; i < 2 && !rc; ++i) {
+            p->dst_lines = opts[i];
+            tl[i] = timed([&]() -> int {
+                return transform(p, dense(p, p->C), p->C, dense(p, p->C), nullptr, none, false, st);
+            });
+        }
+        p->dst_lines = (tl[1] < tl[0]) ? 8 : 0;
+    }
     if (!rc && p->mixed == IDP_PRECISION_MIXED_BF16X3) {
         const View3 none{nullptr, 0, 0, 0};
         float tm[2];
@@ -1442,7 +1459,7 @@ const char *idp_strerror(int code)
 
 const char *idp_last_cuda_error(void) { return g_cuda_err; }
 
-int idp_plan_tuning(idp_plan p, int64_t out[8])
+int idp_plan_tuning(idp_plan p, int64_t out[9])
 {
     if (!p || !out) return IDP_EINVAL;
     out[0] = p->tuned;
@@ -1451,6 +1468,7 @@ int idp_plan_tuning(idp_plan p, int64_t out[8])
         out[2 + a] = p->nchunk[a];
         out[5 + a] = p->pchunk[a];
     }
+    out[8] = p->dst_lines;
     return IDP_OK;
 }
 

@@ -120,7 +120,7 @@ __global__ void gtilde_planes_kernel(const Grid3 gg, const StencilCoef c, const 
 // Forward sine transform of gtilde from the transformed, combined parts
 // (4^{d-1} S of each part, then (a + b, a - b) per pair of faces):
 //   val(k) = sum_s sin4_s(k_s) Qs[k_s odd](k_other),  sin4_s(k) = 4 sin(pi (k+1)/M_s).
-// out = tab * val (+ add); if out2: out2 = (tab2 (+ tab if fold)) * val + add2.
+// out = tab * val (+ add); if out2: out2 = (tab2 (- tab unless fold)) * val + add2.
 __global__ void gtilde_expand_kernel(const Grid3 gg, const double *__restrict__ Q0, const double *__restrict__ Q1,
                                      const double *__restrict__ Q2, const double *__restrict__ sin4,
                                      const double *__restrict__ tab, const double *add, double *out,
@@ -140,7 +140,8 @@ __global__ void gtilde_expand_kernel(const Grid3 gg, const double *__restrict__ 
     const int64_t t = k0 * g.is[0] + (int64_t)k1 * g.is[1] + k2;
     const double tb = tab[t];
     out[t] = add ? fma(tb, v, add[t]) : tb * v;
-    if (out2) out2[t] = fma(fold ? tab2[t] + tb : tab2[t], v, add2[t]);
+    // tab2 holds tabR + tab4 (u1 folded in); without fold, tabR = tab2 - tab4
+    if (out2) out2[t] = fma(fold ? tab2[t] : tab2[t] - tb, v, add2[t]);
 }
 
 // gtilde as a dense interior array from its parts (for the stage output).
@@ -389,18 +390,24 @@ __global__ void rhs6_extrap_kernel(const Grid3 gg, double *R)
 // u-weights of the fourth difference
 __device__ __constant__ double kD4[5] = {1.0, -4.0, 6.0, -4.0, 1.0};
 
+// x with its sign flipped when neg (an integer operation: FP64 issue is scarce)
+__device__ __forceinline__ double flip_if(double x, bool neg)
+{
+    return __longlong_as_double(__double_as_longlong(x) ^ ((long long)neg << 63));
+}
+
 // W of the odd continuation (band array `W`, odd = 1) at node j shifted by o
 // along s: reflected (with a sign change) through the faces of axis s.
 __device__ __forceinline__ double w_odd_at(const Geo &g, const double *__restrict__ W, int64_t nodes, int s,
                                            const int j[3], int o)
 {
     int q = j[s] + o;
-    double sg = 1.0;
-    if (q < 0) { q = -q; sg = -1.0; }
-    else if (q > g.M[s]) { q = 2 * g.M[s] - q; sg = -1.0; }
+    bool neg = false;
+    if (q < 0) { q = -q; neg = true; }
+    else if (q > g.M[s]) { q = 2 * g.M[s] - q; neg = true; }
     int jj[3] = {j[0], j[1], j[2]};
     jj[s] = q;
-    return sg * W[(int64_t)s * nodes + jj[0] * g.ns[0] + (int64_t)jj[1] * g.ns[1] + jj[2]];
+    return flip_if(W[(int64_t)s * nodes + jj[0] * g.ns[0] + (int64_t)jj[1] * g.ns[1] + jj[2]], neg);
 }
 
 // W_s at the face node of axis s nearest to j (j at distance 2 from it), from
@@ -418,14 +425,39 @@ __device__ __forceinline__ double w_face(const Geo &g, const StencilCoef &c, con
     return w;
 }
 
+// [1 -4 6 -4 1] applied to (w(-2), w(-1), w(0), w(1), w(2)): 2 additions, 2 FMAs
+__device__ __forceinline__ double d4(double wm2, double wm1, double w0, double wp1, double wp2)
+{
+    return fma(6.0, w0, fma(-4.0, wm1 + wp1, wm2 + wp2));
+}
+
 // R_spec at node j (any interior node) from the band array of W of the odd continuation
 __device__ __forceinline__ double r_spec_at(const Geo &g, const double *__restrict__ W, int64_t nodes,
                                             const int j[3])
 {
     double acc = 0.0;
+#pragma unroll
     for (int s = 0; s < 3; ++s) {
         if (!g.act[s]) continue;
-        for (int o = -2; o <= 2; ++o) acc = fma(kD4[o + 2], w_odd_at(g, W, nodes, s, j, o), acc);
+        acc += d4(w_odd_at(g, W, nodes, s, j, -2), w_odd_at(g, W, nodes, s, j, -1), w_odd_at(g, W, nodes, s, j, 0),
+                  w_odd_at(g, W, nodes, s, j, 1), w_odd_at(g, W, nodes, s, j, 2));
+    }
+    return acc;
+}
+
+// The same at a node whose stencil stays inside the grid along every axis
+// (all active distances >= 2): no reflections
+__device__ __forceinline__ double r_spec_inside(const Geo &g, const double *__restrict__ W, int64_t nodes,
+                                                const int j[3])
+{
+    const int64_t t = j[0] * g.ns[0] + (int64_t)j[1] * g.ns[1] + j[2];
+    double acc = 0.0;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        if (!g.act[s]) continue;
+        const double *w = W + (int64_t)s * nodes + t;
+        const int64_t st = g.ns[s];
+        acc += d4(w[-2 * st], w[-st], w[0], w[st], w[2 * st]);
     }
     return acc;
 }
@@ -434,7 +466,7 @@ __device__ __forceinline__ double r_spec_at(const Geo &g, const double *__restri
 __device__ __forceinline__ double r_core_at(const Geo &g, const StencilCoef &c, const double *__restrict__ U,
                                             const double *__restrict__ W, int64_t nodes, const int j[3])
 {
-    double acc = r_spec_at(g, W, nodes, j);
+    double acc = r_spec_inside(g, W, nodes, j);
 #pragma unroll
     for (int s = 0; s < 3; ++s)
         if (face_dist(g, s, j[s]) == 2) acc += w_face(g, c, U, s, j);
@@ -512,16 +544,24 @@ __global__ void rhs6_e_kernel(const Grid3 gg, const StencilCoef c, const double 
                 const int f1 = d1 == 1 ? (j1 == 1 ? 1 : g.M[1] - 3) : j1 - 1;
                 const int f2 = d2 == 1 ? (j2 == 1 ? 1 : g.M[2] - 3) : j2 - 1;
                 const int st0 = j0 == 1 ? 1 : -1, st1 = j1 == 1 ? 1 : -1, st2 = j2 == 1 ? 1 : -1;
-                double acc = 0.0;
-                for (int q0 = 0; q0 < nt0; ++q0) {
-                    const double w0 = nt0 == 4 ? extrap_w(q0) : 1.0;
-                    const int64_t c0 = (int64_t)(f0 + q0 * st0) * g.is[0];
-                    for (int q1 = 0; q1 < nt1; ++q1) {
-                        const double w1 = nt1 == 4 ? w0 * extrap_w(q1) : w0;
-                        const int64_t c1 = c0 + (int64_t)(f1 + q1 * st1) * g.is[1];
-                        for (int q2 = 0; q2 < nt2; ++q2) {
-                            const double w2 = nt2 == 4 ? w1 * extrap_w(q2) : w1;
-                            acc = fma(w2, Rt[c1 + f2 + q2 * st2], acc);
+                double acc;
+                if (nt0 + nt1 + nt2 == 6) {
+                    // one axis: 4 (R_2 + R_4) - 6 R_3 - R_5 (2 FMAs, 1 addition)
+                    const int64_t base = (int64_t)f0 * g.is[0] + (int64_t)f1 * g.is[1] + f2;
+                    const int64_t step = nt0 == 4 ? st0 * g.is[0] : nt1 == 4 ? st1 * g.is[1] : st2;
+                    acc = fma(4.0, Rt[base] + Rt[base + 2 * step], fma(-6.0, Rt[base + step], -Rt[base + 3 * step]));
+                } else {
+                    acc = 0.0;
+                    for (int q0 = 0; q0 < nt0; ++q0) {
+                        const double w0 = nt0 == 4 ? extrap_w(q0) : 1.0;
+                        const int64_t c0 = (int64_t)(f0 + q0 * st0) * g.is[0];
+                        for (int q1 = 0; q1 < nt1; ++q1) {
+                            const double w1 = nt1 == 4 ? w0 * extrap_w(q1) : w0;
+                            const int64_t c1 = c0 + (int64_t)(f1 + q1 * st1) * g.is[1];
+                            for (int q2 = 0; q2 < nt2; ++q2) {
+                                const double w2 = nt2 == 4 ? w1 * extrap_w(q2) : w1;
+                                acc = fma(w2, Rt[c1 + f2 + q2 * st2], acc);
+                            }
                         }
                     }
                 }
@@ -673,8 +713,9 @@ __global__ void eigen_tables_kernel(const Grid3 gg, const double *lc, const doub
         tabc[t] = sc / c;
         tab4[t] = sc / d;
         if (tabR) {
-            // tab4 * Lambda_R / Lambda4: maps u1's coefficients (tab4 * 4^d S gtilde)
-            // to those of the smoothing solve of R_spec
+            // tab4 * Lambda_R / Lambda4 maps u1's coefficients (tab4 * 4^d S gtilde)
+            // to those of the smoothing solve of R_spec; tab4 is added so that one
+            // table also carries u1 itself into the final transform
             double sym = 0.0;
             for (int s = 0; s < 3; ++s)
                 for (int r = 0; r < 3; ++r)
@@ -682,7 +723,7 @@ __global__ void eigen_tables_kernel(const Grid3 gg, const double *lc, const doub
                         const double hs2 = g.h[s] * g.h[s], hr2 = g.h[r] * g.h[r];
                         sym += (hs2 * hs2 / 240.0 + hs2 * hr2 / 144.0) * lam[s] * lam[s] * lam[r];
                     }
-            tabR[t] = sc * sym / (d * d);
+            tabR[t] = sc * sym / (d * d) + sc / d;
         }
     }
 }
@@ -815,42 +856,53 @@ cudaError_t launch_rhs6_e_scatter(const Grid3 &g, const double *E0, const double
 }
 
 namespace {
-// One block covers 32 consecutive nodes along axis 2 (one warp each) of 16 rows
-// (axis 1) of one slice (axis 0).  The flags are only ever set to 1, so the stores
-// may race; they are reduced within the block first so that few of them hit the
+// One block covers 32 consecutive nodes along axis 2 of SF_ROWS rows (axis 1)
+// of one slice (axis 0); each of its 8 warps reads SF_ROWS / 8 rows, with all
+// loads in flight at once.  The flags are only ever set to 1, so the stores may
+// race; they are reduced within the block first so that few of them hit the
 // same cache lines.
-constexpr int SF_ROWS = 16;
-__global__ void __launch_bounds__(32 * SF_ROWS) support_flags_kernel(const Grid3 gg, const double *__restrict__ r,
-                                                                   int64_t s0, int64_t s1, int64_t s2, int *row2,
-                                                                   int *row1, int *sl0, int *sl1, int *sl2)
+constexpr int SF_ROWS = 32, SF_WARPS = 8, SF_PER = SF_ROWS / SF_WARPS;
+__global__ void __launch_bounds__(32 * SF_WARPS) support_flags_kernel(const Grid3 gg, const double *__restrict__ r,
+                                                                    int64_t s0, int64_t s1, int64_t s2, int *row2,
+                                                                    int *row1, int *sl0, int *sl1, int *sl2)
 {
     __shared__ unsigned colmask[SF_ROWS];
-    __shared__ int rowany[SF_ROWS];
     const Geo g = make_geo(gg);
     const int lane = threadIdx.x, wy = threadIdx.y;
     const int k2 = blockIdx.x * 32 + lane;
-    const int k1 = blockIdx.y * SF_ROWS + wy;
     const int k0 = blockIdx.z;
-    bool nz = false;
-    if (k2 < g.ni[2] && k1 < g.ni[1]) nz = r[k0 * s0 + (int64_t)k1 * s1 + (int64_t)k2 * s2] != 0.0;
-    const unsigned m = __ballot_sync(0xffffffffu, nz);
-    if (lane == 0) {
-        colmask[wy] = m;
-        rowany[wy] = m != 0u;
-        if (m) row2[(int64_t)k0 * g.ni[1] + k1] = 1;
+    long long bits[SF_PER];
+#pragma unroll
+    for (int i = 0; i < SF_PER; ++i) {
+        const int k1 = blockIdx.y * SF_ROWS + wy + SF_WARPS * i;
+        bits[i] = 0;
+        if (k2 < g.ni[2] && k1 < g.ni[1])
+            bits[i] = __double_as_longlong(r[k0 * s0 + (int64_t)k1 * s1 + (int64_t)k2 * s2]);
+    }
+#pragma unroll
+    for (int i = 0; i < SF_PER; ++i) {
+        // zero test on the bits (+0 and -0 are zero), off the FP64 pipe
+        const unsigned m = __ballot_sync(0xffffffffu, (bits[i] << 1) != 0);
+        const int row = wy + SF_WARPS * i;
+        if (lane == 0) {
+            colmask[row] = m;
+            if (m) row2[(int64_t)k0 * g.ni[1] + blockIdx.y * SF_ROWS + row] = 1;
+        }
     }
     __syncthreads();
     if (wy == 0) {
+        // a flag is read before it is set: the slice flags are shared by many
+        // blocks, and a store to a line that many SMs write is slow (a stale 0
+        // only costs one more store)
         unsigned c = 0;
         for (int j = 0; j < SF_ROWS; ++j) c |= colmask[j];
-        const bool col = (c >> lane) & 1u;
-        if (col) {
-            row1[(int64_t)k0 * g.ni[2] + k2] = 1;
-            sl2[k2] = 1;
+        if ((c >> lane) & 1u) {
+            int *f1 = row1 + (int64_t)k0 * g.ni[2] + k2;
+            if (!*f1) *f1 = 1;
+            if (!sl2[k2]) sl2[k2] = 1;
         }
-        const bool row = lane < SF_ROWS && rowany[lane];
-        if (row) sl1[blockIdx.y * SF_ROWS + lane] = 1;
-        if (lane == 0 && c) sl0[k0] = 1;
+        if (colmask[lane] && !sl1[blockIdx.y * SF_ROWS + lane]) sl1[blockIdx.y * SF_ROWS + lane] = 1;
+        if (lane == 0 && c && !sl0[k0]) sl0[k0] = 1;
     }
 }
 
@@ -865,7 +917,7 @@ cudaError_t launch_support_flags(const Grid3 &g, const double *rho_int, int64_t 
                                  int *row2, int *row1, int *sl0, int *sl1, int *sl2, cudaStream_t st)
 {
     const dim3 grid((g.n2 - 2 + 31) / 32, (g.n1 - 2 + SF_ROWS - 1) / SF_ROWS, g.d == 3 ? g.n0 - 2 : 1);
-    support_flags_kernel<<<grid, dim3(32, SF_ROWS), 0, st>>>(
+    support_flags_kernel<<<grid, dim3(32, SF_WARPS), 0, st>>>(
         g, rho_int, s0, s1, s2, row2, row1, sl0, sl1, sl2);
     return cudaGetLastError();
 }
