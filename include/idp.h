@@ -60,11 +60,17 @@ enum {
 /* keys for idp_plan_set */
 enum {
     IDP_KEY_USE_GRAPH = 1,  /* 1 (default): replay solves from a CUDA graph; 0: plain launches */
-    IDP_KEY_PRECISION = 2,  /* IDP_PRECISION_*: arithmetic of the four full-volume sine transforms */
+    IDP_KEY_PRECISION = 2,  /* IDP_PRECISION_*: arithmetic of the full-volume sine transforms */
     IDP_KEY_AUTOTUNE = 4,   /* value 1: time candidate settings now on the plan's buffers and keep
-                               the fastest -- slice chunking of the 3-D face convolutions and, in
-                               precision MIXED, tensor-core matrix pass vs double-float FFT pass
-                               (both within the mixed accuracy); synchronises the device */
+                               the fastest -- slice chunking of the 3-D face convolutions, block
+                               shape of the full-volume sine passes and, in precision MIXED,
+                               tensor-core matrix pass vs double-float FFT pass (both within the
+                               mixed accuracy); synchronises the device */
+    IDP_KEY_DST_SHAPE = 5,  /* block shape of the full-volume sine passes (results are the same
+                               bits for every shape): 0 by size (default), 8 = 8 lines per block,
+                               -8 = 8 lines on 128 threads (M = 128 only), 32 = 32 lines (M = 128
+                               only), 16 = 16 lines (M = 256 only); a shape that does not apply
+                               to a length falls back to 0 */
     IDP_KEY_STALL_TEST = 3  /* test hook for failure handling (mixed precision only): the next
                                tensor-core pass issues no products, so its bounded wait expires
                                (after ~5 ms); the kernel records the failure, frees its tensor
@@ -169,7 +175,7 @@ int idp_profile_solve(idp_plan plan, const double *rho, double *phi, void *strea
 /* Settings chosen by IDP_KEY_AUTOTUNE (or the defaults): out[0] = 1 if tuned,
  * out[1] = mixed path (0 tensor-core matrix, 1 double-float FFT), out[2..4] =
  * slice chunks of the face passes of axes 0..2, out[5..7] = slices per chunk,
- * out[8] = lines per block of the full-volume sine passes (0 = by size). */
+ * out[8] = block shape of the full-volume sine passes (IDP_KEY_DST_SHAPE values). */
 int idp_plan_tuning(idp_plan plan, int64_t out[9]);
 
 /* Number of kernel launches one solve of this plan queues (valid after the

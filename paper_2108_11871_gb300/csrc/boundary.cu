@@ -29,6 +29,16 @@ struct LineCfg {
 // ---------------------------------------------------------------- stage 1
 // L = M: complex FFT length; input line has M-1 reals at positions 1..M-1 of
 // a zero-padded sequence of length 2M; output X'_m = 2 X_m, m = 0..M.
+// 2 x, exact: for a normal FP64 value by adding 1 to the exponent (integer pipe),
+// otherwise by the multiplication
+__device__ __forceinline__ double times2_exact(double x)
+{
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e >= 1 && e <= 2045) return __longlong_as_double(b + (1LL << 52));
+    return x * 2.0;
+}
+
 template <class R>
 __device__ __forceinline__ R ld_real(const double *p, int64_t i);
 template <>
@@ -140,10 +150,22 @@ __global__ void __launch_bounds__(NT) rfft_kernel(const RfftPass a)
             ol[(int64_t)m * ose] = A::cmake(A::add(Er, Pi), A::sub(Ei, Pr));
             ol[(int64_t)(M - m) * ose] = A::cmake(A::sub(Er, Pi), A::neg(A::add(Ei, Pr)));
         }
-        if (m == 1) {
-            const Cx z0 = zl[0];
-            ol[0] = A::cmake(A::times2(A::add(A::re(z0), A::im(z0))), A::zero());
-            ol[(int64_t)M * ose] = A::cmake(A::times2(A::sub(A::re(z0), A::im(z0))), A::zero());
+        if constexpr (!std::is_same<R, double>::value) {
+            if (m == 1) {
+                const Cx z0 = zl[0];
+                ol[0] = A::cmake(A::times2(A::add(A::re(z0), A::im(z0))), A::zero());
+                ol[(int64_t)M * ose] = A::cmake(A::times2(A::sub(A::re(z0), A::im(z0))), A::zero());
+            }
+        }
+    }
+    if constexpr (std::is_same<R, double>::value) {
+        // m = 0 and m = M, one lane per line (an FP64 warp instruction costs the
+        // pipe the same whatever its active lanes; Z is still intact)
+        if (threadIdx.x < nl) {
+            const double2 z0 = Z[threadIdx.x * L];
+            double2 *ol = outb + (int64_t)threadIdx.x * osv;
+            ol[0] = make_double2(times2_exact(z0.x + z0.y), 0.0);
+            ol[(int64_t)M * ose] = make_double2(times2_exact(z0.x - z0.y), 0.0);
         }
     }
 }

@@ -19,7 +19,7 @@ namespace {
 
 constexpr int NT = 256;
 
-template <int K, int LBO = 0>
+template <int K, int LBO = 0, int NTB = NT>
 struct DstCfg {
     static constexpr int M = 2 * K;
     static constexpr int N = M - 1;
@@ -30,7 +30,8 @@ struct DstCfg {
     // a power of two (so that LB * G = 256)
     static constexpr int LB0 = LBr >= 32 ? 32 : LBr >= 16 ? 16 : LBr >= 8 ? 8 : 4;
     static constexpr int LB = LBO ? LBO : (LB0 < 8 ? 8 : LB0);
-    static constexpr int G = NT / LB;             // threads per line in the scan
+    static constexpr int T = NTB;                 // threads per block
+    static constexpr int G = T / LB;              // threads per line in the scan
     static constexpr int C = (K + G - 1) / G;     // scan elements per thread (the last ones guarded)
 };
 
@@ -57,6 +58,18 @@ struct Io<ddr> {
     }
 };
 
+// 4 x, exact: for a normal FP64 value by adding 2 to the exponent (integer
+// pipe; FP64 issue is scarce and this runs on one lane per line), otherwise by
+// the multiplication
+__device__ __forceinline__ double times4_exact(double x)
+{
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e >= 1 && e <= 2044) return __longlong_as_double(b + (2LL << 52));
+    return x * 4.0;
+}
+__device__ __forceinline__ ddr times4_exact(ddr x) { return Ar<ddr>::times4(x); }
+
 template <class R>
 struct Tabs;
 template <>
@@ -81,10 +94,11 @@ __device__ __forceinline__ void view_strides(const View3 &w, int axis, int64_t &
     else { su = w.s1; sv = w.s2; se = w.s0; }
 }
 
-template <class R, int K, int LBO>
-__global__ void __launch_bounds__(NT) dst_pass_kernel(const DstPass a)
+template <class R, int K, int LBO, int NTB>
+__global__ void __launch_bounds__(NTB) dst_pass_kernel(const DstPass a)
 {
-    using Cfg = DstCfg<K, LBO>;
+    using Cfg = DstCfg<K, LBO, NTB>;
+    constexpr int NT = NTB;
     using A = Ar<R>;
     using Cx = typename A::C;
     constexpr int M = Cfg::M, N = Cfg::N, LB = Cfg::LB;
@@ -125,7 +139,7 @@ __global__ void __launch_bounds__(NT) dst_pass_kernel(const DstPass a)
         R *zl = zf + l * M;
         if (j == 0) {
             zl[0] = A::zero();
-            zl[K] = A::times4(xl[K - 1]);
+            zl[K] = times4_exact(xl[K - 1]);
         } else {
             const R xa = xl[j - 1], xb = xl[M - j - 1];
             const R s = Tabs<R>::sin2(a, j);
@@ -167,20 +181,45 @@ __global__ void __launch_bounds__(NT) dst_pass_kernel(const DstPass a)
             ol[2 * k] = A::add(Er, Pi);
             ol[2 * (K - k)] = A::sub(Er, Pi);
         }
-        if (k == 1) ol[0] = A::add(A::re(zl[0]), A::im(zl[0]));
+        if constexpr (!std::is_same<R, double>::value)
+            if (k == 1) ol[0] = A::add(A::re(zl[0]), A::im(zl[0]));
     }
     __syncthreads();
 
     // 5. prefix sum over the odd slots o[2k], k = 0..K-1
     if constexpr (std::is_same<R, double>::value) {
-        // one thread per line, K-1 additions: the fewest FP64 operations
-        if (threadIdx.x < LB) {
-            double *ol = o + threadIdx.x * M;
-            double run = ol[0];
+        // four lanes per line, each scanning a quarter of the odd slots: every FP64
+        // warp instruction then has all its lanes busy (an FP64 warp instruction
+        // costs the pipe the same whatever its active lanes).  Per lane: the total
+        // of its quarter, an inclusive scan of the four totals by shuffles, then
+        // the quarter again from the lower quarters' sum.  The summation order is
+        // the same for every block shape.  Requires 4 LB <= threads per block and
+        // whole warps of lines (LB >= 8).
+        constexpr int S = 4, Cq = K / S;
+        const int l = threadIdx.x / S, sg = threadIdx.x - l * S;
+        if (l < LB) {
+            double *ol = o + l * M;
+            const Cx z0 = Z[l * K];
+            // slot 0 = Re T_0 + Im T_0, the first odd output
+            const double first = A::re(z0) + A::im(z0);
+            const int kb = sg * Cq;
+            double tot = sg == 0 ? first : ol[2 * kb];
 #pragma unroll 8
-            for (int k = 1; k < K; ++k) {
-                run += ol[2 * k];
-                ol[2 * k] = run;
+            for (int c = 1; c < Cq; ++c) tot += ol[2 * (kb + c)];
+            double incl = tot;
+#pragma unroll
+            for (int dd = 1; dd < S; dd <<= 1) {
+                const double nb = __shfl_up_sync(0xffffffffu, incl, dd, S);
+                incl += sg >= dd ? nb : 0.0;
+            }
+            // sum of the lower quarters: the inclusive sum of the lane below
+            const double below = __shfl_up_sync(0xffffffffu, incl, 1, S);
+            double run = sg == 0 ? first : below + ol[2 * kb];
+            ol[2 * kb] = run;
+#pragma unroll 8
+            for (int c = 1; c < Cq; ++c) {
+                run += ol[2 * (kb + c)];
+                ol[2 * (kb + c)] = run;
             }
         }
     } else {
@@ -240,15 +279,16 @@ __global__ void __launch_bounds__(NT) dst_pass_kernel(const DstPass a)
     }
 }
 
-template <class R, int K, int LBO>
+template <class R, int K, int LBO, int NTB = NT>
 cudaError_t launch_lb(const DstPass &a, int nu, int nv, cudaStream_t st)
 {
-    using Cfg = DstCfg<K, LBO>;
+    using Cfg = DstCfg<K, LBO, NTB>;
     static_assert(Cfg::G <= 32, "scan group must fit a warp");
-    static_assert(Cfg::LB * Cfg::G == NT, "every thread belongs to one scan group");
+    static_assert(Cfg::LB * Cfg::G == NTB, "every thread belongs to one scan group");
+    static_assert(4 * Cfg::LB <= NTB && Cfg::LB >= 8 && K % 4 == 0, "four scan lanes per line in whole warps");
     const size_t sm = 2 * sizeof(double2) * Cfg::LB * K;
     dim3 grid((nv + Cfg::LB - 1) / Cfg::LB, nu);
-    dst_pass_kernel<R, K, LBO><<<grid, NT, sm, st>>>(a);
+    dst_pass_kernel<R, K, LBO, NTB><<<grid, NTB, sm, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -259,21 +299,32 @@ cudaError_t launch_k(const DstPass &a, cudaStream_t st)
     if (a.axis == 2) { nu = a.n0; nv = a.n1; }
     else if (a.axis == 1) { nu = a.n0; nv = a.n2; }
     else { nu = a.n1; nv = a.n2; }
+    // 32 lines (M = 128) or 16 lines (M = 256) per block: the per-line prefix sum
+    // then runs on at least half a warp (an FP64 warp instruction costs the pipe the
+    // same whatever its active lanes)
+    if constexpr (K == 64) {
+        if (a.lines == 32) return launch_lb<R, K, 32>(a, nu, nv, st);
+    }
+    if constexpr (K == 128) {
+        if (a.lines == 16) return launch_lb<R, K, 16>(a, nu, nv, st);
+    }
     if constexpr (DstCfg<K>::LB > 8) {
         // a launch of less than two blocks per SM (the layer transforms) runs
         // faster on more, smaller blocks
         const int64_t blocks = (int64_t)nu * ((nv + DstCfg<K>::LB - 1) / DstCfg<K>::LB);
         if (a.lines == 8 || blocks < 2 * 152) return launch_lb<R, K, 8>(a, nu, nv, st);
+        // 8 lines on 128 threads: one radix-4 unit per thread per pass for K = 64
+        if (a.lines == -8 && K == 64) return launch_lb<R, K, 8, 128>(a, nu, nv, st);
     }
     return launch_lb<R, K, 0>(a, nu, nv, st);
 }
 
-template <class R, int K, int LBO>
+template <class R, int K, int LBO, int NTB = NT>
 cudaError_t attr_lb()
 {
-    using Cfg = DstCfg<K, LBO>;
+    using Cfg = DstCfg<K, LBO, NTB>;
     const int sm = (int)(2 * sizeof(double2) * Cfg::LB * K);
-    return cudaFuncSetAttribute(dst_pass_kernel<R, K, LBO>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    return cudaFuncSetAttribute(dst_pass_kernel<R, K, LBO, NTB>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
 template <class R, int K>
@@ -282,6 +333,13 @@ cudaError_t attr_k()
     cudaError_t e = attr_lb<R, K, 0>();
     if (e != cudaSuccess) return e;
     if constexpr (DstCfg<K>::LB > 8) e = attr_lb<R, K, 8>();
+    if constexpr (K == 64) {
+        if (e == cudaSuccess) e = attr_lb<R, K, 8, 128>();
+        if (e == cudaSuccess) e = attr_lb<R, K, 32>();
+    }
+    if constexpr (K == 128) {
+        if (e == cudaSuccess) e = attr_lb<R, K, 16>();
+    }
     return e;
 }
 

@@ -15,15 +15,27 @@ namespace idp {
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 
+// barrier of the threads that share the buffers: the block, or one warp
+template <bool WARP>
+__device__ __forceinline__ void fft_sync()
+{
+    if constexpr (WARP) __syncwarp();
+    else __syncthreads();
+}
+
 // FFT of LB lines of length L stored contiguously (line stride L) in X;
 // Y is scratch of the same size.  Returns the buffer holding the result.
 // INV selects e^{+2 pi i jk/L} (unnormalised).  If zero_half, the second
 // half of every input line is known to be zero (saves the first stage).
-// All NT threads of the block must call it; it ends with __syncthreads().
-template <class R, int L, int LB, int NT, bool INV>
+// The NT threads that share X and Y call it with tid = 0..NT-1: the whole block
+// (WARP = false; ends with __syncthreads()) or one warp (WARP = true, NT = 32;
+// ends with __syncwarp()).
+template <class R, int L, int LB, int NT, bool INV, bool WARP = false>
 __device__ __forceinline__ typename Ar<R>::C *cta_fft_t(typename Ar<R>::C *X, typename Ar<R>::C *Y,
-                                                        const typename Ar<R>::T *__restrict__ tw, bool zero_half)
+                                                        const typename Ar<R>::T *__restrict__ tw, bool zero_half,
+                                                        int tid = -1)
 {
+    if (tid < 0) tid = threadIdx.x;
     using C = typename Ar<R>::C;
     constexpr int H = L / 2;
     constexpr bool P2 = (L & (L - 1)) == 0;
@@ -31,14 +43,14 @@ __device__ __forceinline__ typename Ar<R>::C *cta_fft_t(typename Ar<R>::C *X, ty
     if (!P2) {
         // radix-3 stage (lengths 3 * 2^m): y[3j + r] = sum_q x[j + q L/3] w3^{qr}
         constexpr int T = L / 3;
-        for (int b = threadIdx.x; b < LB * T; b += NT) {
+        for (int b = tid; b < LB * T; b += NT) {
             const int line = b / T;
             const int j = b - line * T;
             const C *x = X + line * L;
             C *y = Y + line * L;
             Ar<R>::radix3(x[j], x[j + T], x[j + 2 * T], INV, y[3 * j], y[3 * j + 1], y[3 * j + 2]);
         }
-        __syncthreads();
+        fft_sync<WARP>();
         C *t = X;
         X = Y;
         Y = t;
@@ -53,7 +65,7 @@ __device__ __forceinline__ typename Ar<R>::C *cta_fft_t(typename Ar<R>::C *X, ty
 #pragma unroll 1
     for (; Ns * 4 <= L; Ns <<= 2) {
 #pragma unroll
-        for (int b = threadIdx.x; b < LB * Q; b += NT) {
+        for (int b = tid; b < LB * Q; b += NT) {
             const int line = b / Q;
             const int j = b - line * Q;
             const C *x = X + line * L;
@@ -90,7 +102,7 @@ __device__ __forceinline__ typename Ar<R>::C *cta_fft_t(typename Ar<R>::C *X, ty
             y[base + 2 * Ns] = y2;
             y[base + 3 * Ns] = y3;
         }
-        __syncthreads();
+        fft_sync<WARP>();
         C *t = X;
         X = Y;
         Y = t;
@@ -98,7 +110,7 @@ __device__ __forceinline__ typename Ar<R>::C *cta_fft_t(typename Ar<R>::C *X, ty
     }
     if (Ns < L) {   // one radix-2 stage left
 #pragma unroll
-        for (int b = threadIdx.x; b < LB * H; b += NT) {
+        for (int b = tid; b < LB * H; b += NT) {
             const int line = b / H;
             const int j = b - line * H;
             const C *x = X + line * L;
@@ -122,7 +134,7 @@ __device__ __forceinline__ typename Ar<R>::C *cta_fft_t(typename Ar<R>::C *X, ty
             y[o] = A;
             y[o + Ns] = B;
         }
-        __syncthreads();
+        fft_sync<WARP>();
         C *t = X;
         X = Y;
         Y = t;

@@ -1065,19 +1065,22 @@ int autotune(idp_plan p)
         }
     }
     if (!rc) {
-        // lines per block of the full-volume sine passes: the default (up to 32
-        // lines, one wave of large blocks) or 8 (more, smaller blocks whose load,
-        // FFT and store phases overlap)
+        // block shape of the full-volume sine passes: the default, 8 lines on 256
+        // threads, 8 lines on 128 threads (M = 128), 32 lines (M = 128) or 16
+        // lines (M = 256); shapes that do not apply to a length fall back to the
+        // default
         const View3 none{nullptr, 0, 0, 0};
-        float tl[2];
-        const int opts[2] = {0, 8};
-        for (int i = 0; i < 2 && !rc; ++i) {
+        const int opts[5] = {0, 8, -8, 32, 16};
+        int best = 0;
+        float bt = 1e30f;
+        for (int i = 0; i < 5 && !rc; ++i) {
             p->dst_lines = opts[i];
-            tl[i] = timed([&]() -> int {
+            const float t = timed([&]() -> int {
                 return transform(p, dense(p, p->C), p->C, dense(p, p->C), nullptr, none, false, st);
             });
+            if (t < bt) { bt = t; best = opts[i]; }
         }
-        p->dst_lines = (tl[1] < tl[0]) ? 8 : 0;
+        p->dst_lines = best;
     }
     if (!rc && p->mixed == IDP_PRECISION_MIXED_BF16X3) {
         const View3 none{nullptr, 0, 0, 0};
@@ -1201,6 +1204,16 @@ int idp_plan_set(idp_plan p, int key, int64_t value)
     if (key == IDP_KEY_AUTOTUNE) {
         if (!value) return IDP_OK;
         return autotune(p);
+    }
+    if (key == IDP_KEY_DST_SHAPE) {
+        if (value != 0 && value != 8 && value != -8 && value != 32 && value != 16) return IDP_EINVAL;
+        p->dst_lines = (int)value;
+        ++p->version;
+        if (p->gexec) {
+            cudaGraphExecDestroy(p->gexec);
+            p->gexec = nullptr;
+        }
+        return IDP_OK;
     }
     if (key == IDP_KEY_STALL_TEST) {
         if (p->mixed != IDP_PRECISION_MIXED_BF16X3) return IDP_EINVAL;

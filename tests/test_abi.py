@@ -45,3 +45,25 @@ def test_argument_errors_need_no_gpu():
         assert lib.idp_create_plan(ctypes.byref(out), 3, bad, h, 6) == idp.IDP_ESUPPORT
     assert lib.idp_solve(None, None, None, None) == idp.IDP_EINVAL
     assert idp.strerror(idp.IDP_EALIAS) == "input and output overlap"
+
+
+def test_binding_constants_match_the_header():
+    # every IDP_* constant the binding defines has the header's value
+    import paper_2108_11871_gb300.binding as b
+    text = open(HEADER).read()
+    declared = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(IDP_[A-Z0-9_]+)\s*=\s*(-?\d+)", text)}
+    mine = {k: v for k, v in vars(b).items() if k.startswith("IDP_") and isinstance(v, int)}
+    assert mine, "binding defines no constants"
+    for k, v in mine.items():
+        if k in declared:
+            assert declared[k] == v, k
+    for k in ("IDP_KEY_DST_SHAPE", "IDP_KEY_AUTOTUNE", "IDP_STAGE_R", "IDP_PRECISION_DF32"):
+        assert k in mine and k in declared, k
+
+
+def test_package_exports_every_binding_constant():
+    import paper_2108_11871_gb300 as pkg
+    import paper_2108_11871_gb300.binding as b
+    for k, v in vars(b).items():
+        if k.startswith("IDP_") and isinstance(v, int):
+            assert getattr(pkg, k, None) == v, k

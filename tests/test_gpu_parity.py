@@ -305,3 +305,38 @@ def test_513_cube_large_grid(idp):
     sub = w.scaled_bump((129, 129, 129), p=10)
     exact = closed_form.bump_potential_on_grid(sub)
     assert rel_max(out[::4, ::4, ::4].cpu().numpy(), exact) < 1e-11
+
+
+_SHAPE_PROB = w.Problem("c", (65, 33, 129), (0.0, 0.0, 0.0), (1.0, 1.0, 2.0), "gauss", dict(seed=2108))
+_SHAPE_REF = {}
+
+
+def _solve_with_shape(idp, prob, shape):
+    import torch
+    plan = idp.create_plan(prob.d, prob.n, prob.h, 6)
+    idp.plan_set(plan, idp.IDP_KEY_DST_SHAPE, shape)
+    rho = to_dev(prob.rho())
+    phi = torch.empty_like(rho)
+    idp.solve(plan, rho, phi, None)
+    torch.cuda.synchronize()
+    idp.plan_status(plan)
+    return phi.cpu().numpy()
+
+
+@pytest.mark.parametrize("shape", [8, -8, 32, 16])
+def test_dst_block_shapes_give_the_same_bits(idp, shape):
+    # every block shape of the full-volume sine passes runs the same arithmetic per
+    # line (M = 64, 32, 128 here: the 8-line, 128-thread and 32-line blocks apply,
+    # 16 falls back): phi matches the oracle and the default shape bit for bit
+    if "ref" not in _SHAPE_REF:
+        _SHAPE_REF["ref"] = osolve.solve(_SHAPE_PROB.rho(), _SHAPE_PROB.h, 6, boundary="convolution")
+        _SHAPE_REF["default"] = _solve_with_shape(idp, _SHAPE_PROB, 0)
+    got = _solve_with_shape(idp, _SHAPE_PROB, shape)
+    assert rel_max(got, _SHAPE_REF["ref"]) < TOL
+    assert np.array_equal(got, _SHAPE_REF["default"])
+
+
+def test_dst_shape_key_rejects_unknown_values(idp):
+    plan = idp.create_plan(3, (33, 33, 33), (0.1, 0.1, 0.1), 6)
+    lib = idp.library()
+    assert lib.idp_plan_set(plan.handle, idp.IDP_KEY_DST_SHAPE, 3) == idp.IDP_EINVAL
