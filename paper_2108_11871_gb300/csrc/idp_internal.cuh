@@ -84,6 +84,7 @@ struct MpPass {
     const double *add; int64_t as_m, as_p, as_q;
     int *err;                   // set to 1 if a wait on the tensor cores timed out
     int stall_test;             // test hook: issue no products, so the bounded wait expires
+    int modes_per_tile;         // 64 or 128; 0: 64 when 128-mode tiles would give < 2 blocks per SM
 };
 cudaError_t launch_mp_pass(const MpPass &a, cudaStream_t st);
 cudaError_t mp_set_attributes();

@@ -13,12 +13,17 @@
 // FP32 accumulation.  The eigenvalue scaling and the additions of the last
 // pass are done in FP64.
 //
-// Block: 256 threads, a tile of 128 lines x 128 modes, K in blocks of 64.
-// Operands live in shared memory in the canonical K-major layout without
-// swizzle: 8 x 16-byte core matrices, core matrices adjacent along K are
-// LBO = 2048 bytes apart, adjacent along M/N SBO = 128 bytes apart.
+// Block: 256 threads, a tile of 128 lines x NTN modes (NTN = 64 or 128), K in
+// blocks of 64.  Operands live in shared memory in the canonical K-major layout
+// without swizzle: 8 x 16-byte core matrices, core matrices adjacent along K are
+// LBO = 2048 bytes apart, adjacent along M/N SBO = 128 bytes apart.  The sine
+// image of a K block (128 modes) arrives by cp.async while the block loads and
+// splits its input; a 64-mode tile addresses its half of the image through the
+// descriptor's start address.  FP64 <-> FP32 conversions and the factor 4 are
+// integer operations (FP64 issue is scarce on this GPU).
 #include <cuda_bf16.h>
 
+#include "dd.cuh"
 #include "idp_internal.cuh"
 
 namespace idp {
@@ -59,9 +64,8 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr)
     return d;
 }
 
-// instruction descriptor: kind::f16, A = B = BF16, D = F32, K-major, M = 128, N = 128
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NTILE >> 3) << 17) |
-                           ((uint32_t)(MT >> 4) << 24);
+// instruction descriptor (kind::f16, A = B = BF16, D = F32, K-major, M = 128,
+// N = NTN): built in the kernel from the tile width
 
 // x = hi + lo (two floats, |lo| <= 2^-24 |hi|) -> three BF16 pieces.  The
 // residuals hi - a and r1 - b are exact in FP32; lo enters below 2^-16 |x|.
@@ -94,15 +98,27 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
 }
 
 constexpr int NTHR = 256;
+constexpr int GPT = MT * (KB / 8) / NTHR;   // 16-byte row groups of the A tile per thread (4)
 
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+
+template <int NTN>
 __global__ void __launch_bounds__(NTHR) mp_pass_kernel(const MpPass a)
 {
+    static_assert(NTN == 64 || NTN == 128, "tile of 64 or 128 modes");
+    constexpr uint32_t IDESC_N = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NTN >> 3) << 17) |
+                                 ((uint32_t)(MT >> 4) << 24);
     extern __shared__ __align__(128) unsigned char sm[];
     const int t = threadIdx.x;
     const int warp = t >> 5, lane = t & 31;
     const int64_t nlines = (int64_t)a.P * a.Q;
     const int64_t L0 = (int64_t)blockIdx.x * MT;
-    const int m0 = blockIdx.y * NTILE;
+    const int m0 = blockIdx.y * NTN;
+    const int img_tile = m0 / NTILE;                                   // 128-mode image tile
+    const uint32_t b_sub = (uint32_t)(((m0 - img_tile * NTILE) >> 3) * SBO);   // byte offset of the half
     const int nkb = (a.n + KB - 1) / KB;
     const uint32_t bar = smem_u32(sm + SMEM_BAR);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + SMEM_BAR + 8);
@@ -116,7 +132,7 @@ __global__ void __launch_bounds__(NTHR) mp_pass_kernel(const MpPass a)
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                          smem_u32(tmem_slot)),
-                     "r"(NTILE)
+                     "r"(NTN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
@@ -126,13 +142,24 @@ __global__ void __launch_bounds__(NTHR) mp_pass_kernel(const MpPass a)
     const uint32_t tmem = *tmem_slot;
 
     for (int kb = 0; kb < nkb; ++kb) {
+        // B pieces: the pre-split sine image of this K block, copied asynchronously
+        {
+            const unsigned char *src = reinterpret_cast<const unsigned char *>(a.bimg) +
+                                       ((int64_t)img_tile * nkb + kb) * (PIECES * TILE_BYTES);
+            const uint32_t dst = smem_u32(sm + SMEM_B);
+            for (int e = t; e < PIECES * TILE_BYTES / 16; e += NTHR) cp_async16(dst + 16 * e, src + 16 * e);
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+        }
         // A pieces: 128 lines x 64 k of the input, split into BF16 pieces; a
-        // thread takes 8 consecutive k of one line (one 16-byte core-matrix row)
-        for (int e = t; e < MT * (KB / 8); e += NTHR) {
+        // thread takes GPT groups of 8 consecutive k of one line (one 16-byte
+        // core-matrix row each), all loads issued before any is used
+        double xv[GPT][8];
+#pragma unroll
+        for (int g = 0; g < GPT; ++g) {
+            const int e = t + g * NTHR;
             const int r = e >> 3, g8 = e & 7;
             const int64_t L = L0 + r;
             const int kg0 = kb * KB + g8 * 8;
-            unsigned short pa[8], pb[8], pc[8];
             const bool row_ok = L < nlines;
             int64_t base = 0;
             if (row_ok) {
@@ -142,16 +169,30 @@ __global__ void __launch_bounds__(NTHR) mp_pass_kernel(const MpPass a)
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int kg = kg0 + j;
-                float hi = 0.f, lo = 0.f;
+                double x = 0.0;
                 if (row_ok && kg < a.n) {
                     const int64_t off = base + (int64_t)kg * a.is_k;
-                    if (a.in_f64) {
-                        const double x = reinterpret_cast<const double *>(a.in)[off];
-                        hi = (float)x;
-                        lo = (float)(x - (double)hi);
-                    } else {
-                        hi = reinterpret_cast<const float *>(a.in)[off];
-                    }
+                    if (a.in_f64) x = reinterpret_cast<const double *>(a.in)[off];
+                    else x = __longlong_as_double((long long)__float_as_int(reinterpret_cast<const float *>(a.in)[off]));
+                }
+                xv[g][j] = x;
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < GPT; ++g) {
+            const int e = t + g * NTHR;
+            const int r = e >> 3, g8 = e & 7;
+            unsigned short pa[8], pb[8], pc[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                float hi, lo;
+                if (a.in_f64) {
+                    const ddr h2 = dd_from_bits(xv[g][j]);   // integer split, no FP64 instruction
+                    hi = h2.hi;
+                    lo = h2.lo;
+                } else {
+                    hi = __int_as_float((int)__double_as_longlong(xv[g][j]));
+                    lo = 0.f;
                 }
                 split3(hi, lo, pa[j], pb[j], pc[j]);
             }
@@ -167,13 +208,7 @@ __global__ void __launch_bounds__(NTHR) mp_pass_kernel(const MpPass a)
             *reinterpret_cast<uint4 *>(sm + SMEM_A + 1 * TILE_BYTES + o) = vb;
             *reinterpret_cast<uint4 *>(sm + SMEM_A + 2 * TILE_BYTES + o) = vc;
         }
-        // B pieces: pre-split sine-matrix images, copied as 16-byte vectors
-        {
-            const int4 *src = reinterpret_cast<const int4 *>(a.bimg) +
-                              ((int64_t)blockIdx.y * nkb + kb) * (PIECES * TILE_BYTES / 16);
-            int4 *dst = reinterpret_cast<int4 *>(sm + SMEM_B);
-            for (int e = t; e < PIECES * TILE_BYTES / 16; e += NTHR) dst[e] = src[e];
-        }
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
         if (t == 0 && !a.stall_test) {
@@ -184,12 +219,13 @@ __global__ void __launch_bounds__(NTHR) mp_pass_kernel(const MpPass a)
             for (int pr = 0; pr < 6; ++pr) {
                 for (int ks = 0; ks < KB / 16; ++ks) {
                     const uint64_t ad = make_desc(smem_u32(sm + SMEM_A + pa[pr] * TILE_BYTES) + ks * 2 * LBO);
-                    const uint64_t bd = make_desc(smem_u32(sm + SMEM_B + pb[pr] * TILE_BYTES) + ks * 2 * LBO);
+                    const uint64_t bd =
+                        make_desc(smem_u32(sm + SMEM_B + pb[pr] * TILE_BYTES) + ks * 2 * LBO + b_sub);
                     const uint32_t acc = (kb > 0 || pr > 0 || ks > 0) ? 1u : 0u;
                     asm volatile(
                         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                        "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
+                        "l"(ad), "l"(bd), "r"(IDESC_N), "r"(acc)
                         : "memory");
                 }
             }
@@ -207,13 +243,13 @@ __global__ void __launch_bounds__(NTHR) mp_pass_kernel(const MpPass a)
 
     if (!s_fail) {
         // epilogue: warp w reads TMEM lane quadrant w % 4 (lines 32*(w%4) ..),
-        // columns [64 * (w / 4), 64 * (w / 4) + 64)
+        // columns [NTN/2 * (w / 4), NTN/2 * (w / 4) + NTN/2)
         const int quad = warp & 3;
         const int64_t L = L0 + 32 * quad + lane;
         const bool live = L < nlines;
         int64_t p = 0, q = 0;
         if (live) { p = L / a.Q; q = L - p * a.Q; }
-        for (int c0 = 64 * (warp >> 2); c0 < 64 * (warp >> 2) + 64; c0 += 32) {
+        for (int c0 = (NTN / 2) * (warp >> 2); c0 < (NTN / 2) * (warp >> 2) + NTN / 2; c0 += 32) {
             uint32_t v[32];
             const uint32_t taddr = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)c0;
             asm volatile(
@@ -231,9 +267,11 @@ __global__ void __launch_bounds__(NTHR) mp_pass_kernel(const MpPass a)
             for (int j = 0; j < 32; ++j) {
                 const int m = m0 + c0 + j;
                 if (m >= a.n) break;
-                const double y = 4.0 * (double)__uint_as_float(v[j]);
+                // 4 * the FP32 sum, exact in FP32; widened to FP64 by bits
+                const float y4 = __fmul_rn(4.0f, __uint_as_float(v[j]));
                 const int64_t oo = (int64_t)m * a.os_m + p * a.os_p + q * a.os_q;
                 if (a.out_f64) {
+                    const double y = f2d_bits(y4);
                     double r = y;
                     if (a.tab) {
                         const double tv = a.tab[(int64_t)m * a.ts_m + p * a.ts_p + q * a.ts_q];
@@ -243,7 +281,7 @@ __global__ void __launch_bounds__(NTHR) mp_pass_kernel(const MpPass a)
                     }
                     reinterpret_cast<double *>(a.out)[oo] = r;
                 } else {
-                    reinterpret_cast<float *>(a.out)[oo] = (float)y;
+                    reinterpret_cast<float *>(a.out)[oo] = y4;
                 }
             }
         }
@@ -253,7 +291,7 @@ __global__ void __launch_bounds__(NTHR) mp_pass_kernel(const MpPass a)
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(NTILE)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(NTN)
                      : "memory");
     }
 }
@@ -264,14 +302,21 @@ size_t mp_smem_bytes() { return SMEM_TOTAL; }
 
 cudaError_t mp_set_attributes()
 {
-    return cudaFuncSetAttribute(mp_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL);
+    cudaError_t e = cudaFuncSetAttribute(mp_pass_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(mp_pass_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL);
 }
 
 cudaError_t launch_mp_pass(const MpPass &a, cudaStream_t st)
 {
     const int64_t lines = (int64_t)a.P * a.Q;
-    dim3 grid((unsigned)((lines + MT - 1) / MT), (unsigned)((a.n + NTILE - 1) / NTILE));
-    mp_pass_kernel<<<grid, NTHR, SMEM_TOTAL, st>>>(a);
+    const unsigned tiles = (unsigned)((lines + MT - 1) / MT);
+    // 64-mode tiles double the blocks of a launch that fills the GPU less than twice
+    if (a.modes_per_tile == 64 || (a.modes_per_tile == 0 && tiles * ((a.n + NTILE - 1) / NTILE) < 2 * 152)) {
+        mp_pass_kernel<64><<<dim3(tiles, (unsigned)((a.n + 63) / 64)), NTHR, SMEM_TOTAL, st>>>(a);
+    } else {
+        mp_pass_kernel<128><<<dim3(tiles, (unsigned)((a.n + NTILE - 1) / NTILE)), NTHR, SMEM_TOTAL, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
