@@ -13,7 +13,7 @@
 // FP32 accumulation.  The eigenvalue scaling and the additions of the last
 // pass are done in FP64.
 //
-// Block: 256 threads, a tile of 128 lines x NTN modes (NTN = 64 or 128), K in
+// Block: 512 threads, a tile of 128 lines x NTN modes (NTN = 64 or 128), K in
 // blocks of 64.  Operands live in shared memory in the canonical K-major layout
 // without swizzle: 8 x 16-byte core matrices, core matrices adjacent along K are
 // LBO = 2048 bytes apart, adjacent along M/N SBO = 128 bytes apart.  The sine
@@ -97,8 +97,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
     return false;
 }
 
-constexpr int NTHR = 256;
-constexpr int GPT = MT * (KB / 8) / NTHR;   // 16-byte row groups of the A tile per thread (4)
+constexpr int NTHR = 512;
+constexpr int GPT = MT * (KB / 8) / NTHR;   // 16-byte row groups of the A tile per thread (2)
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
 {
@@ -152,12 +152,14 @@ __global__ void __launch_bounds__(NTHR) mp_pass_kernel(const MpPass a)
         }
         // A pieces: 128 lines x 64 k of the input, split into BF16 pieces; a
         // thread takes GPT groups of 8 consecutive k of one line (one 16-byte
-        // core-matrix row each), all loads issued before any is used
+        // core-matrix row each; consecutive lanes take consecutive lines, so a
+        // warp's stores fill 512 contiguous bytes), all loads issued before any
+        // is used
         double xv[GPT][8];
 #pragma unroll
         for (int g = 0; g < GPT; ++g) {
             const int e = t + g * NTHR;
-            const int r = e >> 3, g8 = e & 7;
+            const int r = e & (MT - 1), g8 = e / MT;   // rows fastest: conflict-free 16-byte stores
             const int64_t L = L0 + r;
             const int kg0 = kb * KB + g8 * 8;
             const bool row_ok = L < nlines;
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(NTHR) mp_pass_kernel(const MpPass a)
 #pragma unroll
         for (int g = 0; g < GPT; ++g) {
             const int e = t + g * NTHR;
-            const int r = e >> 3, g8 = e & 7;
+            const int r = e & (MT - 1), g8 = e / MT;   // rows fastest: conflict-free 16-byte stores
             unsigned short pa[8], pb[8], pc[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -243,28 +245,27 @@ __global__ void __launch_bounds__(NTHR) mp_pass_kernel(const MpPass a)
 
     if (!s_fail) {
         // epilogue: warp w reads TMEM lane quadrant w % 4 (lines 32*(w%4) ..),
-        // columns [NTN/2 * (w / 4), NTN/2 * (w / 4) + NTN/2)
+        // columns [NTN/4 * (w / 4), NTN/4 * (w / 4) + NTN/4), 16 at a time
         const int quad = warp & 3;
         const int64_t L = L0 + 32 * quad + lane;
         const bool live = L < nlines;
         int64_t p = 0, q = 0;
         if (live) { p = L / a.Q; q = L - p * a.Q; }
-        for (int c0 = (NTN / 2) * (warp >> 2); c0 < (NTN / 2) * (warp >> 2) + NTN / 2; c0 += 32) {
-            uint32_t v[32];
+        constexpr int CPW = NTN / 4;
+        for (int c0 = CPW * (warp >> 2); c0 < CPW * (warp >> 2) + CPW; c0 += 16) {
+            uint32_t v[16];
             const uint32_t taddr = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)c0;
             asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];\n"
                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
                   "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                  "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
-                  "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
-                  "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                  "=r"(v[14]), "=r"(v[15])
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
             if (!live) continue;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
+            for (int j = 0; j < 16; ++j) {
                 const int m = m0 + c0 + j;
                 if (m >= a.n) break;
                 // 4 * the FP32 sum, exact in FP32; widened to FP64 by bits
