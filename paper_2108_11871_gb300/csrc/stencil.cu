@@ -858,10 +858,10 @@ cudaError_t launch_rhs6_e_scatter(const Grid3 &g, const double *E0, const double
 namespace {
 // One block covers 32 consecutive nodes along axis 2 of SF_ROWS rows (axis 1)
 // of one slice (axis 0); each of its 8 warps reads SF_ROWS / 8 rows, with all
-// loads in flight at once.  The flags are only ever set to 1, so the stores may
+// loads in flight at once (a grid that fits the GPU in one wave at 129^3).  The flags are only ever set to 1, so the stores may
 // race; they are reduced within the block first so that few of them hit the
 // same cache lines.
-constexpr int SF_ROWS = 32, SF_WARPS = 8, SF_PER = SF_ROWS / SF_WARPS;
+constexpr int SF_ROWS = 64, SF_WARPS = 8, SF_PER = SF_ROWS / SF_WARPS;
 __global__ void __launch_bounds__(32 * SF_WARPS) support_flags_kernel(const Grid3 gg, const double *__restrict__ r,
                                                                     int64_t s0, int64_t s1, int64_t s2, int *row2,
                                                                     int *row1, int *sl0, int *sl1, int *sl2)
@@ -901,7 +901,8 @@ __global__ void __launch_bounds__(32 * SF_WARPS) support_flags_kernel(const Grid
             if (!*f1) *f1 = 1;
             if (!sl2[k2]) sl2[k2] = 1;
         }
-        if (colmask[lane] && !sl1[blockIdx.y * SF_ROWS + lane]) sl1[blockIdx.y * SF_ROWS + lane] = 1;
+        for (int j = lane; j < SF_ROWS; j += 32)
+            if (colmask[j] && !sl1[blockIdx.y * SF_ROWS + j]) sl1[blockIdx.y * SF_ROWS + j] = 1;
         if (lane == 0 && c && !sl0[k0]) sl0[k0] = 1;
     }
 }
