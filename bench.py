@@ -405,9 +405,9 @@ def run_ours(args, rank, world):
                          "frac": achieved / FP64_PEAK_TFLOPS,
                          "peak_note": "FP64 derived: 152 SMs x 4 flop/clk x 2.07 GHz; "
                                       "FMA-chain probe measured %.3f" % FP64_PROBE_TFLOPS,
-                         # DRAM bytes per launch from the ncu capture summarised in
-                         # profiles/dst_pass_fp64_129cube.md (valid for the 129^3 workload)
-                         "traffic": 16406272 if prob.n == (129, 129, 129) else None, "avg_launch_ms": dst_ms,
+                         # DRAM bytes (read + write) of one full-volume launch of this kernel,
+                         # from an ncu capture at 129^3 (the input volume once; the output stays in L2)
+                         "traffic": 16408064 if prob.n == (129, 129, 129) else None, "avg_launch_ms": dst_ms,
                          "flops_per_launch": dst_flops_per_launch(prob)},
             "kernel_ms_per_step": shares, "dominant_kernel": names[dom], "tuning": idp.plan_tuning(plan),
             "clocks": clk.summary()}
