@@ -186,6 +186,18 @@ struct idp_plan_s {
     cudaStream_t cap = nullptr;
     cudaStream_t side = nullptr;          // second stream of a solve (forward transform of rho)
     cudaEvent_t fork = nullptr, join = nullptr;
+    // host-buffer solves (3-D, pinned buffers, captured into their own graph): phi
+    // comes down in slabs along axis 0 on a copy stream, each slab as soon as the
+    // last sine pass has finished it, overlapped with the pass on the other slabs
+    static constexpr int NSLAB = 4;
+    cudaStream_t cst = nullptr;
+    cudaEvent_t ev_cfork = nullptr, ev_cjoin = nullptr, ev_out[NSLAB] = {};
+    const double *hio_rho = nullptr;   // host buffers of the solve being queued (null: none)
+    double *hio_phi = nullptr;
+    cudaGraphExec_t hexec = nullptr;
+    const double *hg_rho = nullptr;
+    double *hg_phi = nullptr;
+    uint64_t hg_version = ~0ull;
     cudaGraphExec_t gexec = nullptr;
     const double *g_rho = nullptr;
     double *g_phi = nullptr;
@@ -424,9 +436,37 @@ int transform_mixed(idp_plan p, View3 in, View3 out, const double *tab, View3 ad
 // one full sine transform (all active axes); `first` pass reads `in`, the
 // last pass applies the epilogue (tab, add) and writes `out`; intermediate
 // passes run in place on `work`.
-int transform(idp_plan p, View3 in, double *work, View3 out, const double *tab, View3 add, bool forward,
-              cudaStream_t st, bool allow_reduced = true, bool skip_axis2 = false, int in_dd0 = 0)
+// slabs of a pipelined host-buffer solve: interior slices i0 in [lo, lo + cnt)
+int nslab(idp_plan p) { return std::min((int)idp_plan_s::NSLAB, p->ni[0]); }
+
+void slab_lines(idp_plan p, int s, int &lo, int &cnt)
 {
+    const int S = nslab(p);
+    lo = (int)((int64_t)s * p->ni[0] / S);
+    cnt = (int)((int64_t)(s + 1) * p->ni[0] / S) - lo;
+}
+
+// node slices copied with slab s: its interior slices, and the boundary slice
+// next to the first and the last slab; returned as an element offset and count
+void slab_nodes(idp_plan p, int s, int64_t &off, int64_t &cnt)
+{
+    int lo, n;
+    slab_lines(p, s, lo, n);
+    const int jlo = s == 0 ? 0 : lo + 1, jhi = s == nslab(p) - 1 ? p->n[0] : lo + n + 1;
+    const int64_t slice = (int64_t)p->n[1] * p->n[2];
+    off = jlo * slice;
+    cnt = (int64_t)(jhi - jlo) * slice;
+}
+
+// final_copied: the final transform of a pipelined host-buffer solve (phi is the
+// device copy of the host output): its last pass (along axis 2) runs slab by slab
+// and each slab of phi goes down on the copy stream as soon as it is done;
+// *final_copied tells whether that happened.
+int transform(idp_plan p, View3 in, double *work, View3 out, const double *tab, View3 add, bool forward,
+              cudaStream_t st, bool allow_reduced = true, bool skip_axis2 = false, int in_dd0 = 0,
+              bool *final_copied = nullptr)
+{
+    if (final_copied) *final_copied = false;
     if (p->mixed == IDP_PRECISION_MIXED_BF16X3 && allow_reduced && p->mixed_path == 0)
         return transform_mixed(p, in, out, tab, add, st == p->side ? 1 : 0, st);
     // df32 passes: precision DF32, or precision MIXED when the autotuner found the
@@ -468,6 +508,28 @@ int transform(idp_plan p, View3 in, double *work, View3 out, const double *tab, 
             a.twd = t.fwdd;
             a.halfd = t.halfd;
             a.sin2d = p->sin2d[p->M[s]];
+        }
+        if (final_copied && p->hio_phi && p->d == 3 && s == 2 && q == na - 1) {
+            // the lines of the axis-2 pass are indexed (i0, i1): slab by slab along i0
+            for (int sl = 0; sl < nslab(p); ++sl) {
+                int lo, cnt;
+                slab_lines(p, sl, lo, cnt);
+                a.u0 = lo;
+                a.ucount = cnt;
+                a.lines = 8;   // a quarter of the lines: the smaller blocks fill the GPU (same bits)
+                {
+                    Mark mk(p, IDP_KERNEL_DST, st);
+                    IDP_CK(launch_dst_pass(a, st));
+                }
+                int64_t off, n;
+                slab_nodes(p, sl, off, n);
+                IDP_CK(cudaEventRecord(p->ev_out[sl], st));
+                IDP_CK(cudaStreamWaitEvent(p->cst, p->ev_out[sl], 0));
+                IDP_CK(cudaMemcpyAsync(p->hio_phi + off, p->h_phi + off, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                                       p->cst));
+            }
+            *final_copied = true;
+            continue;
         }
         Mark mk(p, IDP_KERNEL_DST, st);
         IDP_CK(launch_dst_pass(a, st));
@@ -582,25 +644,36 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
     // which rows and slices of rho are non-zero (zero ones are skipped below;
     // their contributions are exactly zero)
     IDP_CK(cudaMemsetAsync(p->flags, 0, sizeof(int) * p->nflags, st));
+    // stage 1a: along axis 2 -> T0[i0][i1][m2]; stage 1b: along axis 1 -> T1[i0][i2][m1]
+    RfftPass a2{}, a1{};
+    a2.in = r.p; a2.is0 = r.s0; a2.is1 = r.s1; a2.is2 = r.s2;
+    a2.out = p->T0;
+    a2.os2 = 1; a2.os1 = p->M[2] + 1; a2.os0 = (int64_t)p->ni[1] * (p->M[2] + 1);
+    a2.n0 = p->ni[0]; a2.n1 = p->ni[1]; a2.n2 = p->ni[2];
+    a2.axis = 2; a2.M = p->M[2];
+    if ((rc = get_fft(p, p->M[2], &t))) return rc;
+    a2.t = t;
+    a2.dd = dd;
+    a2.lineflag = p->row2;
+    a1.in = r.p; a1.is0 = r.s0; a1.is1 = r.s1; a1.is2 = r.s2;
+    a1.out = p->T1;
+    a1.os1 = 1; a1.os2 = p->M[1] + 1; a1.os0 = (int64_t)p->ni[2] * (p->M[1] + 1);
+    a1.n0 = p->ni[0]; a1.n1 = p->ni[1]; a1.n2 = p->ni[2];
+    a1.axis = 1; a1.M = p->M[1];
+    if ((rc = get_fft(p, p->M[1], &t))) return rc;
+    a1.t = t;
+    a1.dd = dd;
+    a1.lineflag = p->row1;
+    // which rows and slices of rho are non-zero (zero ones are skipped below;
+    // their contributions are exactly zero)
     {
         Mark mk(p, IDP_KERNEL_SUPPORT, st);
         IDP_CK(launch_support_flags(p->grid, r.p, r.s0, r.s1, r.s2, p->row2, p->row1, p->sl[0], p->sl[1],
                                     p->sl[2], st));
     }
-    // stage 1a: along axis 2 -> T0[i0][i1][m2]
     {
-        RfftPass a{};
-        a.in = r.p; a.is0 = r.s0; a.is1 = r.s1; a.is2 = r.s2;
-        a.out = p->T0;
-        a.os2 = 1; a.os1 = p->M[2] + 1; a.os0 = (int64_t)p->ni[1] * (p->M[2] + 1);
-        a.n0 = p->ni[0]; a.n1 = p->ni[1]; a.n2 = p->ni[2];
-        a.axis = 2; a.M = p->M[2];
-        if ((rc = get_fft(p, p->M[2], &t))) return rc;
-        a.t = t;
-        a.dd = dd;
-        a.lineflag = p->row2;
         Mark mk(p, IDP_KERNEL_RFFT, st);
-        IDP_CK(launch_rfft_pass(a, st));
+        IDP_CK(launch_rfft_pass(a2, st));
     }
     if (fork_rho) {
         // the rest of the forward transform of rho runs beside the boundary stages
@@ -609,20 +682,9 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
         if ((rc = transform_rho_from_T0(p, p->side))) return rc;
         IDP_CK(cudaEventRecord(p->join, p->side));
     }
-    // stage 1b: along axis 1 -> T1[i0][i2][m1]
     {
-        RfftPass a{};
-        a.in = r.p; a.is0 = r.s0; a.is1 = r.s1; a.is2 = r.s2;
-        a.out = p->T1;
-        a.os1 = 1; a.os2 = p->M[1] + 1; a.os0 = (int64_t)p->ni[2] * (p->M[1] + 1);
-        a.n0 = p->ni[0]; a.n1 = p->ni[1]; a.n2 = p->ni[2];
-        a.axis = 1; a.M = p->M[1];
-        if ((rc = get_fft(p, p->M[1], &t))) return rc;
-        a.t = t;
-        a.dd = dd;
-        a.lineflag = p->row1;
         Mark mk(p, IDP_KERNEL_RFFT, st);
-        IDP_CK(launch_rfft_pass(a, st));
+        IDP_CK(launch_rfft_pass(a1, st));
     }
     if (p->d == 2) {
         // faces of axis 1 (rows i1 = 0, M1; data along axis 2) and of axis 2
@@ -703,6 +765,21 @@ enum { RUN_PHI = 0 };
 
 // Queue the stages of one solve.  stop: 0 = full solve into phi; otherwise an
 // IDP_STAGE_* value whose result is written to `out`.
+// end of a pipelined host-buffer solve: phi goes down (if the final pass did not
+// send it slab by slab) and the copy stream joins the launch stream
+int finish_host_out(idp_plan p, bool copied, cudaStream_t st)
+{
+    if (!p->hio_phi) return IDP_OK;
+    if (!copied) {
+        IDP_CK(cudaEventRecord(p->ev_out[0], st));
+        IDP_CK(cudaStreamWaitEvent(p->cst, p->ev_out[0], 0));
+        IDP_CK(cudaMemcpyAsync(p->hio_phi, p->h_phi, sizeof(double) * p->nodes, cudaMemcpyDeviceToHost, p->cst));
+    }
+    IDP_CK(cudaEventRecord(p->ev_cjoin, p->cst));
+    IDP_CK(cudaStreamWaitEvent(st, p->ev_cjoin, 0));
+    return IDP_OK;
+}
+
 int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t st)
 {
     int rc;
@@ -724,6 +801,13 @@ int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t s
     // FP64 / df32 transforms: the first pass of the forward transform of rho is
     // the imaginary part of the boundary's first real FFT (see transform_rho_from_T0)
     const bool rho_from_T0 = (stop == 0) && !(p->mixed == IDP_PRECISION_MIXED_BF16X3 && p->mixed_path == 0);
+    if (stop == 0 && p->hio_rho) {
+        // host-buffer solve: rho goes up first (splitting the first kernels into
+        // slabs to overlap this copy costs them more than it hides)
+        IDP_CK(cudaMemcpyAsync(p->h_rho, p->hio_rho, sizeof(double) * p->nodes, cudaMemcpyHostToDevice, st));
+        IDP_CK(cudaEventRecord(p->ev_cfork, st));
+        IDP_CK(cudaStreamWaitEvent(p->cst, p->ev_cfork, 0));
+    }
     if (overlap_rho && !rho_from_T0) {
         IDP_CK(cudaEventRecord(p->fork, st));
         IDP_CK(cudaStreamWaitEvent(p->side, p->fork, 0));
@@ -757,7 +841,11 @@ int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t s
             Mark mk(p, IDP_KERNEL_GTILDE_EXPAND, st);
             IDP_CK(launch_gtilde_expand(p->grid, p->Q0, p->Q1, p->Q2, p->sin4, p->tab4, p->A, p->A, st));
         }
-        return transform(p, dense(p, p->A), p->A, node_interior(p, phi), nullptr, none, false, st);
+        bool copied = false;
+        if ((rc = transform(p, dense(p, p->A), p->A, node_interior(p, phi), nullptr, none, false, st, true, false, 0,
+                            &copied)))
+            return rc;
+        return finish_host_out(p, copied, st);
     }
     // 4. u1 = S B, B = tab4 * S gtilde; in a full solve also C = A + tabR * S gtilde,
     //    the solution coefficients less the layer correction (R_spec's share)
@@ -810,8 +898,11 @@ int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t s
         Mark mk(p, IDP_KERNEL_RHS6_EXPAND, st);
         IDP_CK(launch_rhs6_e_expand(p->grid, p->E0, p->E1, p->E2, p->sin4, p->sin4b, p->tab4, p->C, st));
     }
-    return transform(p, dense(p, p->C), p->C, node_interior(p, phi), nullptr,
-                     fold_u1 ? none : node_interior(p, p->U), false, st);
+    bool copied = false;
+    if ((rc = transform(p, dense(p, p->C), p->C, node_interior(p, phi), nullptr,
+                        fold_u1 ? none : node_interior(p, p->U), false, st, true, false, 0, &copied)))
+        return rc;
+    return finish_host_out(p, copied, st);
 }
 
 int plan_setup(idp_plan p)
@@ -858,6 +949,15 @@ int plan_setup(idp_plan p)
     if (!p->cap) IDP_CK(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
     IDP_CK(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming));
     IDP_CK(cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming));
+    if (p->d == 3) {
+        // copy stream and events of pipelined host-buffer solves
+        IDP_CK(cudaStreamCreateWithFlags(&p->cst, cudaStreamNonBlocking));
+        IDP_CK(cudaEventCreateWithFlags(&p->ev_cfork, cudaEventDisableTiming));
+        IDP_CK(cudaEventCreateWithFlags(&p->ev_cjoin, cudaEventDisableTiming));
+        for (int s = 0; s < idp_plan_s::NSLAB; ++s) {
+            IDP_CK(cudaEventCreateWithFlags(&p->ev_out[s], cudaEventDisableTiming));
+        }
+    }
     {
         std::vector<double> s4;
         for (int s = 0; s < 3; ++s) {
@@ -1145,6 +1245,53 @@ int run_solve(idp_plan p, const double *rho, double *phi, cudaStream_t st)
     return IDP_OK;
 }
 
+// host memory that the GPU copies from without staging (page-locked or registered)
+bool pinned(const void *ptr)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost;
+}
+
+// a solve from host buffers with the download pipelined against the last sine
+// pass (3-D, pinned buffers, graphs on): its own cached graph, keyed by the host
+// pointers and the plan's settings
+int run_solve_host(idp_plan p, const double *rho_h, double *phi_h, cudaStream_t st)
+{
+    p->last = st;
+    p->last_valid = 1;
+    if (!p->hexec || p->hg_rho != rho_h || p->hg_phi != phi_h || p->hg_version != p->version) {
+        IDP_CK(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+        p->hio_rho = rho_h;
+        p->hio_phi = phi_h;
+        int rc = enqueue(p, p->h_rho, p->h_phi, 0, p->cap);
+        p->hio_rho = nullptr;
+        p->hio_phi = nullptr;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(p->cap, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        if (p->hexec) {
+            cudaGraphExecDestroy(p->hexec);
+            p->hexec = nullptr;
+        }
+        e = cudaGraphInstantiate(&p->hexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        p->hg_rho = rho_h;
+        p->hg_phi = phi_h;
+        p->hg_version = p->version;
+    }
+    IDP_CK(cudaGraphLaunch(p->hexec, st));
+    return IDP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1280,9 +1427,14 @@ int idp_solve_host(idp_plan p, const double *rho_host, double *phi_host, void *s
     int rc;
     if (!p->h_rho && ((rc = p->alloc(&p->h_rho, p->nodes)) || (rc = p->alloc(&p->h_phi, p->nodes)))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    IDP_CK(cudaMemcpyAsync(p->h_rho, rho_host, b, cudaMemcpyHostToDevice, st));
-    if ((rc = run_solve(p, p->h_rho, p->h_phi, st))) return rc;
-    IDP_CK(cudaMemcpyAsync(phi_host, p->h_phi, b, cudaMemcpyDeviceToHost, st));
+    if (p->d == 3 && p->cst && p->use_graph && !p->stall_test && pinned(rho_host) && pinned(phi_host)) {
+        // phi comes down in slabs, overlapped with the last sine pass
+        if ((rc = run_solve_host(p, rho_host, phi_host, st))) return rc;
+    } else {
+        IDP_CK(cudaMemcpyAsync(p->h_rho, rho_host, b, cudaMemcpyHostToDevice, st));
+        if ((rc = run_solve(p, p->h_rho, p->h_phi, st))) return rc;
+        IDP_CK(cudaMemcpyAsync(phi_host, p->h_phi, b, cudaMemcpyDeviceToHost, st));
+    }
     IDP_CK(cudaStreamSynchronize(st));
     return IDP_OK;
 }
@@ -1438,6 +1590,13 @@ int idp_destroy_plan(idp_plan p)
     if (!p) return IDP_EINVAL;
     cudaDeviceSynchronize();
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->hexec) cudaGraphExecDestroy(p->hexec);
+    if (p->cst) cudaStreamDestroy(p->cst);
+    if (p->ev_cfork) cudaEventDestroy(p->ev_cfork);
+    if (p->ev_cjoin) cudaEventDestroy(p->ev_cjoin);
+    for (int s = 0; s < idp_plan_s::NSLAB; ++s) {
+        if (p->ev_out[s]) cudaEventDestroy(p->ev_out[s]);
+    }
     if (p->cap) cudaStreamDestroy(p->cap);
     if (p->side) cudaStreamDestroy(p->side);
     if (p->bst) cudaStreamDestroy(p->bst);

@@ -159,6 +159,30 @@ def test_host_entry_point_matches_device_entry_point(idp):
     assert np.array_equal(out_h, out_d.cpu().numpy())
 
 
+@pytest.mark.parametrize("mode,order", [("fp64", 6), ("fp64", 4), ("df32", 6), ("mixed", 6)])
+def test_pinned_host_solve_pipelines_copies_and_gives_the_device_bits(idp, mode, order):
+    # from page-locked host buffers the copies go in slabs along axis 0, overlapped
+    # with the kernels (a graph of its own): the result must be the device entry
+    # point's, bit for bit, on repeated calls and after the host buffers change
+    import torch
+    prob = w.Problem("h", (65, 33, 129), (0.0, 0.0, 0.0), (1.0, 1.0, 2.0), "gauss", dict(seed=5))
+    plan = idp.create_plan(3, prob.n, prob.h, order)
+    if mode != "fp64":
+        idp.plan_set(plan, idp.IDP_KEY_PRECISION,
+                     idp.IDP_PRECISION_DF32 if mode == "df32" else idp.IDP_PRECISION_MIXED_BF16X3)
+    rho = prob.rho()
+    ref = to_dev(np.zeros(prob.n))
+    idp.solve(plan, to_dev(rho), ref)
+    ref = ref.cpu().numpy()
+    rho_p = [torch.from_numpy(rho).pin_memory(), torch.from_numpy(rho.copy()).pin_memory()]
+    phi_p = [torch.zeros(prob.n, dtype=torch.float64).pin_memory() for _ in range(2)]
+    for k in (0, 0, 1, 0):
+        phi_p[k].zero_()
+        idp.solve_host(plan, rho_p[k].data_ptr(), phi_p[k].data_ptr())
+        idp.plan_status(plan)
+        assert np.array_equal(phi_p[k].numpy(), ref), k
+
+
 def test_graph_and_plain_launches_agree_and_repeat(idp):
     prob = w.c3_large(65)
     rho = to_dev(prob.rho())
