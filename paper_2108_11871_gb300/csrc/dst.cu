@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(NTB) dst_pass_kernel(const DstPass a)
     // strides are taken from the parameters where they are used, so that none
     // of them stays live across the FFT.
     const int nv = a.axis == 2 ? a.n1 : a.n2;
-    const int u = blockIdx.y + a.u0;
+    const int u = blockIdx.y;
     const int v0 = blockIdx.x * LB;
     const int nl = min(LB, nv - v0);
     const bool contig = (a.axis == 2);
@@ -299,7 +299,6 @@ cudaError_t launch_k(const DstPass &a, cudaStream_t st)
     if (a.axis == 2) { nu = a.n0; nv = a.n1; }
     else if (a.axis == 1) { nu = a.n0; nv = a.n2; }
     else { nu = a.n1; nv = a.n2; }
-    if (a.ucount > 0) nu = a.ucount;
     // 32 lines (M = 128) or 16 lines (M = 256) per block: the per-line prefix sum
     // then runs on at least half a warp (an FP64 warp instruction costs the pipe the
     // same whatever its active lanes)

@@ -63,7 +63,6 @@ struct DstPass {
     const ddr *sin2d;
     int lines;   // lines per block: 0 = by size (8 for launches of < 2 blocks per SM), 8 = always 8,
                  // -8 = 8 lines on 128 threads (M = 128), 32 (M = 128), 16 (M = 256)
-    int u0, ucount;   // optional: only the lines with u in [u0, u0 + ucount) (ucount 0: all)
 };
 
 cudaError_t launch_dst_pass(const DstPass &a, cudaStream_t st);

@@ -186,14 +186,10 @@ struct idp_plan_s {
     cudaStream_t cap = nullptr;
     cudaStream_t side = nullptr;          // second stream of a solve (forward transform of rho)
     cudaEvent_t fork = nullptr, join = nullptr;
-    // host-buffer solves (3-D, pinned buffers, captured into their own graph): phi
-    // comes down in slabs along axis 0 on a copy stream, each slab as soon as the
-    // last sine pass has finished it, overlapped with the pass on the other slabs
-    static constexpr int NSLAB = 4;
-    cudaStream_t cst = nullptr;
-    cudaEvent_t ev_cfork = nullptr, ev_cjoin = nullptr, ev_out[NSLAB] = {};
-    const double *hio_rho = nullptr;   // host buffers of the solve being queued (null: none)
-    double *hio_phi = nullptr;
+    // host-buffer solves (page-locked buffers, captured into their own graph): rho
+    // goes up in one copy, and the kernels that write phi write the host buffer
+    // directly (through its device view), so the download overlaps their work
+    const double *hio_rho = nullptr;   // host rho of the solve being queued (null: none)
     cudaGraphExec_t hexec = nullptr;
     const double *hg_rho = nullptr;
     double *hg_phi = nullptr;
@@ -436,37 +432,9 @@ int transform_mixed(idp_plan p, View3 in, View3 out, const double *tab, View3 ad
 // one full sine transform (all active axes); `first` pass reads `in`, the
 // last pass applies the epilogue (tab, add) and writes `out`; intermediate
 // passes run in place on `work`.
-// slabs of a pipelined host-buffer solve: interior slices i0 in [lo, lo + cnt)
-int nslab(idp_plan p) { return std::min((int)idp_plan_s::NSLAB, p->ni[0]); }
-
-void slab_lines(idp_plan p, int s, int &lo, int &cnt)
-{
-    const int S = nslab(p);
-    lo = (int)((int64_t)s * p->ni[0] / S);
-    cnt = (int)((int64_t)(s + 1) * p->ni[0] / S) - lo;
-}
-
-// node slices copied with slab s: its interior slices, and the boundary slice
-// next to the first and the last slab; returned as an element offset and count
-void slab_nodes(idp_plan p, int s, int64_t &off, int64_t &cnt)
-{
-    int lo, n;
-    slab_lines(p, s, lo, n);
-    const int jlo = s == 0 ? 0 : lo + 1, jhi = s == nslab(p) - 1 ? p->n[0] : lo + n + 1;
-    const int64_t slice = (int64_t)p->n[1] * p->n[2];
-    off = jlo * slice;
-    cnt = (int64_t)(jhi - jlo) * slice;
-}
-
-// final_copied: the final transform of a pipelined host-buffer solve (phi is the
-// device copy of the host output): its last pass (along axis 2) runs slab by slab
-// and each slab of phi goes down on the copy stream as soon as it is done;
-// *final_copied tells whether that happened.
 int transform(idp_plan p, View3 in, double *work, View3 out, const double *tab, View3 add, bool forward,
-              cudaStream_t st, bool allow_reduced = true, bool skip_axis2 = false, int in_dd0 = 0,
-              bool *final_copied = nullptr)
+              cudaStream_t st, bool allow_reduced = true, bool skip_axis2 = false, int in_dd0 = 0)
 {
-    if (final_copied) *final_copied = false;
     if (p->mixed == IDP_PRECISION_MIXED_BF16X3 && allow_reduced && p->mixed_path == 0)
         return transform_mixed(p, in, out, tab, add, st == p->side ? 1 : 0, st);
     // df32 passes: precision DF32, or precision MIXED when the autotuner found the
@@ -508,28 +476,6 @@ int transform(idp_plan p, View3 in, double *work, View3 out, const double *tab, 
             a.twd = t.fwdd;
             a.halfd = t.halfd;
             a.sin2d = p->sin2d[p->M[s]];
-        }
-        if (final_copied && p->hio_phi && p->d == 3 && s == 2 && q == na - 1) {
-            // the lines of the axis-2 pass are indexed (i0, i1): slab by slab along i0
-            for (int sl = 0; sl < nslab(p); ++sl) {
-                int lo, cnt;
-                slab_lines(p, sl, lo, cnt);
-                a.u0 = lo;
-                a.ucount = cnt;
-                a.lines = 8;   // a quarter of the lines: the smaller blocks fill the GPU (same bits)
-                {
-                    Mark mk(p, IDP_KERNEL_DST, st);
-                    IDP_CK(launch_dst_pass(a, st));
-                }
-                int64_t off, n;
-                slab_nodes(p, sl, off, n);
-                IDP_CK(cudaEventRecord(p->ev_out[sl], st));
-                IDP_CK(cudaStreamWaitEvent(p->cst, p->ev_out[sl], 0));
-                IDP_CK(cudaMemcpyAsync(p->hio_phi + off, p->h_phi + off, sizeof(double) * n, cudaMemcpyDeviceToHost,
-                                       p->cst));
-            }
-            *final_copied = true;
-            continue;
         }
         Mark mk(p, IDP_KERNEL_DST, st);
         IDP_CK(launch_dst_pass(a, st));
@@ -765,21 +711,6 @@ enum { RUN_PHI = 0 };
 
 // Queue the stages of one solve.  stop: 0 = full solve into phi; otherwise an
 // IDP_STAGE_* value whose result is written to `out`.
-// end of a pipelined host-buffer solve: phi goes down (if the final pass did not
-// send it slab by slab) and the copy stream joins the launch stream
-int finish_host_out(idp_plan p, bool copied, cudaStream_t st)
-{
-    if (!p->hio_phi) return IDP_OK;
-    if (!copied) {
-        IDP_CK(cudaEventRecord(p->ev_out[0], st));
-        IDP_CK(cudaStreamWaitEvent(p->cst, p->ev_out[0], 0));
-        IDP_CK(cudaMemcpyAsync(p->hio_phi, p->h_phi, sizeof(double) * p->nodes, cudaMemcpyDeviceToHost, p->cst));
-    }
-    IDP_CK(cudaEventRecord(p->ev_cjoin, p->cst));
-    IDP_CK(cudaStreamWaitEvent(st, p->ev_cjoin, 0));
-    return IDP_OK;
-}
-
 int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t st)
 {
     int rc;
@@ -803,10 +734,8 @@ int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t s
     const bool rho_from_T0 = (stop == 0) && !(p->mixed == IDP_PRECISION_MIXED_BF16X3 && p->mixed_path == 0);
     if (stop == 0 && p->hio_rho) {
         // host-buffer solve: rho goes up first (splitting the first kernels into
-        // slabs to overlap this copy costs them more than it hides)
+        // slabs to overlap this copy costs them more than it hides, measured)
         IDP_CK(cudaMemcpyAsync(p->h_rho, p->hio_rho, sizeof(double) * p->nodes, cudaMemcpyHostToDevice, st));
-        IDP_CK(cudaEventRecord(p->ev_cfork, st));
-        IDP_CK(cudaStreamWaitEvent(p->cst, p->ev_cfork, 0));
     }
     if (overlap_rho && !rho_from_T0) {
         IDP_CK(cudaEventRecord(p->fork, st));
@@ -841,11 +770,7 @@ int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t s
             Mark mk(p, IDP_KERNEL_GTILDE_EXPAND, st);
             IDP_CK(launch_gtilde_expand(p->grid, p->Q0, p->Q1, p->Q2, p->sin4, p->tab4, p->A, p->A, st));
         }
-        bool copied = false;
-        if ((rc = transform(p, dense(p, p->A), p->A, node_interior(p, phi), nullptr, none, false, st, true, false, 0,
-                            &copied)))
-            return rc;
-        return finish_host_out(p, copied, st);
+        return transform(p, dense(p, p->A), p->A, node_interior(p, phi), nullptr, none, false, st);
     }
     // 4. u1 = S B, B = tab4 * S gtilde; in a full solve also C = A + tabR * S gtilde,
     //    the solution coefficients less the layer correction (R_spec's share)
@@ -898,11 +823,8 @@ int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t s
         Mark mk(p, IDP_KERNEL_RHS6_EXPAND, st);
         IDP_CK(launch_rhs6_e_expand(p->grid, p->E0, p->E1, p->E2, p->sin4, p->sin4b, p->tab4, p->C, st));
     }
-    bool copied = false;
-    if ((rc = transform(p, dense(p, p->C), p->C, node_interior(p, phi), nullptr,
-                        fold_u1 ? none : node_interior(p, p->U), false, st, true, false, 0, &copied)))
-        return rc;
-    return finish_host_out(p, copied, st);
+    return transform(p, dense(p, p->C), p->C, node_interior(p, phi), nullptr,
+                     fold_u1 ? none : node_interior(p, p->U), false, st);
 }
 
 int plan_setup(idp_plan p)
@@ -949,15 +871,6 @@ int plan_setup(idp_plan p)
     if (!p->cap) IDP_CK(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
     IDP_CK(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming));
     IDP_CK(cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming));
-    if (p->d == 3) {
-        // copy stream and events of pipelined host-buffer solves
-        IDP_CK(cudaStreamCreateWithFlags(&p->cst, cudaStreamNonBlocking));
-        IDP_CK(cudaEventCreateWithFlags(&p->ev_cfork, cudaEventDisableTiming));
-        IDP_CK(cudaEventCreateWithFlags(&p->ev_cjoin, cudaEventDisableTiming));
-        for (int s = 0; s < idp_plan_s::NSLAB; ++s) {
-            IDP_CK(cudaEventCreateWithFlags(&p->ev_out[s], cudaEventDisableTiming));
-        }
-    }
     {
         std::vector<double> s4;
         for (int s = 0; s < 3; ++s) {
@@ -1245,31 +1158,32 @@ int run_solve(idp_plan p, const double *rho, double *phi, cudaStream_t st)
     return IDP_OK;
 }
 
-// host memory that the GPU copies from without staging (page-locked or registered)
-bool pinned(const void *ptr)
+// device view of page-locked (or registered, mapped) host memory: the address at
+// which kernels read and write it directly; null for other memory
+double *device_view(const void *ptr)
 {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return nullptr;
     }
-    return at.type == cudaMemoryTypeHost;
+    return at.type == cudaMemoryTypeHost ? static_cast<double *>(at.devicePointer) : nullptr;
 }
 
-// a solve from host buffers with the download pipelined against the last sine
-// pass (3-D, pinned buffers, graphs on): its own cached graph, keyed by the host
-// pointers and the plan's settings
-int run_solve_host(idp_plan p, const double *rho_h, double *phi_h, cudaStream_t st)
+// a solve from page-locked host buffers: rho goes up in one copy, and the kernels
+// that produce phi (the boundary values and the last sine pass) write the host
+// buffer directly through its device view, so that the download runs inside
+// them instead of after them.  Its own cached graph, keyed by the host pointers
+// and the plan's settings.
+int run_solve_host(idp_plan p, const double *rho_h, double *phi_h, double *phi_view, cudaStream_t st)
 {
     p->last = st;
     p->last_valid = 1;
     if (!p->hexec || p->hg_rho != rho_h || p->hg_phi != phi_h || p->hg_version != p->version) {
         IDP_CK(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
         p->hio_rho = rho_h;
-        p->hio_phi = phi_h;
-        int rc = enqueue(p, p->h_rho, p->h_phi, 0, p->cap);
+        int rc = enqueue(p, p->h_rho, phi_view, 0, p->cap);
         p->hio_rho = nullptr;
-        p->hio_phi = nullptr;
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(p->cap, &g);
         if (rc) {
@@ -1427,9 +1341,10 @@ int idp_solve_host(idp_plan p, const double *rho_host, double *phi_host, void *s
     int rc;
     if (!p->h_rho && ((rc = p->alloc(&p->h_rho, p->nodes)) || (rc = p->alloc(&p->h_phi, p->nodes)))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    if (p->d == 3 && p->cst && p->use_graph && !p->stall_test && pinned(rho_host) && pinned(phi_host)) {
-        // phi comes down in slabs, overlapped with the last sine pass
-        if ((rc = run_solve_host(p, rho_host, phi_host, st))) return rc;
+    double *phi_view = nullptr;
+    if (p->use_graph && !p->stall_test && device_view(rho_host) && (phi_view = device_view(phi_host))) {
+        // page-locked buffers: phi is written in place by the kernels
+        if ((rc = run_solve_host(p, rho_host, phi_host, phi_view, st))) return rc;
     } else {
         IDP_CK(cudaMemcpyAsync(p->h_rho, rho_host, b, cudaMemcpyHostToDevice, st));
         if ((rc = run_solve(p, p->h_rho, p->h_phi, st))) return rc;
@@ -1591,12 +1506,6 @@ int idp_destroy_plan(idp_plan p)
     cudaDeviceSynchronize();
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->hexec) cudaGraphExecDestroy(p->hexec);
-    if (p->cst) cudaStreamDestroy(p->cst);
-    if (p->ev_cfork) cudaEventDestroy(p->ev_cfork);
-    if (p->ev_cjoin) cudaEventDestroy(p->ev_cjoin);
-    for (int s = 0; s < idp_plan_s::NSLAB; ++s) {
-        if (p->ev_out[s]) cudaEventDestroy(p->ev_out[s]);
-    }
     if (p->cap) cudaStreamDestroy(p->cap);
     if (p->side) cudaStreamDestroy(p->side);
     if (p->bst) cudaStreamDestroy(p->bst);

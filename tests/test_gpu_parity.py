@@ -160,9 +160,9 @@ def test_host_entry_point_matches_device_entry_point(idp):
 
 
 @pytest.mark.parametrize("mode,order", [("fp64", 6), ("fp64", 4), ("df32", 6), ("mixed", 6)])
-def test_pinned_host_solve_pipelines_copies_and_gives_the_device_bits(idp, mode, order):
-    # from page-locked host buffers the copies go in slabs along axis 0, overlapped
-    # with the kernels (a graph of its own): the result must be the device entry
+def test_pinned_host_solve_gives_the_device_bits(idp, mode, order):
+    # from page-locked host buffers the kernels that produce phi write the host
+    # buffer directly (a graph of its own): the result must be the device entry
     # point's, bit for bit, on repeated calls and after the host buffers change
     import torch
     prob = w.Problem("h", (65, 33, 129), (0.0, 0.0, 0.0), (1.0, 1.0, 2.0), "gauss", dict(seed=5))
