@@ -20,10 +20,12 @@ namespace idp {
 namespace {
 constexpr int NT = 256;
 
-// lines per block so that 2 buffers of LB x L complex fit in 64 KB
+// lines per block: 2 buffers of LB x L complex in 32 KB (a radix-4 unit per
+// thread per pass; 7 blocks per SM, so that the blocks with non-zero lines of rho
+// keep the FP64 pipe busy while the all-zero ones finish)
 template <int L>
 struct LineCfg {
-    static constexpr int LB = (2048 / L) > 32 ? 32 : ((2048 / L) < 1 ? 1 : 2048 / L);
+    static constexpr int LB = (1024 / L) > 32 ? 32 : ((1024 / L) < 1 ? 1 : 1024 / L);
 };
 
 // ---------------------------------------------------------------- stage 1
