@@ -20,12 +20,12 @@ namespace idp {
 namespace {
 constexpr int NT = 256;
 
-// lines per block: 2 buffers of LB x L complex in 32 KB (a radix-4 unit per
-// thread per pass; 7 blocks per SM, so that the blocks with non-zero lines of rho
-// keep the FP64 pipe busy while the all-zero ones finish)
+// lines per block: 2 buffers of LB x L complex in 16 KB (small blocks: the
+// all-zero line blocks of rho finish at once, and many blocks per SM keep the FP64
+// pipe busy on the others; measured best at M = 128)
 template <int L>
 struct LineCfg {
-    static constexpr int LB = (1024 / L) > 32 ? 32 : ((1024 / L) < 1 ? 1 : 1024 / L);
+    static constexpr int LB = (512 / L) > 32 ? 32 : ((512 / L) < 1 ? 1 : 512 / L);
 };
 
 // ---------------------------------------------------------------- stage 1
