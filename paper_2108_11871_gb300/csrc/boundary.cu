@@ -283,12 +283,21 @@ struct SmallCfg {
     static constexpr int LB = (512 / L) > 32 ? 32 : ((512 / L) < 1 ? 1 : 512 / L);
 };
 
+// columns per block of face_invb: its cost is the FP64 sum of the slice-chunk
+// partials, one value per thread, so half the columns of SmallCfg (twice the blocks)
+template <int L>
+struct InvbCfg {
+    static constexpr int TC = (256 / L) > 32 ? 32 : ((256 / L) < 1 ? 1 : 256 / L);
+};
+template <int L>
+size_t smem_invb() { return 2 * sizeof(double2) * InvbCfg<L>::TC * L; }
+
 template <class R, int L>
 __global__ void __launch_bounds__(NT) face_invb_kernel(const FaceInvB a)
 {
     using A = Ar<R>;
     using Cx = typename A::C;
-    constexpr int TC = SmallCfg<L>::LB;
+    constexpr int TC = InvbCfg<L>::TC;
     constexpr int Mb = L / 2;
     extern __shared__ double2 smem_raw[];
     Cx *bufA = reinterpret_cast<Cx *>(smem_raw), *bufB = bufA + TC * L;
@@ -436,7 +445,7 @@ cudaError_t attrs_len_r()
                                   (int)smem_face<L>())))
         return e;
     if ((e = cudaFuncSetAttribute(face_invb_kernel<R, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem_small<L>())))
+                                  (int)smem_invb<L>())))
         return e;
     return cudaFuncSetAttribute(face_c2r_kernel<R, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem_small<L>());
@@ -534,9 +543,9 @@ cudaError_t launch_face_pass_2d(const FacePass2D &a, cudaStream_t st)
 cudaError_t launch_face_inv_b(const FaceInvB &a, cudaStream_t st)
 {
     IDP_LEN_SWITCH(2 * a.Mb, {
-        dim3 grid((a.nc + SmallCfg<L>::LB - 1) / SmallCfg<L>::LB, 2);
-        if (a.dd) face_invb_kernel<ddr, L><<<grid, NT, smem_small<L>(), st>>>(a);
-        else face_invb_kernel<double, L><<<grid, NT, smem_small<L>(), st>>>(a);
+        dim3 grid((a.nc + InvbCfg<L>::TC - 1) / InvbCfg<L>::TC, 2);
+        if (a.dd) face_invb_kernel<ddr, L><<<grid, NT, smem_invb<L>(), st>>>(a);
+        else face_invb_kernel<double, L><<<grid, NT, smem_invb<L>(), st>>>(a);
         return cudaGetLastError();
     })
 }
