@@ -275,22 +275,23 @@ __global__ void face2d_kernel(const FacePass2D a)
     a.acc[a.nm + m] = hi;
 }
 
-// ---------------------------------------------------------------- stage 3a
-// small lines-per-block for the two inverse stages: they are short and need
-// many blocks to fill the GPU
-template <int L>
-struct SmallCfg {
-    static constexpr int LB = (512 / L) > 32 ? 32 : ((512 / L) < 1 ? 1 : 512 / L);
-};
-
 // columns per block of face_invb: its cost is the FP64 sum of the slice-chunk
-// partials, one value per thread, so half the columns of SmallCfg (twice the blocks)
+// partials, one value per thread (one column of 256 values at M = 128)
 template <int L>
 struct InvbCfg {
     static constexpr int TC = (256 / L) > 32 ? 32 : ((256 / L) < 1 ? 1 : 256 / L);
 };
 template <int L>
 size_t smem_invb() { return 2 * sizeof(double2) * InvbCfg<L>::TC * L; }
+
+// rows per block of face_c2r: a few hundred blocks at M = 128 (the launch is short
+// and latency-bound)
+template <int L>
+struct C2rCfg {
+    static constexpr int LB = (128 / L) > 32 ? 32 : ((128 / L) < 1 ? 1 : 128 / L);
+};
+template <int L>
+size_t smem_c2r() { return 2 * sizeof(double2) * C2rCfg<L>::LB * L; }
 
 template <class R, int L>
 __global__ void __launch_bounds__(NT) face_invb_kernel(const FaceInvB a)
@@ -333,7 +334,7 @@ __global__ void __launch_bounds__(NT) face_c2r_kernel(const FaceC2R a)
 {
     using A = Ar<R>;
     using Cx = typename A::C;
-    constexpr int LB = SmallCfg<L>::LB;
+    constexpr int LB = C2rCfg<L>::LB;
     extern __shared__ double2 smem_raw[];
     Cx *bufA = reinterpret_cast<Cx *>(smem_raw), *bufB = bufA + LB * L;
     const int face = blockIdx.y;
@@ -432,8 +433,6 @@ template <int L>
 size_t smem_lines() { return 2 * sizeof(double2) * LineCfg<L>::LB * L; }
 template <int L>
 size_t smem_face() { return 2 * sizeof(double2) * FaceCfg<L>::TC * L; }
-template <int L>
-size_t smem_small() { return 2 * sizeof(double2) * SmallCfg<L>::LB * L; }
 
 template <class R, int L>
 cudaError_t attrs_len_r()
@@ -448,7 +447,7 @@ cudaError_t attrs_len_r()
                                   (int)smem_invb<L>())))
         return e;
     return cudaFuncSetAttribute(face_c2r_kernel<R, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_small<L>());
+                                (int)smem_c2r<L>());
 }
 template <int L>
 cudaError_t attrs_len()
@@ -553,9 +552,9 @@ cudaError_t launch_face_inv_b(const FaceInvB &a, cudaStream_t st)
 cudaError_t launch_face_c2r(const FaceC2R &a, cudaStream_t st)
 {
     IDP_LEN_SWITCH(a.Mc, {
-        dim3 grid((a.nrows + SmallCfg<L>::LB - 1) / SmallCfg<L>::LB, 2);
-        if (a.dd) face_c2r_kernel<ddr, L><<<grid, NT, smem_small<L>(), st>>>(a);
-        else face_c2r_kernel<double, L><<<grid, NT, smem_small<L>(), st>>>(a);
+        dim3 grid((a.nrows + C2rCfg<L>::LB - 1) / C2rCfg<L>::LB, 2);
+        if (a.dd) face_c2r_kernel<ddr, L><<<grid, NT, smem_c2r<L>(), st>>>(a);
+        else face_c2r_kernel<double, L><<<grid, NT, smem_c2r<L>(), st>>>(a);
         return cudaGetLastError();
     })
 }
