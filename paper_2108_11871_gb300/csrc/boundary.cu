@@ -275,6 +275,7 @@ __global__ void face2d_kernel(const FacePass2D a)
     a.acc[a.nm + m] = hi;
 }
 
+// ---------------------------------------------------------------- stage 3a
 // columns per block of face_invb: its cost is the FP64 sum of the slice-chunk
 // partials, one value per thread (one column of 256 values at M = 128)
 template <int L>
