@@ -97,6 +97,7 @@ __device__ __forceinline__ void view_strides(const View3 &w, int axis, int64_t &
 template <class R, int K, int LBO, int NTB>
 __global__ void __launch_bounds__(NTB) dst_pass_kernel(const DstPass a)
 {
+    pdl_enter();
     using Cfg = DstCfg<K, LBO, NTB>;
     constexpr int NT = NTB;
     using A = Ar<R>;
@@ -288,8 +289,7 @@ cudaError_t launch_lb(const DstPass &a, int nu, int nv, cudaStream_t st)
     static_assert(4 * Cfg::LB <= NTB && Cfg::LB >= 8 && K % 4 == 0, "four scan lanes per line in whole warps");
     const size_t sm = 2 * sizeof(double2) * Cfg::LB * K;
     dim3 grid((nv + Cfg::LB - 1) / Cfg::LB, nu);
-    dst_pass_kernel<R, K, LBO, NTB><<<grid, NTB, sm, st>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(dst_pass_kernel<R, K, LBO, NTB>, grid, dim3(NTB), sm, st, a);
 }
 
 template <class R, int K>

@@ -65,6 +65,31 @@ struct DstPass {
                  // -8 = 8 lines on 128 threads (M = 128), 32 (M = 128), 16 (M = 256)
 };
 
+// Programmatic dependent launch: a kernel launched with launch_pdl lets the next
+// launch of its stream be placed on the GPU while it runs (pdl_enter at its start),
+// and waits for the previous launch to complete and flush before it reads
+// anything (also in pdl_enter).  For a kernel launched otherwise both are no-ops.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+template <class Kern, class... Args>
+cudaError_t launch_pdl(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 cudaError_t launch_dst_pass(const DstPass &a, cudaStream_t st);
 cudaError_t dst_set_attributes();
 cudaError_t boundary_set_attributes();
