@@ -165,7 +165,8 @@ struct idp_plan_s {
     int mixed = 0;
     int stall_test = 0;               // IDP_KEY_STALL_TEST: next tensor-core pass waits in vain
     int mixed_path = 0;               // mixed precision: 0 = tensor-core matrix pass, 1 = df32 FFT pass
-    int64_t part_cap = 0;             // capacity (complex) of the partial face sums
+    int64_t part_cap = 0;             // capacity (complex) of the partial face sums of one axis
+    int64_t f_cap = 0;                // capacity (complex) of the face spectra of one axis
     int tuned = 0;
     std::map<int, void *> mp_img;     // by M: BF16 pieces of the sine matrix
     float *t32[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [stream][ping/pong]
@@ -186,6 +187,10 @@ struct idp_plan_s {
     cudaStream_t cap = nullptr;
     cudaStream_t side = nullptr;          // second stream of a solve (forward transform of rho)
     cudaEvent_t fork = nullptr, join = nullptr;
+    // 3-D faces: axes 0 and 1 run on their own streams beside axis 2 (each axis
+    // with its own partial sums and face spectra)
+    cudaStream_t fst[2] = {nullptr, nullptr};
+    cudaEvent_t fev[3] = {nullptr, nullptr, nullptr};   // T0 ready; axis 0 done; axis 1 done
     // host-buffer solves (page-locked buffers, captured into their own graph): rho
     // goes up in one copy, and the kernels that write phi write the host buffer
     // directly (through its device view), so the download overlaps their work
@@ -628,6 +633,13 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
         if ((rc = transform_rho_from_T0(p, p->side))) return rc;
         IDP_CK(cudaEventRecord(p->join, p->side));
     }
+    // the faces of axes 0 and 1 read only T0: with fork_rho they start on their
+    // own streams while the rest runs on st
+    const bool conc = fork_rho && p->d == 3;
+    if (conc) {
+        IDP_CK(cudaEventRecord(p->fev[0], st));
+        for (int i = 0; i < 2; ++i) IDP_CK(cudaStreamWaitEvent(p->fst[i], p->fev[0], 0));
+    }
     {
         Mark mk(p, IDP_KERNEL_RFFT, st);
         IDP_CK(launch_rfft_pass(a1, st));
@@ -664,6 +676,8 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
     for (int a_ = 0; a_ < 3; ++a_) {
         const int b = a_ == 0 ? 1 : 0;
         const int c = a_ == 2 ? 1 : 2;
+        cudaStream_t sa = (conc && a_ < 2) ? p->fst[a_] : st;
+        double2 *part = p->part + a_ * p->part_cap, *F = p->F + a_ * p->f_cap;
         FacePass f{};
         if (a_ == 0) { f.D = p->T0; f.sp = (int64_t)p->ni[1] * (p->M[2] + 1); f.sb = p->M[2] + 1; f.sc = 1; }
         else if (a_ == 1) { f.D = p->T0; f.sp = p->M[2] + 1; f.sb = (int64_t)p->ni[1] * (p->M[2] + 1); f.sc = 1; }
@@ -672,7 +686,7 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
         f.Mb = p->M[b];
         f.nc = p->M[c] + 1;
         f.khat = p->khat[a_];
-        f.part = p->part;
+        f.part = part;
         f.pchunk = p->pchunk[a_];
         if ((rc = get_fft(p, 2 * p->M[b], &t))) return rc;
         f.t = t;
@@ -680,19 +694,19 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
         f.khatd = p->khatd[a_];
         f.sliceflag = p->sl[a_];
         {
-            Mark mk(p, IDP_KERNEL_FACE, st);
-            IDP_CK(launch_face_pass(f, p->nchunk[a_], st));
+            Mark mk(p, IDP_KERNEL_FACE, sa);
+            IDP_CK(launch_face_pass(f, p->nchunk[a_], sa));
         }
         FaceInvB ib{};
-        ib.part = p->part; ib.nchunk = p->nchunk[a_];
-        ib.Mb = p->M[b]; ib.nc = f.nc; ib.out = p->F; ib.t = t;
+        ib.part = part; ib.nchunk = p->nchunk[a_];
+        ib.Mb = p->M[b]; ib.nc = f.nc; ib.out = F; ib.t = t;
         ib.dd = dd;
         {
-            Mark mk(p, IDP_KERNEL_FACE_INVB, st);
-            IDP_CK(launch_face_inv_b(ib, st));
+            Mark mk(p, IDP_KERNEL_FACE_INVB, sa);
+            IDP_CK(launch_face_inv_b(ib, sa));
         }
         FaceC2R cr{};
-        cr.in = p->F; cr.nrows = p->M[b] + 1; cr.Mc = p->M[c];
+        cr.in = F; cr.nrows = p->M[b] + 1; cr.Mc = p->M[c];
         cr.dst0 = dst0; cr.dst1 = dst1;
         cr.base[0] = 0; cr.base[1] = (int64_t)p->M[a_] * p->ns[a_];
         cr.row_stride = p->ns[b]; cr.col_stride = p->ns[c];
@@ -701,9 +715,14 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
         if ((rc = get_fft(p, p->M[c], &t))) return rc;
         cr.t = t;
         cr.dd = dd;
-        Mark mk(p, IDP_KERNEL_FACE_C2R, st);
-        IDP_CK(launch_face_c2r(cr, st));
+        Mark mk(p, IDP_KERNEL_FACE_C2R, sa);
+        IDP_CK(launch_face_c2r(cr, sa));
     }
+    if (conc)
+        for (int i = 0; i < 2; ++i) {
+            IDP_CK(cudaEventRecord(p->fev[1 + i], p->fst[i]));
+            IDP_CK(cudaStreamWaitEvent(st, p->fev[1 + i], 0));
+        }
     return IDP_OK;
 }
 
@@ -871,6 +890,8 @@ int plan_setup(idp_plan p)
     if (!p->cap) IDP_CK(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
     IDP_CK(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming));
     IDP_CK(cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming));
+    for (int i = 0; i < 2; ++i) IDP_CK(cudaStreamCreateWithFlags(&p->fst[i], cudaStreamNonBlocking));
+    for (int i = 0; i < 3; ++i) IDP_CK(cudaEventCreateWithFlags(&p->fev[i], cudaEventDisableTiming));
     {
         std::vector<double> s4;
         for (int s = 0; s < 3; ++s) {
@@ -1006,8 +1027,9 @@ int plan_setup(idp_plan p)
                                            p->khat[a_] + (int64_t)p0 * per, Mc + 1, per, cnt, 0));
             }
         }
-        if ((rc = p->alloc(&p->part, pmax)) || (rc = p->alloc(&p->F, fmax))) return rc;
+        if ((rc = p->alloc(&p->part, 3 * pmax)) || (rc = p->alloc(&p->F, 3 * fmax))) return rc;
         p->part_cap = pmax;
+        p->f_cap = fmax;
     }
     IDP_CK(cudaDeviceSynchronize());
     return IDP_OK;
@@ -1050,7 +1072,7 @@ int autotune(idp_plan p)
                 const int nch = (np + pch - 1) / pch;
                 if ((int64_t)nch * 2 * L * nc > p->part_cap) {
                     double2 *np_part;
-                    if ((rc = p->alloc(&np_part, (int64_t)nch * 2 * L * nc))) break;
+                    if ((rc = p->alloc(&np_part, 3 * (int64_t)nch * 2 * L * nc))) break;
                     p->part = np_part;
                     p->part_cap = (int64_t)nch * 2 * L * nc;
                 }
@@ -1517,6 +1539,10 @@ int idp_destroy_plan(idp_plan p)
     }
     if (p->fork) cudaEventDestroy(p->fork);
     if (p->join) cudaEventDestroy(p->join);
+    for (int i = 0; i < 2; ++i)
+        if (p->fst[i]) cudaStreamDestroy(p->fst[i]);
+    for (int i = 0; i < 3; ++i)
+        if (p->fev[i]) cudaEventDestroy(p->fev[i]);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
     for (void *q : p->allocs) cudaFree(q);
     delete p;
