@@ -195,8 +195,10 @@ __global__ void __launch_bounds__(NTB) dst_pass_kernel(const DstPass a)
         // of its quarter, an inclusive scan of the four totals by shuffles, then
         // the quarter again from the lower quarters' sum.  The summation order is
         // the same for every block shape.  Requires 4 LB <= threads per block and
-        // whole warps of lines (LB >= 8).
+        // whole warps of lines (LB >= 8), or LB = 2 or 4 in part of warp 0.
         constexpr int S = 4, Cq = K / S;
+        // the scan lanes: whole warps, or the lowest 4 LB lanes of warp 0 (LB = 2, 4)
+        constexpr unsigned SMASK = (S * LB >= 32) ? 0xffffffffu : ((1u << (S * LB)) - 1u);
         const int l = threadIdx.x / S, sg = threadIdx.x - l * S;
         if (l < LB) {
             double *ol = o + l * M;
@@ -210,11 +212,11 @@ __global__ void __launch_bounds__(NTB) dst_pass_kernel(const DstPass a)
             double incl = tot;
 #pragma unroll
             for (int dd = 1; dd < S; dd <<= 1) {
-                const double nb = __shfl_up_sync(0xffffffffu, incl, dd, S);
+                const double nb = __shfl_up_sync(SMASK, incl, dd, S);
                 incl += sg >= dd ? nb : 0.0;
             }
             // sum of the lower quarters: the inclusive sum of the lane below
-            const double below = __shfl_up_sync(0xffffffffu, incl, 1, S);
+            const double below = __shfl_up_sync(SMASK, incl, 1, S);
             double run = sg == 0 ? first : below + ol[2 * kb];
             ol[2 * kb] = run;
 #pragma unroll 8
@@ -284,9 +286,11 @@ template <class R, int K, int LBO, int NTB = NT>
 cudaError_t launch_lb(const DstPass &a, int nu, int nv, cudaStream_t st)
 {
     using Cfg = DstCfg<K, LBO, NTB>;
-    static_assert(Cfg::G <= 32, "scan group must fit a warp");
+    // (the double-float scan runs on G lanes per line; the FP64 one on four)
+    static_assert(std::is_same<R, double>::value || Cfg::G <= 32, "scan group must fit a warp");
     static_assert(Cfg::LB * Cfg::G == NTB, "every thread belongs to one scan group");
-    static_assert(4 * Cfg::LB <= NTB && Cfg::LB >= 8 && K % 4 == 0, "four scan lanes per line in whole warps");
+    static_assert(4 * Cfg::LB <= NTB && (Cfg::LB >= 8 || Cfg::LB == 4 || Cfg::LB == 2) && K % 4 == 0,
+                  "four scan lanes per line: whole warps, or part of warp 0");
     const size_t sm = 2 * sizeof(double2) * Cfg::LB * K;
     dim3 grid((nv + Cfg::LB - 1) / Cfg::LB, nu);
     return launch_pdl(dst_pass_kernel<R, K, LBO, NTB>, grid, dim3(NTB), sm, st, a);
@@ -310,8 +314,12 @@ cudaError_t launch_k(const DstPass &a, cudaStream_t st)
     }
     if constexpr (DstCfg<K>::LB > 8) {
         // a launch of less than two blocks per SM (the layer transforms) runs
-        // faster on more, smaller blocks
+        // faster on more, smaller blocks: FP64 on 2 lines per 128-thread block
+        // (measured against 4 lines on 64, 128 or 256 threads and 8 on 256)
         const int64_t blocks = (int64_t)nu * ((nv + DstCfg<K>::LB - 1) / DstCfg<K>::LB);
+        if constexpr (std::is_same<R, double>::value) {
+            if (blocks < 2 * 152) return launch_lb<R, K, 2, 128>(a, nu, nv, st);
+        }
         if (a.lines == 8 || blocks < 2 * 152) return launch_lb<R, K, 8>(a, nu, nv, st);
         // 8 lines on 128 threads: one radix-4 unit per thread per pass for K = 64
         if (a.lines == -8 && K == 64) return launch_lb<R, K, 8, 128>(a, nu, nv, st);
@@ -332,7 +340,11 @@ cudaError_t attr_k()
 {
     cudaError_t e = attr_lb<R, K, 0>();
     if (e != cudaSuccess) return e;
-    if constexpr (DstCfg<K>::LB > 8) e = attr_lb<R, K, 8>();
+    if constexpr (DstCfg<K>::LB > 8) {
+        e = attr_lb<R, K, 8>();
+        if constexpr (std::is_same<R, double>::value)
+            if (e == cudaSuccess) e = attr_lb<R, K, 2, 128>();
+    }
     if constexpr (K == 64) {
         if (e == cudaSuccess) e = attr_lb<R, K, 8, 128>();
         if (e == cudaSuccess) e = attr_lb<R, K, 32>();
