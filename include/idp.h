@@ -160,7 +160,8 @@ enum {
     IDP_KERNEL_GTILDE_EXPAND = 10, /* sine transform of gtilde assembled from its transformed layers */
     IDP_KERNEL_DST_PARTS = 11,   /* sine passes over the boundary-adjacent layers of gtilde */
     IDP_KERNEL_MIXED = 12,       /* tensor-core sine-matrix pass (IDP_PRECISION_MIXED_BF16X3) */
-    IDP_KERNEL_SUPPORT = 13,     /* flags of the non-zero lines and slices of rho (zero ones skip stage 1 and 2) */
+    IDP_KERNEL_SUPPORT = 13,     /* reserved: no longer launched (the support flags of rho are made by the
+                                    stage-1 pass along axis 2, timed under IDP_KERNEL_RFFT) */
     IDP_KERNEL_RHS6_EXPAND = 14  /* sine transform of the 6th-order layer correction from its layer transforms */
 };
 

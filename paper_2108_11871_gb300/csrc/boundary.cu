@@ -96,37 +96,85 @@ __global__ void __launch_bounds__(NT) rfft_kernel(const RfftPass a)
     const int u = blockIdx.y, v0 = blockIdx.x * LB;
     const int nl = min(LB, nv - v0);
     const bool contig = (ise == 1);
+    // lines that are all zero (rho vanishes near the boundary): zero spectra
+    auto write_zero = [&]() {
+        Cx *outz = reinterpret_cast<Cx *>(a.out) + (int64_t)u * osu + (int64_t)v0 * osv;
+        for (int f = threadIdx.x; f < nl * (M + 1); f += NT) {
+            const int l = f / (M + 1), m = f - l * (M + 1);
+            outz[(int64_t)l * osv + (int64_t)m * ose] = A::cmake(A::zero(), A::zero());
+        }
+    };
     if (a.lineflag) {
-        // lines that are all zero (rho vanishes near the boundary): write zero spectra
         __shared__ int any_nz;
         if (threadIdx.x == 0) any_nz = 0;
         __syncthreads();
         if (threadIdx.x < nl && a.lineflag[(int64_t)u * nv + v0 + threadIdx.x]) any_nz = 1;
         __syncthreads();
         if (!any_nz) {
-            Cx *outz = reinterpret_cast<Cx *>(a.out) + (int64_t)u * osu + (int64_t)v0 * osv;
-            for (int f = threadIdx.x; f < nl * (M + 1); f += NT) {
-                const int l = f / (M + 1), m = f - l * (M + 1);
-                outz[(int64_t)l * osv + (int64_t)m * ose] = A::cmake(A::zero(), A::zero());
-            }
+            write_zero();
             return;
         }
     }
+    // stage 1a: non-zero marks of the block's lines and of their element
+    // positions, in the FFT scratch (free until the FFT)
+    const bool mk = a.fl_row2 != nullptr;
+    int *colnz = reinterpret_cast<int *>(bufB), *rownz = colnz + L;
     R *zf = reinterpret_cast<R *>(bufA);   // [LB][2L] reals
     const int64_t inb = (int64_t)u * isu + (int64_t)v0 * isv;
     for (int f = threadIdx.x; f < LB * 2 * L; f += NT) {
         const int l = f / (2 * L), q = f - l * 2 * L;
         if (q == 0 || q >= M) zf[f] = A::zero();
     }
+    if (mk) {
+        for (int f = threadIdx.x; f < L + LB; f += NT) colnz[f] = 0;
+        __syncthreads();
+    }
+    int nz = 0;
     for (int f = threadIdx.x; f < LB * N; f += NT) {
         int l, e;
         if (contig) { l = f / N; e = f - l * N; }
         else { e = f / LB; l = f - e * LB; }
         R x = A::zero();
-        if (l < nl) x = ld_real<R>(a.in, inb + (int64_t)l * isv + (int64_t)e * ise);
+        if (l < nl) {
+            const int64_t i = inb + (int64_t)l * isv + (int64_t)e * ise;
+            const double xd = a.in[i];
+            if (a.copy) a.copy[i] = xd;
+            // zero test on the bits (+0 and -0 are zero), off the FP64 pipe
+            if (mk && (__double_as_longlong(xd) << 1) != 0) {
+                colnz[e] = 1;
+                rownz[l] = 1;
+                nz = 1;
+            }
+            x = ld_real<R>(&xd, 0);
+        }
         zf[l * 2 * L + e + 1] = x;
     }
-    __syncthreads();
+    if (mk) {
+        const int any = __syncthreads_or(nz);
+        if (threadIdx.x < nl) {
+            const int rf = rownz[threadIdx.x];
+            a.fl_row2[(int64_t)u * nv + v0 + threadIdx.x] = rf;
+            // flags shared by many blocks are read before they are set (a store to
+            // a line that many SMs write is slow; a stale 0 costs one more store)
+            if (rf && !a.fl_sl1[v0 + threadIdx.x]) a.fl_sl1[v0 + threadIdx.x] = 1;
+        }
+        if (any) {
+            if (threadIdx.x == 0 && !a.fl_sl0[u]) a.fl_sl0[u] = 1;
+            for (int e = threadIdx.x; e < N; e += NT)
+                if (colnz[e]) {
+                    int *f1 = a.fl_row1 + (int64_t)u * a.n2 + e;
+                    if (!*f1) *f1 = 1;
+                    if (!a.fl_sl2[e]) a.fl_sl2[e] = 1;
+                }
+        }
+        __syncthreads();
+        if (!any) {
+            write_zero();
+            return;
+        }
+    } else {
+        __syncthreads();
+    }
     Cx *Z = cta_fft_t<R, L, LB, NT, false>(bufA, bufB, fwd_tw<R>(a.t), true);
     Cx *outb = reinterpret_cast<Cx *>(a.out) + (int64_t)u * osu + (int64_t)v0 * osv;
     for (int f = threadIdx.x; f < LB * (L / 2); f += NT) {

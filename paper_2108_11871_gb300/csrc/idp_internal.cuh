@@ -126,6 +126,11 @@ struct RfftPass {
     FftTables t;                                  // tables for complex length M
     int dd;                                       // 1: double-float arithmetic, output as pairs
     const int *lineflag;   // optional: lineflag[u * nv + v] != 0 iff line (u, v) has a non-zero value
+    // stage 1a (axis 2) only, optional: the pass also makes the support flags of
+    // its input, zero on entry: rows row2[i0 * n1 + i1] (every entry written),
+    // row1[i0 * n2 + i2], slices sl0[i0], sl1[i1], sl2[i2] (set to 1 where non-zero)
+    int *fl_row2, *fl_row1, *fl_sl0, *fl_sl1, *fl_sl2;
+    double *copy;          // optional: the input is also copied here (same strides)
 };
 cudaError_t launch_rfft_pass(const RfftPass &a, cudaStream_t st);
 
@@ -234,16 +239,10 @@ cudaError_t launch_rhs6_w(const Grid3 &g, const StencilCoef &c, const double *U,
 // R on the core (indices 2..M-2) into dense interior `R`, then extrapolation to the layers 1, M-1.
 cudaError_t launch_rhs6_core(const Grid3 &g, const double *W, double *R, cudaStream_t st);
 cudaError_t launch_rhs6_extrap(const Grid3 &g, double *R, cudaStream_t st);
-// tabc = sc / lambda_c(k) and tab4 = sc / Lambda4(k) on the dense mode grid;
-// lc / ld hold the per-axis 1-D eigenvalues, axis s at offset off_s (axis 0 at 0).
-// Support flags of rho (interior view with node strides): row2[i0*n1+i1] for the
-// lines along axis 2, row1[i0*n2+i2] for the lines along axis 1, and the slice
-// flags sl0[i0], sl1[i1], sl2[i2]; each set to 1 where some value is non-zero
-// (the arrays must be zeroed before).
-cudaError_t launch_support_flags(const Grid3 &g, const double *rho_int, int64_t s0, int64_t s1, int64_t s2,
-                                 int *row2, int *row1, int *sl0, int *sl1, int *sl2, cudaStream_t st);
 // y = double-float pairs of x (set-up only)
 cudaError_t launch_to_dd(const double *x, ddr *y, int64_t n, cudaStream_t st);
+// tabc = sc / lambda_c(k) and tab4 = sc / Lambda4(k) on the dense mode grid;
+// lc / ld hold the per-axis 1-D eigenvalues, axis s at offset off_s (axis 0 at 0).
 // tabR (optional) = tab4 * Lambda_R / Lambda4 + tab4 with Lambda_R the symbol of
 // the 6th-order right-hand side.
 cudaError_t launch_eigen_tables(const Grid3 &g, const double *lc, const double *ld, int64_t off1,

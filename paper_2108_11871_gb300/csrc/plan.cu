@@ -191,10 +191,12 @@ struct idp_plan_s {
     // with its own partial sums and face spectra)
     cudaStream_t fst[2] = {nullptr, nullptr};
     cudaEvent_t fev[3] = {nullptr, nullptr, nullptr};   // T0 ready; axis 0 done; axis 1 done
-    // host-buffer solves (page-locked buffers, captured into their own graph): rho
-    // goes up in one copy, and the kernels that write phi write the host buffer
-    // directly (through its device view), so the download overlaps their work
+    // host-buffer solves (page-locked buffers, captured into their own graph): the
+    // first row transform reads rho from the host buffer (through its device view)
+    // and the kernels that write phi write the host buffer directly, so that the
+    // upload and the download overlap their work
     const double *hio_rho = nullptr;   // host rho of the solve being queued (null: none)
+    const double *hio_view = nullptr;  // its device view
     cudaGraphExec_t hexec = nullptr;
     const double *hg_rho = nullptr;
     double *hg_phi = nullptr;
@@ -583,21 +585,25 @@ int transform_rho_from_T0(idp_plan p, cudaStream_t st)
     return transform(p, im, p->A, dense(p, p->A), p->tabc2, none, true, st, true, true, dd);
 }
 
-// boundary values g into the boundary nodes of dst0 (and dst1 if not null)
+// boundary values g into the boundary nodes of dst0 (and dst1 if not null).
+// rho_src (optional): the node array that the first row transform reads instead
+// of rho, copying its interior into rho for the later stages (a page-locked host
+// buffer, through its device view: the upload then runs inside that pass)
 int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStream_t st,
-             bool fork_rho = false)
+             bool fork_rho = false, const double *rho_src = nullptr)
 {
     const View3 r = node_interior(p, rho);
     int rc;
     FftTables t;
     // double-float arithmetic for the 3-D convolutions in precision DF32
     const int dd = (p->mixed == IDP_PRECISION_DF32 && p->d == 3) ? 1 : 0;
-    // which rows and slices of rho are non-zero (zero ones are skipped below;
-    // their contributions are exactly zero)
+    // support flags of rho: set by the first row transform
     IDP_CK(cudaMemsetAsync(p->flags, 0, sizeof(int) * p->nflags, st));
     // stage 1a: along axis 2 -> T0[i0][i1][m2]; stage 1b: along axis 1 -> T1[i0][i2][m1]
     RfftPass a2{}, a1{};
-    a2.in = r.p; a2.is0 = r.s0; a2.is1 = r.s1; a2.is2 = r.s2;
+    a2.in = rho_src ? node_interior(p, rho_src).p : r.p;
+    a2.copy = rho_src ? r.p : nullptr;
+    a2.is0 = r.s0; a2.is1 = r.s1; a2.is2 = r.s2;
     a2.out = p->T0;
     a2.os2 = 1; a2.os1 = p->M[2] + 1; a2.os0 = (int64_t)p->ni[1] * (p->M[2] + 1);
     a2.n0 = p->ni[0]; a2.n1 = p->ni[1]; a2.n2 = p->ni[2];
@@ -605,7 +611,11 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
     if ((rc = get_fft(p, p->M[2], &t))) return rc;
     a2.t = t;
     a2.dd = dd;
-    a2.lineflag = p->row2;
+    // the pass along axis 2 reads every value of rho once: it also marks which
+    // rows and slices are non-zero (zero ones are skipped below; their
+    // contributions are exactly zero)
+    a2.fl_row2 = p->row2; a2.fl_row1 = p->row1;
+    a2.fl_sl0 = p->sl[0]; a2.fl_sl1 = p->sl[1]; a2.fl_sl2 = p->sl[2];
     a1.in = r.p; a1.is0 = r.s0; a1.is1 = r.s1; a1.is2 = r.s2;
     a1.out = p->T1;
     a1.os1 = 1; a1.os2 = p->M[1] + 1; a1.os0 = (int64_t)p->ni[2] * (p->M[1] + 1);
@@ -615,13 +625,6 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
     a1.t = t;
     a1.dd = dd;
     a1.lineflag = p->row1;
-    // which rows and slices of rho are non-zero (zero ones are skipped below;
-    // their contributions are exactly zero)
-    {
-        Mark mk(p, IDP_KERNEL_SUPPORT, st);
-        IDP_CK(launch_support_flags(p->grid, r.p, r.s0, r.s1, r.s2, p->row2, p->row1, p->sl[0], p->sl[1],
-                                    p->sl[2], st));
-    }
     {
         Mark mk(p, IDP_KERNEL_RFFT, st);
         IDP_CK(launch_rfft_pass(a2, st));
@@ -751,11 +754,12 @@ int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t s
     // FP64 / df32 transforms: the first pass of the forward transform of rho is
     // the imaginary part of the boundary's first real FFT (see transform_rho_from_T0)
     const bool rho_from_T0 = (stop == 0) && !(p->mixed == IDP_PRECISION_MIXED_BF16X3 && p->mixed_path == 0);
-    if (stop == 0 && p->hio_rho) {
-        // host-buffer solve: rho goes up first (splitting the first kernels into
-        // slabs to overlap this copy costs them more than it hides, measured)
+    // host-buffer solve: the first row transform reads rho from the host buffer
+    // and leaves the device copy for the later stages; where rho is needed before
+    // it (the tensor-core transform of rho starts at once), rho goes up first
+    const double *rho_src = (stop == 0 && p->hio_rho && rho_from_T0) ? p->hio_view : nullptr;
+    if (stop == 0 && p->hio_rho && !rho_src)
         IDP_CK(cudaMemcpyAsync(p->h_rho, p->hio_rho, sizeof(double) * p->nodes, cudaMemcpyHostToDevice, st));
-    }
     if (overlap_rho && !rho_from_T0) {
         IDP_CK(cudaEventRecord(p->fork, st));
         IDP_CK(cudaStreamWaitEvent(p->side, p->fork, 0));
@@ -765,7 +769,7 @@ int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t s
     }
     // 1. boundary values: phi boundary and U boundary
     if ((rc = boundary(p, rho, stop == 0 ? phi : p->U, stop == 0 ? p->U : nullptr, st,
-                       overlap_rho && rho_from_T0)))
+                       overlap_rho && rho_from_T0, rho_src)))
         return rc;
     // 2. gtilde on the boundary-adjacent layers, and the transforms of its parts
     if ((rc = gtilde_parts(p, stop != IDP_STAGE_GTILDE, st))) return rc;
@@ -1192,11 +1196,12 @@ double *device_view(const void *ptr)
     return at.type == cudaMemoryTypeHost ? static_cast<double *>(at.devicePointer) : nullptr;
 }
 
-// a solve from page-locked host buffers: rho goes up in one copy, and the kernels
-// that produce phi (the boundary values and the last sine pass) write the host
-// buffer directly through its device view, so that the download runs inside
-// them instead of after them.  Its own cached graph, keyed by the host pointers
-// and the plan's settings.
+// a solve from page-locked host buffers: the first row transform reads rho through
+// the buffer's device view (leaving a device copy for the later stages), and the
+// kernels that produce phi (the boundary values and the last sine pass) write the
+// host buffer directly, so that the upload and the download run inside those
+// kernels instead of before and after them.  Its own cached graph, keyed by the
+// host pointers and the plan's settings.
 int run_solve_host(idp_plan p, const double *rho_h, double *phi_h, double *phi_view, cudaStream_t st)
 {
     p->last = st;
@@ -1204,8 +1209,10 @@ int run_solve_host(idp_plan p, const double *rho_h, double *phi_h, double *phi_v
     if (!p->hexec || p->hg_rho != rho_h || p->hg_phi != phi_h || p->hg_version != p->version) {
         IDP_CK(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
         p->hio_rho = rho_h;
+        p->hio_view = device_view(rho_h);
         int rc = enqueue(p, p->h_rho, phi_view, 0, p->cap);
         p->hio_rho = nullptr;
+        p->hio_view = nullptr;
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(p->cap, &g);
         if (rc) {

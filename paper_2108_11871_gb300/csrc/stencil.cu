@@ -856,72 +856,12 @@ cudaError_t launch_rhs6_e_scatter(const Grid3 &g, const double *E0, const double
 }
 
 namespace {
-// One block covers 32 consecutive nodes along axis 2 of SF_ROWS rows (axis 1)
-// of one slice (axis 0); each of its 8 warps reads SF_ROWS / 8 rows, with all
-// loads in flight at once (a grid that fits the GPU in one wave at 129^3).  The flags are only ever set to 1, so the stores may
-// race; they are reduced within the block first so that few of them hit the
-// same cache lines.
-constexpr int SF_ROWS = 64, SF_WARPS = 8, SF_PER = SF_ROWS / SF_WARPS;
-__global__ void __launch_bounds__(32 * SF_WARPS) support_flags_kernel(const Grid3 gg, const double *__restrict__ r,
-                                                                    int64_t s0, int64_t s1, int64_t s2, int *row2,
-                                                                    int *row1, int *sl0, int *sl1, int *sl2)
-{
-    __shared__ unsigned colmask[SF_ROWS];
-    const Geo g = make_geo(gg);
-    const int lane = threadIdx.x, wy = threadIdx.y;
-    const int k2 = blockIdx.x * 32 + lane;
-    const int k0 = blockIdx.z;
-    long long bits[SF_PER];
-#pragma unroll
-    for (int i = 0; i < SF_PER; ++i) {
-        const int k1 = blockIdx.y * SF_ROWS + wy + SF_WARPS * i;
-        bits[i] = 0;
-        if (k2 < g.ni[2] && k1 < g.ni[1])
-            bits[i] = __double_as_longlong(r[k0 * s0 + (int64_t)k1 * s1 + (int64_t)k2 * s2]);
-    }
-#pragma unroll
-    for (int i = 0; i < SF_PER; ++i) {
-        // zero test on the bits (+0 and -0 are zero), off the FP64 pipe
-        const unsigned m = __ballot_sync(0xffffffffu, (bits[i] << 1) != 0);
-        const int row = wy + SF_WARPS * i;
-        if (lane == 0) {
-            colmask[row] = m;
-            if (m) row2[(int64_t)k0 * g.ni[1] + blockIdx.y * SF_ROWS + row] = 1;
-        }
-    }
-    __syncthreads();
-    if (wy == 0) {
-        // a flag is read before it is set: the slice flags are shared by many
-        // blocks, and a store to a line that many SMs write is slow (a stale 0
-        // only costs one more store)
-        unsigned c = 0;
-        for (int j = 0; j < SF_ROWS; ++j) c |= colmask[j];
-        if ((c >> lane) & 1u) {
-            int *f1 = row1 + (int64_t)k0 * g.ni[2] + k2;
-            if (!*f1) *f1 = 1;
-            if (!sl2[k2]) sl2[k2] = 1;
-        }
-        for (int j = lane; j < SF_ROWS; j += 32)
-            if (colmask[j] && !sl1[blockIdx.y * SF_ROWS + j]) sl1[blockIdx.y * SF_ROWS + j] = 1;
-        if (lane == 0 && c && !sl0[k0]) sl0[k0] = 1;
-    }
-}
-
 __global__ void to_dd_kernel(const double *x, ddr *y, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = dd_from(x[i]);
 }
 }  // namespace
-
-cudaError_t launch_support_flags(const Grid3 &g, const double *rho_int, int64_t s0, int64_t s1, int64_t s2,
-                                 int *row2, int *row1, int *sl0, int *sl1, int *sl2, cudaStream_t st)
-{
-    const dim3 grid((g.n2 - 2 + 31) / 32, (g.n1 - 2 + SF_ROWS - 1) / SF_ROWS, g.d == 3 ? g.n0 - 2 : 1);
-    support_flags_kernel<<<grid, dim3(32, SF_WARPS), 0, st>>>(
-        g, rho_int, s0, s1, s2, row2, row1, sl0, sl1, sl2);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_to_dd(const double *x, ddr *y, int64_t n, cudaStream_t st)
 {
