@@ -4,7 +4,7 @@
  *   g(x_b) = sum_p G(|x_b - s_p|) rho_p * prod_s h_s
  *
  * over the listed source points p (the non-zero interior values of rho).
- * G(r) = log(r)/(2 pi) in 2-D and -1/(4 pi r) in 3-D (section 1).  Each sum
+ * G(r) = |r|/2 in 1-D, log(r)/(2 pi) in 2-D and -1/(4 pi r) in 3-D (section 1).  Each sum
  * is accumulated with Neumaier's compensated summation in double precision;
  * boundary targets run in parallel with OpenMP.
  */
@@ -14,11 +14,12 @@
 static double green(int d, double r2)
 {
     const double pi = 3.14159265358979323846;
+    if (d == 1) return 0.5 * sqrt(r2);               /* |r| / 2 */
     if (d == 2) return 0.5 * log(r2) / (2.0 * pi);   /* log(r) = log(r^2)/2 */
     return -1.0 / (4.0 * pi * sqrt(r2));
 }
 
-/* d: dimension (2 or 3); h[d]: mesh widths;
+/* d: dimension (1, 2 or 3); h[d]: mesh widths;
  * nsrc sources: src_idx[nsrc*d] integer node indices, src_val[nsrc] values;
  * ntgt targets: tgt_idx[ntgt*d] integer node indices; out[ntgt] receives g. */
 void oracle_boundary_direct(int d, const double *h, int64_t nsrc,

@@ -66,3 +66,42 @@ def test_linearity_and_boundary_assembly():
     from oracle import greens
     m = greens.boundary_mask(p.n)
     np.testing.assert_array_equal(phi_ab[m], parts["g"][m])
+
+
+def _bump_potential_1d(x, c, eps, p):
+    """(1/2) int |x - y| (1 - (y-c)^2/eps^2)^p dy over |y - c| < eps, exactly
+    (polynomial algebra): the free-space potential of the bump in 1-D, G = |x|/2."""
+    from numpy.polynomial import polynomial as P
+    q = P.polypow([1.0, 0.0, -1.0 / eps ** 2], p)   # in s = y - c
+    Q0 = P.polyint(q)                                # int q
+    Q1 = P.polyint(P.polymul(q, [0.0, 1.0]))         # int s q
+    out = []
+    for xv in x:
+        t = xv - c
+        s = min(max(t, -eps), eps)
+        left = t * (P.polyval(s, Q0) - P.polyval(-eps, Q0)) - (P.polyval(s, Q1) - P.polyval(-eps, Q1))
+        right = (P.polyval(eps, Q1) - P.polyval(s, Q1)) - t * (P.polyval(eps, Q0) - P.polyval(s, Q0))
+        out.append(0.5 * (left + right))
+    return np.array(out)
+
+
+def test_1d_solve_matches_exact_potential():
+    # d = 1 (section 5): phi* by the sine series and the straight line through
+    # the trapezoid end values g(a), g(b); the whole potential converges to the
+    # exact one, fast (the bump is C^9 and vanishes with its derivatives at the ends)
+    errs = []
+    for n in (33, 65):   # 129 is at the rounding floor (2e-14)
+        p = w.scaled_bump((n,), centre=(0.1,), eps=0.6, p=10)
+        phi = solve.solve(p.rho(), p.h, 6)
+        ex = _bump_potential_1d(p.coords()[0], 0.1, 0.6, 10)
+        errs.append(np.abs(phi - ex).max() / np.abs(ex).max())
+    assert errs[1] < 1e-12
+    assert errs[0] / errs[1] > 2.0 ** 8
+    # the end values are the trapezoid sums themselves: phi(a) = (h^2/2) sum p rho_p
+    p = w.scaled_bump((33,), centre=(-0.2,), eps=0.5, p=4)
+    rho = p.rho()
+    phi = solve.solve(rho, p.h, 4)
+    M, h = 32, p.h[0]
+    k = np.arange(1, M)
+    assert abs(phi[0] - 0.5 * h * h * np.dot(k, rho[1:M])) < 1e-15 * np.abs(phi).max()
+    assert abs(phi[M] - 0.5 * h * h * np.dot(M - k, rho[1:M])) < 1e-15 * np.abs(phi).max()
