@@ -109,10 +109,15 @@ typedef struct idp_plan_s *idp_plan;
 
 /* Create a plan for one grid (section 3 grid, section 5 order).
  *   out   : receives the plan handle (owned by the caller; free with idp_destroy_plan)
- *   d     : 2 or 3
+ *   d     : 1, 2 or 3
  *   n[d]  : node counts including boundary nodes
  *   h[d]  : mesh widths
- *   order : 4 or 6 (accuracy order of the harmonic correction, section 5)
+ *   order : 4 or 6 (accuracy order of the harmonic correction, section 5; for
+ *           d = 1 the correction is exact, the straight line through the two
+ *           end values of g (section 5), and order has no effect)
+ * d = 1 plans run FP64 only (IDP_KEY_PRECISION other than FP64: IDP_ESUPPORT);
+ * their stages are BOUNDARY, PHISTAR, U1 (the straight line, g at the ends)
+ * and PHI (GTILDE and R: IDP_ESUPPORT).
  * Allocates all device workspace and precomputes the sine/twiddle tables,
  * the eigenvalue tables and the spectra of the boundary convolution kernels
  * on the current CUDA device; synchronises that device before returning. */
@@ -162,7 +167,8 @@ enum {
     IDP_KERNEL_MIXED = 12,       /* tensor-core sine-matrix pass (IDP_PRECISION_MIXED_BF16X3) */
     IDP_KERNEL_SUPPORT = 13,     /* reserved: no longer launched (the support flags of rho are made by the
                                     stage-1 pass along axis 2, timed under IDP_KERNEL_RFFT) */
-    IDP_KERNEL_RHS6_EXPAND = 14  /* sine transform of the 6th-order layer correction from its layer transforms */
+    IDP_KERNEL_RHS6_EXPAND = 14, /* sine transform of the 6th-order layer correction from its layer transforms */
+    IDP_KERNEL_LINE1D = 15       /* d = 1: g at the two ends and the straight-line correction (section 5) */
 };
 
 /* Run one solve (as idp_solve, but with plain launches, all on `stream`, none

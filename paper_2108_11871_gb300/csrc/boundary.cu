@@ -423,6 +423,66 @@ __global__ void __launch_bounds__(NT) face_c2r_kernel(const FaceC2R a)
     }
 }
 
+// ---------------------------------------------------------------- 1-D
+// d = 1 (section 5): the trapezoid sums for g at the two ends, with G = |x|/2,
+//   g(a) = (h^2/2) sum_{p=1}^{M-1} p rho_p,   g(b) = (h^2/2) sum_{p=1}^{M-1} (M-p) rho_p,
+// and the harmonic correction, the straight line through them,
+//   u_i = g(a) (1 - i/M) + g(b) i/M.
+// One block; the sums are compensated (Neumaier per thread, error-free pair sums
+// in the reduction).  mode: LINE1D_ENDS writes g at the ends and 0 inside,
+// LINE1D_LINE writes u on every node, LINE1D_ADD writes g at the ends and adds u
+// to the interior of phi.
+constexpr int L1_NT = 256;
+
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e)
+{
+    s = a + b;
+    const double bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__global__ void __launch_bounds__(L1_NT) line1d_kernel(const double *rho, double *phi, int M, double h, int mode)
+{
+    __shared__ double red[4][L1_NT];
+    double sa = 0.0, ca = 0.0, sb = 0.0, cb = 0.0;
+    for (int p = 1 + (int)threadIdx.x; p < M; p += L1_NT) {
+        const double r = rho[p];
+        double e;
+        two_sum(sa, (double)p * r, sa, e);
+        ca += e;
+        two_sum(sb, (double)(M - p) * r, sb, e);
+        cb += e;
+    }
+    red[0][threadIdx.x] = sa;
+    red[1][threadIdx.x] = ca;
+    red[2][threadIdx.x] = sb;
+    red[3][threadIdx.x] = cb;
+    __syncthreads();
+    for (int w = L1_NT / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            const int o = threadIdx.x + w;
+            double s, e;
+            two_sum(red[0][threadIdx.x], red[0][o], s, e);
+            red[0][threadIdx.x] = s;
+            red[1][threadIdx.x] += red[1][o] + e;
+            two_sum(red[2][threadIdx.x], red[2][o], s, e);
+            red[2][threadIdx.x] = s;
+            red[3][threadIdx.x] += red[3][o] + e;
+        }
+        __syncthreads();
+    }
+    const double ga = 0.5 * h * h * (red[0][0] + red[1][0]);
+    const double gb = 0.5 * h * h * (red[2][0] + red[3][0]);
+    for (int i = threadIdx.x; i <= M; i += L1_NT) {
+        const double t = (double)i / (double)M;
+        const double u = ga * (1.0 - t) + gb * t;
+        if (i == 0 || i == M) phi[i] = (i == 0) ? ga : gb;
+        else if (mode == LINE1D_ENDS) phi[i] = 0.0;
+        else if (mode == LINE1D_LINE) phi[i] = u;
+        else phi[i] += u;
+    }
+}
+
 // ---------------------------------------------------------------- kernel spectra
 __global__ void kernel_fill_kernel(const KernelFill a)
 {
@@ -606,6 +666,12 @@ cudaError_t launch_face_c2r(const FaceC2R &a, cudaStream_t st)
         else face_c2r_kernel<double, L><<<grid, NT, smem_c2r<L>(), st>>>(a);
         return cudaGetLastError();
     })
+}
+
+cudaError_t launch_line1d(const double *rho, double *phi, int M, double h, int mode, cudaStream_t st)
+{
+    line1d_kernel<<<1, L1_NT, 0, st>>>(rho, phi, M, h, mode);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_kernel_fill(const KernelFill &a, cudaStream_t st)

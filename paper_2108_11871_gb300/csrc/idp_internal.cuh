@@ -191,6 +191,11 @@ struct FaceC2R {
 };
 cudaError_t launch_face_c2r(const FaceC2R &a, cudaStream_t st);
 
+// d = 1 (section 5): g at the two end nodes from rho (node array, M + 1 values)
+// and the straight line through them; see line1d_kernel for the modes
+enum { LINE1D_ENDS = 0, LINE1D_LINE = 1, LINE1D_ADD = 2 };
+cudaError_t launch_line1d(const double *rho, double *phi, int M, double h, int mode, cudaStream_t st);
+
 // Cyclic-kernel samples k[p][tb][tc] = G(sqrt(((p0+p+1) h_a)^2 + (tb h_b)^2 + (tc h_c)^2)),
 // tb = 0..Mb, tc = 0..Mc (2-D: Mc = 0).
 struct KernelFill {

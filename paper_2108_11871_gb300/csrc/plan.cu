@@ -733,11 +733,37 @@ enum { RUN_PHI = 0 };
 
 // Queue the stages of one solve.  stop: 0 = full solve into phi; otherwise an
 // IDP_STAGE_* value whose result is written to `out`.
+// d = 1 (section 5): phi* by one forward and one inverse sine pass, then g at
+// the two ends and the straight line through them added inside
+int enqueue_1d(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t st)
+{
+    const View3 none{nullptr, 0, 0, 0};
+    const size_t node_bytes = sizeof(double) * p->nodes;
+    const int M = p->M[2];
+    if (stop == 0 && p->hio_rho)
+        IDP_CK(cudaMemcpyAsync(p->h_rho, p->hio_rho, node_bytes, cudaMemcpyHostToDevice, st));
+    if (stop == IDP_STAGE_BOUNDARY || stop == IDP_STAGE_U1) {
+        Mark mk(p, IDP_KERNEL_LINE1D, st);
+        IDP_CK(launch_line1d(rho, phi, M, p->h[2], stop == IDP_STAGE_BOUNDARY ? LINE1D_ENDS : LINE1D_LINE, st));
+        return IDP_OK;
+    }
+    if (stop != 0 && stop != IDP_STAGE_PHISTAR) return IDP_ESUPPORT;
+    int rc;
+    if (stop == IDP_STAGE_PHISTAR) IDP_CK(cudaMemsetAsync(phi, 0, node_bytes, st));
+    if ((rc = transform(p, node_interior(p, rho), p->A, dense(p, p->A), p->tabc, none, true, st))) return rc;
+    if ((rc = transform(p, dense(p, p->A), p->A, node_interior(p, phi), nullptr, none, false, st))) return rc;
+    if (stop == IDP_STAGE_PHISTAR) return IDP_OK;
+    Mark mk(p, IDP_KERNEL_LINE1D, st);
+    IDP_CK(launch_line1d(rho, phi, M, p->h[2], LINE1D_ADD, st));
+    return IDP_OK;
+}
+
 int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t st)
 {
+    if (p->d == 1) return enqueue_1d(p, rho, phi, stop, st);
     int rc;
     const View3 none{nullptr, 0, 0, 0};
-    const size_t node_bytes = sizeof(double) * p->nodes, int_bytes = sizeof(double) * p->nint;
+    const size_t node_bytes = sizeof(double) * p->nodes;
     if (stop == IDP_STAGE_BOUNDARY) {
         IDP_CK(cudaMemsetAsync(phi, 0, node_bytes, st));
         return boundary(p, rho, phi, nullptr, st);
@@ -850,6 +876,38 @@ int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t s
                      fold_u1 ? none : node_interior(p, p->U), false, st);
 }
 
+// the plan's streams and events (graph capture forks and joins through them)
+int plan_streams(idp_plan p)
+{
+    IDP_CK(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+    IDP_CK(cudaStreamCreateWithFlags(&p->bst, cudaStreamNonBlocking));
+    if (!p->cap) IDP_CK(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
+    IDP_CK(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming));
+    IDP_CK(cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming));
+    for (int i = 0; i < 2; ++i) IDP_CK(cudaStreamCreateWithFlags(&p->fst[i], cudaStreamNonBlocking));
+    for (int i = 0; i < 3; ++i) IDP_CK(cudaEventCreateWithFlags(&p->fev[i], cudaEventDisableTiming));
+    return IDP_OK;
+}
+
+// d = 1: the sine-pass tables (made by plan_setup), the coefficient array and
+// tabc = (2/M) / lambda_c(k) / 16 with lambda_c(k) = -(pi k / L)^2, L = M h: the
+// forward sums scaled by 2/M and divided by the continuum eigenvalue (section 3);
+// each sine pass returns 4 S x, hence the 1/16
+int plan_setup_1d(idp_plan p)
+{
+    int rc;
+    const int M = p->M[2], N = p->ni[2];
+    if ((rc = p->alloc(&p->A, p->nint)) || (rc = p->alloc(&p->tabc, p->nint))) return rc;
+    std::vector<double> tc(N);
+    const double L = (double)M * p->h[2];
+    for (int k = 1; k <= N; ++k) {
+        const double w = 3.14159265358979323846 * k / L;
+        tc[k - 1] = (2.0 / M) / (-(w * w)) / 16.0;
+    }
+    IDP_CK(cudaMemcpy(p->tabc, tc.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+    return plan_streams(p);
+}
+
 int plan_setup(idp_plan p)
 {
     int rc;
@@ -863,6 +921,7 @@ int plan_setup(idp_plan p)
             (rc = get_fft(p, 2 * p->M[s], &t)) || (rc = get_sin2(p, p->M[s], &sn)))
             return rc;
     }
+    if (p->d == 1) return plan_setup_1d(p);
     // workspace
     if ((rc = p->alloc(&p->A, p->nint)) || (rc = p->alloc(&p->B, p->nint)) || (rc = p->alloc(&p->C, p->nint)) ||
         (rc = p->alloc(&p->U, p->nodes)) || (rc = p->alloc(&p->W, 3 * p->nodes)) ||
@@ -889,13 +948,7 @@ int plan_setup(idp_plan p)
         p->sl[1] = p->sl[0] + n0;
         p->sl[2] = p->sl[1] + n1;
     }
-    IDP_CK(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
-    IDP_CK(cudaStreamCreateWithFlags(&p->bst, cudaStreamNonBlocking));
-    if (!p->cap) IDP_CK(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
-    IDP_CK(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming));
-    IDP_CK(cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming));
-    for (int i = 0; i < 2; ++i) IDP_CK(cudaStreamCreateWithFlags(&p->fst[i], cudaStreamNonBlocking));
-    for (int i = 0; i < 3; ++i) IDP_CK(cudaEventCreateWithFlags(&p->fev[i], cudaEventDisableTiming));
+    if ((rc = plan_streams(p))) return rc;
     {
         std::vector<double> s4;
         for (int s = 0; s < 3; ++s) {
@@ -1045,6 +1098,10 @@ int plan_setup(idp_plan p)
 // transforms.  Results depend only on timing, not on the data.
 int autotune(idp_plan p)
 {
+    if (p->d == 1) {   // one line per pass: nothing to choose
+        p->tuned = 1;
+        return IDP_OK;
+    }
     cudaStream_t st = p->cap;
     cudaEvent_t e0, e1;
     IDP_CK(cudaEventCreate(&e0));
@@ -1243,7 +1300,7 @@ int idp_create_plan(idp_plan *out, int d, const int64_t n[], const double h[], i
 {
     if (!out || !n || !h) return IDP_EINVAL;
     *out = nullptr;
-    if (d != 2 && d != 3) return IDP_EINVAL;
+    if (d < 1 || d > 3) return IDP_EINVAL;
     if (order != 4 && order != 6) return IDP_EINVAL;
     for (int s = 0; s < d; ++s) {
         if (!(h[s] > 0.0) || !std::isfinite(h[s])) return IDP_EINVAL;
@@ -1318,6 +1375,7 @@ int idp_plan_set(idp_plan p, int key, int64_t value)
     if (key == IDP_KEY_PRECISION) {
         if (value != IDP_PRECISION_FP64 && value != IDP_PRECISION_MIXED_BF16X3 && value != IDP_PRECISION_DF32)
             return IDP_EINVAL;
+        if (p->d == 1 && value != IDP_PRECISION_FP64) return IDP_ESUPPORT;
         if (value == IDP_PRECISION_MIXED_BF16X3) {
             int rc;
             if (!p->d_err) {

@@ -39,6 +39,11 @@ def test_argument_errors_need_no_gpu():
     n = (ctypes.c_int64 * 3)(33, 33, 33)
     h = (ctypes.c_double * 3)(0.1, 0.1, 0.1)
     assert lib.idp_create_plan(ctypes.byref(out), 4, n, h, 6) == idp.IDP_EINVAL
+    assert lib.idp_create_plan(ctypes.byref(out), 0, n, h, 6) == idp.IDP_EINVAL
+    one = (ctypes.c_int64 * 1)(2)       # d = 1 with fewer than 3 nodes
+    assert lib.idp_create_plan(ctypes.byref(out), 1, one, h, 6) == idp.IDP_EINVAL
+    one = (ctypes.c_int64 * 1)(34)      # d = 1, M = 33 panels
+    assert lib.idp_create_plan(ctypes.byref(out), 1, one, h, 6) == idp.IDP_ESUPPORT
     assert lib.idp_create_plan(ctypes.byref(out), 3, n, h, 5) == idp.IDP_EINVAL
     for bad_n in ((33, 34, 33), (25, 33, 33), (33, 33, 1025)):   # M = 33, 24, 1024
         bad = (ctypes.c_int64 * 3)(*bad_n)

@@ -364,3 +364,95 @@ def test_dst_shape_key_rejects_unknown_values(idp):
     plan = idp.create_plan(3, (33, 33, 33), (0.1, 0.1, 0.1), 6)
     lib = idp.library()
     assert lib.idp_plan_set(plan.handle, idp.IDP_KEY_DST_SHAPE, 3) == idp.IDP_EINVAL
+
+
+# d = 1 (section 5): phi* by the sine series, g at the two ends, and the
+# straight line through them; every panel-count family and the largest size
+ONE_D = [
+    ("1d_17_bump", w.scaled_bump((17,), centre=(0.1,), eps=0.6, p=10)),
+    ("1d_65_gauss", w.Problem("o1", (65,), (0.0,), (2.0,), "gauss", dict(seed=5))),
+    ("1d_97_random", w.Problem("o2", (97,), (-1.0,), (0.5,), "random", dict(seed=9))),
+    ("1d_129_points", w.Problem("o3", (129,), (0.0,), (1.0,), "points", dict(seed=13, count=3))),
+    ("1d_385_gauss", w.Problem("o4", (385,), (-3.0,), (1.0,), "gauss", dict(seed=21))),
+    ("1d_513_random", w.Problem("o5", (513,), (0.0,), (4.0,), "random", dict(seed=4))),
+]
+
+
+@pytest.mark.parametrize("name,prob", ONE_D, ids=[c[0] for c in ONE_D])
+def test_one_dimensional_solve_matches_oracle(idp, name, prob):
+    rho = prob.rho()
+    parts = {}
+    ref = osolve.solve(rho, prob.h, 6, parts=parts)
+    line = ref - parts["phistar"]          # the oracle's straight line, g at the ends
+    plan = idp.create_plan(1, prob.n, prob.h, 6)
+    r = to_dev(rho)
+    g = run_stage(idp, plan, idp.IDP_STAGE_BOUNDARY, r, prob.n)
+    assert rel_max(g[[0, -1]], parts["g"][[0, -1]]) < TOL
+    assert np.all(g[1:-1] == 0)
+    ps = run_stage(idp, plan, idp.IDP_STAGE_PHISTAR, r, prob.n)
+    assert rel_max(ps, parts["phistar"]) < TOL
+    assert ps[0] == 0 and ps[-1] == 0
+    u1 = run_stage(idp, plan, idp.IDP_STAGE_U1, r, prob.n)
+    assert rel_max(u1, line) < TOL
+    phi = run_stage(idp, plan, idp.IDP_STAGE_PHI, r, prob.n)
+    assert rel_max(phi, ref) < TOL
+    out = to_dev(np.zeros(prob.n))
+    idp.solve(plan, r, out)
+    idp.plan_status(plan)
+    assert np.array_equal(out.cpu().numpy(), phi)
+    # order has no effect in 1-D
+    plan4 = idp.create_plan(1, prob.n, prob.h, 4)
+    out4 = to_dev(np.zeros(prob.n))
+    idp.solve(plan4, r, out4)
+    idp.plan_status(plan4)
+    assert np.array_equal(out4.cpu().numpy(), phi)
+
+
+def test_one_dimensional_edge_cases(idp):
+    n, h = (65,), (0.03,)
+    plan = idp.create_plan(1, n, h, 6)
+    # zero density, and values only on the two boundary entries (ignored): phi = 0
+    for rho in (np.zeros(n), np.array([3.0] + [0.0] * 63 + [-2.0])):
+        out = to_dev(np.full(n, 7.0))
+        idp.solve(plan, to_dev(rho), out)
+        idp.plan_status(plan)
+        assert np.all(out.cpu().numpy() == 0)
+    # stages without a 1-D meaning, and reduced precision, are refused
+    r = to_dev(w.random_interior(n, seed=3))
+    for stage in (idp.IDP_STAGE_GTILDE, idp.IDP_STAGE_R):
+        with pytest.raises(idp.IdpError) as e:
+            run_stage(idp, plan, stage, r, (63,))
+        assert e.value.code == idp.IDP_ESUPPORT
+    for prec in (idp.IDP_PRECISION_DF32, idp.IDP_PRECISION_MIXED_BF16X3):
+        with pytest.raises(idp.IdpError) as e:
+            idp.plan_set(plan, idp.IDP_KEY_PRECISION, prec)
+        assert e.value.code == idp.IDP_ESUPPORT
+    idp.plan_set(plan, idp.IDP_KEY_AUTOTUNE, 1)
+
+
+def test_one_dimensional_host_and_batched_give_the_device_bits(idp):
+    import torch
+    p1 = w.Problem("o6", (257,), (-1.0,), (1.0,), "gauss", dict(seed=8))
+    p3 = w.c2_3d(33)
+    plans = [idp.create_plan(1, p1.n, p1.h, 6), idp.create_plan(3, p3.n, p3.h, 6)]
+    rhos = [to_dev(p1.rho()), to_dev(p3.rho())]
+    refs = []
+    for pl, r, pr in zip(plans, rhos, (p1, p3)):
+        o = to_dev(np.zeros(pr.n))
+        idp.solve(pl, r, o)
+        idp.plan_status(pl)
+        refs.append(o.cpu().numpy())
+    outs = [to_dev(np.zeros(p1.n)), to_dev(np.zeros(p3.n))]
+    idp.solve_batched(plans, rhos, outs)
+    torch.cuda.synchronize()
+    for pl in plans:
+        idp.plan_status(pl)
+    for o, ref in zip(outs, refs):
+        assert np.array_equal(o.cpu().numpy(), ref)
+    rho_p = torch.from_numpy(p1.rho()).pin_memory()
+    phi_p = torch.zeros(p1.n, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        phi_p.zero_()
+        idp.solve_host(plans[0], rho_p.data_ptr(), phi_p.data_ptr())
+        idp.plan_status(plans[0])
+        assert np.array_equal(phi_p.numpy(), refs[0])
