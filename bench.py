@@ -286,11 +286,10 @@ def run_ours(args, rank, world):
     e2e = {"value": world * prob.points / e2e_t, "unit": UNIT,
            "h2d_bytes_per_step": 8 * prob.points, "d2h_bytes_per_step": 8 * prob.points}
 
-    # mixed-precision variant (tensor-core sine transforms), same workload and timing rules
-    mixed = None
-    if not args.fp64_only:
+    # mixed-precision variants (tensor-core sine transforms), same workload and timing rules
+    def tensor_variant(prec, label):
         mplan = idp.create_plan(3, prob.n, prob.h, args.order)
-        idp.plan_set(mplan, idp.IDP_KEY_PRECISION, idp.IDP_PRECISION_MIXED_BF16X3)
+        idp.plan_set(mplan, idp.IDP_KEY_PRECISION, prec)
         idp.plan_set(mplan, idp.IDP_KEY_AUTOTUNE, 1)
         phi_m = torch.empty_like(rho)
         for _ in range(args.warmup):
@@ -317,12 +316,20 @@ def run_ours(args, rank, world):
                                                 ctypes.c_void_p(stream.cuda_stream), cap, kinds, ms)
             for j in range(max(n, 0)):
                 mk.setdefault(names.get(kinds[j], str(kinds[j])), []).append(ms[j])
-        mixed = {"variant": "bf16x3 pieces, fp32 accumulate, tcgen05 (rho, R and final transforms)",
-                 "tuning": idp.plan_tuning(mplan),
-                 "value": world * prob.points * args.steps / (t_m / 1e3), "unit": UNIT,
-                 "ms_per_step": t_m / args.steps, "max_rel_error_vs_fp64": diff,
-                 "kernel_ms_per_step": {k: sum(v) / 3 for k, v in mk.items()},
-                 "mixed_pass_avg_ms": statistics.mean(mk["mixed_pass"]) if "mixed_pass" in mk else None}
+        return {"variant": label,
+                "tuning": idp.plan_tuning(mplan),
+                "value": world * prob.points * args.steps / (t_m / 1e3), "unit": UNIT,
+                "ms_per_step": t_m / args.steps, "max_rel_error_vs_fp64": diff,
+                "kernel_ms_per_step": {k: sum(v) / 3 for k, v in mk.items()},
+                "mixed_pass_avg_ms": statistics.mean(mk["mixed_pass"]) if "mixed_pass" in mk else None}
+
+    mixed = mixed_tf32 = None
+    if not args.fp64_only:
+        mixed = tensor_variant(idp.IDP_PRECISION_MIXED_BF16X3,
+                               "bf16x3 pieces, fp32 accumulate, tcgen05 (rho, R and final transforms)")
+        mixed_tf32 = tensor_variant(idp.IDP_PRECISION_MIXED_TF32X3,
+                                    "tf32x3: two tf32 pieces, products hi*hi + hi*lo + lo*hi, fp32 accumulate, "
+                                    "tcgen05 kind::tf32 (rho, R and final transforms)")
 
     # double-float variant (FFT butterflies on the FP32 pipe, FP64-level accuracy)
     df32 = None
@@ -397,6 +404,7 @@ def run_ours(args, rank, world):
             "config": config_of(prob, args.order, {"parallelism": "replicas" if world > 1 else "single"}),
             "precision": precision,
             "mixed_precision": mixed,
+            "mixed_tf32x3": mixed_tf32,
             "df32": df32,
             "e2e": e2e,
             "gpu_launches": int(launches.value) * args.steps,
@@ -436,10 +444,11 @@ def run_batched(args, rank, world):
     stream = torch.cuda.current_stream(dev)
     out = {}
     for label, prec in (("fp64", idp.IDP_PRECISION_FP64), ("df32", idp.IDP_PRECISION_DF32),
-                        ("mixed_bf16x3", idp.IDP_PRECISION_MIXED_BF16X3)):
+                        ("mixed_bf16x3", idp.IDP_PRECISION_MIXED_BF16X3),
+                        ("mixed_tf32x3", idp.IDP_PRECISION_MIXED_TF32X3)):
         for pl in plans:
             idp.plan_set(pl, idp.IDP_KEY_PRECISION, prec)
-            if prec == idp.IDP_PRECISION_MIXED_BF16X3:
+            if prec in (idp.IDP_PRECISION_MIXED_BF16X3, idp.IDP_PRECISION_MIXED_TF32X3):
                 idp.plan_set(pl, idp.IDP_KEY_AUTOTUNE, 1)
         for _ in range(args.warmup):
             idp.solve_batched(plans, rhos, phis, stream)

@@ -87,12 +87,15 @@ enum {
                                       the boundary values, the stencils and the transform that produces
                                       u1 (whose sixth differences form R) stay FP64.  Setting it
                                       allocates the pieces of the sine matrices and FP32 temporaries. */
-    IDP_PRECISION_DF32 = 2         /* the FFT-based transforms (sine transforms of rho, R and the final
+    IDP_PRECISION_DF32 = 2,        /* the FFT-based transforms (sine transforms of rho, R and the final
                                       inverse, and the 3-D boundary convolutions) in double-float
                                       arithmetic (a value is a pair of FP32 numbers, ~48 significant
                                       bits) on the FP32 pipe, FP64 arrays in and out; the transform
                                       producing u1 and all stencils stay FP64.  Results agree with
                                       FP64 to a few 1e-13 relative. */
+    IDP_PRECISION_MIXED_TF32X3 = 3 /* as MIXED_BF16X3, with the operands split into two TF32 pieces
+                                      (hi + lo, ~22 significant bits) and three products (hi*hi,
+                                      hi*lo, lo*hi; tcgen05 kind::tf32), FP32 accumulation */
 };
 
 /* stages for idp_solve_stage */
@@ -164,7 +167,7 @@ enum {
     IDP_KERNEL_RHS6_EXTRAP = 9,  /* layers of E = R - R_spec: cubic extrapolation and boundary terms */
     IDP_KERNEL_GTILDE_EXPAND = 10, /* sine transform of gtilde assembled from its transformed layers */
     IDP_KERNEL_DST_PARTS = 11,   /* sine passes over the boundary-adjacent layers of gtilde */
-    IDP_KERNEL_MIXED = 12,       /* tensor-core sine-matrix pass (IDP_PRECISION_MIXED_BF16X3) */
+    IDP_KERNEL_MIXED = 12,       /* tensor-core sine-matrix pass (IDP_PRECISION_MIXED_BF16X3 / _TF32X3) */
     IDP_KERNEL_SUPPORT = 13,     /* reserved: no longer launched (the support flags of rho are made by the
                                     stage-1 pass along axis 2, timed under IDP_KERNEL_RFFT) */
     IDP_KERNEL_RHS6_EXPAND = 14, /* sine transform of the 6th-order layer correction from its layer transforms */

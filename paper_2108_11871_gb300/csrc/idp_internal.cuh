@@ -104,7 +104,9 @@ struct MpPass {
     void *out; int out_f64;
     int64_t os_m, os_p, os_q;
     int P, Q, n;
-    const void *bimg;           // BF16 pieces of S: [ntile][kblock][3][128 x 64 tile]
+    int variant;                // 0: BF16X3, 1: TF32X3
+    const void *bimg;           // pieces of S: [ntile][kblock][piece][16 KB tile] (BF16: 3 x 128 x 64,
+                                // TF32: 2 x 128 x 32)
     const double *tab; int64_t ts_m, ts_p, ts_q;
     const double *add; int64_t as_m, as_p, as_q;
     int *err;                   // set to 1 if a wait on the tensor cores timed out

@@ -6,17 +6,25 @@
 // the transformed axis outermost (the pass rotates the axes; three passes of
 // a 3-D transform, two of a 2-D one, return to the original layout).
 //
-// Precision: X and S are split into three BF16 pieces each (x = x0 + x1 + x2,
-// |x_i| ~ 2^-8i |x|); the six products with i + j <= 2 are accumulated by
-// tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) in one TMEM accumulator.
-// The dropped products are below 2^-24 relative, so the error is set by the
-// FP32 accumulation.  The eigenvalue scaling and the additions of the last
-// pass are done in FP64.
+// Precision, two variants:
+//  * BF16X3: X and S are split into three BF16 pieces each (x = x0 + x1 + x2,
+//    |x_i| ~ 2^-8i |x|); the six products with i + j <= 2 are accumulated by
+//    tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) in one TMEM accumulator.  The
+//    dropped products are below 2^-24 relative, so the error is set by the FP32
+//    accumulation.
+//  * TF32X3: two TF32 pieces each (x = x0 + x1, |x1| <= 2^-11 |x|, ~22 bits
+//    kept); the three products hi*hi, hi*lo, lo*hi by tcgen05.mma kind::tf32
+//    (FP32 accumulation); the dropped lo*lo and the rounding of lo are ~2^-22
+//    relative.
+// The eigenvalue scaling and the additions of the last pass are done in FP64.
 //
 // Block: 512 threads, a tile of 128 lines x NTN modes (NTN = 64 or 128), K in
-// blocks of 64.  Operands live in shared memory in the canonical K-major layout
-// without swizzle: 8 x 16-byte core matrices, core matrices adjacent along K are
-// LBO = 2048 bytes apart, adjacent along M/N SBO = 128 bytes apart.  The sine
+// blocks of 64 (BF16) or 32 (TF32): 16 KB per operand piece either way.
+// Operands live in shared memory in the canonical K-major layout without
+// swizzle: 8 x 16-byte core matrices (8 BF16 or 4 TF32 values per row), core
+// matrices adjacent along K are LBO = 2048 bytes apart, adjacent along M/N
+// SBO = 128 bytes apart; one MMA takes K = 16 (BF16) or 8 (TF32), two core
+// matrices along K, in both variants.  The sine
 // image of a K block (128 modes) arrives by cp.async while the block loads and
 // splits its input; a 64-mode tile addresses its half of the image through the
 // descriptor's start address.  FP64 <-> FP32 conversions and the factor 4 are
@@ -32,14 +40,21 @@ namespace {
 
 constexpr int MT = 128;            // lines per tile (MMA M)
 constexpr int NTILE = 128;         // modes per tile (MMA N)
-constexpr int KB = 64;             // K per shared-memory block
-constexpr int PIECES = 3;
-constexpr int TILE_BYTES = MT * KB * 2;                 // 16 KB per operand piece
-constexpr int SMEM_A = 0;
-constexpr int SMEM_B = PIECES * TILE_BYTES;
-constexpr int SMEM_BAR = 2 * PIECES * TILE_BYTES;       // mbarrier (8 B) + TMEM address (4 B)
-constexpr int SMEM_TOTAL = SMEM_BAR + 64;
+constexpr int TILE_BYTES = 16384;  // one operand piece: 128 rows x 16 core-matrix columns
 constexpr uint32_t LBO = 2048, SBO = 128;
+
+// per variant (0 = BF16X3, 1 = TF32X3): element bytes, K per block, pieces
+template <int V>
+struct MpCfg {
+    static constexpr int ESZ = V ? 4 : 2;
+    static constexpr int EPC = 16 / ESZ;                 // elements per core-matrix row
+    static constexpr int KB = TILE_BYTES / (MT * ESZ);   // 64 or 32
+    static constexpr int PIECES = V ? 2 : 3;
+    static constexpr int SMEM_A = 0;
+    static constexpr int SMEM_B = PIECES * TILE_BYTES;
+    static constexpr int SMEM_BAR = 2 * PIECES * TILE_BYTES;   // mbarrier (8 B) + TMEM address (4 B)
+    static constexpr int SMEM_TOTAL = SMEM_BAR + 64;
+};
 constexpr long long WAIT_CYCLES = 2000000000ll;       // bounded mbarrier polling (~1 s)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -47,10 +62,12 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p)
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// byte offset of element (row r, k) of a 128 x 64 BF16 tile
+// byte offset of element (row r, k) of a 128-row tile (K-major, no swizzle)
+template <int V>
 __device__ __forceinline__ uint32_t tile_off(int r, int k)
 {
-    return (uint32_t)((k >> 3) * LBO + (r >> 3) * SBO + (r & 7) * 16 + (k & 7) * 2);
+    using C = MpCfg<V>;
+    return (uint32_t)((k / C::EPC) * LBO + (r >> 3) * SBO + (r & 7) * 16 + (k % C::EPC) * C::ESZ);
 }
 
 // shared-memory matrix descriptor: start, LBO, SBO (>> 4), version 1, no swizzle
@@ -64,8 +81,23 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr)
     return d;
 }
 
-// instruction descriptor (kind::f16, A = B = BF16, D = F32, K-major, M = 128,
-// N = NTN): built in the kernel from the tile width
+// instruction descriptor (D = F32, A = B = BF16 for kind::f16 or TF32 for
+// kind::tf32, K-major, M = 128, N = NTN): built in the kernel from the tile width
+
+// x rounded to TF32 (11 significant bits, to nearest, ties to even), by integer
+// operations; the tensor cores read these FP32 containers unchanged
+__device__ __forceinline__ float tf32_rn(float x)
+{
+    const uint32_t u = __float_as_uint(x);
+    return __uint_as_float((u + 0xFFFu + ((u >> 13) & 1u)) & 0xFFFFE000u);
+}
+
+// x = hi + lo (two floats) -> two TF32 pieces; hi - a is exact in FP32
+__device__ __forceinline__ void split2(float hi, float lo, float &a, float &b)
+{
+    a = tf32_rn(hi);
+    b = tf32_rn((hi - a) + lo);
+}
 
 // x = hi + lo (two floats, |lo| <= 2^-24 |hi|) -> three BF16 pieces.  The
 // residuals hi - a and r1 - b are exact in FP32; lo enters below 2^-16 |x|.
@@ -98,18 +130,23 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
 }
 
 constexpr int NTHR = 512;
-constexpr int GPT = MT * (KB / 8) / NTHR;   // 16-byte row groups of the A tile per thread (2)
+constexpr int GPT = MT * (TILE_BYTES / MT / 16) / NTHR;   // 16-byte core-matrix rows of the A tile per thread (2)
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
 }
 
-template <int NTN>
+template <int NTN, int V>
 __global__ void __launch_bounds__(NTHR) mp_pass_kernel(const MpPass a)
 {
     static_assert(NTN == 64 || NTN == 128, "tile of 64 or 128 modes");
-    constexpr uint32_t IDESC_N = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NTN >> 3) << 17) |
+    using C = MpCfg<V>;
+    constexpr int KB = C::KB, PIECES = C::PIECES, SMEM_A = C::SMEM_A, SMEM_B = C::SMEM_B, SMEM_BAR = C::SMEM_BAR;
+    constexpr int EPC = C::EPC;
+    // D = F32 (bit 4); A, B = BF16 (1) for kind::f16 or TF32 (2) for kind::tf32
+    constexpr uint32_t FMT = V ? 2u : 1u;
+    constexpr uint32_t IDESC_N = (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(NTN >> 3) << 17) |
                                  ((uint32_t)(MT >> 4) << 24);
     extern __shared__ __align__(128) unsigned char sm[];
     const int t = threadIdx.x;
@@ -150,18 +187,18 @@ __global__ void __launch_bounds__(NTHR) mp_pass_kernel(const MpPass a)
             for (int e = t; e < PIECES * TILE_BYTES / 16; e += NTHR) cp_async16(dst + 16 * e, src + 16 * e);
             asm volatile("cp.async.commit_group;\n" ::: "memory");
         }
-        // A pieces: 128 lines x 64 k of the input, split into BF16 pieces; a
-        // thread takes GPT groups of 8 consecutive k of one line (one 16-byte
+        // A pieces: 128 lines x KB k of the input, split into pieces; a thread
+        // takes GPT groups of EPC consecutive k of one line (one 16-byte
         // core-matrix row each; consecutive lanes take consecutive lines, so a
         // warp's stores fill 512 contiguous bytes), all loads issued before any
         // is used
-        double xv[GPT][8];
+        double xv[GPT][EPC];
 #pragma unroll
         for (int g = 0; g < GPT; ++g) {
             const int e = t + g * NTHR;
             const int r = e & (MT - 1), g8 = e / MT;   // rows fastest: conflict-free 16-byte stores
             const int64_t L = L0 + r;
-            const int kg0 = kb * KB + g8 * 8;
+            const int kg0 = kb * KB + g8 * EPC;
             const bool row_ok = L < nlines;
             int64_t base = 0;
             if (row_ok) {
@@ -169,7 +206,7 @@ __global__ void __launch_bounds__(NTHR) mp_pass_kernel(const MpPass a)
                 base = p * a.is_p + q * a.is_q;
             }
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int j = 0; j < EPC; ++j) {
                 const int kg = kg0 + j;
                 double x = 0.0;
                 if (row_ok && kg < a.n) {
@@ -184,51 +221,71 @@ __global__ void __launch_bounds__(NTHR) mp_pass_kernel(const MpPass a)
         for (int g = 0; g < GPT; ++g) {
             const int e = t + g * NTHR;
             const int r = e & (MT - 1), g8 = e / MT;   // rows fastest: conflict-free 16-byte stores
-            unsigned short pa[8], pb[8], pc[8];
+            float hi[EPC], lo[EPC];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                float hi, lo;
+            for (int j = 0; j < EPC; ++j) {
                 if (a.in_f64) {
                     const ddr h2 = dd_from_bits(xv[g][j]);   // integer split, no FP64 instruction
-                    hi = h2.hi;
-                    lo = h2.lo;
+                    hi[j] = h2.hi;
+                    lo[j] = h2.lo;
                 } else {
-                    hi = __int_as_float((int)__double_as_longlong(xv[g][j]));
-                    lo = 0.f;
+                    hi[j] = __int_as_float((int)__double_as_longlong(xv[g][j]));
+                    lo[j] = 0.f;
                 }
-                split3(hi, lo, pa[j], pb[j], pc[j]);
             }
-            const uint32_t o = tile_off(r, g8 * 8);
-            uint4 va, vb, vc;
-            va.x = pa[0] | ((uint32_t)pa[1] << 16); va.y = pa[2] | ((uint32_t)pa[3] << 16);
-            va.z = pa[4] | ((uint32_t)pa[5] << 16); va.w = pa[6] | ((uint32_t)pa[7] << 16);
-            vb.x = pb[0] | ((uint32_t)pb[1] << 16); vb.y = pb[2] | ((uint32_t)pb[3] << 16);
-            vb.z = pb[4] | ((uint32_t)pb[5] << 16); vb.w = pb[6] | ((uint32_t)pb[7] << 16);
-            vc.x = pc[0] | ((uint32_t)pc[1] << 16); vc.y = pc[2] | ((uint32_t)pc[3] << 16);
-            vc.z = pc[4] | ((uint32_t)pc[5] << 16); vc.w = pc[6] | ((uint32_t)pc[7] << 16);
-            *reinterpret_cast<uint4 *>(sm + SMEM_A + 0 * TILE_BYTES + o) = va;
-            *reinterpret_cast<uint4 *>(sm + SMEM_A + 1 * TILE_BYTES + o) = vb;
-            *reinterpret_cast<uint4 *>(sm + SMEM_A + 2 * TILE_BYTES + o) = vc;
+            const uint32_t o = tile_off<V>(r, g8 * EPC);
+            if constexpr (V == 1) {
+                float4 va, vb;
+                split2(hi[0], lo[0], va.x, vb.x);
+                split2(hi[1], lo[1], va.y, vb.y);
+                split2(hi[2], lo[2], va.z, vb.z);
+                split2(hi[3], lo[3], va.w, vb.w);
+                *reinterpret_cast<float4 *>(sm + SMEM_A + 0 * TILE_BYTES + o) = va;
+                *reinterpret_cast<float4 *>(sm + SMEM_A + 1 * TILE_BYTES + o) = vb;
+            } else {
+                unsigned short pa[8], pb[8], pc[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) split3(hi[j], lo[j], pa[j], pb[j], pc[j]);
+                uint4 va, vb, vc;
+                va.x = pa[0] | ((uint32_t)pa[1] << 16); va.y = pa[2] | ((uint32_t)pa[3] << 16);
+                va.z = pa[4] | ((uint32_t)pa[5] << 16); va.w = pa[6] | ((uint32_t)pa[7] << 16);
+                vb.x = pb[0] | ((uint32_t)pb[1] << 16); vb.y = pb[2] | ((uint32_t)pb[3] << 16);
+                vb.z = pb[4] | ((uint32_t)pb[5] << 16); vb.w = pb[6] | ((uint32_t)pb[7] << 16);
+                vc.x = pc[0] | ((uint32_t)pc[1] << 16); vc.y = pc[2] | ((uint32_t)pc[3] << 16);
+                vc.z = pc[4] | ((uint32_t)pc[5] << 16); vc.w = pc[6] | ((uint32_t)pc[7] << 16);
+                *reinterpret_cast<uint4 *>(sm + SMEM_A + 0 * TILE_BYTES + o) = va;
+                *reinterpret_cast<uint4 *>(sm + SMEM_A + 1 * TILE_BYTES + o) = vb;
+                *reinterpret_cast<uint4 *>(sm + SMEM_A + 2 * TILE_BYTES + o) = vc;
+            }
         }
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
         if (t == 0 && !a.stall_test) {
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            // products (i, j) with i + j <= 2
+            // products (i, j) with i + j <= 2 (BF16X3) or <= 1 (TF32X3); one
+            // MMA per two core matrices along K
+            constexpr int NPR = V ? 3 : 6;
             const int pa[6] = {0, 0, 1, 0, 1, 2};
             const int pb[6] = {0, 1, 0, 2, 1, 0};
-            for (int pr = 0; pr < 6; ++pr) {
-                for (int ks = 0; ks < KB / 16; ++ks) {
+            for (int pr = 0; pr < NPR; ++pr) {
+                for (int ks = 0; ks < KB / (2 * EPC); ++ks) {
                     const uint64_t ad = make_desc(smem_u32(sm + SMEM_A + pa[pr] * TILE_BYTES) + ks * 2 * LBO);
                     const uint64_t bd =
                         make_desc(smem_u32(sm + SMEM_B + pb[pr] * TILE_BYTES) + ks * 2 * LBO + b_sub);
                     const uint32_t acc = (kb > 0 || pr > 0 || ks > 0) ? 1u : 0u;
-                    asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                        "l"(ad), "l"(bd), "r"(IDESC_N), "r"(acc)
-                        : "memory");
+                    if constexpr (V == 1)
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                            "l"(ad), "l"(bd), "r"(IDESC_N), "r"(acc)
+                            : "memory");
+                    else
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                            "l"(ad), "l"(bd), "r"(IDESC_N), "r"(acc)
+                            : "memory");
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
@@ -299,26 +356,38 @@ __global__ void __launch_bounds__(NTHR) mp_pass_kernel(const MpPass a)
 
 }  // namespace
 
-size_t mp_smem_bytes() { return SMEM_TOTAL; }
-
 cudaError_t mp_set_attributes()
 {
-    cudaError_t e = cudaFuncSetAttribute(mp_pass_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(mp_pass_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(mp_pass_kernel<128, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  MpCfg<0>::SMEM_TOTAL)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(mp_pass_kernel<64, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  MpCfg<0>::SMEM_TOTAL)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(mp_pass_kernel<128, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  MpCfg<1>::SMEM_TOTAL)) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(mp_pass_kernel<64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                MpCfg<1>::SMEM_TOTAL);
 }
 
-cudaError_t launch_mp_pass(const MpPass &a, cudaStream_t st)
+template <int V>
+cudaError_t launch_mp_v(const MpPass &a, cudaStream_t st)
 {
     const int64_t lines = (int64_t)a.P * a.Q;
     const unsigned tiles = (unsigned)((lines + MT - 1) / MT);
     // 64-mode tiles double the blocks of a launch that fills the GPU less than twice
     if (a.modes_per_tile == 64 || (a.modes_per_tile == 0 && tiles * ((a.n + NTILE - 1) / NTILE) < 2 * 152)) {
-        mp_pass_kernel<64><<<dim3(tiles, (unsigned)((a.n + 63) / 64)), NTHR, SMEM_TOTAL, st>>>(a);
+        mp_pass_kernel<64, V><<<dim3(tiles, (unsigned)((a.n + 63) / 64)), NTHR, MpCfg<V>::SMEM_TOTAL, st>>>(a);
     } else {
-        mp_pass_kernel<128><<<dim3(tiles, (unsigned)((a.n + NTILE - 1) / NTILE)), NTHR, SMEM_TOTAL, st>>>(a);
+        mp_pass_kernel<128, V>
+            <<<dim3(tiles, (unsigned)((a.n + NTILE - 1) / NTILE)), NTHR, MpCfg<V>::SMEM_TOTAL, st>>>(a);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_mp_pass(const MpPass &a, cudaStream_t st)
+{
+    return a.variant ? launch_mp_v<1>(a, st) : launch_mp_v<0>(a, st);
 }
 
 }  // namespace idp

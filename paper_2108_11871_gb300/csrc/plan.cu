@@ -344,15 +344,71 @@ double bf16_value(uint16_t b)
     return (double)f;
 }
 
-// BF16 pieces of S_{m,k} = sin(pi (m+1)(k+1)/M), laid out as the kernel's
-// shared-memory tiles: [ntile][kblock][piece][128 rows m x 64 k], element
-// (r, c) at byte (c/8)*2048 + (r/8)*128 + (r%8)*16 + (c%8)*2.
-int get_mp_image(idp_plan p, int M, const void **out)
+// FP32 bits rounded to TF32 (11 significant bits, to nearest, ties to even)
+uint32_t tf32_bits(float x)
 {
-    auto it = p->mp_img.find(M);
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    return (u + 0xFFFu + ((u >> 13) & 1u)) & 0xFFFFE000u;
+}
+double tf32_value(uint32_t u)
+{
+    float f;
+    std::memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+// TF32 pieces of S (variant 1): [ntile][kblock][2][128 rows m x 32 k] FP32
+// containers, element (r, c) at byte (c/4)*2048 + (r/8)*128 + (r%8)*16 + (c%4)*4
+int get_mp_image_tf32(idp_plan p, int M, const void **out)
+{
+    const int n = M - 1, nt = (n + 127) / 128, nkb = (n + 31) / 32;
+    const size_t tile = 128 * 32;
+    std::vector<uint32_t> img((size_t)nt * nkb * 2 * tile, 0);
+    for (int t = 0; t < nt; ++t)
+        for (int kb = 0; kb < nkb; ++kb)
+            for (int r = 0; r < 128; ++r)
+                for (int c = 0; c < 32; ++c) {
+                    const int m = t * 128 + r, k = kb * 32 + c;
+                    const double s = (m < n && k < n) ? sinpi_frac((int64_t)(m + 1) * (k + 1), M) : 0.0;
+                    const uint32_t a = tf32_bits((float)s);
+                    const uint32_t b = tf32_bits((float)(s - tf32_value(a)));
+                    const size_t off = ((size_t)(c / 4) * 2048 + (r / 8) * 128 + (r % 8) * 16 + (c % 4) * 4) / 4;
+                    const size_t base = (((size_t)t * nkb + kb) * 2) * tile;
+                    img[base + off] = a;
+                    img[base + tile + off] = b;
+                }
+    uint32_t *d;
+    int rc = p->alloc(&d, (int64_t)img.size());
+    if (rc) return rc;
+    IDP_CK(cudaMemcpy(d, img.data(), img.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    *out = d;
+    return IDP_OK;
+}
+
+// the tensor-core pass variant of the plan's precision (0: BF16X3, 1: TF32X3)
+int mp_variant(idp_plan p) { return p->mixed == IDP_PRECISION_MIXED_TF32X3 ? 1 : 0; }
+bool tensor_mode(idp_plan p)
+{
+    return p->mixed == IDP_PRECISION_MIXED_BF16X3 || p->mixed == IDP_PRECISION_MIXED_TF32X3;
+}
+
+// Pieces of S_{m,k} = sin(pi (m+1)(k+1)/M) for a tensor-core variant, laid out
+// as the kernel's shared-memory tiles.  BF16 (variant 0):
+// [ntile][kblock][3][128 rows m x 64 k], element (r, c) at byte
+// (c/8)*2048 + (r/8)*128 + (r%8)*16 + (c%8)*2.  Cached per (M, variant).
+int get_mp_image(idp_plan p, int M, int variant, const void **out)
+{
+    const int key = M + (variant << 24);
+    auto it = p->mp_img.find(key);
     if (it != p->mp_img.end()) {
         *out = it->second;
         return IDP_OK;
+    }
+    if (variant) {
+        int rc = get_mp_image_tf32(p, M, out);
+        if (!rc) p->mp_img[key] = const_cast<void *>(*out);
+        return rc;
     }
     const int n = M - 1, nt = (n + 127) / 128, nkb = (n + 63) / 64;
     const size_t tile = 128 * 64;
@@ -378,7 +434,7 @@ int get_mp_image(idp_plan p, int M, const void **out)
     int rc = p->alloc(&d, (int64_t)img.size());
     if (rc) return rc;
     IDP_CK(cudaMemcpy(d, img.data(), img.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
-    p->mp_img[M] = d;
+    p->mp_img[key] = d;
     *out = d;
     return IDP_OK;
 }
@@ -392,6 +448,7 @@ int transform_mixed(idp_plan p, View3 in, View3 out, const double *tab, View3 ad
     std::vector<MpPass> ps;
     MpPass a{};
     a.err = p->d_err;
+    a.variant = mp_variant(p);
     if (p->d == 3) {
         a.in = in.p; a.in_f64 = 1; a.is_p = in.s0; a.is_q = in.s1; a.is_k = in.s2;
         a.out = ta; a.out_f64 = 0; a.os_m = (int64_t)n0 * n1; a.os_p = n1; a.os_q = 1;
@@ -428,7 +485,7 @@ int transform_mixed(idp_plan p, View3 in, View3 out, const double *tab, View3 ad
     }
     for (size_t i = 0; i < ps.size(); ++i) {
         const int ax = p->d == 3 ? axes3[i] : axes2[i];
-        int rc = get_mp_image(p, p->M[ax], &ps[i].bimg);
+        int rc = get_mp_image(p, p->M[ax], ps[i].variant, &ps[i].bimg);
         if (rc) return rc;
         Mark mk(p, IDP_KERNEL_MIXED, st);
         IDP_CK(launch_mp_pass(ps[i], st));
@@ -442,12 +499,12 @@ int transform_mixed(idp_plan p, View3 in, View3 out, const double *tab, View3 ad
 int transform(idp_plan p, View3 in, double *work, View3 out, const double *tab, View3 add, bool forward,
               cudaStream_t st, bool allow_reduced = true, bool skip_axis2 = false, int in_dd0 = 0)
 {
-    if (p->mixed == IDP_PRECISION_MIXED_BF16X3 && allow_reduced && p->mixed_path == 0)
+    if (tensor_mode(p) && allow_reduced && p->mixed_path == 0)
         return transform_mixed(p, in, out, tab, add, st == p->side ? 1 : 0, st);
     // df32 passes: precision DF32, or precision MIXED when the autotuner found the
     // double-float FFT faster than the matrix pass (it is also more accurate)
     const bool dd = (p->mixed == IDP_PRECISION_DF32 ||
-                     (p->mixed == IDP_PRECISION_MIXED_BF16X3 && p->mixed_path == 1)) && allow_reduced;
+                     (tensor_mode(p) && p->mixed_path == 1)) && allow_reduced;
     int axes[3], na = 0;
     if (forward) {
         for (int s = skip_axis2 ? 1 : 2; s >= 0; --s)
@@ -779,7 +836,7 @@ int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t s
     const bool overlap_rho = (stop == 0) && !p->profiling;
     // FP64 / df32 transforms: the first pass of the forward transform of rho is
     // the imaginary part of the boundary's first real FFT (see transform_rho_from_T0)
-    const bool rho_from_T0 = (stop == 0) && !(p->mixed == IDP_PRECISION_MIXED_BF16X3 && p->mixed_path == 0);
+    const bool rho_from_T0 = (stop == 0) && !(tensor_mode(p) && p->mixed_path == 0);
     // host-buffer solve: the first row transform reads rho from the host buffer
     // and leaves the device copy for the later stages; where rho is needed before
     // it (the tensor-core transform of rho starts at once), rho goes up first
@@ -826,7 +883,7 @@ int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t s
     if (stop == 0 && overlap_rho) IDP_CK(cudaStreamWaitEvent(st, p->join, 0));
     // FP64 / df32 final transforms take u1 in C (S C + S B = S (C + B)); the
     // tensor-core one adds the FP64 u1 afterwards instead
-    const bool fold_u1 = !(p->mixed == IDP_PRECISION_MIXED_BF16X3 && p->mixed_path == 0);
+    const bool fold_u1 = !(tensor_mode(p) && p->mixed_path == 0);
     {
         Mark mk(p, IDP_KERNEL_GTILDE_EXPAND, st);
         IDP_CK(launch_gtilde_expand(p->grid, p->Q0, p->Q1, p->Q2, p->sin4, p->tab4, nullptr, p->B, st,
@@ -1178,7 +1235,7 @@ int autotune(idp_plan p)
         }
         p->dst_lines = best;
     }
-    if (!rc && p->mixed == IDP_PRECISION_MIXED_BF16X3) {
+    if (!rc && tensor_mode(p)) {
         const View3 none{nullptr, 0, 0, 0};
         float tm[2];
         for (int path = 0; path < 2 && !rc; ++path) {
@@ -1363,7 +1420,7 @@ int idp_plan_set(idp_plan p, int key, int64_t value)
         return IDP_OK;
     }
     if (key == IDP_KEY_STALL_TEST) {
-        if (p->mixed != IDP_PRECISION_MIXED_BF16X3) return IDP_EINVAL;
+        if (!tensor_mode(p)) return IDP_EINVAL;
         p->stall_test = value ? 1 : 0;
         ++p->version;
         if (p->gexec) {
@@ -1373,10 +1430,11 @@ int idp_plan_set(idp_plan p, int key, int64_t value)
         return IDP_OK;
     }
     if (key == IDP_KEY_PRECISION) {
-        if (value != IDP_PRECISION_FP64 && value != IDP_PRECISION_MIXED_BF16X3 && value != IDP_PRECISION_DF32)
+        if (value != IDP_PRECISION_FP64 && value != IDP_PRECISION_MIXED_BF16X3 && value != IDP_PRECISION_DF32 &&
+            value != IDP_PRECISION_MIXED_TF32X3)
             return IDP_EINVAL;
         if (p->d == 1 && value != IDP_PRECISION_FP64) return IDP_ESUPPORT;
-        if (value == IDP_PRECISION_MIXED_BF16X3) {
+        if (value == IDP_PRECISION_MIXED_BF16X3 || value == IDP_PRECISION_MIXED_TF32X3) {
             int rc;
             if (!p->d_err) {
                 if ((rc = p->alloc(&p->d_err, 1))) return rc;
@@ -1387,7 +1445,9 @@ int idp_plan_set(idp_plan p, int key, int64_t value)
                     if (!p->t32[s][q] && (rc = p->alloc(&p->t32[s][q], p->nint))) return rc;
             for (int s = 0; s < 3; ++s) {
                 const void *img;
-                if (p->act[s] && (rc = get_mp_image(p, p->M[s], &img))) return rc;
+                if (p->act[s] &&
+                    (rc = get_mp_image(p, p->M[s], value == IDP_PRECISION_MIXED_TF32X3 ? 1 : 0, &img)))
+                    return rc;
             }
         }
         if (value == IDP_PRECISION_DF32 && p->d == 3 && !p->khatd[0]) {
