@@ -113,7 +113,16 @@ typedef struct idp_plan_s *idp_plan;
 /* Create a plan for one grid (section 3 grid, section 5 order).
  *   out   : receives the plan handle (owned by the caller; free with idp_destroy_plan)
  *   d     : 1, 2 or 3
- *   n[d]  : node counts including boundary nodes
+ *   n[d]  : node counts including boundary nodes, n[s] >= 3.  Panel counts
+ *           n[s] - 1 of 16, 32, 48, 64, 96, 128, 192, 256, 384 or 512 are solved
+ *           as given; any other count up to 512 is padded (section 2: the domain
+ *           is extended by a few panels, h unchanged, the extra panels split
+ *           between the two ends) to the next of these, the solve runs on the
+ *           larger grid and phi is returned at the caller's nodes (the
+ *           free-space potential there, to the method's accuracy); larger counts
+ *           give IDP_ESUPPORT.  A padded plan offers full solves only
+ *           (idp_solve, _host, _batched, _profile_solve, stage PHI; other stages:
+ *           IDP_ESUPPORT).  idp_plan_grid reports the grid solved on.
  *   h[d]  : mesh widths
  *   order : 4 or 6 (accuracy order of the harmonic correction, section 5; for
  *           d = 1 the correction is exact, the straight line through the two
@@ -171,7 +180,8 @@ enum {
     IDP_KERNEL_SUPPORT = 13,     /* reserved: no longer launched (the support flags of rho are made by the
                                     stage-1 pass along axis 2, timed under IDP_KERNEL_RFFT) */
     IDP_KERNEL_RHS6_EXPAND = 14, /* sine transform of the 6th-order layer correction from its layer transforms */
-    IDP_KERNEL_LINE1D = 15       /* d = 1: g at the two ends and the straight-line correction (section 5) */
+    IDP_KERNEL_LINE1D = 15,      /* d = 1: g at the two ends and the straight-line correction (section 5) */
+    IDP_KERNEL_PAD = 16          /* padded plans: rho into the padded grid, phi back to the caller's nodes */
 };
 
 /* Run one solve (as idp_solve, but with plain launches, all on `stream`, none
@@ -192,8 +202,15 @@ int idp_plan_tuning(idp_plan plan, int64_t out[9]);
  * first solve). */
 int idp_plan_launches(idp_plan plan, int64_t *launches);
 
-/* Query the plan: node count, interior count and device workspace bytes. */
+/* Query the plan: node count of the caller's arrays, interior count of the grid
+ * solved on, and device workspace bytes. */
 int idp_plan_info(idp_plan plan, int64_t *nodes, int64_t *interior, int64_t *workspace_bytes);
+
+/* The grid a plan solves on (section 2: a panel count the transforms do not
+ * take is met by extending the domain by a few panels): n_solved[d] node counts
+ * per axis, offset[d] the index of the caller's node 0 in it.  Equal to n[] and
+ * 0 when no axis needed padding. */
+int idp_plan_grid(idp_plan plan, int64_t n_solved[], int64_t offset[]);
 
 /* Release the plan and all its device memory (synchronises the device). */
 int idp_destroy_plan(idp_plan plan);

@@ -65,6 +65,7 @@ def library(path: str = None):
         "idp_plan_tuning": (_int, [_vp, ctypes.POINTER(_i64)]),
         "idp_profile_solve": (_int, [_vp, _vp, _vp, _vp, _int, ctypes.POINTER(_int), ctypes.POINTER(ctypes.c_float)]),
         "idp_plan_launches": (_int, [_vp, ctypes.POINTER(_i64)]),
+        "idp_plan_grid": (_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
         "idp_rhs6_noalloc": (_int, [_int, ctypes.POINTER(_i64), ctypes.POINTER(_dbl), _vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
@@ -172,6 +173,14 @@ def plan_info(plan: Plan):
     _check(library().idp_plan_info(plan.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
            "idp_plan_info")
     return dict(nodes=a.value, interior=b.value, workspace_bytes=c.value)
+
+
+def plan_grid(plan: Plan):
+    """(node counts of the grid solved on, offset of the caller's node 0 in it)."""
+    n = (_i64 * plan.d)()
+    off = (_i64 * plan.d)()
+    _check(library().idp_plan_grid(plan.handle, n, off), "idp_plan_grid")
+    return [int(v) for v in n], [int(v) for v in off]
 
 
 def plan_tuning(plan: Plan):

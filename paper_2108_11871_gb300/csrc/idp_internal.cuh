@@ -267,6 +267,11 @@ cudaError_t launch_rhs6_e_expand(const Grid3 &g, const double *E0, const double 
 // x *= Lambda_R (per mode) and out += E on its layers: the stage output of R
 cudaError_t launch_rhs6_symbol(const Grid3 &g, const double *ld, int64_t off1, int64_t off2, double *x,
                                cudaStream_t st);
+// dst[i0*d0 + i1*d1 + i2] = src[i0*s0 + i1*s1 + i2] over the box e0 x e1 x e2
+// (innermost axis contiguous on both sides): the copies between the caller's
+// grid and a padded grid
+cudaError_t launch_box_copy(const double *src, int64_t s0, int64_t s1, double *dst, int64_t d0, int64_t d1,
+                            int e0, int e1, int e2, cudaStream_t st);
 cudaError_t launch_rhs6_e_scatter(const Grid3 &g, const double *E0, const double *E1, const double *E2,
                                   double *out, cudaStream_t st);
 

@@ -38,6 +38,14 @@ bool supported_panels(int64_t M)
     return M >= 16 && M <= 512 && (is_pow2(M) || (M >= 48 && M % 3 == 0 && is_pow2(M / 3)));
 }
 
+// the smallest supported panel count >= M (0 if there is none)
+int64_t padded_panels(int64_t M)
+{
+    for (int64_t m = M < 16 ? 16 : M; m <= 512; ++m)
+        if (supported_panels(m)) return m;
+    return 0;
+}
+
 // host tables ----------------------------------------------------------------
 // sin(pi m / L) and cos(pi m / L) with the integer argument reduced to [0, 2L).
 double sinpi_frac(int64_t m, int64_t L)
@@ -132,6 +140,14 @@ struct idp_plan_s {
     int act[3] = {0, 0, 0};
     double h[3] = {1, 1, 1};
     int64_t nodes = 0, nint = 0;
+    // automatic padding (section 2: the domain is extended by a few panels so that
+    // every panel count suits the transforms): the caller's node counts, the offset
+    // of the caller's node 0 in the grid solved on, the caller's node count, and
+    // the padded copies of rho and phi
+    int padded = 0;
+    int un[3] = {1, 1, 1}, uoff[3] = {0, 0, 0};
+    int64_t unodes = 0;
+    double *rho_pad = nullptr, *phi_pad = nullptr;
     int64_t ns[3] = {0, 0, 0};  // node strides
     int64_t is[3] = {0, 0, 0};  // interior strides
     Grid3 grid{};
@@ -815,7 +831,49 @@ int enqueue_1d(idp_plan p, const double *rho, double *phi, int stop, cudaStream_
     return IDP_OK;
 }
 
+int enqueue_grid(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t st);
+
+// A padded plan: the interior nodes of the caller's rho go into the padded array
+// (the rest of it stays zero: the caller's boundary entries of rho are not used,
+// as in an unpadded solve), the solve runs on the padded grid, and phi is read
+// back at the caller's nodes.  Full solves only.
+int enqueue_padded(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t st)
+{
+    if (stop != 0) return IDP_ESUPPORT;
+    if (p->hio_rho)
+        IDP_CK(cudaMemcpyAsync(p->h_rho, p->hio_rho, sizeof(double) * p->unodes, cudaMemcpyHostToDevice, st));
+    int lo[3], ext[3];
+    for (int s = 0; s < 3; ++s) {
+        lo[s] = p->act[s] ? 1 : 0;
+        ext[s] = p->act[s] ? p->un[s] - 2 : 1;
+    }
+    const int64_t u1 = p->un[2], u0 = (int64_t)p->un[1] * p->un[2];
+    const int64_t n1 = p->n[2], n0 = (int64_t)p->n[1] * p->n[2];
+    const int64_t uo = (int64_t)p->uoff[0] * n0 + (int64_t)p->uoff[1] * n1 + p->uoff[2];
+    {
+        Mark mk(p, IDP_KERNEL_PAD, st);
+        IDP_CK(launch_box_copy(rho + lo[0] * u0 + lo[1] * u1 + lo[2], u0, u1,
+                               p->rho_pad + uo + lo[0] * n0 + lo[1] * n1 + lo[2], n0, n1, ext[0], ext[1], ext[2],
+                               st));
+    }
+    const double *hio = p->hio_rho;
+    p->hio_rho = nullptr;
+    const int rc = enqueue_grid(p, p->rho_pad, p->phi_pad, 0, st);
+    p->hio_rho = hio;
+    if (rc) return rc;
+    Mark mk(p, IDP_KERNEL_PAD, st);
+    IDP_CK(launch_box_copy(p->phi_pad + uo, n0, n1, phi, u0, u1, p->un[0], p->un[1], p->un[2], st));
+    return IDP_OK;
+}
+
 int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t st)
+{
+    if (p->padded) return enqueue_padded(p, rho, phi, stop, st);
+    return enqueue_grid(p, rho, phi, stop, st);
+}
+
+// one solve (or stage) on the plan's own grid
+int enqueue_grid(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t st)
 {
     if (p->d == 1) return enqueue_1d(p, rho, phi, stop, st);
     int rc;
@@ -977,6 +1035,10 @@ int plan_setup(idp_plan p)
         if ((rc = get_fft(p, p->M[s] / 2, &t)) || (rc = get_fft(p, p->M[s], &t)) ||
             (rc = get_fft(p, 2 * p->M[s], &t)) || (rc = get_sin2(p, p->M[s], &sn)))
             return rc;
+    }
+    if (p->padded) {
+        if ((rc = p->alloc(&p->rho_pad, p->nodes)) || (rc = p->alloc(&p->phi_pad, p->nodes))) return rc;
+        IDP_CK(cudaMemset(p->rho_pad, 0, sizeof(double) * p->nodes));
     }
     if (p->d == 1) return plan_setup_1d(p);
     // workspace
@@ -1362,8 +1424,7 @@ int idp_create_plan(idp_plan *out, int d, const int64_t n[], const double h[], i
     for (int s = 0; s < d; ++s) {
         if (!(h[s] > 0.0) || !std::isfinite(h[s])) return IDP_EINVAL;
         if (n[s] < 3) return IDP_EINVAL;
-        const int64_t M = n[s] - 1;
-        if (!supported_panels(M)) return IDP_ESUPPORT;
+        if (!padded_panels(n[s] - 1)) return IDP_ESUPPORT;
     }
     idp_plan p = new (std::nothrow) idp_plan_s();
     if (!p) return IDP_ENOMEM;
@@ -1372,10 +1433,17 @@ int idp_create_plan(idp_plan *out, int d, const int64_t n[], const double h[], i
     p->serial = g_serial.fetch_add(1);
     const int o = 3 - d;
     for (int s = 0; s < d; ++s) {
-        p->n[s + o] = (int)n[s];
+        // an unsupported panel count is padded to the next supported one, the
+        // extra panels split between the two ends (h unchanged)
+        const int64_t Mp = padded_panels(n[s] - 1);
+        p->n[s + o] = (int)Mp + 1;
+        p->un[s + o] = (int)n[s];
+        p->uoff[s + o] = (int)((Mp - (n[s] - 1)) / 2);
+        if (Mp != n[s] - 1) p->padded = 1;
         p->h[s + o] = h[s];
         p->act[s + o] = 1;
     }
+    p->unodes = (int64_t)p->un[0] * p->un[1] * p->un[2];
     for (int s = 0; s < 3; ++s) {
         p->M[s] = p->n[s] - 1;
         p->ni[s] = p->act[s] ? p->n[s] - 2 : 1;
@@ -1475,7 +1543,7 @@ int idp_plan_set(idp_plan p, int key, int64_t value)
 int idp_solve(idp_plan p, const double *rho, double *phi, void *stream)
 {
     if (!p || !rho || !phi) return IDP_EINVAL;
-    const size_t b = sizeof(double) * p->nodes;
+    const size_t b = sizeof(double) * p->unodes;
     if (overlap(rho, b, phi, b)) return IDP_EALIAS;
     return run_solve(p, rho, phi, (cudaStream_t)stream);
 }
@@ -1483,10 +1551,10 @@ int idp_solve(idp_plan p, const double *rho, double *phi, void *stream)
 int idp_solve_host(idp_plan p, const double *rho_host, double *phi_host, void *stream)
 {
     if (!p || !rho_host || !phi_host) return IDP_EINVAL;
-    const size_t b = sizeof(double) * p->nodes;
+    const size_t b = sizeof(double) * p->unodes;
     if (overlap(rho_host, b, phi_host, b)) return IDP_EALIAS;
     int rc;
-    if (!p->h_rho && ((rc = p->alloc(&p->h_rho, p->nodes)) || (rc = p->alloc(&p->h_phi, p->nodes)))) return rc;
+    if (!p->h_rho && ((rc = p->alloc(&p->h_rho, p->unodes)) || (rc = p->alloc(&p->h_phi, p->unodes)))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     double *phi_view = nullptr;
     if (p->use_graph && !p->stall_test && device_view(rho_host) && (phi_view = device_view(phi_host))) {
@@ -1509,7 +1577,7 @@ int idp_solve_batched(int count, const idp_plan plans[], const double *const rho
         if (!plans[i] || !rho[i] || !phi[i]) return IDP_EINVAL;
         for (int j = 0; j < i; ++j)
             if (plans[j] == plans[i]) return IDP_EINVAL;
-        const size_t b = sizeof(double) * plans[i]->nodes;
+        const size_t b = sizeof(double) * plans[i]->unodes;
         if (overlap(rho[i], b, phi[i], b)) return IDP_EALIAS;
     }
     if (count == 0) return IDP_OK;
@@ -1585,7 +1653,7 @@ int idp_solve_stage(idp_plan p, int stage, const double *rho, double *out, void 
     if (!p || !rho || !out) return IDP_EINVAL;
     if (stage < IDP_STAGE_BOUNDARY || stage > IDP_STAGE_PHI) return IDP_EINVAL;
     if (stage == IDP_STAGE_R && p->order != 6) return IDP_EINVAL;
-    const size_t b = sizeof(double) * p->nodes;
+    const size_t b = sizeof(double) * p->unodes;
     if (overlap(rho, b, out, b)) return IDP_EALIAS;
     p->last = (cudaStream_t)stream;
     p->last_valid = 1;
@@ -1612,7 +1680,7 @@ int idp_profile_solve(idp_plan p, const double *rho, double *phi, void *stream, 
                       float *ms)
 {
     if (!p || !rho || !phi || capacity < 0 || (capacity > 0 && (!kinds || !ms))) return IDP_EINVAL;
-    const size_t b = sizeof(double) * p->nodes;
+    const size_t b = sizeof(double) * p->unodes;
     if (overlap(rho, b, phi, b)) return IDP_EALIAS;
     cudaStream_t st = (cudaStream_t)stream;
     while ((int)p->ev.size() < 2 * capacity) {
@@ -1638,10 +1706,21 @@ int idp_profile_solve(idp_plan p, const double *rho, double *phi, void *stream, 
     return n;
 }
 
+int idp_plan_grid(idp_plan p, int64_t n_solved[], int64_t offset[])
+{
+    if (!p || !n_solved || !offset) return IDP_EINVAL;
+    const int o = 3 - p->d;
+    for (int s = 0; s < p->d; ++s) {
+        n_solved[s] = p->n[s + o];
+        offset[s] = p->uoff[s + o];
+    }
+    return IDP_OK;
+}
+
 int idp_plan_info(idp_plan p, int64_t *nodes, int64_t *interior, int64_t *workspace_bytes)
 {
     if (!p) return IDP_EINVAL;
-    if (nodes) *nodes = p->nodes;
+    if (nodes) *nodes = p->unodes;
     if (interior) *interior = p->nint;
     if (workspace_bytes) *workspace_bytes = p->bytes;
     return IDP_OK;

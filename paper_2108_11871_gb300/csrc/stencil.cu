@@ -856,12 +856,34 @@ cudaError_t launch_rhs6_e_scatter(const Grid3 &g, const double *E0, const double
 }
 
 namespace {
+__global__ void box_copy_kernel(const double *__restrict__ src, int64_t s0, int64_t s1, double *__restrict__ dst,
+                                int64_t d0, int64_t d1, int e0, int e1, int e2)
+{
+    const int64_t total = (int64_t)e0 * e1 * e2;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = i / e2;
+        const int i2 = (int)(i - row * e2);
+        const int i0 = (int)(row / e1), i1 = (int)(row - (int64_t)i0 * e1);
+        dst[i0 * d0 + i1 * d1 + i2] = src[i0 * s0 + i1 * s1 + i2];
+    }
+}
+
 __global__ void to_dd_kernel(const double *x, ddr *y, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = dd_from(x[i]);
 }
 }  // namespace
+
+cudaError_t launch_box_copy(const double *src, int64_t s0, int64_t s1, double *dst, int64_t d0, int64_t d1,
+                            int e0, int e1, int e2, cudaStream_t st)
+{
+    const int64_t total = (int64_t)e0 * e1 * e2;
+    if (total <= 0) return cudaSuccess;
+    box_copy_kernel<<<grid_for(total), 256, 0, st>>>(src, s0, s1, dst, d0, d1, e0, e1, e2);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_to_dd(const double *x, ddr *y, int64_t n, cudaStream_t st)
 {

@@ -42,10 +42,12 @@ def test_argument_errors_need_no_gpu():
     assert lib.idp_create_plan(ctypes.byref(out), 0, n, h, 6) == idp.IDP_EINVAL
     one = (ctypes.c_int64 * 1)(2)       # d = 1 with fewer than 3 nodes
     assert lib.idp_create_plan(ctypes.byref(out), 1, one, h, 6) == idp.IDP_EINVAL
-    one = (ctypes.c_int64 * 1)(34)      # d = 1, M = 33 panels
+    one = (ctypes.c_int64 * 1)(600)     # d = 1, M = 599 panels
     assert lib.idp_create_plan(ctypes.byref(out), 1, one, h, 6) == idp.IDP_ESUPPORT
     assert lib.idp_create_plan(ctypes.byref(out), 3, n, h, 5) == idp.IDP_EINVAL
-    for bad_n in ((33, 34, 33), (25, 33, 33), (33, 33, 1025)):   # M = 33, 24, 1024
+    # panel counts above 512 have no padded size (smaller unsupported counts are
+    # padded, which needs the GPU)
+    for bad_n in ((33, 34, 1026), (514, 33, 33), (33, 33, 1025)):   # M = 1025, 513, 1024
         bad = (ctypes.c_int64 * 3)(*bad_n)
         assert lib.idp_create_plan(ctypes.byref(out), 3, bad, h, 6) == idp.IDP_ESUPPORT
     assert lib.idp_solve(None, None, None, None) == idp.IDP_EINVAL

@@ -456,3 +456,111 @@ def test_one_dimensional_host_and_batched_give_the_device_bits(idp):
         idp.solve_host(plans[0], rho_p.data_ptr(), phi_p.data_ptr())
         idp.plan_status(plans[0])
         assert np.array_equal(phi_p.numpy(), refs[0])
+
+
+# Automatic padding (section 2: a panel count the transforms do not take is met
+# by extending the domain by a few panels, h unchanged)
+PADDED = [
+    ("3d_41x50x37", w.Problem("p1", (41, 50, 37), (-1.0, -1.2, -0.9), (1.0, 1.25, 0.9), "bump",
+                              dict(centre=(0.05, 0.0, 0.02), eps=0.6, p=10))),
+    ("2d_70x45", w.Problem("p2", (70, 45), (-1.0, -0.7), (1.2, 0.7), "bump",
+                           dict(centre=(0.1, 0.0), eps=0.55, p=8))),
+    ("1d_100", w.Problem("p3", (100,), (-1.0,), (1.0,), "bump", dict(centre=(0.1,), eps=0.6, p=10))),
+    ("3d_20x129x33", w.Problem("p4", (20, 129, 33), (0.0, 0.0, 0.0), (0.6, 4.0, 1.0), "gauss",
+                               dict(seed=17))),
+]
+SUPPORTED = (16, 32, 48, 64, 96, 128, 192, 256, 384, 512)
+
+
+def _embed(rho, n_solved, off):
+    """The padded rho the library builds: the caller's interior values at their
+    nodes of the larger grid, zero elsewhere."""
+    out = np.zeros(n_solved)
+    inner = tuple(slice(1, k - 1) for k in rho.shape)
+    dst = tuple(slice(o + 1, o + k - 1) for o, k in zip(off, rho.shape))
+    out[dst] = rho[inner]
+    return out
+
+
+def _restrict(phi, n, off):
+    return phi[tuple(slice(o, o + k) for o, k in zip(off, n))]
+
+
+@pytest.mark.parametrize("name,prob", PADDED, ids=[c[0] for c in PADDED])
+def test_padded_plan_matches_the_oracle_on_the_padded_grid(idp, name, prob):
+    rho = prob.rho()
+    plan = idp.create_plan(prob.d, prob.n, prob.h, 6)
+    n_solved, off = idp.plan_grid(plan)
+    for k, m, o in zip(prob.n, n_solved, off):
+        M = k - 1
+        assert m - 1 == min(s for s in SUPPORTED if s >= M) and o == (m - 1 - M) // 2
+    assert idp.plan_info(plan)["nodes"] == int(np.prod(prob.n))
+    out = to_dev(np.zeros(prob.n))
+    idp.solve(plan, to_dev(rho), out)
+    idp.plan_status(plan)
+    ref = _restrict(osolve.solve(_embed(rho, n_solved, off), prob.h, 6,
+                                 boundary="convolution" if prob.d > 1 else "direct"), prob.n, off)
+    assert rel_max(out.cpu().numpy(), ref) < TOL
+    # the caller's boundary entries of rho are not used, as in an unpadded solve
+    rho_b = rho.copy()
+    for s in range(prob.d):
+        idx = [slice(None)] * prob.d
+        idx[s] = 0
+        rho_b[tuple(idx)] = 5.0
+    out_b = to_dev(np.zeros(prob.n))
+    idp.solve(plan, to_dev(rho_b), out_b)
+    idp.plan_status(plan)
+    assert np.array_equal(out_b.cpu().numpy(), out.cpu().numpy())
+    # full solves only
+    with pytest.raises(idp.IdpError) as e:
+        run_stage(idp, plan, idp.IDP_STAGE_BOUNDARY, to_dev(rho), prob.n)
+    assert e.value.code == idp.IDP_ESUPPORT
+
+
+@pytest.mark.parametrize("name,prob", PADDED[:3], ids=[c[0] for c in PADDED[:3]])
+def test_padded_solve_is_as_accurate_as_the_unpadded_method(idp, name, prob):
+    # against the exact free-space potential of the bump: the padded GPU solve
+    # and the oracle on the caller's own (unpadded) grid have errors of the same size
+    from oracle import closed_form
+    from tests.test_oracle_full import _bump_potential_1d
+    rho = prob.rho()
+    if prob.d == 1:
+        ex = _bump_potential_1d(prob.coords()[0], prob.params["centre"][0], prob.params["eps"], prob.params["p"])
+    else:
+        ex = closed_form.bump_potential_on_grid(prob)
+    plan = idp.create_plan(prob.d, prob.n, prob.h, 6)
+    out = to_dev(np.zeros(prob.n))
+    idp.solve(plan, to_dev(rho), out)
+    idp.plan_status(plan)
+    err_pad = rel_max(out.cpu().numpy(), ex)
+    err_own = rel_max(osolve.solve(rho, prob.h, 6, boundary="convolution" if prob.d > 1 else "direct"), ex)
+    print("padding", name, err_pad, err_own)
+    assert err_pad < 3 * err_own + 1e-13
+
+
+def test_padded_host_and_batched_give_the_device_bits(idp):
+    import torch
+    probs = [PADDED[0][1], w.c2_3d(33), PADDED[2][1]]
+    plans = [idp.create_plan(p.d, p.n, p.h, 6) for p in probs]
+    rhos = [to_dev(p.rho()) for p in probs]
+    refs = []
+    for pl, r, pr in zip(plans, rhos, probs):
+        o = to_dev(np.zeros(pr.n))
+        idp.solve(pl, r, o)
+        idp.plan_status(pl)
+        refs.append(o.cpu().numpy())
+    outs = [to_dev(np.zeros(p.n)) for p in probs]
+    idp.solve_batched(plans, rhos, outs)
+    torch.cuda.synchronize()
+    for pl in plans:
+        idp.plan_status(pl)
+    for o, ref in zip(outs, refs):
+        assert np.array_equal(o.cpu().numpy(), ref)
+    for k in (0, 2):
+        rho_p = torch.from_numpy(probs[k].rho()).pin_memory()
+        phi_p = torch.zeros(probs[k].n, dtype=torch.float64).pin_memory()
+        for _ in range(2):
+            phi_p.zero_()
+            idp.solve_host(plans[k], rho_p.data_ptr(), phi_p.data_ptr())
+            idp.plan_status(plans[k])
+            assert np.array_equal(phi_p.numpy(), refs[k])
