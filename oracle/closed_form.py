@@ -37,15 +37,19 @@ def _A(r, eps: float, p: int):
 
 
 def bump_potential_3d(r, eps: float, p: int):
+    # inside the support: -A(r)/r - B(r); outside: -A(eps)/r (the quadrature
+    # runs only where r < eps)
     r = np.asarray(r, dtype=np.float64)
-    rc = np.minimum(r, eps)
-    A = _A(rc, eps, p)
-    u = rc ** 2 / eps ** 2
+    out = np.empty_like(r)
+    inner = r < eps
+    ro = r[~inner]
+    out[~inner] = -float(_A(np.array(eps), eps, p)) / ro
+    ri = r[inner]
+    A = _A(ri, eps, p)
+    u = ri ** 2 / eps ** 2
     B = eps ** 2 * (1.0 - u) ** (p + 1) / (2.0 * (p + 1))
-    with np.errstate(divide="ignore", invalid="ignore"):
-        inside = np.where(rc > 0, -A / np.where(rc > 0, rc, 1.0), 0.0) - B
-        outside = -_A(np.full_like(r, eps), eps, p) / np.where(r > 0, r, 1.0)
-    return np.where(r < eps, inside, outside)
+    out[inner] = np.where(ri > 0, -A / np.where(ri > 0, ri, 1.0), 0.0) - B
+    return out
 
 
 def bump_total_charge(eps: float, p: int, d: int) -> float:
