@@ -116,33 +116,29 @@ __global__ void __launch_bounds__(NTB) dst_pass_kernel(const DstPass a)
     const int nl = min(LB, nv - v0);
     const bool contig = (a.axis == 2);
 
-    // 1. load raw lines into bufB viewed as R[LB][M] (entries 0..N-1)
-    R *raw = reinterpret_cast<R *>(bufB);
+    // 1. load and pre-process in one step: the thread that forms y'_j and
+    //    y'_{M-j} loads x_j and x_{M-j} itself (consecutive threads take
+    //    consecutive j of a contiguous line, or consecutive lines), into bufA
+    //    viewed as R[LB][M] (zf[j] = y'_j); lines past the end give zeros
+    R *zf = reinterpret_cast<R *>(bufA);
     int64_t isu, isv, ise;
     view_strides(a.in, a.axis, isu, isv, ise);
     const int64_t inb = (int64_t)u * isu + (int64_t)v0 * isv;
-    for (int f = threadIdx.x; f < LB * N; f += NT) {
-        int l, e;
-        if (contig) { l = f / N; e = f - l * N; }
-        else { e = f / LB; l = f - e * LB; }
-        R x = A::zero();
-        if (l < nl) x = Io<R>::ld(a.in.p, inb + (int64_t)l * isv + (int64_t)e * ise, a.in_dd);
-        raw[l * M + e] = x;
-    }
-    __syncthreads();
-
-    // 2. pre-processing into bufA viewed as R[LB][M] (zf[j] = y'_j)
-    R *zf = reinterpret_cast<R *>(bufA);
     for (int f = threadIdx.x; f < LB * K; f += NT) {
-        const int l = f / K;
-        const int j = f - l * K;
-        const R *xl = raw + l * M;   // x_i at xl[i-1]
+        int l, j;
+        if (contig) { l = f / K; j = f - l * K; }
+        else { j = f / LB; l = f - j * LB; }
         R *zl = zf + l * M;
+        const int64_t lb = inb + (int64_t)l * isv;   // x_i at element i-1 of the line
         if (j == 0) {
             zl[0] = A::zero();
-            zl[K] = times4_exact(xl[K - 1]);
+            zl[K] = l < nl ? times4_exact(Io<R>::ld(a.in.p, lb + (int64_t)(K - 1) * ise, a.in_dd)) : A::zero();
         } else {
-            const R xa = xl[j - 1], xb = xl[M - j - 1];
+            R xa = A::zero(), xb = A::zero();
+            if (l < nl) {
+                xa = Io<R>::ld(a.in.p, lb + (int64_t)(j - 1) * ise, a.in_dd);
+                xb = Io<R>::ld(a.in.p, lb + (int64_t)(M - j - 1) * ise, a.in_dd);
+            }
             const R s = Tabs<R>::sin2(a, j);
             const R p = A::add(xa, xb), m = A::sub(xa, xb);
             zl[j] = A::fma(s, p, m);

@@ -1283,18 +1283,40 @@ int autotune(idp_plan p)
         // block shape of the full-volume sine passes: the default, 8 lines on 256
         // threads, 8 lines on 128 threads (M = 128), 32 lines (M = 128) or 16
         // lines (M = 256); shapes that do not apply to a length fall back to the
-        // default
-        const View3 none{nullptr, 0, 0, 0};
+        // default.  Timed in whole solves: the transform of rho runs beside the
+        // boundary stages, so what a shape costs depends on what runs next to it
+        // (a shape can win alone and lose in the solve).  The density is a smooth
+        // bump over the middle of the box, zero near the boundary.
+        std::vector<double> hr((size_t)p->nodes, 0.0);
+        for (int i0 = 0; i0 < p->n[0]; ++i0)
+            for (int i1 = 0; i1 < p->n[1]; ++i1)
+                for (int i2 = 0; i2 < p->n[2]; ++i2) {
+                    const int ii[3] = {i0, i1, i2};
+                    double r2 = 0.0;
+                    for (int s = 0; s < 3; ++s)
+                        if (p->act[s]) {
+                            const double t = 2.0 * ii[s] / p->M[s] - 1.0;
+                            r2 += t * t;
+                        }
+                    const double q = 1.0 - r2 / 0.36;
+                    hr[((size_t)i0 * p->n[1] + i1) * p->n[2] + i2] = q > 0.0 ? q * q * q * q : 0.0;
+                }
+        double *trho = nullptr, *tphi = nullptr;
+        cudaError_t e = cudaMalloc(&trho, sizeof(double) * p->nodes);
+        if (e == cudaSuccess) e = cudaMalloc(&tphi, sizeof(double) * p->nodes);
+        if (e == cudaSuccess) e = cudaMemcpy(trho, hr.data(), sizeof(double) * p->nodes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) rc = cuda_fail(e, "autotune buffers");
         const int opts[5] = {0, 8, -8, 32, 16};
         int best = 0;
         float bt = 1e30f;
         for (int i = 0; i < 5 && !rc; ++i) {
             p->dst_lines = opts[i];
-            const float t = timed([&]() -> int {
-                return transform(p, dense(p, p->C), p->C, dense(p, p->C), nullptr, none, false, st);
-            });
+            const float t = timed([&]() -> int { return enqueue_grid(p, trho, tphi, 0, st); });
             if (t < bt) { bt = t; best = opts[i]; }
         }
+        cudaStreamSynchronize(st);
+        if (trho) cudaFree(trho);
+        if (tphi) cudaFree(tphi);
         p->dst_lines = best;
     }
     if (!rc && tensor_mode(p)) {
