@@ -235,8 +235,11 @@ __device__ __forceinline__ double ld_khat<double>(const FacePass &a, int64_t i) 
 template <>
 __device__ __forceinline__ ddr ld_khat<ddr>(const FacePass &a, int64_t i) { return a.khatd[i]; }
 
+// four blocks per SM (64 registers; at 72, with the fused first pass, three fit
+// and the pass ran 8 % slower; the cap costs a 68-byte spill at L = 256, measured
+// 1 % faster than the unfused kernel)
 template <class R, int L>
-__global__ void __launch_bounds__(NT) face_kernel(const FacePass a)
+__global__ void __launch_bounds__(NT, 4) face_kernel(const FacePass a)
 {
     using A = Ar<R>;
     using Cx = typename A::C;
@@ -260,16 +263,40 @@ __global__ void __launch_bounds__(NT) face_kernel(const FacePass a)
     const Cx *D = reinterpret_cast<const Cx *>(a.D);
     for (int p = p0; p < p1; ++p) {
         if (a.sliceflag && !a.sliceflag[p]) continue;   // slice of zeros: contributes nothing
-        // load TC columns: positions 1..Mb-1 (interior index 0..Mb-2), rest zero
+        // TC columns of the slice: positions 1..Mb-1 (interior index 0..Mb-2), rest zero
         const Cx *Dp = D + (int64_t)p * a.sp + (int64_t)c0 * a.sc;
-        for (int f = threadIdx.x; f < TC * L; f += NT) {
-            const int q = f / TC, t = f - q * TC;
-            Cx x = A::cmake(A::zero(), A::zero());
-            if (q >= 1 && q <= Mb - 1 && t < ncl) x = Dp[(int64_t)(q - 1) * a.sb + (int64_t)t * a.sc];
-            bufA[t * L + q] = x;
+        const Cx *Z;
+        if constexpr ((L & (L - 1)) == 0) {
+            // the load fused with the first radix-4 pass: a thread reads the two
+            // non-zero inputs x_j, x_{j+L/4} of its unit (the upper half is zero)
+            // and writes the unit's four outputs
+            constexpr int Q = L / 4;
+            for (int f = threadIdx.x; f < TC * Q; f += NT) {
+                const int j = f / TC, t = f - j * TC;   // consecutive threads: consecutive columns
+                Cx a0 = A::cmake(A::zero(), A::zero()), a1 = a0;
+                if (t < ncl) {
+                    if (j >= 1) a0 = Dp[(int64_t)(j - 1) * a.sb + (int64_t)t * a.sc];
+                    a1 = Dp[(int64_t)(j + Q - 1) * a.sb + (int64_t)t * a.sc];
+                }
+                const Cx m1 = mul_mi(a1);
+                Cx *y = bufB + t * L + 4 * j;
+                y[0] = A::cadd(a0, a1);
+                y[1] = A::cadd(a0, m1);
+                y[2] = A::csub(a0, a1);
+                y[3] = A::csub(a0, m1);
+            }
+            __syncthreads();
+            Z = cta_fft_t<R, L, TC, NT, false>(bufB, bufA, fwd_tw<R>(a.t), false, -1, 4);
+        } else {
+            for (int f = threadIdx.x; f < TC * L; f += NT) {
+                const int q = f / TC, t = f - q * TC;
+                Cx x = A::cmake(A::zero(), A::zero());
+                if (q >= 1 && q <= Mb - 1 && t < ncl) x = Dp[(int64_t)(q - 1) * a.sb + (int64_t)t * a.sc];
+                bufA[t * L + q] = x;
+            }
+            __syncthreads();
+            Z = cta_fft_t<R, L, TC, NT, false>(bufA, bufB, fwd_tw<R>(a.t), true);
         }
-        __syncthreads();
-        const Cx *Z = cta_fft_t<R, L, TC, NT, false>(bufA, bufB, fwd_tw<R>(a.t), true);
         const int64_t klo = (int64_t)p * kstride + c0;
         const int64_t khi = (int64_t)(a.np - 1 - p) * kstride + c0;
 #pragma unroll

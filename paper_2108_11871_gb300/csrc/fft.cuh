@@ -29,18 +29,19 @@ __device__ __forceinline__ void fft_sync()
 // half of every input line is known to be zero (saves the first stage).
 // The NT threads that share X and Y call it with tid = 0..NT-1: the whole block
 // (WARP = false; ends with __syncthreads()) or one warp (WARP = true, NT = 32;
-// ends with __syncwarp()).
+// ends with __syncwarp()).  ns0 > 1 (powers of two only): X already holds the
+// result of the stages up to span ns0 (the caller fused them into its load).
 template <class R, int L, int LB, int NT, bool INV, bool WARP = false>
 __device__ __forceinline__ typename Ar<R>::C *cta_fft_t(typename Ar<R>::C *X, typename Ar<R>::C *Y,
                                                         const typename Ar<R>::T *__restrict__ tw, bool zero_half,
-                                                        int tid = -1)
+                                                        int tid = -1, int ns0 = 1)
 {
     if (tid < 0) tid = threadIdx.x;
     using C = typename Ar<R>::C;
     constexpr int H = L / 2;
     constexpr bool P2 = (L & (L - 1)) == 0;
-    int first = 1;
-    if (!P2) {
+    int first = ns0;
+    if (!P2 && ns0 == 1) {
         // radix-3 stage (lengths 3 * 2^m): y[3j + r] = sum_q x[j + q L/3] w3^{qr}
         constexpr int T = L / 3;
         for (int b = tid; b < LB * T; b += NT) {
