@@ -47,6 +47,13 @@ def parse():
                          "sweep_long: Gaussian sum on [0,1]^3 with (n-2)^3 / (1.5(n-1)-1)x(n-2)^2 interior nodes")
     ap.add_argument("--order", type=int, default=6)
     ap.add_argument("--fp64-only", action="store_true", help="skip the mixed-precision variant")
+    ap.add_argument("--dst-shape", type=int, default=None, choices=[0, 8, -8, 32, 16],
+                    help="block shape of the FP64 sine passes (IDP_KEY_DST_SHAPE) instead of the "
+                         "autotuner's: profiled runs, whose timings the profiler perturbs, then run "
+                         "the shape of the plain run")
+    ap.add_argument("--profile-window", type=int, default=0,
+                    help="after the timed steps, run this many more FP64 solves between "
+                         "cudaProfilerStart and cudaProfilerStop (for ncu --profile-from-start off)")
     ap.add_argument("--batched", action="store_true",
                     help="the 96-problem batched workload (uneven sizes) instead of the 129^3 solve")
     return ap.parse_args()
@@ -214,6 +221,8 @@ def run_ours(args, rank, world):
     prob = workload(args.workload, args.n)
     plan = idp.create_plan(3, prob.n, prob.h, args.order)
     idp.plan_set(plan, idp.IDP_KEY_AUTOTUNE, 1)
+    if args.dst_shape is not None:
+        idp.plan_set(plan, idp.IDP_KEY_DST_SHAPE, args.dst_shape)
     rho_h = prob.rho()
     rho = torch.from_numpy(rho_h).to(dev)
     phi = torch.empty_like(rho)
@@ -272,6 +281,16 @@ def run_ours(args, rank, world):
     dst_ms = statistics.mean(per_kind[1])
     achieved = dst_flops_per_launch(prob) / (dst_ms / 1e3) / 1e12
 
+    if args.profile_window > 0:
+        # a window of plain solves for a profiler that starts collecting here
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStart()
+        for i in range(args.profile_window):
+            flush.fill_(float(i))
+            idp.solve(plan, rho, phi, stream)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStop()
+
     # end to end through the host-buffer entry point (pinned host memory)
     rho_pin = torch.from_numpy(rho_h).pin_memory()
     phi_pin = torch.empty_like(rho_pin).pin_memory()
@@ -316,20 +335,20 @@ def run_ours(args, rank, world):
                                                 ctypes.c_void_p(stream.cuda_stream), cap, kinds, ms)
             for j in range(max(n, 0)):
                 mk.setdefault(names.get(kinds[j], str(kinds[j])), []).append(ms[j])
-        return {"variant": label,
+        return phi_m, {"variant": label,
                 "tuning": idp.plan_tuning(mplan),
                 "value": world * prob.points * args.steps / (t_m / 1e3), "unit": UNIT,
                 "ms_per_step": t_m / args.steps, "max_rel_error_vs_fp64": diff,
                 "kernel_ms_per_step": {k: sum(v) / 3 for k, v in mk.items()},
                 "mixed_pass_avg_ms": statistics.mean(mk["mixed_pass"]) if "mixed_pass" in mk else None}
 
-    mixed = mixed_tf32 = None
+    mixed = mixed_tf32 = phi_m = phi_t = None
     if not args.fp64_only:
-        mixed = tensor_variant(idp.IDP_PRECISION_MIXED_BF16X3,
-                               "bf16x3 pieces, fp32 accumulate, tcgen05 (rho, R and final transforms)")
-        mixed_tf32 = tensor_variant(idp.IDP_PRECISION_MIXED_TF32X3,
-                                    "tf32x3: two tf32 pieces, products hi*hi + hi*lo + lo*hi, fp32 accumulate, "
-                                    "tcgen05 kind::tf32 (rho, R and final transforms)")
+        phi_m, mixed = tensor_variant(idp.IDP_PRECISION_MIXED_BF16X3,
+                                      "bf16x3 pieces, fp32 accumulate, tcgen05 (rho, R and final transforms)")
+        phi_t, mixed_tf32 = tensor_variant(idp.IDP_PRECISION_MIXED_TF32X3,
+                                           "tf32x3: two tf32 pieces, products hi*hi + hi*lo + lo*hi, fp32 "
+                                           "accumulate, tcgen05 kind::tf32 (rho, R and final transforms)")
 
     # double-float variant (FFT butterflies on the FP32 pipe, FP64-level accuracy)
     df32 = None
@@ -390,6 +409,8 @@ def run_ours(args, rank, world):
         variants = []
         if mixed is not None:
             variants.append((mixed, phi_m))
+        if mixed_tf32 is not None:
+            variants.append((mixed_tf32, phi_t))
         if df32 is not None:
             variants.append((df32, phi_d))
         for rec, ph in variants:
@@ -413,9 +434,11 @@ def run_ours(args, rank, world):
                          "frac": achieved / FP64_PEAK_TFLOPS,
                          "peak_note": "FP64 derived: 152 SMs x 4 flop/clk x 2.07 GHz; "
                                       "FMA-chain probe measured %.3f" % FP64_PROBE_TFLOPS,
-                         # DRAM bytes (read + write) of one full-volume launch of this kernel,
-                         # from an ncu capture at 129^3 (the input volume once; the output stays in L2)
-                         "traffic": 16408064 if prob.n == (129, 129, 129) else None, "avg_launch_ms": dst_ms,
+                         # DRAM bytes (read + write) of one full-volume launch of this kernel
+                         # (dense in, dense out), from an ncu capture at 129^3: the input volume
+                         # once, the output stays in L2.  The first pass of the transform of rho
+                         # reads the interleaved T0 instead (35.9 MB)
+                         "traffic": 16410624 if prob.n == (129, 129, 129) else None, "avg_launch_ms": dst_ms,
                          "flops_per_launch": dst_flops_per_launch(prob)},
             "kernel_ms_per_step": shares, "dominant_kernel": names[dom], "tuning": idp.plan_tuning(plan),
             "clocks": clk.summary()}
