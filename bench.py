@@ -274,7 +274,7 @@ def run_ours(args, rank, world):
             per_kind.setdefault(kinds[j], []).append(ms[j])
     names = {1: "dst_pass", 2: "rfft", 3: "face", 4: "face_invb", 5: "face_c2r", 6: "gtilde_layers",
              7: "rhs6_w", 8: "rhs6_core", 9: "rhs6_extrap", 10: "gtilde_expand", 11: "dst_pass_layers", 12: "mixed_pass",
-             13: "support_flags", 14: "rhs6_expand", 15: "line1d", 16: "pad"}
+             13: "support_flags", 14: "rhs6_expand", 15: "line1d", 16: "pad", 17: "validate"}
     prof_steps = max(3, min(args.steps, 10))
     shares = {names[k]: sum(v) / prof_steps for k, v in per_kind.items()}
     dom = max(per_kind, key=lambda k: sum(per_kind[k]))

@@ -71,10 +71,18 @@ enum {
                                -8 = 8 lines on 128 threads (M = 128 only), 32 = 32 lines (M = 128
                                only), 16 = 16 lines (M = 256 only); a shape that does not apply
                                to a length falls back to 0 */
-    IDP_KEY_STALL_TEST = 3  /* test hook for failure handling (mixed precision only): the next
+    IDP_KEY_STALL_TEST = 3, /* test hook for failure handling (mixed precision only): the next
                                tensor-core pass issues no products, so its bounded wait expires
                                (after ~5 ms); the kernel records the failure, frees its tensor
                                memory and returns, and idp_plan_status reports IDP_ETIMEOUT */
+    IDP_KEY_VALIDATE = 6    /* validation mode, value k >= 0 (0, the default: off).  Every solve
+                               or stage first checks the caller's rho on the device: a NaN or
+                               infinite value anywhere makes the next idp_plan_status return
+                               IDP_EINVAL; a non-zero value on a node within k layers of the
+                               boundary (some index i_s with 0 < i_s < k or M_s - k < i_s < M_s;
+                               section 2 assumes rho vanishes near the boundary) makes it return
+                               IDP_ESUPPORT (checked first: IDP_EINVAL).  The solve itself still
+                               runs; its output is then not to be used.  Costs one read of rho. */
 };
 
 /* values of IDP_KEY_PRECISION */
@@ -158,9 +166,11 @@ int idp_solve_batched(int count, const idp_plan plans[], const double *const rho
 int idp_solve_stage(idp_plan plan, int stage, const double *rho, double *out, void *stream);
 
 /* Device-side status of the plan's last queued work: IDP_OK, IDP_ECUDA if a
- * launch or asynchronous error was recorded, or IDP_ETIMEOUT if a bounded
- * device-side wait gave up (reported once; the outputs of that solve are
- * invalid, the plan stays usable).  Synchronises the plan's last stream. */
+ * launch or asynchronous error was recorded, IDP_ETIMEOUT if a bounded
+ * device-side wait gave up, or (validation mode, IDP_KEY_VALIDATE) IDP_EINVAL /
+ * IDP_ESUPPORT if a rho checked since the last call failed the check (each
+ * reported once; the outputs of that solve are invalid, the plan stays usable).
+ * Synchronises the plan's last stream. */
 int idp_plan_status(idp_plan plan);
 
 /* kernel families reported by idp_profile_solve */
@@ -181,7 +191,8 @@ enum {
                                     stage-1 pass along axis 2, timed under IDP_KERNEL_RFFT) */
     IDP_KERNEL_RHS6_EXPAND = 14, /* sine transform of the 6th-order layer correction from its layer transforms */
     IDP_KERNEL_LINE1D = 15,      /* d = 1: g at the two ends and the straight-line correction (section 5) */
-    IDP_KERNEL_PAD = 16          /* padded plans: rho into the padded grid, phi back to the caller's nodes */
+    IDP_KERNEL_PAD = 16,         /* padded plans: rho into the padded grid, phi back to the caller's nodes */
+    IDP_KERNEL_VALIDATE = 17     /* validation mode (IDP_KEY_VALIDATE): the check of rho */
 };
 
 /* Run one solve (as idp_solve, but with plain launches, all on `stream`, none

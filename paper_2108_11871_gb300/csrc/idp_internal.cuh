@@ -272,6 +272,11 @@ cudaError_t launch_rhs6_symbol(const Grid3 &g, const double *ld, int64_t off1, i
 // grid and a padded grid
 cudaError_t launch_box_copy(const double *src, int64_t s0, int64_t s1, double *dst, int64_t d0, int64_t d1,
                             int e0, int e1, int e2, cudaStream_t st);
+// Validation of rho (node array n0 x n1 x n2, inactive axes of extent 1): bit 1
+// of *word for a NaN or infinite value on an interior node, bit 2 for a non-zero
+// value on an interior node within k layers of the boundary (of an active axis)
+cudaError_t launch_validate_rho(const double *rho, int n0, int n1, int n2, int act0, int act1, int act2, int k,
+                                int *word, cudaStream_t st);
 cudaError_t launch_rhs6_e_scatter(const Grid3 &g, const double *E0, const double *E1, const double *E2,
                                   double *out, cudaStream_t st);
 

@@ -187,6 +187,8 @@ struct idp_plan_s {
     std::map<int, void *> mp_img;     // by M: BF16 pieces of the sine matrix
     float *t32[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [stream][ping/pong]
     int *d_err = nullptr;
+    int validate = 0;                 // IDP_KEY_VALIDATE: margin k (0: off)
+    int *d_val = nullptr;             // validation word (bit 1: NaN/inf, bit 2: support too close)
 
     // per-launch timing (idp_profile_solve)
     int profiling = 0;
@@ -868,6 +870,23 @@ int enqueue_padded(idp_plan p, const double *rho, double *phi, int stop, cudaStr
 
 int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t st)
 {
+    if (p->validate) {
+        // validation mode: the caller's rho is checked first (in a host-buffer
+        // solve it goes up in one copy, and the check reads the copy)
+        const double *hio = p->hio_rho;
+        if (hio) {
+            IDP_CK(cudaMemcpyAsync(p->h_rho, hio, sizeof(double) * p->unodes, cudaMemcpyHostToDevice, st));
+            p->hio_rho = nullptr;
+        }
+        {
+            Mark mk(p, IDP_KERNEL_VALIDATE, st);
+            IDP_CK(launch_validate_rho(rho, p->un[0], p->un[1], p->un[2], p->act[0], p->act[1], p->act[2],
+                                       p->validate, p->d_val, st));
+        }
+        const int rc = p->padded ? enqueue_padded(p, rho, phi, stop, st) : enqueue_grid(p, rho, phi, stop, st);
+        p->hio_rho = hio;
+        return rc;
+    }
     if (p->padded) return enqueue_padded(p, rho, phi, stop, st);
     return enqueue_grid(p, rho, phi, stop, st);
 }
@@ -1509,6 +1528,21 @@ int idp_plan_set(idp_plan p, int key, int64_t value)
         }
         return IDP_OK;
     }
+    if (key == IDP_KEY_VALIDATE) {
+        if (value < 0 || value > 1 << 20) return IDP_EINVAL;
+        if (value && !p->d_val) {
+            int rc;
+            if ((rc = p->alloc(&p->d_val, 1))) return rc;
+            IDP_CK(cudaMemset(p->d_val, 0, sizeof(int)));
+        }
+        p->validate = (int)value;
+        ++p->version;
+        if (p->gexec) {
+            cudaGraphExecDestroy(p->gexec);
+            p->gexec = nullptr;
+        }
+        return IDP_OK;
+    }
     if (key == IDP_KEY_STALL_TEST) {
         if (!tensor_mode(p)) return IDP_EINVAL;
         p->stall_test = value ? 1 : 0;
@@ -1687,6 +1721,14 @@ int idp_plan_status(idp_plan p)
     if (!p) return IDP_EINVAL;
     if (p->last_valid) IDP_CK(cudaStreamSynchronize(p->last));
     IDP_CK(cudaGetLastError());
+    if (p->d_val) {
+        int v = 0;
+        IDP_CK(cudaMemcpy(&v, p->d_val, sizeof(int), cudaMemcpyDeviceToHost));
+        if (v) {
+            IDP_CK(cudaMemset(p->d_val, 0, sizeof(int)));   // reported once
+            return (v & 1) ? IDP_EINVAL : IDP_ESUPPORT;
+        }
+    }
     if (p->d_err) {
         int e = 0;
         IDP_CK(cudaMemcpy(&e, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));

@@ -869,6 +869,33 @@ __global__ void box_copy_kernel(const double *__restrict__ src, int64_t s0, int6
     }
 }
 
+__global__ void validate_rho_kernel(const double *__restrict__ rho, int n0, int n1, int n2, int act0, int act1,
+                                    int act2, int k, int *word)
+{
+    const int64_t total = (int64_t)n0 * n1 * n2;
+    int bits = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = i / n2;
+        const int i2 = (int)(i - row * n2);
+        const int i0 = (int)(row / n1), i1 = (int)(row - (int64_t)i0 * n1);
+        // interior nodes only (the boundary entries of rho are not used)
+        const bool b0 = act0 && (i0 == 0 || i0 == n0 - 1), b1 = act1 && (i1 == 0 || i1 == n1 - 1),
+                   b2 = act2 && (i2 == 0 || i2 == n2 - 1);
+        if (b0 || b1 || b2) continue;
+        // integer tests on the bits: exponent all ones = NaN or infinity; zero = +-0
+        const long long u = __double_as_longlong(rho[i]);
+        if (((u >> 52) & 0x7ff) == 0x7ff) {
+            bits |= 1;
+        } else if ((u << 1) != 0) {
+            const bool near0 = act0 && (i0 < k || i0 > n0 - 1 - k), near1 = act1 && (i1 < k || i1 > n1 - 1 - k),
+                       near2 = act2 && (i2 < k || i2 > n2 - 1 - k);
+            if (near0 || near1 || near2) bits |= 2;
+        }
+    }
+    if (bits) atomicOr(word, bits);
+}
+
 __global__ void to_dd_kernel(const double *x, ddr *y, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -882,6 +909,14 @@ cudaError_t launch_box_copy(const double *src, int64_t s0, int64_t s1, double *d
     const int64_t total = (int64_t)e0 * e1 * e2;
     if (total <= 0) return cudaSuccess;
     box_copy_kernel<<<grid_for(total), 256, 0, st>>>(src, s0, s1, dst, d0, d1, e0, e1, e2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate_rho(const double *rho, int n0, int n1, int n2, int act0, int act1, int act2, int k,
+                                int *word, cudaStream_t st)
+{
+    validate_rho_kernel<<<grid_for((int64_t)n0 * n1 * n2), 256, 0, st>>>(rho, n0, n1, n2, act0, act1, act2, k,
+                                                                          word);
     return cudaGetLastError();
 }
 

@@ -564,3 +564,68 @@ def test_padded_host_and_batched_give_the_device_bits(idp):
             idp.solve_host(plans[k], rho_p.data_ptr(), phi_p.data_ptr())
             idp.plan_status(plans[k])
             assert np.array_equal(phi_p.numpy(), refs[k])
+
+
+def _status(idp, plan):
+    try:
+        idp.plan_status(plan)
+        return idp.IDP_OK
+    except idp.IdpError as e:
+        return e.code
+
+
+def test_validation_mode_reports_bad_densities(idp):
+    # IDP_KEY_VALIDATE = k: NaN/inf in rho -> IDP_EINVAL, non-zero rho on a node
+    # within k layers of the boundary -> IDP_ESUPPORT, each reported once by
+    # idp_plan_status; the boundary entries of rho are not checked (not used)
+    import torch
+    prob = w.c2_3d(33)
+    rho = prob.rho()
+    plan = idp.create_plan(3, prob.n, prob.h, 6)
+    ref = to_dev(np.zeros(prob.n))
+    idp.solve(plan, to_dev(rho), ref)
+    idp.plan_status(plan)
+    idp.plan_set(plan, idp.IDP_KEY_VALIDATE, 3)
+
+    def run(r, pl=plan, shape=prob.n):
+        out = to_dev(np.zeros(shape))
+        idp.solve(pl, to_dev(r), out)
+        return _status(idp, pl), out
+
+    code, out = run(rho)
+    assert code == idp.IDP_OK and np.array_equal(out.cpu().numpy(), ref.cpu().numpy())
+    near = rho.copy()
+    near[2, 16, 16] = 1.0                       # 2 layers from the face i0 = 0
+    assert run(near)[0] == idp.IDP_ESUPPORT
+    assert _status(idp, plan) == idp.IDP_OK     # reported once
+    far = rho.copy()
+    far[3, 16, 16] = 1.0                        # 3 layers: allowed with k = 3
+    assert run(far)[0] == idp.IDP_OK
+    bad = rho.copy()
+    bad[16, 16, 16] = np.nan
+    assert run(bad)[0] == idp.IDP_EINVAL
+    both = near.copy()
+    both[16, 16, 31] = np.inf
+    assert run(both)[0] == idp.IDP_EINVAL       # NaN/inf is reported first
+    edge = rho.copy()
+    edge[0, 16, 16] = 5.0                       # a boundary entry: not used, not checked
+    assert run(edge)[0] == idp.IDP_OK
+    idp.plan_set(plan, idp.IDP_KEY_VALIDATE, 0)
+    assert run(near)[0] == idp.IDP_OK           # validation off
+    # host buffers, a 2-D, a 1-D and a padded plan check the caller's grid too
+    idp.plan_set(plan, idp.IDP_KEY_VALIDATE, 3)
+    rp = torch.from_numpy(near).pin_memory()
+    pp = torch.zeros(prob.n, dtype=torch.float64).pin_memory()
+    idp.solve_host(plan, rp.data_ptr(), pp.data_ptr())
+    assert _status(idp, plan) == idp.IDP_ESUPPORT
+    for n in ((33, 65), (129,), (41, 50, 37)):
+        p2 = w.random_interior(n, seed=5, margin=4)
+        pl = idp.create_plan(len(n), n, (0.01,) * len(n), 6)
+        idp.plan_set(pl, idp.IDP_KEY_VALIDATE, 4)
+        assert run(p2, pl, n)[0] == idp.IDP_OK
+        q = p2.copy()
+        q[(1,) * len(n)] = 0.5                  # the corner-most interior node
+        assert run(q, pl, n)[0] == idp.IDP_ESUPPORT
+    with pytest.raises(idp.IdpError) as e:
+        idp.plan_set(plan, idp.IDP_KEY_VALIDATE, -1)
+    assert e.value.code == idp.IDP_EINVAL
