@@ -54,7 +54,8 @@ enum {
     IDP_EALIAS = -4,     /* rho and phi overlap */
     IDP_ESUPPORT = -5,   /* size or option outside the supported set */
     IDP_ESCRATCH = -6,   /* problem larger than the fixed scratch of idp_rhs6_noalloc */
-    IDP_ETIMEOUT = -7    /* a device-side wait exceeded its iteration limit */
+    IDP_ETIMEOUT = -7,   /* a device-side wait exceeded its iteration limit */
+    IDP_EGUARD = -8      /* a guard region around a workspace buffer was overwritten (idp_plan_check_guards) */
 };
 
 /* keys for idp_plan_set */
@@ -216,6 +217,13 @@ int idp_plan_launches(idp_plan plan, int64_t *launches);
 /* Query the plan: node count of the caller's arrays, interior count of the grid
  * solved on, and device workspace bytes. */
 int idp_plan_info(idp_plan plan, int64_t *nodes, int64_t *interior, int64_t *workspace_bytes);
+
+/* Check the guard regions around every device buffer the plan allocated (256
+ * bytes on each side, filled with a fixed byte at allocation): IDP_OK if all are
+ * intact, IDP_EGUARD if a kernel wrote past the start or end of a buffer.  A
+ * check for tests in place of a memory checker; synchronises the device and reads
+ * back 512 bytes per buffer.  The paper has no counterpart. */
+int idp_plan_check_guards(idp_plan plan);
 
 /* The grid a plan solves on (section 2: a panel count the transforms do not
  * take is met by extending the domain by a few panels): n_solved[d] node counts

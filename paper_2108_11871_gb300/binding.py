@@ -13,6 +13,7 @@ import numpy as np
 from . import build as _build
 
 IDP_OK, IDP_EINVAL, IDP_ENOMEM, IDP_ECUDA, IDP_EALIAS, IDP_ESUPPORT, IDP_ESCRATCH = 0, -1, -2, -3, -4, -5, -6
+IDP_EGUARD = -8
 IDP_RHS6_NOALLOC_MAX_NODES = 524288
 IDP_KEY_USE_GRAPH = 1
 IDP_KEY_PRECISION = 2
@@ -67,6 +68,7 @@ def library(path: str = None):
         "idp_profile_solve": (_int, [_vp, _vp, _vp, _vp, _int, ctypes.POINTER(_int), ctypes.POINTER(ctypes.c_float)]),
         "idp_plan_launches": (_int, [_vp, ctypes.POINTER(_i64)]),
         "idp_plan_grid": (_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+        "idp_plan_check_guards": (_int, [_vp]),
         "idp_rhs6_noalloc": (_int, [_int, ctypes.POINTER(_i64), ctypes.POINTER(_dbl), _vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
@@ -174,6 +176,11 @@ def plan_info(plan: Plan):
     _check(library().idp_plan_info(plan.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
            "idp_plan_info")
     return dict(nodes=a.value, interior=b.value, workspace_bytes=c.value)
+
+
+def plan_check_guards(plan: Plan):
+    """Raise IdpError(IDP_EGUARD) if a kernel wrote outside one of the plan's buffers."""
+    _check(library().idp_plan_check_guards(plan.handle), "idp_plan_check_guards")
 
 
 def plan_grid(plan: Plan):

@@ -157,6 +157,9 @@ struct idp_plan_s {
     std::map<int, double *> sin2;     // by M: 2 sin(pi j / M), j = 0..M/2
     std::map<int, ddr *> sin2d;       // double-float form
     std::vector<void *> allocs;
+    static constexpr size_t GUARD = 256;              // keeps the buffers 256-byte aligned
+    static constexpr unsigned char GUARD_BYTE = 0xA5;
+    std::vector<std::pair<char *, size_t>> guarded;   // allocation base, payload bytes
     int64_t bytes = 0;
 
     double *A = nullptr, *B = nullptr, *C = nullptr, *U = nullptr, *W = nullptr;
@@ -228,16 +231,25 @@ struct idp_plan_s {
     template <class T>
     int alloc(T **p, int64_t count)
     {
+        // every buffer sits between two guard regions of GUARD bytes filled with
+        // GUARD_BYTE; idp_plan_check_guards reports one that was overwritten (an
+        // out-of-bounds write), in place of a memory checker
         void *q = nullptr;
         const size_t b = (size_t)count * sizeof(T);
-        cudaError_t e = cudaMalloc(&q, b > 0 ? b : 16);
+        const size_t payload = b > 0 ? b : 16;
+        cudaError_t e = cudaMalloc(&q, payload + 2 * GUARD);
         if (e != cudaSuccess) {
             cuda_fail(e, "cudaMalloc");
             return IDP_ENOMEM;
         }
+        char *c = static_cast<char *>(q);
+        e = cudaMemset(c, GUARD_BYTE, GUARD);
+        if (e == cudaSuccess) e = cudaMemset(c + GUARD + payload, GUARD_BYTE, GUARD);
         allocs.push_back(q);
+        guarded.emplace_back(c, payload);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemset (guards)");
         bytes += (int64_t)b;
-        *p = (T *)q;
+        *p = (T *)(c + GUARD);
         return IDP_OK;
     }
 };
@@ -1770,6 +1782,22 @@ int idp_profile_solve(idp_plan p, const double *rho, double *phi, void *stream, 
     return n;
 }
 
+int idp_plan_check_guards(idp_plan p)
+{
+    if (!p) return IDP_EINVAL;
+    IDP_CK(cudaDeviceSynchronize());
+    std::vector<unsigned char> h(idp_plan_s::GUARD);
+    for (const auto &g : p->guarded) {
+        for (int side = 0; side < 2; ++side) {
+            const char *src = side ? g.first + idp_plan_s::GUARD + g.second : g.first;
+            IDP_CK(cudaMemcpy(h.data(), src, idp_plan_s::GUARD, cudaMemcpyDeviceToHost));
+            for (unsigned char v : h)
+                if (v != idp_plan_s::GUARD_BYTE) return IDP_EGUARD;
+        }
+    }
+    return IDP_OK;
+}
+
 int idp_plan_grid(idp_plan p, int64_t n_solved[], int64_t offset[])
 {
     if (!p || !n_solved || !offset) return IDP_EINVAL;
@@ -1827,6 +1855,7 @@ const char *idp_strerror(int code)
     case IDP_EALIAS: return "input and output overlap";
     case IDP_ESUPPORT: return "size or option not supported (panel counts must be 2^a in [16, 512] or 3*2^a in [48, 384])";
     case IDP_ETIMEOUT: return "a device-side wait exceeded its iteration limit";
+    case IDP_EGUARD: return "a guard region around a workspace buffer was overwritten";
     case IDP_ESCRATCH: return "problem larger than the fixed scratch of idp_rhs6_noalloc (524288 nodes)";
     default: return "unknown error";
     }
