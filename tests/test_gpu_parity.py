@@ -124,13 +124,15 @@ def test_single_sine_transform_pass_against_library_dst(idp):
 
 @pytest.mark.parametrize("precision", ["fp64", "df32"])
 def test_129_cube_sampled_against_direct_sum_and_full_oracle(idp, precision):
-    # the bench workload (129^3 bump, order 6): g at sampled boundary nodes
-    # against the direct trapezoid sum, and phi against the oracle everywhere
+    # the bench workload (129^3 bump, order 6) in the bench's configuration
+    # (autotuned plan, graph replay): g at sampled boundary nodes against the
+    # direct trapezoid sum, and phi against the oracle everywhere
     prob = w.c2_3d(129)
     rho = prob.rho()
     plan = idp.create_plan(3, prob.n, prob.h, 6)
     if precision == "df32":
         idp.plan_set(plan, idp.IDP_KEY_PRECISION, idp.IDP_PRECISION_DF32)
+    idp.plan_set(plan, idp.IDP_KEY_AUTOTUNE, 1)
     r = to_dev(rho)
     g = run_stage(idp, plan, idp.IDP_STAGE_BOUNDARY, r, prob.n)
     idx = ogreens.boundary_indices(prob.n)
