@@ -631,3 +631,45 @@ def test_validation_mode_reports_bad_densities(idp):
     with pytest.raises(idp.IdpError) as e:
         idp.plan_set(plan, idp.IDP_KEY_VALIDATE, -1)
     assert e.value.code == idp.IDP_EINVAL
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_zero_and_single_point_densities(idp, d):
+    # the degenerate inputs: rho = 0 gives phi = 0 exactly (every line and slice is
+    # skipped), and a single non-zero node (one line, one slice per axis) matches
+    # the oracle; values on the boundary entries of rho are not used
+    n = (33, 17, 49)[:d] if d == 3 else (33, 49)
+    h = (0.05, 0.07, 0.03)[:d]
+    plan = idp.create_plan(d, n, h, 6)
+    out = to_dev(np.full(n, 3.0))
+    idp.solve(plan, to_dev(np.zeros(n)), out)
+    idp.plan_status(plan)
+    assert np.all(out.cpu().numpy() == 0)
+    rho = np.zeros(n)
+    rho[tuple(k // 2 for k in n)] = 1.0
+    rho[(0,) * d] = 7.0                       # a boundary entry: ignored
+    out = to_dev(np.zeros(n))
+    idp.solve(plan, to_dev(rho), out)
+    idp.plan_status(plan)
+    rho0 = rho.copy()
+    rho0[(0,) * d] = 0.0
+    ref = osolve.solve(rho0, h, 6, boundary="convolution")
+    assert rel_max(out.cpu().numpy(), ref) < TOL
+
+
+@pytest.mark.parametrize("n", [(3,), (3, 3), (3, 3, 3), (3, 18, 5)])
+def test_smallest_grids(idp, n):
+    # n = 3 nodes per axis (one interior node): padded to 16 panels (section 2),
+    # phi at the caller's nodes equals the oracle's on the padded grid
+    d = len(n)
+    h = (0.1, 0.13, 0.07)[:d]
+    rho = np.zeros(n)
+    rho[tuple(1 if k == 3 else k // 2 for k in n)] = 1.0
+    plan = idp.create_plan(d, n, h, 6)
+    n_solved, off = idp.plan_grid(plan)
+    out = to_dev(np.zeros(n))
+    idp.solve(plan, to_dev(rho), out)
+    idp.plan_status(plan)
+    ref = _restrict(osolve.solve(_embed(rho, n_solved, off), h, 6,
+                                 boundary="convolution" if d > 1 else "direct"), n, off)
+    assert rel_max(out.cpu().numpy(), ref) < TOL
