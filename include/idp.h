@@ -1,7 +1,7 @@
 /*
  * idp.h -- C ABI of the GB300 infinite-domain Poisson solver.
  *
- * The library evaluates, at every node of a uniform 2-D or 3-D grid, the
+ * The library evaluates, at every node of a uniform 1-D, 2-D or 3-D grid, the
  * convolution of the free-space Green's function of the Laplacian with a
  * density rho whose support lies inside the grid (arXiv 2108.11871, section 1,
  * eqs. GreensFcnIntegral / InfDomainPoisson):
@@ -19,14 +19,17 @@
  *           to the boundary (section 5, eqs. 6thOrderRelation2D/3D).
  *
  * Conventions shared by every entry point
- *   - Grids: d in {2, 3}; n[s] = node count along array axis s INCLUDING the
- *     two boundary nodes (n[s] = M_s + 1, M_s panels); h[s] > 0 is the mesh
- *     width.  Arrays are FP64, C order, last axis contiguous, prod(n) entries.
- *   - Supported sizes: M_s = 2^a with 16 <= M_s <= 512, or M_s = 3 * 2^a with
- *     48 <= M_s <= 384.
+ *   - Grids: d in {1, 2, 3}; n[s] = node count along array axis s INCLUDING
+ *     the two boundary nodes (n[s] = M_s + 1, M_s panels, n[s] >= 3); h[s] > 0
+ *     is the mesh width.  Arrays are FP64, C order, last axis contiguous,
+ *     prod(n) entries.
+ *   - Sizes: the transforms take M_s = 2^a with 16 <= M_s <= 512 or
+ *     M_s = 3 * 2^a with 48 <= M_s <= 384; any other M_s <= 512 is padded to
+ *     the next of these (section 2; see idp_create_plan); M_s > 512 gives
+ *     IDP_ESUPPORT.
  *   - rho is read on interior nodes only; its boundary entries are ignored.
  *     The method assumes rho vanishes near the boundary (section 2); the
- *     library does not check it.
+ *     library checks it only in validation mode (IDP_KEY_VALIDATE).
  *   - Device pointers are CUDA device memory owned by the caller and must
  *     stay valid until the work queued on `stream` has finished.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
@@ -151,9 +154,13 @@ int idp_plan_set(idp_plan plan, int key, int64_t value);
  * doubles; they must not overlap (IDP_EALIAS). */
 int idp_solve(idp_plan plan, const double *rho, double *phi, void *stream);
 
-/* Same as idp_solve with HOST arrays: copies rho to the device, solves, copies
- * phi back and waits for the stream.  The plan allocates its device staging
- * buffers on the first call. */
+/* Same as idp_solve with HOST arrays of prod(n) doubles; waits for the stream
+ * before returning.  Page-locked buffers (cudaHostAlloc / cudaHostRegister)
+ * are read and written by the kernels themselves through their device views
+ * (the first real-FFT pass reads rho and leaves a device copy; the kernels that
+ * produce phi write it), from a CUDA graph of their own keyed by the two
+ * pointers; pageable buffers are copied up and back around the solve.  The plan
+ * allocates its device staging buffers on the first call. */
 int idp_solve_host(idp_plan plan, const double *rho_host, double *phi_host, void *stream);
 
 /* Solve `count` independent problems, plans[i] with rho[i] -> phi[i]
