@@ -185,15 +185,17 @@ __global__ void __launch_bounds__(NTB) dst_pass_kernel(const DstPass a)
 
     // 5. prefix sum over the odd slots o[2k], k = 0..K-1
     if constexpr (std::is_same<R, double>::value) {
-        // four lanes per line, each scanning a quarter of the odd slots: every FP64
+        // eight lanes per line, each scanning an eighth of the odd slots: every FP64
         // warp instruction then has all its lanes busy (an FP64 warp instruction
-        // costs the pipe the same whatever its active lanes).  Per lane: the total
-        // of its quarter, an inclusive scan of the four totals by shuffles, then
-        // the quarter again from the lower quarters' sum.  The summation order is
-        // the same for every block shape.  Requires 4 LB <= threads per block and
-        // whole warps of lines (LB >= 8), or LB = 2 or 4 in part of warp 0.
-        constexpr int S = 4, Cq = K / S;
-        // the scan lanes: whole warps, or the lowest 4 LB lanes of warp 0 (LB = 2, 4)
+        // costs the pipe the same whatever its active lanes), and each lane's chain
+        // of dependent additions is K/4 + 3 long (against K/2 + 2 with four lanes,
+        // measured 2 us per solve faster at 129^3).  Per lane: the total of its
+        // eighth, an inclusive scan of the eight totals by shuffles, then the
+        // eighth again from the lower eighths' sum.  The summation order is the
+        // same for every block shape.  Requires 8 LB <= threads per block and
+        // whole warps of lines (LB >= 4), or LB = 2 in part of warp 0.
+        constexpr int S = 8, Cq = K / S;
+        // the scan lanes: whole warps, or the lowest 8 LB lanes of warp 0 (LB = 2)
         constexpr unsigned SMASK = (S * LB >= 32) ? 0xffffffffu : ((1u << (S * LB)) - 1u);
         const int l = threadIdx.x / S, sg = threadIdx.x - l * S;
         if (l < LB) {
@@ -285,8 +287,8 @@ cudaError_t launch_lb(const DstPass &a, int nu, int nv, cudaStream_t st)
     // (the double-float scan runs on G lanes per line; the FP64 one on four)
     static_assert(std::is_same<R, double>::value || Cfg::G <= 32, "scan group must fit a warp");
     static_assert(Cfg::LB * Cfg::G == NTB, "every thread belongs to one scan group");
-    static_assert(4 * Cfg::LB <= NTB && (Cfg::LB >= 8 || Cfg::LB == 4 || Cfg::LB == 2) && K % 4 == 0,
-                  "four scan lanes per line: whole warps, or part of warp 0");
+    static_assert(8 * Cfg::LB <= NTB && (Cfg::LB >= 8 || Cfg::LB == 4 || Cfg::LB == 2) && K % 8 == 0,
+                  "eight scan lanes per line: whole warps, or part of warp 0");
     const size_t sm = 2 * sizeof(double2) * Cfg::LB * K;
     dim3 grid((nv + Cfg::LB - 1) / Cfg::LB, nu);
     return launch_pdl(dst_pass_kernel<R, K, LBO, NTB>, grid, dim3(NTB), sm, st, a);
