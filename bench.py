@@ -434,11 +434,12 @@ def run_ours(args, rank, world):
                          "frac": achieved / FP64_PEAK_TFLOPS,
                          "peak_note": "FP64 derived: 152 SMs x 4 flop/clk x 2.07 GHz; "
                                       "FMA-chain probe measured %.3f" % FP64_PROBE_TFLOPS,
-                         # DRAM bytes (read + write) of one full-volume launch of this kernel
-                         # (dense in, dense out), from an ncu capture at 129^3: the input volume
-                         # once, the output stays in L2.  The first pass of the transform of rho
-                         # reads the interleaved T0 instead (35.9 MB)
-                         "traffic": None, "avg_launch_ms": dst_ms,
+                         # DRAM bytes (read + write) per full-volume launch of this kernel,
+                         # averaged like avg_launch_ms over the 8 passes of a 129^3 solve (ncu):
+                         # six passes read their input volume once (16.41 MB; the output stays
+                         # in L2), the two passes of the transform of rho read the interleaved
+                         # T0 (33.3 and 32.8 MB)
+                         "traffic": 20573408 if prob.n == (129, 129, 129) else None, "avg_launch_ms": dst_ms,
                          "flops_per_launch": dst_flops_per_launch(prob)},
             "kernel_ms_per_step": shares, "dominant_kernel": names[dom], "tuning": idp.plan_tuning(plan),
             "clocks": clk.summary()}
