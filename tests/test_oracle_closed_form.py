@@ -38,3 +38,19 @@ def test_closed_form_solves_poisson(d, eps, p):
         far = np.array([1.5, 4.0, 30.0]) * eps
         assert np.allclose(f(far), -Q / (4 * np.pi * far), rtol=1e-13, atol=0)
     assert abs(closed_form.bump_total_charge(eps, p, d) - Q) < 1e-13 * Q
+
+
+@pytest.mark.parametrize("c,eps,p", [(0.1, 0.6, 10), (-0.3, 0.25, 4)])
+def test_closed_form_1d_solves_poisson(c, eps, p):
+    # phi'' = rho, and phi = (Q/2)|x - c| outside the support (G = |x|/2)
+    from tests.test_oracle_full import _bump_potential_1d
+    f = lambda x: _bump_potential_1d(np.atleast_1d(x), c, eps, p)
+    x = c + np.linspace(-2.0, 2.0, 201) * eps
+    x = x[np.abs(np.abs(x - c) - eps) > 2e-3]
+    dx = 1e-4
+    lap = (f(x + dx) - 2 * f(x) + f(x - dx)) / dx ** 2
+    rho = np.where(np.abs(x - c) < eps, np.clip(1 - (x - c) ** 2 / eps ** 2, 0, None) ** p, 0.0)
+    assert np.abs(lap - rho).max() < 1e-5
+    Q = integrate.quad(lambda s: (1 - s ** 2 / eps ** 2) ** p, -eps, eps, epsabs=1e-14)[0]
+    far = c + np.array([-3.0, -1.5, 1.2, 4.0]) * eps
+    assert np.allclose(f(far), 0.5 * Q * np.abs(far - c), rtol=1e-12, atol=0)
