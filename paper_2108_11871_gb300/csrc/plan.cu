@@ -338,8 +338,8 @@ int get_sin2(idp_plan p, int M, const double **out)
         s[j] = 2.0 * sinpi_frac(j, M);
         sd[j] = host_dd(s[j]);
     }
-    double *d;
-    ddr *dd;
+    double *d = nullptr;
+    ddr *dd = nullptr;
     int rc;
     if ((rc = p->alloc(&d, M / 2 + 1)) || (rc = p->alloc(&dd, M / 2 + 1))) return rc;
     IDP_CK(cudaMemcpy(d, s.data(), sizeof(double) * (M / 2 + 1), cudaMemcpyHostToDevice));

@@ -45,11 +45,6 @@ __device__ __forceinline__ int face_dist(const Geo &g, int s, int js)
     return g.act[s] ? min(js, g.M[s] - js) : (1 << 20);
 }
 
-__device__ __forceinline__ int min_dist(const Geo &g, const int j[3])
-{
-    return min(face_dist(g, 0, j[0]), min(face_dist(g, 1, j[1]), face_dist(g, 2, j[2])));
-}
-
 // gtilde = -L4(ghat) at interior node i, ghat = U on boundary nodes and 0 inside
 // (eq. harmonic4thOrderNH2D).  L4 weights (host-computed in c): face +-e_s:
 // 1/h_s^2 - 2 sum_r c_sr/(h_s^2 h_r^2); edge +-e_s +-e_r: c_sr/(h_s^2 h_r^2),
@@ -386,9 +381,6 @@ __global__ void rhs6_extrap_kernel(const Grid3 gg, double *R)
 //     E = R_extrap - R_spec there.
 // So S R = Lambda_R (S S b) + S E, and the sine transform of E is assembled
 // from the (d-1)-dimensional transforms of its layers.
-
-// u-weights of the fourth difference
-__device__ __constant__ double kD4[5] = {1.0, -4.0, 6.0, -4.0, 1.0};
 
 // x with its sign flipped when neg (an integer operation: FP64 issue is scarce)
 __device__ __forceinline__ double flip_if(double x, bool neg)
