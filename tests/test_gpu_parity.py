@@ -17,7 +17,7 @@ import numpy as np
 import pytest
 
 import workloads as w
-from oracle import dst as odst, greens as ogreens, harmonic as oharm, solve as osolve
+from oracle import greens as ogreens, solve as osolve
 from tests.gpu_util import device, r_amplification, rel_max, run_stage, to_dev
 
 pytestmark = pytest.mark.gpu

@@ -25,7 +25,6 @@ Densities:
 from __future__ import annotations
 
 import dataclasses
-import math
 from typing import Sequence
 
 import numpy as np
