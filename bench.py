@@ -95,8 +95,17 @@ def config_of(prob, order, extra=None):
 
 # ----------------------------------------------------------------------------- multi-rank helpers
 def shard(items, rank, world):
-    """Problems of rank `rank` (round robin; the batched workload needs no collective)."""
-    return items[rank::world]
+    """Problems of rank `rank`: a size-balanced greedy split (largest problem first,
+    each to the rank with the fewest nodes so far, ties to the lower rank), which
+    every rank computes alike, so the batched workload needs no collective.  The
+    problems keep their order within a rank."""
+    load = [0] * world
+    owner = [0] * len(items)
+    for i in sorted(range(len(items)), key=lambda i: (-items[i].points, i)):
+        r = min(range(world), key=lambda k: (load[k], k))
+        owner[i] = r
+        load[r] += items[i].points
+    return [it for it, o in zip(items, owner) if o == rank]
 
 
 def max_over_ranks(value, world, device=None):

@@ -2,7 +2,7 @@
 
 On the GPU every rank solves its own problems ("replicas only": a single solve
 is not sharded), the job time is the slowest rank's, and the batched workload
-is split round robin with no collective on the data path.
+is split by a size-balanced greedy assignment with no collective on the data path.
 """
 import os
 import socket
@@ -55,3 +55,18 @@ def test_two_gloo_ranks_shard_and_take_the_slowest_time():
     assert not set(names0) & set(names1)
     assert sorted(names0 + names1) == sorted(allnames)
     assert res[0][2] == res[1][2] == 11.0
+
+
+def test_batched_split_is_balanced_and_complete():
+    # every problem on exactly one rank, and the ranks' node counts within a few
+    # per cent of each other (largest-first greedy on the 470x volume spread)
+    import bench
+    import workloads as w
+    probs = w.c5_batch()
+    total = sum(p.points for p in probs)
+    for world in (2, 4, 8):
+        parts = [bench.shard(probs, r, world) for r in range(world)]
+        names = sorted(p.name for part in parts for p in part)
+        assert names == sorted(p.name for p in probs)
+        loads = [sum(p.points for p in part) for part in parts]
+        assert max(loads) <= 1.05 * total / world, (world, loads)
