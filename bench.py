@@ -1,12 +1,17 @@
 """Throughput of the infinite-domain Poisson solve (grid points / s at 6th order).
 
-Workload: the 3-D FP64 6th-order problem of 129^3 nodes on [-1,1]^3 with
-rho = (1 - r^2/0.49)^10 for r < 0.7 around (0.05, 0.1, -0.08) (synthetic,
-seeded, generated on the host, resident in HBM before timing).  One step =
-one complete solve phi = phi* + phi_H (boundary convolutions, three sine
-solves, 6th-order correction) through the C ABI.
+Headline workload (the largest single-GPU configuration): 513^3 nodes on
+[0,2]x[0,1]x[0,1] (anisotropic h), rho = a sum of 6 seeded Gaussians tapered to
+zero near the edges, order 6, FP64.  Inputs are synthetic, generated on the
+host and resident in HBM before timing.  One step = one complete solve
+phi = phi* + phi_H (boundary convolutions, sine solves, 6th-order correction)
+through the C ABI.  The same JSON line also carries the mixed-precision and
+double-float variants of that workload, the 129^3 bump workload, the precision
+sweep at 257^3 with every variant's error against the oracle, the 96-problem
+batched workload, and two CPU baselines.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 129]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload large|bump|sweep|sweep_long] [--n N] [--headline-only]
 
 --impl reference times the CPU oracle on the host cores (the reference arm of
 this comparison: there is no runnable reference implementation, only the
@@ -32,6 +37,14 @@ UNIT = "grid points/s"
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB of L2
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 4 FP64 flop/clk x 2.07 GHz
 FP64_PROBE_TFLOPS = 1.198           # FMA-chain probe on this GPU model, 1995 MHz
+KERNEL_NAMES = {1: "dst_pass", 2: "rfft", 3: "face", 4: "face_invb", 5: "face_c2r", 6: "gtilde_layers",
+                7: "rhs6_w", 8: "rhs6_core", 9: "rhs6_extrap", 10: "gtilde_expand", 11: "dst_pass_layers",
+                12: "mixed_pass", 13: "support_flags", 14: "rhs6_expand", 15: "line1d", 16: "pad",
+                17: "validate"}
+# DRAM bytes (read + write) per full-volume launch of the FP64 sine pass, from ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum over the 8 passes of one solve,
+# averaged); a grid not listed reports null
+DST_TRAFFIC = {}
 
 
 def parse():
@@ -41,12 +54,15 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=None,
-                    help="nodes per axis (default: 129 bump, 513 large, 257 sweep)")
-    ap.add_argument("--workload", default="bump", choices=["bump", "large", "sweep", "sweep_long"],
-                    help="bump: 3-D bump on [-1,1]^3; large: 6-Gaussian sum on [0,2]x[0,1]^2; sweep / "
-                         "sweep_long: Gaussian sum on [0,1]^3 with (n-2)^3 / (1.5(n-1)-1)x(n-2)^2 interior nodes")
+                    help="nodes per axis (default: 513 large, 129 bump, 257 sweep)")
+    ap.add_argument("--workload", default="large", choices=["large", "bump", "sweep", "sweep_long"],
+                    help="large: 6-Gaussian sum on [0,2]x[0,1]^2 (the headline); bump: 3-D bump on "
+                         "[-1,1]^3; sweep / sweep_long: Gaussian sum on [0,1]^3 with (n-2)^3 / "
+                         "(1.5(n-1)-1)x(n-2)^2 interior nodes")
     ap.add_argument("--order", type=int, default=6)
-    ap.add_argument("--fp64-only", action="store_true", help="skip the mixed-precision variant")
+    ap.add_argument("--fp64-only", action="store_true", help="skip the reduced-precision variants")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="skip the 129^3, sweep and batched workloads and the CPU baselines")
     ap.add_argument("--dst-shape", type=int, default=None, choices=[0, 8, -8, 32, 16],
                     help="block shape of the FP64 sine passes (IDP_KEY_DST_SHAPE) instead of the "
                          "autotuner's: profiled runs, whose timings the profiler perturbs, then run "
@@ -55,7 +71,7 @@ def parse():
                     help="after the timed steps, run this many more FP64 solves between "
                          "cudaProfilerStart and cudaProfilerStop (for ncu --profile-from-start off)")
     ap.add_argument("--batched", action="store_true",
-                    help="the 96-problem batched workload (uneven sizes) instead of the 129^3 solve")
+                    help="only the 96-problem batched workload (uneven sizes)")
     return ap.parse_args()
 
 
@@ -87,7 +103,8 @@ def describe(prob, order):
 def config_of(prob, order, extra=None):
     c = {"workload": describe(prob, order),
          "nodes": prob.points, "order": order, "grid": list(prob.n), "h": list(prob.h),
-         "l2": "flushed between timed steps (512 MiB write)"}
+         "l2": "flushed between timed steps (512 MiB write)" + (
+             "; inputs and workspace also exceed L2" if prob.points * 8 > (129 << 20) else "")}
     if extra:
         c.update(extra)
     return c
@@ -169,7 +186,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# ----------------------------------------------------------------------------- oracle timing
+# ----------------------------------------------------------------------------- CPU legs
 def oracle_step(rho, h, order):
     from oracle import solve as osolve
     t = time.perf_counter()
@@ -177,35 +194,66 @@ def oracle_step(rho, h, order):
     return time.perf_counter() - t
 
 
-def cpu_baseline(prob, order, kind, reps=1):
-    """One complete oracle solve of the workload; grids above 129^3 are sampled by
-    the same density family at 129^3 (the oracle's direct sine sums grow as n^4)."""
-    sample = prob if max(prob.n) <= 129 else workload(kind, 129)
+def reference_sample(prob, kind):
+    """The oracle's bounded sample of a workload: the workload itself up to 129^3,
+    else the same density family at 129^3 (the oracle's direct sine sums grow as n^4)."""
+    return prob if max(prob.n) <= 129 else workload(kind, 129)
+
+
+def cpu_baseline(prob, order, kind, budget_s=10.0):
+    """Complete oracle solves of a bounded sample of the workload, repeated for
+    about `budget_s` seconds (at least 2)."""
+    sample = reference_sample(prob, kind)
     rho = sample.rho()
-    ts = [oracle_step(rho, sample.h, order) for _ in range(reps)]
-    t = min(ts)
-    what = "the same" if sample is prob else "a 129^3 sample of the same family as the"
+    ts = [oracle_step(rho, sample.h, order)]
+    while len(ts) < 2 or sum(ts) < budget_s:
+        ts.append(oracle_step(rho, sample.h, order))
+    t = statistics.mean(ts)
+    what = "the same" if sample is prob else "a 129^3-node sample (same domain and density family) of the"
     return {"value": sample.points / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "one complete oracle solve of %s %s-node workload (convolution form of the "
-                      "boundary sum, numpy BLAS sine sums), %.1f s" % (what, "x".join(map(str, prob.n)), t)}
+            "sample": "%d complete oracle solves (convolution form of the boundary sum, numpy BLAS sine "
+                      "sums) of %s %s-node workload, %.2f s each" % (len(ts), what,
+                                                                    "x".join(map(str, prob.n)), t)}
+
+
+def cpu_paper_method(prob, order, kind):
+    """The method with fast transforms on the host cores (scipy's multithreaded
+    DST-I and FFT convolutions, the paper's FFTW setup of section 6), one solve
+    of the workload, or of a 257^3 sample of it above 257^3."""
+    try:
+        from oracle import fft_baseline
+    except ImportError as e:   # scipy missing on the host
+        return {"value": None, "unit": UNIT, "unavailable": str(e)}
+    sample = prob if max(prob.n) <= 257 else workload(kind, 257)
+    rho = sample.rho()
+    t = time.perf_counter()
+    fft_baseline.solve(rho, sample.h, order, workers=os.cpu_count())
+    t = time.perf_counter() - t
+    what = "the" if sample is prob else "a 257^3-node sample (same domain and density family) of the"
+    return {"value": sample.points / t, "unit": UNIT, "cores": os.cpu_count(),
+            "kind": "fast transforms: scipy.fft DST-I and FFT convolutions, all host cores",
+            "sample": "one solve of %s %s-node workload, %.2f s" % (what, "x".join(map(str, prob.n)), t)}
 
 
 def run_reference(args, rank, world):
     prob = workload(args.workload, args.n)
     if rank != 0:
         return
-    rho = prob.rho()
+    sample = reference_sample(prob, args.workload)
+    rho = sample.rho()
     for _ in range(args.warmup):
-        oracle_step(rho, prob.h, args.order)
-    ts = [oracle_step(rho, prob.h, args.order) for _ in range(args.steps)]
+        oracle_step(rho, sample.h, args.order)
+    ts = [oracle_step(rho, sample.h, args.order) for _ in range(args.steps)]
     t = sum(ts)
-    value = prob.points * args.steps / t
+    value = sample.points * args.steps / t
+    what = "the workload" if sample is prob else "a 129^3-node sample (same domain and density family) " \
+                                                 "of the workload"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference", "config": config_of(prob, args.order),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": "%d complete oracle solves of the workload" % args.steps},
+                             "sample": "%d complete oracle solves of %s" % (args.steps, what)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -218,308 +266,316 @@ def dst_flops_per_launch(prob):
     return 2.5 * lg * float(np.prod([k - 2 for k in prob.n]))
 
 
-def run_ours(args, rank, world):
-    import torch
-    import torch.distributed as dist
-    import ctypes
-    import paper_2108_11871_gb300 as idp
+class Gpu:
+    """Device, stream, L2 flush buffer and the timing helpers of the GPU arm."""
 
-    local = int(os.environ.get("LOCAL_RANK", 0))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    prob = workload(args.workload, args.n)
-    plan = idp.create_plan(3, prob.n, prob.h, args.order)
-    idp.plan_set(plan, idp.IDP_KEY_AUTOTUNE, 1)
-    if args.dst_shape is not None:
-        idp.plan_set(plan, idp.IDP_KEY_DST_SHAPE, args.dst_shape)
-    rho_h = prob.rho()
-    rho = torch.from_numpy(rho_h).to(dev)
-    phi = torch.empty_like(rho)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    def __init__(self, world):
+        import torch
+        import paper_2108_11871_gb300 as idp
+        self.torch, self.idp, self.world = torch, idp, world
+        self.local = int(os.environ.get("LOCAL_RANK", 0))
+        torch.cuda.set_device(self.local)
+        self.dev = torch.device("cuda", self.local)
+        self.stream = torch.cuda.current_stream(self.dev)
+        self.flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=self.dev)
 
-    def barrier():
-        if world > 1:
+    def barrier(self):
+        if self.world > 1:
+            import torch.distributed as dist
             dist.barrier()
 
-    for _ in range(args.warmup):
-        idp.solve(plan, rho, phi, stream)
-    torch.cuda.synchronize()
-    idp.plan_status(plan)
+    def plan(self, prob, order, prec=None, shape=None):
+        idp = self.idp
+        plan = idp.create_plan(prob.d, prob.n, prob.h, order)
+        if prec is not None:
+            idp.plan_set(plan, idp.IDP_KEY_PRECISION, prec)
+        idp.plan_set(plan, idp.IDP_KEY_AUTOTUNE, 1)
+        if shape is not None:
+            idp.plan_set(plan, idp.IDP_KEY_DST_SHAPE, shape)
+        return plan
 
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            flush.fill_(float(i))
-            starts[i].record(stream)
-            idp.solve(plan, rho, phi, stream)
-            ends[i].record(stream)
+    def timed(self, fn, steps, warmup):
+        """Per-step ms of `fn()` by CUDA events on the launch stream, the L2
+        flushed before each step (outside the events)."""
+        torch = self.torch
+        for _ in range(warmup):
+            fn()
         torch.cuda.synchronize()
-    barrier()
-    idp.plan_status(plan)
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    launches = ctypes.c_int64()
-    idp.library().idp_plan_launches(plan.handle, ctypes.byref(launches))
-    total_ms = max_over_ranks(total_ms, world, dev)
-    value = world * prob.points * args.steps / (total_ms / 1e3)
+        ev = []
+        for i in range(steps):
+            self.flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(self.stream)
+            fn()
+            b.record(self.stream)
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
 
-    # per-kernel durations (plain launches, events on the launch stream)
-    cap = 256
-    kinds = (ctypes.c_int * cap)()
-    ms = (ctypes.c_float * cap)()
-    per_kind = {}
-    for i in range(max(3, min(args.steps, 10))):
-        flush.fill_(float(i))
-        n = idp.library().idp_profile_solve(plan.handle, ctypes.c_void_p(rho.data_ptr()),
-                                            ctypes.c_void_p(phi.data_ptr()),
-                                            ctypes.c_void_p(stream.cuda_stream), cap, kinds, ms)
-        if n < 0:
-            raise RuntimeError("idp_profile_solve: %s" % idp.strerror(n))
-        for j in range(n):
-            per_kind.setdefault(kinds[j], []).append(ms[j])
-    names = {1: "dst_pass", 2: "rfft", 3: "face", 4: "face_invb", 5: "face_c2r", 6: "gtilde_layers",
-             7: "rhs6_w", 8: "rhs6_core", 9: "rhs6_extrap", 10: "gtilde_expand", 11: "dst_pass_layers", 12: "mixed_pass",
-             13: "support_flags", 14: "rhs6_expand", 15: "line1d", 16: "pad", 17: "validate"}
-    prof_steps = max(3, min(args.steps, 10))
-    shares = {names[k]: sum(v) / prof_steps for k, v in per_kind.items()}
-    dom = max(per_kind, key=lambda k: sum(per_kind[k]))
-    dst_ms = statistics.mean(per_kind[1])
+    def kernels(self, plan, rho, phi, reps=3):
+        """Per-kernel durations of `reps` solves with plain launches (CUDA events on
+        the launch stream): {family: [ms of each launch]}."""
+        import ctypes
+        idp = self.idp
+        cap = 256
+        kinds = (ctypes.c_int * cap)()
+        ms = (ctypes.c_float * cap)()
+        out = {}
+        for i in range(reps):
+            self.flush.fill_(float(i))
+            n = idp.library().idp_profile_solve(plan.handle, ctypes.c_void_p(rho.data_ptr()),
+                                                ctypes.c_void_p(phi.data_ptr()),
+                                                ctypes.c_void_p(self.stream.cuda_stream), cap, kinds, ms)
+            if n < 0:
+                raise RuntimeError("idp_profile_solve: %s" % idp.strerror(n))
+            for j in range(n):
+                out.setdefault(KERNEL_NAMES.get(kinds[j], str(kinds[j])), []).append(ms[j])
+        return out
+
+    def launches(self, plan):
+        import ctypes
+        v = ctypes.c_int64()
+        self.idp.library().idp_plan_launches(plan.handle, ctypes.byref(v))
+        return int(v.value)
+
+
+def rel(a, b):
+    return float((a - b).abs().max().item() / b.abs().max().item())
+
+
+def variant_record(g, prob, order, prec, label, rho, phi_ref, steps, warmup):
+    """A reduced-precision variant of the workload: throughput, per-kernel times and
+    its max difference from the FP64 result."""
+    idp = g.idp
+    plan = g.plan(prob, order, prec)
+    phi = g.torch.empty_like(rho)
+    ms = g.timed(lambda: idp.solve(plan, rho, phi, g.stream), steps, warmup)
+    idp.plan_status(plan)
+    t = max_over_ranks(sum(ms), g.world, g.dev)
+    ks = g.kernels(plan, rho, phi)
+    rec = {"variant": label, "tuning": idp.plan_tuning(plan),
+           "value": g.world * prob.points * steps / (t / 1e3), "unit": UNIT, "ms_per_step": t / steps,
+           "max_rel_error_vs_fp64": rel(phi, phi_ref),
+           "kernel_ms_per_step": {k: sum(v) / 3 for k, v in ks.items()}}
+    for fam in ("mixed_pass", "dst_pass"):
+        if fam in ks:
+            rec[fam + "_avg_ms"] = statistics.mean(ks[fam])
+    del plan
+    return phi, rec
+
+
+VARIANTS = (("mixed_precision", "MIXED_BF16X3",
+             "bf16x3 pieces, fp32 accumulate, tcgen05 (rho, R and final transforms)"),
+            ("mixed_tf32x3", "MIXED_TF32X3",
+             "tf32x3: two tf32 pieces, products hi*hi + hi*lo + lo*hi, fp32 accumulate, tcgen05 "
+             "kind::tf32 (rho, R and final transforms)"),
+            ("df32", "DF32", "double-float (FP32 pairs) FFT arithmetic"))
+
+
+def run_headline(g, args, prob):
+    """The workload's FP64 solve (the line's value), its variants, e2e and roofline."""
+    idp, torch = g.idp, g.torch
+    plan = g.plan(prob, args.order, shape=args.dst_shape)
+    rho_h = prob.rho()
+    rho = torch.from_numpy(rho_h).to(g.dev)
+    phi = torch.empty_like(rho)
+    g.barrier()
+    with ClockSampler(g.local) as clk:
+        ms = g.timed(lambda: idp.solve(plan, rho, phi, g.stream), args.steps, args.warmup)
+    g.barrier()
+    idp.plan_status(plan)
+    total_ms = max_over_ranks(sum(ms), g.world, g.dev)
+    out = {"value": g.world * prob.points * args.steps / (total_ms / 1e3),
+           "ms_per_step": total_ms / args.steps, "clocks": clk.summary(),
+           "gpu_launches": g.launches(plan) * args.steps}
+
+    ks = g.kernels(plan, rho, phi, reps=max(3, min(args.steps, 10)))
+    reps = max(3, min(args.steps, 10))
+    out["kernel_ms_per_step"] = {k: sum(v) / reps for k, v in ks.items()}
+    out["dominant_kernel"] = max(ks, key=lambda k: sum(ks[k]))
+    dst_ms = statistics.mean(ks["dst_pass"])
     achieved = dst_flops_per_launch(prob) / (dst_ms / 1e3) / 1e12
+    out["roofline"] = {"bound": "alu", "kernel": "dst_pass (FP64 sine-transform pass)",
+                       "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                       "frac": achieved / FP64_PEAK_TFLOPS,
+                       "peak_note": "FP64 derived: 152 SMs x 4 flop/clk x 2.07 GHz; "
+                                    "FMA-chain probe measured %.3f" % FP64_PROBE_TFLOPS,
+                       "traffic": DST_TRAFFIC.get(tuple(prob.n)), "avg_launch_ms": dst_ms,
+                       "flops_per_launch": dst_flops_per_launch(prob)}
+    out["tuning"] = idp.plan_tuning(plan)
 
     if args.profile_window > 0:
         # a window of plain solves for a profiler that starts collecting here
         torch.cuda.synchronize()
         torch.cuda.cudart().cudaProfilerStart()
         for i in range(args.profile_window):
-            flush.fill_(float(i))
-            idp.solve(plan, rho, phi, stream)
+            g.flush.fill_(float(i))
+            idp.solve(plan, rho, phi, g.stream)
         torch.cuda.synchronize()
         torch.cuda.cudart().cudaProfilerStop()
 
-    # end to end through the host-buffer entry point (pinned host memory)
+    # end to end through the host-buffer entry point (pinned host memory, both
+    # copies inside the timed region)
     rho_pin = torch.from_numpy(rho_h).pin_memory()
     phi_pin = torch.empty_like(rho_pin).pin_memory()
     e2e_steps = max(3, min(args.steps, 10))
-    idp.solve_host(plan, rho_pin.data_ptr(), phi_pin.data_ptr(), stream)
+    idp.solve_host(plan, rho_pin.data_ptr(), phi_pin.data_ptr(), g.stream)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for i in range(e2e_steps):
-        idp.solve_host(plan, rho_pin.data_ptr(), phi_pin.data_ptr(), stream)
+    for _ in range(e2e_steps):
+        idp.solve_host(plan, rho_pin.data_ptr(), phi_pin.data_ptr(), g.stream)
     torch.cuda.synchronize()
-    e2e_t = (time.perf_counter() - t0) / e2e_steps
-    e2e = {"value": world * prob.points / e2e_t, "unit": UNIT,
-           "h2d_bytes_per_step": 8 * prob.points, "d2h_bytes_per_step": 8 * prob.points}
+    e2e_t = max_over_ranks((time.perf_counter() - t0) / e2e_steps, g.world, g.dev)
+    out["e2e"] = {"value": g.world * prob.points / e2e_t, "unit": UNIT,
+                  "h2d_bytes_per_step": 8 * prob.points, "d2h_bytes_per_step": 8 * prob.points}
+    del rho_pin, phi_pin
 
-    # mixed-precision variants (tensor-core sine transforms), same workload and timing rules
-    def tensor_variant(prec, label):
-        mplan = idp.create_plan(3, prob.n, prob.h, args.order)
-        idp.plan_set(mplan, idp.IDP_KEY_PRECISION, prec)
-        idp.plan_set(mplan, idp.IDP_KEY_AUTOTUNE, 1)
-        phi_m = torch.empty_like(rho)
-        for _ in range(args.warmup):
-            idp.solve(mplan, rho, phi_m, stream)
-        torch.cuda.synchronize()
-        idp.plan_status(mplan)
-        ms_m = []
-        for i in range(args.steps):
-            flush.fill_(float(i))
-            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s0.record(stream)
-            idp.solve(mplan, rho, phi_m, stream)
-            s1.record(stream)
-            ms_m.append((s0, s1))
-        torch.cuda.synchronize()
-        idp.plan_status(mplan)
-        t_m = sum(a.elapsed_time(b) for a, b in ms_m)
-        diff = (phi_m - phi).abs().max().item() / phi.abs().max().item()
-        mk = {}
-        for i in range(3):
-            flush.fill_(float(i))
-            n = idp.library().idp_profile_solve(mplan.handle, ctypes.c_void_p(rho.data_ptr()),
-                                                ctypes.c_void_p(phi_m.data_ptr()),
-                                                ctypes.c_void_p(stream.cuda_stream), cap, kinds, ms)
-            for j in range(max(n, 0)):
-                mk.setdefault(names.get(kinds[j], str(kinds[j])), []).append(ms[j])
-        return phi_m, {"variant": label,
-                "tuning": idp.plan_tuning(mplan),
-                "value": world * prob.points * args.steps / (t_m / 1e3), "unit": UNIT,
-                "ms_per_step": t_m / args.steps, "max_rel_error_vs_fp64": diff,
-                "kernel_ms_per_step": {k: sum(v) / 3 for k, v in mk.items()},
-                "mixed_pass_avg_ms": statistics.mean(mk["mixed_pass"]) if "mixed_pass" in mk else None}
-
-    mixed = mixed_tf32 = phi_m = phi_t = None
-    if not args.fp64_only:
-        phi_m, mixed = tensor_variant(idp.IDP_PRECISION_MIXED_BF16X3,
-                                      "bf16x3 pieces, fp32 accumulate, tcgen05 (rho, R and final transforms)")
-        phi_t, mixed_tf32 = tensor_variant(idp.IDP_PRECISION_MIXED_TF32X3,
-                                           "tf32x3: two tf32 pieces, products hi*hi + hi*lo + lo*hi, fp32 "
-                                           "accumulate, tcgen05 kind::tf32 (rho, R and final transforms)")
-
-    # double-float variant (FFT butterflies on the FP32 pipe, FP64-level accuracy)
-    df32 = None
-    if not args.fp64_only:
-        dplan = idp.create_plan(3, prob.n, prob.h, args.order)
-        idp.plan_set(dplan, idp.IDP_KEY_PRECISION, idp.IDP_PRECISION_DF32)
-        idp.plan_set(dplan, idp.IDP_KEY_AUTOTUNE, 1)
-        phi_d = torch.empty_like(rho)
-        for _ in range(args.warmup):
-            idp.solve(dplan, rho, phi_d, stream)
-        torch.cuda.synchronize()
-        idp.plan_status(dplan)
-        ev = []
-        for i in range(args.steps):
-            flush.fill_(float(i))
-            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s0.record(stream)
-            idp.solve(dplan, rho, phi_d, stream)
-            s1.record(stream)
-            ev.append((s0, s1))
-        torch.cuda.synchronize()
-        idp.plan_status(dplan)
-        t_d = sum(x.elapsed_time(y) for x, y in ev)
-        dk = {}
-        for i in range(3):
-            flush.fill_(float(i))
-            n = idp.library().idp_profile_solve(dplan.handle, ctypes.c_void_p(rho.data_ptr()),
-                                                ctypes.c_void_p(phi_d.data_ptr()),
-                                                ctypes.c_void_p(stream.cuda_stream), cap, kinds, ms)
-            for j in range(max(n, 0)):
-                dk.setdefault(names.get(kinds[j], str(kinds[j])), []).append(ms[j])
-        df32 = {"variant": "double-float (FP32 pairs) FFT arithmetic",
-                "value": world * prob.points * args.steps / (t_d / 1e3), "unit": UNIT,
-                "ms_per_step": t_d / args.steps,
-                "max_rel_error_vs_fp64": (phi_d - phi).abs().max().item() / phi.abs().max().item(),
-                "kernel_ms_per_step": {k: sum(v) / 3 for k, v in dk.items()},
-                "dst_pass_avg_ms": statistics.mean(dk["dst_pass"]) if "dst_pass" in dk else None}
-
-    if rank != 0:
-        return
+    # FP64 accuracy evidence at full size: g against the direct trapezoid sum
+    # (eq. TrapOrig2D) on sampled boundary nodes; the bump also against its exact
+    # potential
+    from oracle import greens as ogreens
+    gstage = torch.empty_like(rho)
+    idp.solve_stage(plan, idp.IDP_STAGE_BOUNDARY, rho, gstage, g.stream)
+    idp.plan_status(plan)
+    idx = ogreens.boundary_indices(prob.n)
+    pick = idx[np.random.default_rng(7).choice(len(idx), 64 if prob.points > 3e7 else 512, replace=False)]
+    gsamp = gstage.cpu().numpy()[tuple(pick.T)]
+    gref = ogreens.boundary_direct(rho_h, prob.h, pick)
+    prec = {"variant": "fp64", "g_vs_direct_sum": float(np.abs(gsamp - gref).max() / np.abs(gref).max()),
+            "g_sample": "%d seeded boundary nodes" % len(pick)}
+    del gstage
     if prob.density == "bump":
         from oracle import closed_form
-        # error against the exact potential (every node up to 129^3, a stride-4 sample above)
         stride = 1 if prob.n[0] <= 129 else 4
         sub = w.Problem(prob.name, tuple(len(range(0, k, stride)) for k in prob.n), prob.lo,
                         tuple(lo + (len(range(0, k, stride)) - 1) * stride * hh
                               for lo, k, hh in zip(prob.lo, prob.n, prob.h)), prob.density, prob.params)
-        out = phi[::stride, ::stride, ::stride].cpu().numpy()
         exact = closed_form.bump_potential_on_grid(sub)
-        precision = {"variant": "fp64",
-                     "max_rel_error_vs_exact_potential": float(np.abs(out - exact).max() / np.abs(exact).max())}
-    elif prob.points <= 30_000_000:
-        # no closed form for the tapered Gaussian sum: every variant against the oracle
-        from oracle import solve as osolve
-        ref = osolve.solve(rho_h, prob.h, args.order, boundary="convolution")
-        scale = np.abs(ref).max()
-        precision = {"variant": "fp64", "max_rel_error_vs_oracle": float(np.abs(phi.cpu().numpy() - ref).max() / scale)}
-        variants = []
-        if mixed is not None:
-            variants.append((mixed, phi_m))
-        if mixed_tf32 is not None:
-            variants.append((mixed_tf32, phi_t))
-        if df32 is not None:
-            variants.append((df32, phi_d))
-        for rec, ph in variants:
-            rec["max_rel_error_vs_oracle"] = float(np.abs(ph.cpu().numpy() - ref).max() / scale)
-    else:
-        precision = {"variant": "fp64", "max_rel_error_vs_oracle": None,
-                     "note": "no closed form for the tapered Gaussian sum and the oracle is too slow at this size; "
-                             "FP64 parity at 513^3 is checked in the GPU parity tests"}
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(prob, args.order, {"parallelism": "replicas" if world > 1 else "single"}),
-            "precision": precision,
-            "mixed_precision": mixed,
-            "mixed_tf32x3": mixed_tf32,
-            "df32": df32,
-            "e2e": e2e,
-            "gpu_launches": int(launches.value) * args.steps,
-            "roofline": {"bound": "alu", "kernel": "dst_pass (FP64 sine-transform pass)",
-                         "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS,
-                         "peak_note": "FP64 derived: 152 SMs x 4 flop/clk x 2.07 GHz; "
-                                      "FMA-chain probe measured %.3f" % FP64_PROBE_TFLOPS,
-                         # DRAM bytes (read + write) per full-volume launch of this kernel,
-                         # averaged like avg_launch_ms over the 8 passes of a 129^3 solve (ncu):
-                         # six passes read their input volume once (16.41 MB; the output stays
-                         # in L2), the two passes of the transform of rho read the interleaved
-                         # T0 (33.3 and 32.8 MB)
-                         "traffic": 20573408 if prob.n == (129, 129, 129) else None, "avg_launch_ms": dst_ms,
-                         "flops_per_launch": dst_flops_per_launch(prob)},
-            "kernel_ms_per_step": shares, "dominant_kernel": names[dom], "tuning": idp.plan_tuning(plan),
-            "clocks": clk.summary()}
-    if world == 1:
-        line["cpu_baseline"] = cpu_baseline(prob, args.order, args.workload)
-    print(json.dumps(line), flush=True)
+        o = phi[::stride, ::stride, ::stride].cpu().numpy()
+        prec["max_rel_error_vs_exact_potential"] = float(np.abs(o - exact).max() / np.abs(exact).max())
+    out["precision"] = prec
+    del plan
+
+    phis = {}
+    if not args.fp64_only:
+        for key, name, label in VARIANTS:
+            ph, rec = variant_record(g, prob, args.order, getattr(idp, "IDP_PRECISION_" + name), label, rho, phi,
+                                     args.steps, args.warmup)
+            out[key] = rec
+            phis[key] = ph
+    return out, rho_h, phi, phis
 
 
-def run_batched(args, rank, world):
+def run_sweep(g, args):
+    """The precision sweep at its nearest supported size (257^3 nodes, interior
+    255^3): FP64 and every variant, each with its error against the oracle."""
+    from oracle import solve as osolve
+    prob = workload("sweep")
+    head, rho_h, phi, phis = run_headline(g, argparse.Namespace(**{**vars(args), "profile_window": 0,
+                                                                   "dst_shape": None}), prob)
+    ref = osolve.solve(rho_h, prob.h, args.order, boundary="convolution")
+    scale = np.abs(ref).max()
+    rec = {"workload": describe(prob, args.order), "value": head["value"], "ms_per_step": head["ms_per_step"],
+           "max_rel_error_vs_oracle": float(np.abs(phi.cpu().numpy() - ref).max() / scale)}
+    for key, _, _ in VARIANTS:
+        if key in head:
+            rec[key] = {"value": head[key]["value"], "ms_per_step": head[key]["ms_per_step"],
+                        "max_rel_error_vs_oracle": float(np.abs(phis[key].cpu().numpy() - ref).max() / scale)}
+    return rec
+
+
+def run_bump(g, args):
+    """The 129^3 bump workload (FP64): throughput and the error against its exact potential."""
+    prob = workload("bump")
+    ns = argparse.Namespace(**{**vars(args), "profile_window": 0, "dst_shape": None, "fp64_only": True})
+    head, _, _, _ = run_headline(g, ns, prob)
+    return {"workload": describe(prob, args.order), "value": head["value"], "ms_per_step": head["ms_per_step"],
+            "max_rel_error_vs_exact_potential": head["precision"].get("max_rel_error_vs_exact_potential"),
+            "roofline_frac": head["roofline"]["frac"], "dst_pass_avg_ms": head["roofline"]["avg_launch_ms"]}
+
+
+def run_batched(g, args, rank):
     """96 independent problems, per-axis nodes from {33,65,97,129,193,257} (seed 21081),
-    Gaussian-sum densities; one graph launch per step (idp_solve_batched)."""
-    import torch
-    import paper_2108_11871_gb300 as idp
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    Gaussian-sum densities; one idp_solve_batched call per step."""
+    idp, torch = g.idp, g.torch
     probs = w.c5_batch()
-    mine = shard(probs, rank, world)
+    mine = shard(probs, rank, g.world)
     total = sum(p.points for p in mine)
     t0 = time.perf_counter()
-    plans = [idp.create_plan(3, p.n, p.h, args.order) for p in mine]
-    for pl in plans:
-        idp.plan_set(pl, idp.IDP_KEY_AUTOTUNE, 1)
+    plans = [g.plan(p, args.order) for p in mine]
     setup_s = time.perf_counter() - t0
-    rhos = [torch.from_numpy(p.rho()).to(dev) for p in mine]
+    rhos = [torch.from_numpy(p.rho()).to(g.dev) for p in mine]
     phis = [torch.empty_like(r) for r in rhos]
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream(dev)
     out = {}
+    fp64 = None
     for label, prec in (("fp64", idp.IDP_PRECISION_FP64), ("df32", idp.IDP_PRECISION_DF32),
                         ("mixed_bf16x3", idp.IDP_PRECISION_MIXED_BF16X3),
                         ("mixed_tf32x3", idp.IDP_PRECISION_MIXED_TF32X3)):
+        if args.fp64_only and label != "fp64":
+            continue
         for pl in plans:
             idp.plan_set(pl, idp.IDP_KEY_PRECISION, prec)
-            if prec in (idp.IDP_PRECISION_MIXED_BF16X3, idp.IDP_PRECISION_MIXED_TF32X3):
+            if prec != idp.IDP_PRECISION_FP64:
                 idp.plan_set(pl, idp.IDP_KEY_AUTOTUNE, 1)
-        for _ in range(args.warmup):
-            idp.solve_batched(plans, rhos, phis, stream)
-        torch.cuda.synchronize()
-        ev = []
-        for i in range(args.steps):
-            flush.fill_(float(i))
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            idp.solve_batched(plans, rhos, phis, stream)
-            b.record(stream)
-            ev.append((a, b))
-        torch.cuda.synchronize()
+        ms = g.timed(lambda: idp.solve_batched(plans, rhos, phis, g.stream), args.steps, args.warmup)
         for pl in plans:
             idp.plan_status(pl)
-        t = max_over_ranks(sum(x.elapsed_time(y) for x, y in ev) / args.steps, world, dev)
+        t = max_over_ranks(sum(ms) / args.steps, g.world, g.dev)
         # the same problems one after another (separate graph launches)
-        for i in range(2):
-            flush.fill_(float(i))
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for pl, r, ph in zip(plans, rhos, phis):
-            idp.solve(pl, r, ph, stream)
-        b.record(stream)
-        torch.cuda.synchronize()
-        out[label] = {"value": world * total / (t / 1e3), "ms_per_step": t,
-                      "sequential_ms": a.elapsed_time(b)}
+        seq = g.timed(lambda: [idp.solve(pl, r, ph, g.stream) for pl, r, ph in zip(plans, rhos, phis)], 2, 1)
+        rec = {"value": g.world * total / (t / 1e3), "ms_per_step": t, "sequential_ms": statistics.mean(seq)}
+        if label == "fp64":
+            fp64 = [ph.clone() for ph in phis]
+        else:
+            rec["max_rel_error_vs_fp64"] = max(rel(a, b) for a, b in zip(phis, fp64))
+        out[label] = rec
+    return {"workload": "96 independent 3-D order-%d problems, per-axis nodes from {33,65,97,129,193,257} "
+                        "(seed 21081), Gaussian sums (seed 2108+i), one idp_solve_batched call per step"
+                        % args.order,
+            "nodes": total * g.world, "problems": len(probs), "plan_setup_s": setup_s,
+            "value": out["fp64"]["value"], "ms_per_step": out["fp64"]["ms_per_step"], "variants": out}
+
+
+def run_ours(args, rank, world):
+    g = Gpu(world)
+    prob = workload(args.workload, args.n)
+    head, rho_h, phi, phis = run_headline(g, args, prob)
+    del phi, phis
+    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(prob, args.order, {"parallelism": "replicas" if world > 1 else "single"})}
+    for k in ("precision", "mixed_precision", "mixed_tf32x3", "df32", "e2e", "gpu_launches", "roofline",
+              "kernel_ms_per_step", "dominant_kernel", "tuning", "clocks"):
+        if k in head:
+            line[k] = head[k]
+    if not args.headline_only:
+        g.torch.cuda.empty_cache()
+        line["bump_129"] = run_bump(g, args)
+        line["sweep_257"] = run_sweep(g, args)
+        g.torch.cuda.empty_cache()
+        line["batched"] = run_batched(g, args, rank)
     if rank != 0:
         return
-    line = {"metric": METRIC + " (batched)", "value": out["fp64"]["value"], "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["fp64"]["ms_per_step"],
+    if world == 1 and not args.headline_only:
+        line["cpu_baseline"] = cpu_baseline(prob, args.order, args.workload)
+        line["cpu_paper_method"] = cpu_paper_method(prob, args.order, args.workload)
+    elif world == 1:
+        line["cpu_baseline"] = cpu_baseline(prob, args.order, args.workload, budget_s=1.0)
+    print(json.dumps(line), flush=True)
+
+
+def run_batched_only(args, rank, world):
+    g = Gpu(world)
+    rec = run_batched(g, args, rank)
+    if rank != 0:
+        return
+    line = {"metric": METRIC + " (batched)", "value": rec["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": "96 independent 3-D order-%d problems, per-axis nodes from "
-                                   "{33,65,97,129,193,257} (seed 21081), Gaussian sums (seed 2108+i), "
-                                   "one CUDA graph launch per step" % args.order,
-                       "nodes": total * world, "problems": len(probs), "plan_setup_s": setup_s},
-            "variants": out}
+            "data": "synthetic", "config": {"workload": rec["workload"], "nodes": rec["nodes"],
+                                            "problems": rec["problems"], "plan_setup_s": rec["plan_setup_s"]},
+            "variants": rec["variants"]}
     print(json.dumps(line), flush=True)
 
 
@@ -538,7 +594,7 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
     elif args.batched:
-        run_batched(args, rank, world)
+        run_batched_only(args, rank, world)
     else:
         run_ours(args, rank, world)
     if world > 1:

@@ -79,6 +79,10 @@ enum {
                                tensor-core pass issues no products, so its bounded wait expires
                                (after ~5 ms); the kernel records the failure, frees its tensor
                                memory and returns, and idp_plan_status reports IDP_ETIMEOUT */
+    IDP_KEY_GUARD_TEST = 7, /* test hook for idp_plan_check_guards: value 1 overwrites the first
+                               byte of the guard region in front of the plan's first buffer (a
+                               write inside that allocation, from the host), value 0 restores it;
+                               synchronises the device */
     IDP_KEY_VALIDATE = 6    /* validation mode, value k >= 0 (0, the default: off).  Every solve
                                or stage first checks the caller's rho on the device: a NaN or
                                infinite value anywhere makes the next idp_plan_status return
@@ -164,7 +168,9 @@ int idp_solve(idp_plan plan, const double *rho, double *phi, void *stream);
 int idp_solve_host(idp_plan plan, const double *rho_host, double *phi_host, void *stream);
 
 /* Solve `count` independent problems, plans[i] with rho[i] -> phi[i]
- * (device arrays), all queued on `stream`.  The plans must be distinct. */
+ * (device arrays), all queued on `stream`.  The plans must be distinct.  The
+ * problems run concurrently, so no phi[i] may overlap any rho[j] or any other
+ * phi[j] (IDP_EALIAS). */
 int idp_solve_batched(int count, const idp_plan plans[], const double *const rho[],
                       double *const phi[], void *stream);
 
@@ -247,7 +253,9 @@ int idp_destroy_plan(idp_plan plan);
  * time-critical loops that cannot afford cudaMalloc's implicit
  * synchronisation).
  *
- * Computes the same R as the 6th-order step of idp_solve (IDP_STAGE_R):
+ * Computes the R of the 6th-order step of idp_solve (IDP_STAGE_R) up to
+ * rounding -- here by the direct stencil, where the plan-based solver forms R
+ * in spectral form plus a correction next to the boundary:
  * R = sum over ordered axis pairs s != r of (h_s^4/240 + h_s^2 h_r^2/144)
  * D2_s D2_s D2_r u1 on the nodes whose indices all lie in 2..M-2, extended
  * to the layers next to the boundary by cubic extrapolation.
@@ -257,9 +265,11 @@ int idp_destroy_plan(idp_plan plan);
  * Scratch: a fixed device array of 3 * IDP_RHS6_NOALLOC_MAX_NODES doubles
  * (12 MiB), held by every GPU that loads the library until the process exits.
  * Problems with more than IDP_RHS6_NOALLOC_MAX_NODES nodes return IDP_ESCRATCH.
- * The call allocates nothing.  Its first call on a device looks up the
- * scratch's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  All calls share the one scratch array, which
+ * The call allocates nothing.  Every call looks up the scratch's device
+ * address on the current device (cudaGetSymbolAddress; the host-side symbol is
+ * not a device address); the first call on a device also loads the library's
+ * device code there, so make that first call before any stream capture.
+ * All calls share the one scratch array, which
  * keeps the last call's contents: calls whose work overlaps on the GPU (other
  * streams, other host threads) race and must be serialised by the caller. */
 #define IDP_RHS6_NOALLOC_MAX_NODES 524288

@@ -8,9 +8,6 @@
 // right-hand side R as the plan-based solver, but keeps its scratch (the three
 // second-difference arrays W_s) in the fixed device array below instead of
 // plan workspace.  The caller passes u1 and R; nothing is allocated.
-#include <cstring>
-#include <mutex>
-
 #include "idp_internal.cuh"
 #include "../../include/idp.h"
 
@@ -23,26 +20,17 @@ namespace {
 // exits, and it is shared by all calls.
 static __device__ __align__(256) double g_rhs6_scratch[3 * IDP_RHS6_NOALLOC_MAX_NODES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double *g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device, looked up once
-// per device (the host-side symbol is only a stand-in, not a device address).
+// Device address of the scratch array on the current device.  The host-side
+// symbol is only a stand-in, not a device address, so the address is looked up
+// on every call (cheap once the device code is loaded): a cached address would
+// go stale when the caller resets the device and the library's device code is
+// loaded again, possibly elsewhere.
 int scratch_for_current_device(double **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return IDP_ECUDA;
-    if (dev < 0 || dev >= kMaxDevices) return IDP_ESUPPORT;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_rhs6_scratch);
-        if (e != cudaSuccess || !p) return IDP_ECUDA;
-        g_scratch_ptr[dev] = static_cast<double *>(p);
-    }
-    *out = g_scratch_ptr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_rhs6_scratch);
+    if (e != cudaSuccess || !p) return IDP_ECUDA;
+    *out = static_cast<double *>(p);
     return IDP_OK;
 }
 
@@ -57,10 +45,11 @@ extern "C" int idp_rhs6_noalloc(int d, const int64_t n[], const double h[], cons
     for (int s = 0; s < d; ++s) {
         if (!(h[s] > 0.0)) return IDP_EINVAL;
         if (n[s] < 8) return IDP_EINVAL;   // the extrapolation reads layers 2..5
+        // checked before each product, so that no product can overflow
+        if (n[s] > IDP_RHS6_NOALLOC_MAX_NODES / nodes) return IDP_ESCRATCH;
         nodes *= n[s];
         interior *= n[s] - 2;
     }
-    if (nodes > IDP_RHS6_NOALLOC_MAX_NODES) return IDP_ESCRATCH;
     const char *a = (const char *)u1, *b = (const char *)R;
     if (a < b + interior * 8 && b < a + nodes * 8) return IDP_EALIAS;
     double *W = nullptr;

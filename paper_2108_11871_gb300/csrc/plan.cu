@@ -1555,6 +1555,17 @@ int idp_plan_set(idp_plan p, int key, int64_t value)
         }
         return IDP_OK;
     }
+    if (key == IDP_KEY_GUARD_TEST) {
+        // test hook: overwrite (1) or restore (0) the first byte of the guard
+        // region in front of the plan's first buffer; the write stays inside
+        // that allocation
+        if (value != 0 && value != 1) return IDP_EINVAL;
+        if (p->guarded.empty()) return IDP_ESUPPORT;
+        IDP_CK(cudaDeviceSynchronize());
+        IDP_CK(cudaMemset(p->guarded.front().first, value ? 0x5A : idp_plan_s::GUARD_BYTE, 1));
+        IDP_CK(cudaDeviceSynchronize());
+        return IDP_OK;
+    }
     if (key == IDP_KEY_STALL_TEST) {
         if (!tensor_mode(p)) return IDP_EINVAL;
         p->stall_test = value ? 1 : 0;
@@ -1645,8 +1656,16 @@ int idp_solve_batched(int count, const idp_plan plans[], const double *const rho
         if (!plans[i] || !rho[i] || !phi[i]) return IDP_EINVAL;
         for (int j = 0; j < i; ++j)
             if (plans[j] == plans[i]) return IDP_EINVAL;
-        const size_t b = sizeof(double) * plans[i]->unodes;
-        if (overlap(rho[i], b, phi[i], b)) return IDP_EALIAS;
+    }
+    // the problems run concurrently (branches of one graph): an output may
+    // overlap no input and no other output, of its own problem or another
+    for (int i = 0; i < count; ++i) {
+        const size_t bi = sizeof(double) * plans[i]->unodes;
+        for (int j = 0; j < count; ++j) {
+            const size_t bj = sizeof(double) * plans[j]->unodes;
+            if (overlap(phi[i], bi, rho[j], bj)) return IDP_EALIAS;
+            if (j != i && overlap(phi[i], bi, phi[j], bj)) return IDP_EALIAS;
+        }
     }
     if (count == 0) return IDP_OK;
     cudaStream_t st = (cudaStream_t)stream;

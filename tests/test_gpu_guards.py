@@ -76,3 +76,16 @@ def test_guards_stay_intact_on_every_path(idp, prob):
     torch.cuda.synchronize()
     idp.plan_check_guards(plan)
     idp.plan_check_guards(other)
+
+
+def test_guard_check_detects_a_changed_guard_byte(idp):
+    # the check itself: a guard byte changed from the host (inside the allocation,
+    # through the test hook) is reported as IDP_EGUARD; restored, the check passes
+    plan = idp.create_plan(3, (17, 17, 17), (0.1, 0.1, 0.1), 6)
+    idp.plan_check_guards(plan)
+    idp.plan_set(plan, idp.IDP_KEY_GUARD_TEST, 1)
+    with pytest.raises(idp.IdpError) as e:
+        idp.plan_check_guards(plan)
+    assert e.value.code == idp.IDP_EGUARD
+    idp.plan_set(plan, idp.IDP_KEY_GUARD_TEST, 0)
+    idp.plan_check_guards(plan)

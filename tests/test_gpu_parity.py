@@ -62,6 +62,16 @@ def _oracle_parts(prob, order):
     return parts
 
 
+_DIRECT = {}
+
+
+def _direct_g(name, prob):
+    """g on every boundary node by the direct trapezoid sum (eq. TrapOrig2D), cached."""
+    if name not in _DIRECT:
+        _DIRECT[name] = ogreens.boundary_direct_nodes(prob.rho(), prob.h)
+    return _DIRECT[name]
+
+
 @pytest.mark.parametrize("precision", ["fp64", "df32"])
 @pytest.mark.parametrize("order", [4, 6])
 @pytest.mark.parametrize("name,prob", CASES, ids=[c[0] for c in CASES])
@@ -79,6 +89,8 @@ def test_components_match_oracle(idp, name, prob, order, precision):
     g = run_stage(idp, plan, idp.IDP_STAGE_BOUNDARY, r, nshape)
     mask = ogreens.boundary_mask(prob.n)
     assert rel_max(g[mask], ref["g"][mask]) < TOL
+    # and against the direct trapezoid sum of section 4 on every boundary node
+    assert rel_max(g[mask], _direct_g(name, prob)[mask]) < TOL
     assert np.all(g[~mask] == 0)
     ps = run_stage(idp, plan, idp.IDP_STAGE_PHISTAR, r, nshape)
     assert rel_max(ps, ref["phistar"]) < TOL
@@ -275,6 +287,26 @@ def test_autotuned_plan_still_matches_oracle(idp, precision):
     idp.plan_status(plan)
     ref = osolve.solve(rho, prob.h, 6, boundary="convolution")
     assert rel_max(out.cpu().numpy(), ref) < tol
+
+
+def test_batched_rejects_outputs_that_overlap_other_problems(idp):
+    # the problems of a batch run concurrently: phi[i] overlapping rho[j] or phi[j]
+    # (i != j) is refused before anything is queued
+    import torch
+    n = (17, 17, 17)
+    plans = [idp.create_plan(3, n, (0.1, 0.1, 0.1), 6) for _ in range(2)]
+    big = torch.zeros(3 * 17 ** 3, dtype=torch.float64, device=device())
+    k = 17 ** 3
+    rho0, rho1 = to_dev(np.zeros(n)), to_dev(np.zeros(n))
+    cases = [([rho0, rho1], [big[:k], big[k // 2:k // 2 + k]]),      # outputs overlap
+             ([rho0, big[:k]], [big[k // 2:k // 2 + k], big[2 * k:]])]   # an output overlaps another input
+    for rhos, phis in cases:
+        with pytest.raises(idp.IdpError) as e:
+            idp.solve_batched(plans, rhos, phis)
+        assert e.value.code == idp.IDP_EALIAS
+    idp.solve_batched(plans, [rho0, rho1], [big[:k], big[k:2 * k]])
+    for pl in plans:
+        idp.plan_status(pl)
 
 
 def test_alias_and_bad_arguments_are_rejected(idp):

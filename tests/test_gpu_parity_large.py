@@ -1,0 +1,193 @@
+"""GPU path against the FP64 oracle at the panel counts of the large workloads.
+
+Every intermediate (g, phi*, gtilde, u1, R, phi) and the full solve are compared
+element by element with the oracle at panel counts 192, 256, 384 and 512 (sine
+lengths 96..256 and boundary-convolution lengths 384..1024: the kernel
+instantiations the 513^3, 257^3 and batched workloads use), in FP64 and
+double-float arithmetic at the 1e-12 target, and in the two tensor-core modes at
+their stated bounds (1e-6 sqrt(n_max) for BF16x3, 4e-6 sqrt(n_max) for TF32x3,
+see test_gpu_mixed.py).  The boundary values are also held to the direct
+trapezoid sum of section 4 (eq. TrapOrig2D): on every boundary node of the 2-D
+grid and on a seeded sample of boundary nodes plus all corners in 3-D.
+
+Oracle cost: one complete oracle solve per grid (about 20 s at 257^3 on eight
+cores), cached for the module.
+"""
+import numpy as np
+import pytest
+
+import workloads as w
+from oracle import greens as ogreens, solve as osolve
+from tests.gpu_util import device, r_amplification, rel_max, run_stage, to_dev
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+LARGE = [
+    # panel counts 192, 32, 256 on three axes (anisotropic h)
+    ("3d_193x33x257", w.Problem("L1", (193, 33, 257), (0.0, 0.0, 0.0), (1.5, 0.25, 2.0), "gauss",
+                                dict(seed=31))),
+    # panel counts 384 and 512 (the longest sine and convolution lengths in 2-D)
+    ("2d_385x513", w.Problem("L2", (385, 513), (0.0, 0.0), (1.5, 2.0), "gauss", dict(seed=32))),
+    # the precision-sweep workload at its nearest supported size (interior 255^3)
+    ("3d_257", w.c4_sweep((255, 255, 255))),
+]
+_REF = {}
+
+
+@pytest.fixture(scope="module")
+def idp():
+    import paper_2108_11871_gb300 as m
+    device()
+    m.library()
+    return m
+
+
+def _oracle(name, prob, order):
+    key = (name, order)
+    if key not in _REF:
+        parts = {}
+        phi = osolve.solve(prob.rho(), prob.h, order, boundary="convolution", parts=parts)
+        parts["phi"] = phi
+        _REF[key] = parts
+    return _REF[key]
+
+
+def _direct_targets(prob):
+    idx = ogreens.boundary_indices(prob.n)
+    if prob.d == 2:
+        return idx
+    rng = np.random.default_rng(2108)
+    pick = idx[rng.choice(len(idx), 4096, replace=False)]
+    corners = np.array([[i, j, k] for i in (0, prob.n[0] - 1) for j in (0, prob.n[1] - 1)
+                        for k in (0, prob.n[2] - 1)], dtype=np.int32)
+    return np.concatenate([pick, corners])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df32"])
+@pytest.mark.parametrize("name,prob", LARGE, ids=[c[0] for c in LARGE])
+def test_large_components_match_oracle(idp, name, prob, precision):
+    order = 6
+    rho = prob.rho()
+    ref = _oracle(name, prob, order)
+    plan = idp.create_plan(prob.d, prob.n, prob.h, order)
+    if precision == "df32":
+        idp.plan_set(plan, idp.IDP_KEY_PRECISION, idp.IDP_PRECISION_DF32)
+    r = to_dev(rho)
+    ishape = tuple(k - 2 for k in prob.n)
+    g = run_stage(idp, plan, idp.IDP_STAGE_BOUNDARY, r, prob.n)
+    mask = ogreens.boundary_mask(prob.n)
+    assert rel_max(g[mask], ref["g"][mask]) < TOL
+    assert np.all(g[~mask] == 0)
+    tg = _direct_targets(prob)
+    assert rel_max(g[tuple(tg.T)], ogreens.boundary_direct(rho, prob.h, tg)) < TOL
+    ps = run_stage(idp, plan, idp.IDP_STAGE_PHISTAR, r, prob.n)
+    assert rel_max(ps, ref["phistar"]) < TOL
+    gt = run_stage(idp, plan, idp.IDP_STAGE_GTILDE, r, ishape)
+    assert rel_max(gt, ref["gtilde"]) < TOL
+    u1 = run_stage(idp, plan, idp.IDP_STAGE_U1, r, prob.n)
+    assert rel_max(u1, ref["u1"]) < TOL
+    du = np.abs(u1 - ref["u1"]).max() + 4 * np.finfo(np.float64).eps * np.abs(ref["u1"]).max()
+    R = run_stage(idp, plan, idp.IDP_STAGE_R, r, ishape)
+    amp = r_amplification(prob.h)
+    core = tuple(slice(1, -1) for _ in ishape)
+    assert np.abs(R - ref["R"])[core].max() <= amp * du
+    assert np.abs(R - ref["R"]).max() <= amp * 15 ** prob.d * du
+    phi = run_stage(idp, plan, idp.IDP_STAGE_PHI, r, prob.n)
+    assert rel_max(phi, ref["phi"]) < TOL
+    # the autotuned plan replayed from its graph (the bench's configuration)
+    idp.plan_set(plan, idp.IDP_KEY_AUTOTUNE, 1)
+    out = to_dev(np.zeros(prob.n))
+    idp.solve(plan, r, out)
+    idp.plan_status(plan)
+    assert rel_max(out.cpu().numpy(), ref["phi"]) < TOL
+
+
+@pytest.mark.parametrize("name,prob", LARGE[:2], ids=[c[0] for c in LARGE[:2]])
+def test_large_order4_matches_oracle(idp, name, prob):
+    ref = _oracle(name, prob, 4)
+    plan = idp.create_plan(prob.d, prob.n, prob.h, 4)
+    r = to_dev(prob.rho())
+    u1 = run_stage(idp, plan, idp.IDP_STAGE_U1, r, prob.n)
+    assert rel_max(u1, ref["u1"]) < TOL
+    phi = run_stage(idp, plan, idp.IDP_STAGE_PHI, r, prob.n)
+    assert rel_max(phi, ref["phi"]) < TOL
+
+
+@pytest.mark.parametrize("variant", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("name,prob", LARGE, ids=[c[0] for c in LARGE])
+def test_large_tensor_core_modes_within_their_bounds(idp, name, prob, variant):
+    nmax = max(prob.n) - 2
+    tol = (4e-6 if variant == "tf32x3" else 1e-6) * np.sqrt(nmax)
+    ref = _oracle(name, prob, 6)
+    plan = idp.create_plan(prob.d, prob.n, prob.h, 6)
+    idp.plan_set(plan, idp.IDP_KEY_PRECISION,
+                 idp.IDP_PRECISION_MIXED_TF32X3 if variant == "tf32x3" else idp.IDP_PRECISION_MIXED_BF16X3)
+    r = to_dev(prob.rho())
+    ps = run_stage(idp, plan, idp.IDP_STAGE_PHISTAR, r, prob.n)
+    e1 = rel_max(ps, ref["phistar"])
+    out = to_dev(np.zeros(prob.n))
+    idp.solve(plan, r, out)
+    idp.plan_status(plan)
+    e2 = rel_max(out.cpu().numpy(), ref["phi"])
+    print("tensor-core mode", variant, prob.n, e1, e2)
+    assert e1 < tol and e2 < tol
+
+
+def _c5_pick():
+    """One problem of the batched workload whose longest axis has 193 nodes and
+    one whose longest axis has 257 (the two largest size classes)."""
+    probs = w.c5_batch()
+    out = []
+    for m in (193, 257):
+        cand = [p for p in probs if max(p.n) == m]
+        out.append(min(cand, key=lambda p: p.points))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df32", "bf16x3"])
+def test_batched_size_classes_193_and_257_against_oracle(idp, precision):
+    # inside one batched launch with two smaller problems of the same workload
+    probs = _c5_pick() + [p for p in w.c5_batch() if max(p.n) <= 65][:2]
+    plans = [idp.create_plan(3, p.n, p.h, 6) for p in probs]
+    prec = {"fp64": idp.IDP_PRECISION_FP64, "df32": idp.IDP_PRECISION_DF32,
+            "bf16x3": idp.IDP_PRECISION_MIXED_BF16X3}[precision]
+    for pl in plans:
+        idp.plan_set(pl, idp.IDP_KEY_PRECISION, prec)
+        idp.plan_set(pl, idp.IDP_KEY_AUTOTUNE, 1)
+    rhos = [to_dev(p.rho()) for p in probs]
+    outs = [to_dev(np.zeros(p.n)) for p in probs]
+    for _ in range(2):   # the captured graph and its replay
+        idp.solve_batched(plans, rhos, outs)
+        for pl in plans:
+            idp.plan_status(pl)
+        for p, o in zip(probs, outs):
+            key = ("c5_%s" % "x".join(map(str, p.n)), 6)
+            if key not in _REF:
+                _REF[key] = {"phi": osolve.solve(p.rho(), p.h, 6, boundary="convolution")}
+            tol = TOL if precision != "bf16x3" else 1e-6 * np.sqrt(max(p.n) - 2)
+            assert rel_max(o.cpu().numpy(), _REF[key]["phi"]) < tol, (precision, p.n)
+
+
+def test_257_cube_sine_mode_in_every_mode(idp):
+    # phi* of one sine mode is exact (closed form): the sine transforms at M = 256
+    # in every precision mode, independent of the oracle
+    n = (257, 257, 257)
+    box = ((0.0, 1.0), (0.0, 1.0), (0.0, 1.0))
+    coords = [np.linspace(a, b, k) for (a, b), k in zip(box, n)]
+    h = [c[1] - c[0] for c in coords]
+    X = np.meshgrid(*coords, indexing="ij")
+    modes = (5, 2, 9)
+    rho = np.ones(n)
+    lam = 0.0
+    for s in range(3):
+        rho = rho * np.sin(modes[s] * np.pi * X[s])
+        lam += (modes[s] * np.pi) ** 2
+    plan = idp.create_plan(3, n, h, 6)
+    r = to_dev(rho)
+    for prec, tol in ((idp.IDP_PRECISION_FP64, TOL), (idp.IDP_PRECISION_DF32, TOL),
+                      (idp.IDP_PRECISION_MIXED_BF16X3, 1e-6 * np.sqrt(255)),
+                      (idp.IDP_PRECISION_MIXED_TF32X3, 4e-6 * np.sqrt(255))):
+        idp.plan_set(plan, idp.IDP_KEY_PRECISION, prec)
+        ps = run_stage(idp, plan, idp.IDP_STAGE_PHISTAR, r, n)
+        assert rel_max(ps, -rho / lam) < tol, prec

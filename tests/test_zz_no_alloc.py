@@ -32,11 +32,13 @@ def idp():
 
 
 def _reference(idp, prob):
-    """u1 from the plan-based entry point and the oracle's R of that u1."""
+    """u1 from the plan-based entry point, the oracle's R of that u1, and the
+    plan-based entry point's own R (IDP_STAGE_R, spectral form)."""
     plan = idp.create_plan(prob.d, prob.n, prob.h, 6)
     r = to_dev(prob.rho())
     u1 = run_stage(idp, plan, idp.IDP_STAGE_U1, r, prob.n)
-    return u1, oharm.rhs6(u1, prob.h)
+    R_plan = run_stage(idp, plan, idp.IDP_STAGE_R, r, tuple(k - 2 for k in prob.n))
+    return u1, oharm.rhs6(u1, prob.h), R_plan
 
 
 def test_noalloc_rhs_matches_plan_rhs_on_consecutive_calls(idp):
@@ -49,7 +51,7 @@ def test_noalloc_rhs_matches_plan_rhs_on_consecutive_calls(idp):
     # two calls in a row per problem, problems interleaved, so each call starts
     # from scratch contents left by a different problem
     for rep in range(2):
-        for p, (u1, Rref) in zip(probs, refs):
+        for p, (u1, Rref, R_plan) in zip(probs, refs):
             u1d = to_dev(u1)
             out = torch.full(tuple(k - 2 for k in p.n), float("nan"), dtype=torch.float64,
                              device=u1d.device)
@@ -62,6 +64,13 @@ def test_noalloc_rhs_matches_plan_rhs_on_consecutive_calls(idp):
             core = tuple(slice(1, -1) for _ in got.shape)
             assert np.abs(got - Rref)[core].max() <= amp * du, (rep, p.name)
             assert np.abs(got - Rref).max() <= amp * 15 ** p.d * du, (rep, p.name)
+            # the same R as the existing entry point: the plan's IDP_STAGE_R is formed
+            # in spectral form from u1's sine coefficients, so the two differ by the
+            # stencil applied to the rounding of u1's nodal values, which come out of
+            # an FP64 transform (at most 2 eps per FFT stage, log2(n) stages per axis)
+            du_t = 2 * sum(np.log2(k) for k in p.n) * np.finfo(np.float64).eps * np.abs(u1).max()
+            assert np.abs(got - R_plan)[core].max() <= amp * du_t, (rep, p.name)
+            assert np.abs(got - R_plan).max() <= amp * 15 ** p.d * du_t, (rep, p.name)
             if rep == 0:
                 first[p.name] = got
             else:
@@ -79,3 +88,9 @@ def test_noalloc_rejects_problems_beyond_its_scratch(idp):
                               None)
     assert rc == idp.IDP_ESCRATCH
     assert "scratch" in idp.strerror(rc)
+    # node counts whose product would overflow 64 bits are refused the same way
+    huge = (2 ** 31 + 8, 2 ** 31 + 8, 8)
+    rc = lib.idp_rhs6_noalloc(3, (ctypes.c_int64 * 3)(*huge), (ctypes.c_double * 3)(0.1, 0.1, 0.1),
+                              ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr() + 8),
+                              None)
+    assert rc == idp.IDP_ESCRATCH
