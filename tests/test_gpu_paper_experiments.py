@@ -93,12 +93,22 @@ def test_table1_convergence_rates(idp):
             assert abs(r4 - g4) < 1.5, (diff, r4, g4)
 
 
+ORACLE_RATES = os.path.join(os.path.dirname(__file__), "golden", "table1_oracle_rates.txt")
+
+
+def _oracle_rates():
+    """The oracle's rates on the same workload and grids (tests/golden/make_table1_oracle.py)."""
+    rows = [l.split() for l in open(ORACLE_RATES) if l.strip() and not l.startswith("#")]
+    return {(int(r[0]), r[1]): (float(r[2]), float(r[3])) for r in rows}
+
+
 def test_table1_at_the_papers_panel_counts(idp):
     # the paper's own window: 6th-order rates over M = 20..100 (h = 0.1..0.02),
     # 4th-order rates over M = 100..200 (h = 0.02..0.01).  Counts the transforms
     # do not take are padded (section 2: the domain is extended by a few panels,
-    # h unchanged); the error is measured at the nodes of the [-1,1]^3 grid
+    # h unchanged); the error is measured at the nodes of the [-1,1]^3 grid.
     gold = _golden()
+    orc = _oracle_rates()
     M6 = (20, 28, 40, 56, 80, 100)
     M4 = (100, 140, 200)
     report = []
@@ -110,8 +120,17 @@ def test_table1_at_the_papers_panel_counts(idp):
     for diff, r4, g4, r6, g6 in report:
         print("  %d     %5.2f (%4.1f)        %5.2f (%4.1f)" % (diff, r4, g4, r6, g6))
     for diff, r4, g4, r6, g6 in report:
-        assert abs(r6 - g6) < 1.0 or (diff >= 6 and r6 > 8.0), (diff, r6, g6)
-        assert abs(r4 - g4) < 1.0, (diff, r4, g4)
+        # the GPU solver reproduces the oracle's rates on the same (padded) grids
+        o4, o6 = orc[diff, "padded"]
+        assert abs(r6 - o6) < 0.05 and abs(r4 - o4) < 0.05, (diff, r4, o4, r6, o6)
+        # and the paper's, except where the method as read does not (documented):
+        # 6th order C^6 (8.7 against 9.8) and 4th order C^4 (5.8 against 6.6; three
+        # grids in the window, where the 4th-order harmonic error and the spectral
+        # error of a C^4 density are of one size)
+        if diff != 6:
+            assert abs(r6 - g6) < 0.2, (diff, r6, g6)
+        if diff != 4:
+            assert abs(r4 - g4) < 0.2, (diff, r4, g4)
 
 
 def test_domain_size_invariance(idp):
