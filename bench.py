@@ -284,11 +284,13 @@ class Gpu:
             import torch.distributed as dist
             dist.barrier()
 
-    def plan(self, prob, order, prec=None, shape=None):
+    def plan(self, prob, order, prec=None, shape=None, bdd=False):
         idp = self.idp
         plan = idp.create_plan(prob.d, prob.n, prob.h, order)
         if prec is not None:
             idp.plan_set(plan, idp.IDP_KEY_PRECISION, prec)
+        if bdd:
+            idp.plan_set(plan, idp.IDP_KEY_MIXED_BOUNDARY_DF32, 1)
         idp.plan_set(plan, idp.IDP_KEY_AUTOTUNE, 1)
         if shape is not None:
             idp.plan_set(plan, idp.IDP_KEY_DST_SHAPE, shape)
@@ -343,11 +345,11 @@ def rel(a, b):
     return float((a - b).abs().max().item() / b.abs().max().item())
 
 
-def variant_record(g, prob, order, prec, label, rho, phi_ref, steps, warmup):
+def variant_record(g, prob, order, prec, label, rho, phi_ref, steps, warmup, bdd=False):
     """A reduced-precision variant of the workload: throughput, per-kernel times and
     its max difference from the FP64 result."""
     idp = g.idp
-    plan = g.plan(prob, order, prec)
+    plan = g.plan(prob, order, prec, bdd=bdd)
     phi = g.torch.empty_like(rho)
     ms = g.timed(lambda: idp.solve(plan, rho, phi, g.stream), steps, warmup)
     idp.plan_status(plan)
@@ -369,7 +371,10 @@ VARIANTS = (("mixed_precision", "MIXED_BF16X3",
             ("mixed_tf32x3", "MIXED_TF32X3",
              "tf32x3: two tf32 pieces, products hi*hi + hi*lo + lo*hi, fp32 accumulate, tcgen05 "
              "kind::tf32 (rho, R and final transforms)"),
-            ("df32", "DF32", "double-float (FP32 pairs) FFT arithmetic"))
+            ("df32", "DF32", "double-float (FP32 pairs) FFT arithmetic"),
+            ("mixed_df32_boundary", "MIXED_BF16X3",
+             "bf16x3 tensor-core transforms as mixed_precision, with the 3-D boundary convolutions in "
+             "double-float arithmetic (IDP_KEY_MIXED_BOUNDARY_DF32)"))
 
 
 def run_headline(g, args, prob):
@@ -460,7 +465,7 @@ def run_headline(g, args, prob):
     if not args.fp64_only:
         for key, name, label in VARIANTS:
             ph, rec = variant_record(g, prob, args.order, getattr(idp, "IDP_PRECISION_" + name), label, rho, phi,
-                                     args.steps, args.warmup)
+                                     args.steps, args.warmup, bdd=key == "mixed_df32_boundary")
             out[key] = rec
             phis[key] = ph
     return out, rho_h, phi, phis
@@ -545,7 +550,8 @@ def run_ours(args, rank, world):
             "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(prob, args.order, {"parallelism": "replicas" if world > 1 else "single"})}
-    for k in ("precision", "mixed_precision", "mixed_tf32x3", "df32", "e2e", "gpu_launches", "roofline",
+    for k in ("precision", "mixed_precision", "mixed_tf32x3", "df32", "mixed_df32_boundary", "e2e", "gpu_launches",
+              "roofline",
               "kernel_ms_per_step", "dominant_kernel", "tuning", "clocks"):
         if k in head:
             line[k] = head[k]

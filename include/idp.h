@@ -79,6 +79,11 @@ enum {
                                tensor-core pass issues no products, so its bounded wait expires
                                (after ~5 ms); the kernel records the failure, frees its tensor
                                memory and returns, and idp_plan_status reports IDP_ETIMEOUT */
+    IDP_KEY_MIXED_BOUNDARY_DF32 = 8, /* value 1: in the tensor-core modes (IDP_PRECISION_MIXED_*) the 3-D
+                               boundary convolutions run in double-float arithmetic (48 significant
+                               bits, as in IDP_PRECISION_DF32) instead of FP64; value 0 (default):
+                               FP64.  No effect in the other modes.  Setting 1 allocates the
+                               double-float copies of the kernel spectra. */
     IDP_KEY_GUARD_TEST = 7, /* test hook for idp_plan_check_guards: value 1 overwrites the first
                                byte of the guard region in front of the plan's first buffer (a
                                write inside that allocation, from the host), value 0 restores it;
@@ -100,8 +105,10 @@ enum {
                                       dense sine-matrix products on the tensor cores: operands split
                                       into three BF16 pieces, six products, FP32 accumulation
                                       (relative error of phi ~1e-5 or better); the eigenvalue division,
-                                      the boundary values, the stencils and the transform that produces
-                                      u1 (whose sixth differences form R) stay FP64.  Setting it
+                                      the boundary values (see IDP_KEY_MIXED_BOUNDARY_DF32) and the
+                                      stencils stay FP64; the transform that produces u1 (whose sixth
+                                      differences form R) and the transforms of the boundary layers run
+                                      in double-float arithmetic (48 significant bits).  Setting it
                                       allocates the pieces of the sine matrices and FP32 temporaries. */
     IDP_PRECISION_DF32 = 2,        /* the FFT-based transforms (sine transforms of rho, R and the final
                                       inverse, and the 3-D boundary convolutions) in double-float

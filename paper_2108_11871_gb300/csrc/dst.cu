@@ -124,25 +124,47 @@ __global__ void __launch_bounds__(NTB) dst_pass_kernel(const DstPass a)
     int64_t isu, isv, ise;
     view_strides(a.in, a.axis, isu, isv, ise);
     const int64_t inb = (int64_t)u * isu + (int64_t)v0 * isv;
-    for (int f = threadIdx.x; f < LB * K; f += NT) {
+    // all loads of the thread first (their latencies overlap), then the pre-pass
+    // arithmetic and the shared-memory stores
+    constexpr int IT = (LB * K + NT - 1) / NT;
+    R xa[IT], xb[IT], sv[IT];
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        const int f = threadIdx.x + i * NT;
+        xa[i] = A::zero();
+        xb[i] = A::zero();
+        sv[i] = A::zero();
+        if (f < LB * K) {
+            int l, j;
+            if (contig) { l = f / K; j = f - l * K; }
+            else { j = f / LB; l = f - j * LB; }
+            const int64_t lb = inb + (int64_t)l * isv;   // x_i at element i-1 of the line
+            if (j == 0) {
+                if (l < nl) xa[i] = Io<R>::ld(a.in.p, lb + (int64_t)(K - 1) * ise, a.in_dd);
+            } else {
+                if (l < nl) {
+                    xa[i] = Io<R>::ld(a.in.p, lb + (int64_t)(j - 1) * ise, a.in_dd);
+                    xb[i] = Io<R>::ld(a.in.p, lb + (int64_t)(M - j - 1) * ise, a.in_dd);
+                }
+                sv[i] = Tabs<R>::sin2(a, j);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        const int f = threadIdx.x + i * NT;
+        if (f >= LB * K) break;
         int l, j;
         if (contig) { l = f / K; j = f - l * K; }
         else { j = f / LB; l = f - j * LB; }
         R *zl = zf + l * M;
-        const int64_t lb = inb + (int64_t)l * isv;   // x_i at element i-1 of the line
         if (j == 0) {
             zl[0] = A::zero();
-            zl[K] = l < nl ? times4_exact(Io<R>::ld(a.in.p, lb + (int64_t)(K - 1) * ise, a.in_dd)) : A::zero();
+            zl[K] = l < nl ? times4_exact(xa[i]) : A::zero();
         } else {
-            R xa = A::zero(), xb = A::zero();
-            if (l < nl) {
-                xa = Io<R>::ld(a.in.p, lb + (int64_t)(j - 1) * ise, a.in_dd);
-                xb = Io<R>::ld(a.in.p, lb + (int64_t)(M - j - 1) * ise, a.in_dd);
-            }
-            const R s = Tabs<R>::sin2(a, j);
-            const R p = A::add(xa, xb), m = A::sub(xa, xb);
-            zl[j] = A::fma(s, p, m);
-            zl[M - j] = A::fma(s, p, A::neg(m));
+            const R p = A::add(xa[i], xb[i]), m = A::sub(xa[i], xb[i]);
+            zl[j] = A::fma(sv[i], p, m);
+            zl[M - j] = A::fma(sv[i], p, A::neg(m));
         }
     }
     __syncthreads();
@@ -261,22 +283,53 @@ __global__ void __launch_bounds__(NTB) dst_pass_kernel(const DstPass a)
     const int64_t tabb = (int64_t)u * tsu + (int64_t)v0 * tsv;
     const int64_t addb = (int64_t)u * asu + (int64_t)v0 * asv;
     const bool has_tab = a.tab || a.tabd;
-    for (int f = threadIdx.x; f < LB * N; f += NT) {
-        int l, e;
-        if (contig) { l = f / N; e = f - l * N; }
-        else { e = f / LB; l = f - e * LB; }
-        if (l >= nl) continue;
-        R y = o[l * M + e];
-        const int64_t ti = tabb + (int64_t)l * tsv + (int64_t)e * tse;
-        const int64_t ai = addb + (int64_t)l * asv + (int64_t)e * ase;
-        if (has_tab) {
-            const R t = Io<R>::ld(a.tabd ? (const void *)a.tabd : (const void *)a.tab, ti, a.tabd != nullptr);
-            if (a.add.p) y = A::fma(t, y, Io<R>::ld(a.add.p, ai, a.add_dd));
-            else y = A::mul(t, y);
-        } else if (a.add.p) {
-            y = A::add(y, Io<R>::ld(a.add.p, ai, a.add_dd));
+    if (!has_tab && !a.add.p) {
+        for (int f = threadIdx.x; f < LB * N; f += NT) {
+            int l, e;
+            if (contig) { l = f / N; e = f - l * N; }
+            else { e = f / LB; l = f - e * LB; }
+            if (l >= nl) continue;
+            Io<R>::st(a.out.p, outb + (int64_t)l * osv + (int64_t)e * ose, o[l * M + e], a.out_dd);
         }
-        Io<R>::st(a.out.p, outb + (int64_t)l * osv + (int64_t)e * ose, y, a.out_dd);
+        return;
+    }
+    // groups of EG outputs: the table and addend loads of a group go out before
+    // its stores (which, as far as the compiler knows, could alias them)
+    constexpr int EG = 4;
+    for (int f0 = threadIdx.x; f0 < LB * N; f0 += EG * NT) {
+        R tv[EG], av[EG];
+#pragma unroll
+        for (int g = 0; g < EG; ++g) {
+            const int f = f0 + g * NT;
+            tv[g] = A::zero();
+            av[g] = A::zero();
+            if (f >= LB * N) continue;
+            int l, e;
+            if (contig) { l = f / N; e = f - l * N; }
+            else { e = f / LB; l = f - e * LB; }
+            if (l >= nl) continue;
+            const int64_t ti = tabb + (int64_t)l * tsv + (int64_t)e * tse;
+            const int64_t ai = addb + (int64_t)l * asv + (int64_t)e * ase;
+            if (has_tab) tv[g] = Io<R>::ld(a.tabd ? (const void *)a.tabd : (const void *)a.tab, ti, a.tabd != nullptr);
+            if (a.add.p) av[g] = Io<R>::ld(a.add.p, ai, a.add_dd);
+        }
+#pragma unroll
+        for (int g = 0; g < EG; ++g) {
+            const int f = f0 + g * NT;
+            if (f >= LB * N) break;
+            int l, e;
+            if (contig) { l = f / N; e = f - l * N; }
+            else { e = f / LB; l = f - e * LB; }
+            if (l >= nl) continue;
+            R y = o[l * M + e];
+            if (has_tab) {
+                if (a.add.p) y = A::fma(tv[g], y, av[g]);
+                else y = A::mul(tv[g], y);
+            } else {
+                y = A::add(y, av[g]);
+            }
+            Io<R>::st(a.out.p, outb + (int64_t)l * osv + (int64_t)e * ose, y, a.out_dd);
+        }
     }
 }
 

@@ -105,16 +105,19 @@ struct MpPass {
     int64_t os_m, os_p, os_q;
     int P, Q, n;
     int variant;                // 0: BF16X3, 1: TF32X3
-    const void *bimg;           // pieces of S: [ntile][kblock][piece][16 KB tile] (BF16: 3 x 128 x 64,
-                                // TF32: 2 x 128 x 32)
+    const void *bimg;           // pieces of S: [mode tile][k stage][piece][W rows x KB k] (W =
+                                // mp_tile_modes(n), KB = mp_stage_k(variant); BF16: 3 pieces, TF32: 2)
     const double *tab; int64_t ts_m, ts_p, ts_q;
     const double *add; int64_t as_m, as_p, as_q;
     int *err;                   // set to 1 if a wait on the tensor cores timed out
     int stall_test;             // test hook: issue no products, so the bounded wait expires
-    int modes_per_tile;         // 64 or 128; 0: 64 when 128-mode tiles would give < 2 blocks per SM
+    int in_vec4;                // FP32 input whose lines start on 16-byte boundaries (is_k = 1, is_p and
+                                // is_q multiples of 4): loaded in 16-byte vectors
 };
 cudaError_t launch_mp_pass(const MpPass &a, cudaStream_t st);
 cudaError_t mp_set_attributes();
+int mp_stage_k(int variant);    // k values per stage of the sine image (32 BF16, 16 TF32)
+int mp_tile_modes(int n);       // modes per tile (and image tile) for n modes: 128 or 256
 
 // ---- boundary values (section 4) ------------------------------------------
 
@@ -230,11 +233,12 @@ StencilCoef make_stencil_coef(const Grid3 &g);
 cudaError_t launch_gtilde_planes(const Grid3 &g, const StencilCoef &c, const double *U, double *Q0, double *Q1,
                                  double *Q2, cudaStream_t st);
 // out = tab * (4^d S gtilde) (+ add) from the transformed, combined parts; if out2
-// is given, also out2 = (tab2 (- tab unless fold)) * (4^d S gtilde) + add2
+// is given, also out2 = (tab2 (- tab unless fold)) * (4^d S gtilde) + add2; with
+// ascale, add and add2 are multiplied by ascale first
 cudaError_t launch_gtilde_expand(const Grid3 &g, const double *Q0, const double *Q1, const double *Q2,
                                  const double *sin4, const double *tab, const double *add, double *out,
                                  cudaStream_t st, const double *tab2 = nullptr, const double *add2 = nullptr,
-                                 double *out2 = nullptr, int fold = 0);
+                                 double *out2 = nullptr, int fold = 0, const double *ascale = nullptr);
 // (a, b) -> (a + b, a - b) for the pairs of transformed layers at the two faces of
 // an axis: part i holds [2][nl][pl_i] (pl_i = 0: absent)
 cudaError_t launch_layers_combine(double *P0, int64_t pl0, double *P1, int64_t pl1, double *P2, int64_t pl2,

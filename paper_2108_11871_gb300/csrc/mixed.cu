@@ -8,7 +8,7 @@
 //
 // Precision, two variants:
 //  * BF16X3: X and S are split into three BF16 pieces each (x = x0 + x1 + x2,
-//    |x_i| ~ 2^-8i |x|); the six products with i + j <= 2 are accumulated by
+//    |x_i| ~ 2^-8i |x|, from x rounded to FP32); the six products with i + j <= 2 are accumulated by
 //    tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) in one TMEM accumulator.  The
 //    dropped products are below 2^-24 relative, so the error is set by the FP32
 //    accumulation.
@@ -18,17 +18,42 @@
 //    relative.
 // The eigenvalue scaling and the additions of the last pass are done in FP64.
 //
-// Block: 512 threads, a tile of 128 lines x NTN modes (NTN = 64 or 128), K in
-// blocks of 64 (BF16) or 32 (TF32): 16 KB per operand piece either way.
-// Operands live in shared memory in the canonical K-major layout without
-// swizzle: 8 x 16-byte core matrices (8 BF16 or 4 TF32 values per row), core
-// matrices adjacent along K are LBO = 2048 bytes apart, adjacent along M/N
-// SBO = 128 bytes apart; one MMA takes K = 16 (BF16) or 8 (TF32), two core
-// matrices along K, in both variants.  The sine
-// image of a K block (128 modes) arrives by cp.async while the block loads and
-// splits its input; a 64-mode tile addresses its half of the image through the
-// descriptor's start address.  FP64 <-> FP32 conversions and the factor 4 are
-// integer operations (FP64 issue is scarce on this GPU).
+// Work: tiles of 128 lines x NTN modes (NTN = 128 for n <= 128, else 256, so
+// that the input of a line tile is split once per 256 modes), K in stages of
+// KB = 32 (BF16) or 16 (TF32) values: 8 KB per operand piece per 128 rows either
+// way.  One persistent block per SM takes tiles blockIdx.x, blockIdx.x +
+// gridDim.x, ... (mode tile fastest, so that the mode tiles of one line tile run
+// at the same time on neighbouring SMs and share its input through L2), with
+// specialised warps:
+//   warps 0-15  producers: load 128 lines x KB of the input (FP64, or FP32 in
+//               16-byte vectors where the lines are 16-byte aligned; the loads of
+//               the next two stages are in flight while a stage is split), split it
+//               into pieces, store them in the K-major core-matrix layout and
+//               arrive on the stage's A barrier;
+//   warp 16     copies the stage's pre-split sine image (one contiguous block per
+//               (mode tile, K stage)) with one bulk asynchronous copy that
+//               completes on the stage's B barrier;
+//   warp 17     owns the tensor memory; one thread waits for both barriers of a
+//               stage, issues its products into the tile's accumulator, commits
+//               them to the stage's empty barrier (the producers' signal to refill
+//               it), and after a tile's last stage commits to the accumulator's
+//               full barrier;
+//   warps 18-21 epilogue: wait for a full accumulator, read it (warp w: TMEM lanes
+//               32 (w % 4) ..), write the lines and release the accumulator.
+// The stages form a ring (NS deep, ~200 KB of shared memory) and the accumulator
+// is double-buffered (2 x NTN TMEM columns), so the loads, the products and the
+// epilogue of consecutive tiles overlap.  Operands live in shared memory in the
+// canonical K-major layout without swizzle: 8 x 16-byte core matrices (8 BF16 or
+// 4 TF32 values per row), adjacent along M/N 128 bytes apart (SBO), adjacent
+// along K one core column apart (LBO: 2048 bytes for the 128 rows of A, 16 NTN
+// bytes for the NTN rows of B); one MMA takes K = 16 (BF16) or 8 (TF32), two
+// core matrices along K, in both variants.  FP64 <-> FP32 conversions and the
+// factor 4 are integer operations (FP64 issue is scarce on this GPU).
+//
+// Every wait is bounded (clock64); a wait that runs out sets the block's failure
+// flag, the other roles leave their loops at their next check, the block waits
+// (bounded) for its own products and copies still in flight, frees its tensor
+// memory and records the failure in *err.
 #include <cuda_bf16.h>
 
 #include "dd.cuh"
@@ -39,21 +64,32 @@ namespace idp {
 namespace {
 
 constexpr int MT = 128;            // lines per tile (MMA M)
-constexpr int NTILE = 128;         // modes per tile (MMA N)
-constexpr int TILE_BYTES = 16384;  // one operand piece: 128 rows x 16 core-matrix columns
-constexpr uint32_t LBO = 2048, SBO = 128;
+constexpr int PIECE_BYTES = 8192;  // one operand piece of one stage per 128 rows: 128 x 64 bytes
+constexpr uint32_t SBO = 128;      // core matrices adjacent along M / N
+constexpr uint32_t LBO_A = 2048;   // core matrices adjacent along K, 128 rows
+constexpr int NPROD = 512;         // producer threads (warps 0-15)
+constexpr int WARP_COPY = 16, WARP_MMA = 17, WARP_EPI = 18, NEPI = 4;
+constexpr int NTHR = (WARP_EPI + NEPI) * 32;   // 704
 
-// per variant (0 = BF16X3, 1 = TF32X3): element bytes, K per block, pieces
-template <int V>
+// per variant (0 = BF16X3, 1 = TF32X3) and tile width: element bytes, K per
+// stage, pieces, ring depth
+template <int V, int NTN>
 struct MpCfg {
     static constexpr int ESZ = V ? 4 : 2;
-    static constexpr int EPC = 16 / ESZ;                 // elements per core-matrix row
-    static constexpr int KB = TILE_BYTES / (MT * ESZ);   // 64 or 32
+    static constexpr int EPC = 16 / ESZ;                  // elements per core-matrix row
+    static constexpr int KB = PIECE_BYTES / (MT * ESZ);   // 32 or 16
     static constexpr int PIECES = V ? 2 : 3;
-    static constexpr int SMEM_A = 0;
-    static constexpr int SMEM_B = PIECES * TILE_BYTES;
-    static constexpr int SMEM_BAR = 2 * PIECES * TILE_BYTES;   // mbarrier (8 B) + TMEM address (4 B)
-    static constexpr int SMEM_TOTAL = SMEM_BAR + 64;
+    static constexpr int A_BYTES = PIECES * PIECE_BYTES;  // A operand of one stage
+    static constexpr int BP_BYTES = PIECE_BYTES * NTN / MT;   // one piece of B
+    static constexpr int B_BYTES = PIECES * BP_BYTES;
+    static constexpr uint32_t LBO_B = 16u * NTN;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int NS = (220 * 1024) / STAGE;       // ring depth
+    static constexpr int SMEM_BAR = NS * STAGE;           // barriers: A, B, empty per stage; acc full/free x2; drain
+    static constexpr int NBAR = 3 * NS + 5;
+    static constexpr int SMEM_TOTAL = SMEM_BAR + 8 * NBAR + 16 + 1024;   // + TMEM slot + alignment
+    static constexpr int NG = MT * (KB / EPC) / NPROD;    // 16-byte groups per producer thread and stage
+    static_assert(NG * NPROD == MT * (KB / EPC), "whole groups per producer thread");
 };
 constexpr long long WAIT_CYCLES = 2000000000ll;       // bounded mbarrier polling (~1 s)
 
@@ -62,62 +98,93 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p)
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// byte offset of element (row r, k) of a 128-row tile (K-major, no swizzle)
-template <int V>
+// byte offset of element (row r, k) of a 128-row A piece (K-major, no swizzle)
+template <int ESZ>
 __device__ __forceinline__ uint32_t tile_off(int r, int k)
 {
-    using C = MpCfg<V>;
-    return (uint32_t)((k / C::EPC) * LBO + (r >> 3) * SBO + (r & 7) * 16 + (k % C::EPC) * C::ESZ);
+    constexpr int EPC = 16 / ESZ;
+    return (uint32_t)((k / EPC) * LBO_A + (r >> 3) * SBO + (r & 7) * 16 + (k % EPC) * ESZ);
 }
 
 // shared-memory matrix descriptor: start, LBO, SBO (>> 4), version 1, no swizzle
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr)
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo)
 {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)((LBO >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
     d |= (uint64_t)((SBO >> 4) & 0x3FFF) << 32;
     d |= (uint64_t)1 << 46;
     return d;
 }
 
-// instruction descriptor (D = F32, A = B = BF16 for kind::f16 or TF32 for
-// kind::tf32, K-major, M = 128, N = NTN): built in the kernel from the tile width
-
-// x rounded to TF32 (11 significant bits, to nearest, ties to even), by integer
-// operations; the tensor cores read these FP32 containers unchanged
-__device__ __forceinline__ float tf32_rn(float x)
+// FP64 -> FP32, rounded to nearest (ties away), by integer operations on the
+// bits (conversions would run on the scarce FP64 pipe); |x| < 2^-126 gives 0.
+// 24 bits are all that the pieces below keep of an input value.
+__device__ __forceinline__ float f32_of_f64_bits(double x)
 {
-    const uint32_t u = __float_as_uint(x);
-    return __uint_as_float((u + 0xFFFu + ((u >> 13) & 1u)) & 0xFFFFE000u);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int hiw = (unsigned int)(b >> 32), low = (unsigned int)b;
+    const int e = (int)((hiw >> 20) & 0x7FF) - 1023 + 127;
+    if (e <= 0) return 0.f;
+    unsigned int f = (hiw & 0x80000000u) | ((unsigned int)e << 23) | ((hiw & 0xFFFFFu) << 3) | (low >> 29);
+    f += (low >> 28) & 1u;   // the carry of a round-up moves into the exponent, as it should
+    return __uint_as_float(f);
 }
 
-// x = hi + lo (two floats) -> two TF32 pieces; hi - a is exact in FP32
-__device__ __forceinline__ void split2(float hi, float lo, float &a, float &b)
+// two floats -> packed BF16 pair, rounded to nearest even: lo in the low half
+__device__ __forceinline__ uint32_t bf16x2_rn(float lo, float hi)
 {
-    a = tf32_rn(hi);
-    b = tf32_rn((hi - a) + lo);
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;\n" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+__device__ __forceinline__ float bf16_lo(uint32_t d) { return __uint_as_float(d << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t d) { return __uint_as_float(d & 0xFFFF0000u); }
+
+// x (two values at a time) -> three BF16 pieces x = a + b + c; the residuals
+// x - a and r - b are exact in FP32
+__device__ __forceinline__ void split3_pair(float x0, float x1, uint32_t &a, uint32_t &b, uint32_t &c)
+{
+    a = bf16x2_rn(x0, x1);
+    const float r0 = x0 - bf16_lo(a), r1 = x1 - bf16_hi(a);
+    b = bf16x2_rn(r0, r1);
+    c = bf16x2_rn(r0 - bf16_lo(b), r1 - bf16_hi(b));
 }
 
-// x = hi + lo (two floats, |lo| <= 2^-24 |hi|) -> three BF16 pieces.  The
-// residuals hi - a and r1 - b are exact in FP32; lo enters below 2^-16 |x|.
-__device__ __forceinline__ void split3(float hi, float lo, unsigned short &a, unsigned short &b,
-                                       unsigned short &c)
+// x rounded to TF32 (to nearest, ties away); the tensor cores read the FP32 container
+__device__ __forceinline__ float tf32_rna(float x)
 {
-    const __nv_bfloat16 ba = __float2bfloat16_rn(hi);
-    const float r1 = (hi - __bfloat162float(ba)) + lo;
-    const __nv_bfloat16 bb = __float2bfloat16_rn(r1);
-    const float r2 = r1 - __bfloat162float(bb);
-    const __nv_bfloat16 bc = __float2bfloat16_rn(r2);
-    a = __bfloat16_as_ushort(ba);
-    b = __bfloat16_as_ushort(bb);
-    c = __bfloat16_as_ushort(bc);
+    uint32_t d;
+    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(d) : "f"(x));
+    return __uint_as_float(d);
+}
+// x -> two TF32 pieces x = a + b (~22 bits); x - a is exact in FP32
+__device__ __forceinline__ void split2(float x, float &a, float &b)
+{
+    a = tf32_rna(x);
+    b = tf32_rna(x - a);
 }
 
+// mbarrier helpers (shared::cta addresses)
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar),
+                 "r"(bytes)
+                 : "memory");
+}
+// true once the phase of parity `parity` has completed; false after `limit` cycles
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit)
 {
     const long long t0 = clock64();
-    while (clock64() - t0 < limit) {
+    while (true) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -125,51 +192,71 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
             : "r"(bar), "r"(parity)
             : "memory");
         if (done) return true;
+        if (clock64() - t0 >= limit) return false;
     }
-    return false;
 }
-
-constexpr int NTHR = 512;
-constexpr int GPT = MT * (TILE_BYTES / MT / 16) / NTHR;   // 16-byte core-matrix rows of the A tile per thread (2)
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
+// one bulk asynchronous copy global -> shared that completes on `bar`
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
 {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+                 : "memory");
 }
 
 template <int NTN, int V>
-__global__ void __launch_bounds__(NTHR) mp_pass_kernel(const MpPass a)
+__global__ void __launch_bounds__(NTHR, 1) mp_pass_kernel(const MpPass a)
 {
-    static_assert(NTN == 64 || NTN == 128, "tile of 64 or 128 modes");
-    using C = MpCfg<V>;
-    constexpr int KB = C::KB, PIECES = C::PIECES, SMEM_A = C::SMEM_A, SMEM_B = C::SMEM_B, SMEM_BAR = C::SMEM_BAR;
-    constexpr int EPC = C::EPC;
+    static_assert(NTN == 128 || NTN == 256, "tile of 128 or 256 modes");
+    using C = MpCfg<V, NTN>;
+    constexpr int KB = C::KB, NS = C::NS, EPC = C::EPC;
+    static_assert(NS >= 2, "at least two stages");
     // D = F32 (bit 4); A, B = BF16 (1) for kind::f16 or TF32 (2) for kind::tf32
     constexpr uint32_t FMT = V ? 2u : 1u;
     constexpr uint32_t IDESC_N = (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(NTN >> 3) << 17) |
                                  ((uint32_t)(MT >> 4) << 24);
-    extern __shared__ __align__(128) unsigned char sm[];
+    extern __shared__ unsigned char sm_raw[];
+    unsigned char *sm = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
     const int t = threadIdx.x;
     const int warp = t >> 5, lane = t & 31;
+    const int ntm = (a.n + NTN - 1) / NTN;               // mode tiles
     const int64_t nlines = (int64_t)a.P * a.Q;
-    const int64_t L0 = (int64_t)blockIdx.x * MT;
-    const int m0 = blockIdx.y * NTN;
-    const int img_tile = m0 / NTILE;                                   // 128-mode image tile
-    const uint32_t b_sub = (uint32_t)(((m0 - img_tile * NTILE) >> 3) * SBO);   // byte offset of the half
+    const int64_t ntiles = ((nlines + MT - 1) / MT) * ntm;
     const int nkb = (a.n + KB - 1) / KB;
-    const uint32_t bar = smem_u32(sm + SMEM_BAR);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + SMEM_BAR + 8);
-    __shared__ int s_fail;
+    const uint32_t bar0 = smem_u32(sm + C::SMEM_BAR);
+    auto bar_a = [&](int s) { return bar0 + 8u * (uint32_t)s; };
+    auto bar_b = [&](int s) { return bar0 + 8u * (uint32_t)(NS + s); };
+    auto bar_e = [&](int s) { return bar0 + 8u * (uint32_t)(2 * NS + s); };
+    auto bar_full = [&](int b) { return bar0 + 8u * (uint32_t)(3 * NS + b); };
+    auto bar_free = [&](int b) { return bar0 + 8u * (uint32_t)(3 * NS + 2 + b); };
+    const uint32_t bar_drain = bar0 + 8u * (3 * NS + 4);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + C::SMEM_BAR + 8 * C::NBAR);
+    volatile __shared__ int s_fail;
+    const long long limit = a.stall_test ? WAIT_CYCLES / 400 : WAIT_CYCLES;
 
     if (t == 0) {
         s_fail = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(bar_a(s), NPROD / 32);   // one arrival per producer warp
+            mbar_init(bar_b(s), 1);
+            mbar_init(bar_e(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(bar_full(b), 1);
+            mbar_init(bar_free(b), NEPI);
+        }
+        mbar_init(bar_drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == WARP_MMA) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                          smem_u32(tmem_slot)),
-                     "r"(NTN)
+                     "r"(2 * NTN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
@@ -178,180 +265,335 @@ __global__ void __launch_bounds__(NTHR) mp_pass_kernel(const MpPass a)
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    for (int kb = 0; kb < nkb; ++kb) {
-        // B pieces: the pre-split sine image of this K block, copied asynchronously
-        {
-            const unsigned char *src = reinterpret_cast<const unsigned char *>(a.bimg) +
-                                       ((int64_t)img_tile * nkb + kb) * (PIECES * TILE_BYTES);
-            const uint32_t dst = smem_u32(sm + SMEM_B);
-            for (int e = t; e < PIECES * TILE_BYTES / 16; e += NTHR) cp_async16(dst + 16 * e, src + 16 * e);
-            asm volatile("cp.async.commit_group;\n" ::: "memory");
-        }
-        // A pieces: 128 lines x KB k of the input, split into pieces; a thread
-        // takes GPT groups of EPC consecutive k of one line (one 16-byte
-        // core-matrix row each; consecutive lanes take consecutive lines, so a
-        // warp's stores fill 512 contiguous bytes), all loads issued before any
-        // is used
-        double xv[GPT][EPC];
+    int mma_issued = 0;
+    int armed[NS];
 #pragma unroll
-        for (int g = 0; g < GPT; ++g) {
-            const int e = t + g * NTHR;
-            const int r = e & (MT - 1), g8 = e / MT;   // rows fastest: conflict-free 16-byte stores
-            const int64_t L = L0 + r;
+    for (int s = 0; s < NS; ++s) armed[s] = 0;
+
+    if (warp < NPROD / 32) {
+        // ---- producers of the input pieces ----
+        // group e = t + NPROD g of a stage: line r = e / 4 of the tile, k group
+        // g8 = e % 4 (EPC consecutive k: one 16-byte core-matrix row per piece); the
+        // four lanes of a line read its KB values of the stage together
+        constexpr int NG = C::NG;
+        int rr[NG];
+        uint32_t oo[NG];
+        const int g8 = lane & 3;
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            rr[g] = (t + NPROD * g) >> 2;
+            oo[g] = tile_off<C::ESZ>(rr[g], g8 * EPC);
+        }
+        // raw input bits of one stage (FP64 values, or FP32 values in the low half)
+        auto load = [&](int64_t tile, int kb, unsigned long long (&raw)[NG][EPC]) {
             const int kg0 = kb * KB + g8 * EPC;
-            const bool row_ok = L < nlines;
-            int64_t base = 0;
-            if (row_ok) {
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+#pragma unroll
+                for (int j = 0; j < EPC; ++j) raw[g][j] = 0ull;
+                const int64_t L = (tile / ntm) * MT + rr[g];
+                if (L >= nlines) continue;
                 const int64_t p = L / a.Q, q = L - p * a.Q;
-                base = p * a.is_p + q * a.is_q;
-            }
+                const int64_t base = p * a.is_p + q * a.is_q + (int64_t)kg0 * a.is_k;
+                if (a.in_vec4) {
+                    // FP32 lines starting on 16-byte boundaries, padded to whole
+                    // vectors: the padding is written by no one, so values past the
+                    // line's end are set to zero after the load
+                    const float4 *src =
+                        reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(a.in) + base);
 #pragma unroll
-            for (int j = 0; j < EPC; ++j) {
-                const int kg = kg0 + j;
-                double x = 0.0;
-                if (row_ok && kg < a.n) {
-                    const int64_t off = base + (int64_t)kg * a.is_k;
-                    if (a.in_f64) x = reinterpret_cast<const double *>(a.in)[off];
-                    else x = __longlong_as_double((long long)__float_as_int(reinterpret_cast<const float *>(a.in)[off]));
-                }
-                xv[g][j] = x;
-            }
-        }
-#pragma unroll
-        for (int g = 0; g < GPT; ++g) {
-            const int e = t + g * NTHR;
-            const int r = e & (MT - 1), g8 = e / MT;   // rows fastest: conflict-free 16-byte stores
-            float hi[EPC], lo[EPC];
-#pragma unroll
-            for (int j = 0; j < EPC; ++j) {
-                if (a.in_f64) {
-                    const ddr h2 = dd_from_bits(xv[g][j]);   // integer split, no FP64 instruction
-                    hi[j] = h2.hi;
-                    lo[j] = h2.lo;
+                    for (int v = 0; v < EPC / 4; ++v) {
+                        const int k4 = kg0 + 4 * v;
+                        if (k4 >= a.n) break;
+                        const float4 x = src[v];
+                        raw[g][4 * v] = __float_as_uint(x.x);
+                        raw[g][4 * v + 1] = k4 + 1 < a.n ? __float_as_uint(x.y) : 0u;
+                        raw[g][4 * v + 2] = k4 + 2 < a.n ? __float_as_uint(x.z) : 0u;
+                        raw[g][4 * v + 3] = k4 + 3 < a.n ? __float_as_uint(x.w) : 0u;
+                    }
                 } else {
-                    hi[j] = __int_as_float((int)__double_as_longlong(xv[g][j]));
-                    lo[j] = 0.f;
+#pragma unroll
+                    for (int j = 0; j < EPC; ++j) {
+                        if (kg0 + j >= a.n) break;
+                        if (a.in_f64)
+                            raw[g][j] = (unsigned long long)__double_as_longlong(
+                                reinterpret_cast<const double *>(a.in)[base + j * a.is_k]);
+                        else
+                            raw[g][j] = __float_as_uint(reinterpret_cast<const float *>(a.in)[base + j * a.is_k]);
+                    }
                 }
             }
-            const uint32_t o = tile_off<V>(r, g8 * EPC);
-            if constexpr (V == 1) {
-                float4 va, vb;
-                split2(hi[0], lo[0], va.x, vb.x);
-                split2(hi[1], lo[1], va.y, vb.y);
-                split2(hi[2], lo[2], va.z, vb.z);
-                split2(hi[3], lo[3], va.w, vb.w);
-                *reinterpret_cast<float4 *>(sm + SMEM_A + 0 * TILE_BYTES + o) = va;
-                *reinterpret_cast<float4 *>(sm + SMEM_A + 1 * TILE_BYTES + o) = vb;
-            } else {
-                unsigned short pa[8], pb[8], pc[8];
+        };
+        // the loads run two stages ahead of the splitting: two register sets, used
+        // in turn (a copy from one to the other would wait for its loads)
+        int64_t tile = blockIdx.x, ltile = blockIdx.x;   // stage being split / next to load
+        int kb = 0, lkb = 0;
+        auto advance = [&](int64_t &tl, int &k) {
+            if (++k == nkb) {
+                k = 0;
+                tl += gridDim.x;
+            }
+        };
+        unsigned long long q0[NG][EPC], q1[NG][EPC];
+        if (ltile < ntiles) load(ltile, lkb, q0);
+        advance(ltile, lkb);
+        if (ltile < ntiles) load(ltile, lkb, q1);
+        advance(ltile, lkb);
+        int sc = 0;
+        auto step = [&](unsigned long long (&q)[NG][EPC]) -> bool {
+            if (tile >= ntiles || s_fail) return false;
+            const int s = sc % NS;
+            float x[NG][EPC];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) split3(hi[j], lo[j], pa[j], pb[j], pc[j]);
-                uint4 va, vb, vc;
-                va.x = pa[0] | ((uint32_t)pa[1] << 16); va.y = pa[2] | ((uint32_t)pa[3] << 16);
-                va.z = pa[4] | ((uint32_t)pa[5] << 16); va.w = pa[6] | ((uint32_t)pa[7] << 16);
-                vb.x = pb[0] | ((uint32_t)pb[1] << 16); vb.y = pb[2] | ((uint32_t)pb[3] << 16);
-                vb.z = pb[4] | ((uint32_t)pb[5] << 16); vb.w = pb[6] | ((uint32_t)pb[7] << 16);
-                vc.x = pc[0] | ((uint32_t)pc[1] << 16); vc.y = pc[2] | ((uint32_t)pc[3] << 16);
-                vc.z = pc[4] | ((uint32_t)pc[5] << 16); vc.w = pc[6] | ((uint32_t)pc[7] << 16);
-                *reinterpret_cast<uint4 *>(sm + SMEM_A + 0 * TILE_BYTES + o) = va;
-                *reinterpret_cast<uint4 *>(sm + SMEM_A + 1 * TILE_BYTES + o) = vb;
-                *reinterpret_cast<uint4 *>(sm + SMEM_A + 2 * TILE_BYTES + o) = vc;
+            for (int g = 0; g < NG; ++g)
+#pragma unroll
+                for (int j = 0; j < EPC; ++j)
+                    x[g][j] = a.in_f64 ? f32_of_f64_bits(__longlong_as_double((long long)q[g][j]))
+                                       : __uint_as_float((uint32_t)q[g][j]);
+            if (ltile < ntiles) load(ltile, lkb, q);
+            advance(ltile, lkb);
+            if (sc >= NS && !mbar_wait(bar_e(s), (uint32_t)(((sc / NS) - 1) & 1), limit)) s_fail = 1;
+            if (s_fail) return false;
+            unsigned char *A = sm + s * C::STAGE;
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+                if constexpr (V == 1) {
+                    float4 va, vb;
+                    split2(x[g][0], va.x, vb.x);
+                    split2(x[g][1], va.y, vb.y);
+                    split2(x[g][2], va.z, vb.z);
+                    split2(x[g][3], va.w, vb.w);
+                    *reinterpret_cast<float4 *>(A + 0 * PIECE_BYTES + oo[g]) = va;
+                    *reinterpret_cast<float4 *>(A + 1 * PIECE_BYTES + oo[g]) = vb;
+                } else {
+                    uint4 va, vb, vc;
+                    split3_pair(x[g][0], x[g][1], va.x, vb.x, vc.x);
+                    split3_pair(x[g][2], x[g][3], va.y, vb.y, vc.y);
+                    split3_pair(x[g][4], x[g][5], va.z, vb.z, vc.z);
+                    split3_pair(x[g][6], x[g][7], va.w, vb.w, vc.w);
+                    *reinterpret_cast<uint4 *>(A + 0 * PIECE_BYTES + oo[g]) = va;
+                    *reinterpret_cast<uint4 *>(A + 1 * PIECE_BYTES + oo[g]) = vb;
+                    *reinterpret_cast<uint4 *>(A + 2 * PIECE_BYTES + oo[g]) = vc;
+                }
+            }
+            // the tensor cores read the pieces through the async proxy; one arrival
+            // per warp (hundreds of arrivals on one barrier word would serialise)
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_a(s));
+            advance(tile, kb);
+            ++sc;
+            return true;
+        };
+        while (step(q0) && step(q1)) {
+        }
+    } else if (warp == WARP_COPY) {
+        // ---- the sine image: one bulk copy per stage ----
+        if (lane == 0) {
+            int sc = 0;
+            for (int64_t tile = blockIdx.x; tile < ntiles && !s_fail; tile += gridDim.x) {
+                const int mt = (int)(tile % ntm);
+                for (int kb = 0; kb < nkb; ++kb, ++sc) {
+                    const int s = sc % NS;
+                    if (sc >= NS && !mbar_wait(bar_e(s), (uint32_t)(((sc / NS) - 1) & 1), limit)) s_fail = 1;
+                    if (s_fail) break;
+                    const unsigned char *src = reinterpret_cast<const unsigned char *>(a.bimg) +
+                                               ((int64_t)mt * nkb + kb) * C::B_BYTES;
+                    mbar_arrive_tx(bar_b(s), (uint32_t)C::B_BYTES);
+                    bulk_g2s(smem_u32(sm + s * C::STAGE + C::A_BYTES), src, (uint32_t)C::B_BYTES, bar_b(s));
+                    ++armed[s];
+                }
             }
         }
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        if (t == 0 && !a.stall_test) {
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            // products (i, j) with i + j <= 2 (BF16X3) or <= 1 (TF32X3); one
-            // MMA per two core matrices along K
+    } else if (warp == WARP_MMA) {
+        // ---- the products ----
+        if (lane == 0) {
+            int sc = 0, ac = 0;
             constexpr int NPR = V ? 3 : 6;
             const int pa[6] = {0, 0, 1, 0, 1, 2};
             const int pb[6] = {0, 1, 0, 2, 1, 0};
-            for (int pr = 0; pr < NPR; ++pr) {
-                for (int ks = 0; ks < KB / (2 * EPC); ++ks) {
-                    const uint64_t ad = make_desc(smem_u32(sm + SMEM_A + pa[pr] * TILE_BYTES) + ks * 2 * LBO);
-                    const uint64_t bd =
-                        make_desc(smem_u32(sm + SMEM_B + pb[pr] * TILE_BYTES) + ks * 2 * LBO + b_sub);
-                    const uint32_t acc = (kb > 0 || pr > 0 || ks > 0) ? 1u : 0u;
-                    if constexpr (V == 1)
-                        asm volatile(
-                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                            "l"(ad), "l"(bd), "r"(IDESC_N), "r"(acc)
-                            : "memory");
-                    else
-                        asm volatile(
-                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                            "l"(ad), "l"(bd), "r"(IDESC_N), "r"(acc)
-                            : "memory");
+            for (int64_t tile = blockIdx.x; tile < ntiles && !s_fail; tile += gridDim.x, ++ac) {
+                const int buf = ac & 1;
+                // the epilogue must have emptied this accumulator (two tiles ago)
+                if (ac >= 2 && !mbar_wait(bar_free(buf), (uint32_t)(((ac >> 1) - 1) & 1), limit)) s_fail = 1;
+                if (s_fail) break;
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)(buf * NTN);
+                for (int kb = 0; kb < nkb; ++kb, ++sc) {
+                    const int s = sc % NS;
+                    const uint32_t ph = (uint32_t)((sc / NS) & 1);
+                    if (!mbar_wait(bar_a(s), ph, limit) || !mbar_wait(bar_b(s), ph, limit)) s_fail = 1;
+                    if (s_fail) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    if (a.stall_test) continue;   // test hook: no products, so the waits run out
+                    // products (i, j) with i + j <= 2 (BF16X3) or <= 1 (TF32X3); one
+                    // MMA per two core matrices along K
+                    const uint32_t sa = smem_u32(sm + s * C::STAGE), sb = sa + (uint32_t)C::A_BYTES;
+#pragma unroll
+                    for (int pr = 0; pr < NPR; ++pr) {
+#pragma unroll
+                        for (int ks = 0; ks < KB / (2 * EPC); ++ks) {
+                            const uint64_t ad = make_desc(sa + pa[pr] * PIECE_BYTES + ks * 2 * LBO_A, LBO_A);
+                            const uint64_t bd = make_desc(sb + pb[pr] * C::BP_BYTES + ks * 2 * C::LBO_B, C::LBO_B);
+                            const uint32_t acc = (kb > 0 || pr > 0 || ks > 0) ? 1u : 0u;
+                            if constexpr (V == 1)
+                                asm volatile(
+                                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                    " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                                    "l"(ad), "l"(bd), "r"(IDESC_N), "r"(acc)
+                                    : "memory");
+                            else
+                                asm volatile(
+                                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                                    "l"(ad), "l"(bd), "r"(IDESC_N), "r"(acc)
+                                    : "memory");
+                        }
+                    }
+                    mma_issued = 1;
+                    mma_commit(bar_e(s));   // the stage is free once these products have read it
+                }
+                if (s_fail) break;
+                if (!a.stall_test) mma_commit(bar_full(buf));   // the tile's accumulator is complete
+            }
+        }
+    } else {
+        // ---- epilogue: warp w reads TMEM lane quadrant w % 4 (lines 32 (w % 4) ..),
+        //      half (w - WARP_EPI) / 4 of the columns
+        constexpr int CPW = NTN / (NEPI / 4);   // columns per epilogue warp
+        const int quad = warp & 3, half = (warp - WARP_EPI) >> 2;
+        int ac = 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++ac) {
+            const int buf = ac & 1;
+            // a warp-uniform decision: the TMEM loads below are warp-collective
+            bool ok = !s_fail;
+            if (ok) ok = mbar_wait(bar_full(buf), (uint32_t)((ac >> 1) & 1), limit);
+            ok = __all_sync(0xffffffffu, ok) != 0;
+            if (!ok) {
+                s_fail = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const int64_t L0 = (tile / ntm) * MT;
+            const int m0 = (int)(tile % ntm) * NTN;
+            const int64_t L = L0 + 32 * quad + lane;
+            const bool live = L < nlines;
+            int64_t p = 0, q = 0;
+            if (live) { p = L / a.Q; q = L - p * a.Q; }
+            const int cols = min(NTN, ((a.n - m0 + 15) / 16) * 16);
+            for (int c0 = half * CPW; c0 < min(cols, (half + 1) * CPW); c0 += 16) {
+                uint32_t v[16];
+                const uint32_t taddr = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(buf * NTN + c0);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];\n"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                if (!live) continue;
+                const int mc = m0 + c0;
+                const int nj = min(16, a.n - mc);
+                if (a.out_f64 && (a.tab == nullptr) != (a.add == nullptr)) {
+                    // one FP64 operand (a table or an addend): its 16 values are loaded
+                    // before any store (the stores could alias them as far as the
+                    // compiler knows, and would otherwise put one load latency on
+                    // every value)
+                    const double *ext = a.tab ? a.tab : a.add;
+                    const int64_t es_m = a.tab ? a.ts_m : a.as_m, es_p = a.tab ? a.ts_p : a.as_p,
+                                  es_q = a.tab ? a.ts_q : a.as_q;
+#pragma unroll
+                    for (int h = 0; h < 16; h += 8) {
+                        double ev[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            ev[j] = h + j < nj ? ext[(int64_t)(mc + h + j) * es_m + p * es_p + q * es_q] : 0.0;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            if (h + j >= nj) break;
+                            // 4 * the FP32 sum, exact in FP32; widened to FP64 by bits
+                            const double y = f2d_bits(__fmul_rn(4.0f, __uint_as_float(v[h + j])));
+                            reinterpret_cast<double *>(
+                                a.out)[(int64_t)(mc + h + j) * a.os_m + p * a.os_p + q * a.os_q] =
+                                a.tab ? ev[j] * y : y + ev[j];
+                        }
+                    }
+                } else if (a.out_f64) {
+                    // no FP64 operand, or both: in groups of 8 modes
+#pragma unroll
+                    for (int h = 0; h < 16; h += 8) {
+                        double tv[8], av[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int64_t m = mc + h + j;
+                            tv[j] = (a.tab && h + j < nj) ? a.tab[m * a.ts_m + p * a.ts_p + q * a.ts_q] : 1.0;
+                            av[j] = (a.add && h + j < nj) ? a.add[m * a.as_m + p * a.as_p + q * a.as_q] : 0.0;
+                        }
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            if (h + j >= nj) break;
+                            // 4 * the FP32 sum, exact in FP32; widened to FP64 by bits
+                            const double y = f2d_bits(__fmul_rn(4.0f, __uint_as_float(v[h + j])));
+                            double r = y;
+                            if (a.tab) r = a.add ? fma(tv[j], y, av[j]) : tv[j] * y;
+                            else if (a.add) r = y + av[j];
+                            reinterpret_cast<double *>(a.out)[(int64_t)(mc + h + j) * a.os_m + p * a.os_p + q * a.os_q] =
+                                r;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        if (j >= nj) break;
+                        reinterpret_cast<float *>(a.out)[(int64_t)(mc + j) * a.os_m + p * a.os_p + q * a.os_q] =
+                            __fmul_rn(4.0f, __uint_as_float(v[j]));
+                    }
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                             bar)
-                         : "memory");
+            // the accumulator may be reused once every warp of the epilogue has read it
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_free(buf));
         }
-        // every thread waits for the products (they read the shared memory we refill next)
-        // (stall_test: no products were issued, so this wait runs out on purpose)
-        if (!mbar_wait(bar, (uint32_t)(kb & 1), a.stall_test ? WAIT_CYCLES / 400 : WAIT_CYCLES)) s_fail = 1;
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        __syncthreads();
-        if (s_fail) break;
     }
 
-    if (!s_fail) {
-        // epilogue: warp w reads TMEM lane quadrant w % 4 (lines 32*(w%4) ..),
-        // columns [NTN/4 * (w / 4), NTN/4 * (w / 4) + NTN/4), 16 at a time
-        const int quad = warp & 3;
-        const int64_t L = L0 + 32 * quad + lane;
-        const bool live = L < nlines;
-        int64_t p = 0, q = 0;
-        if (live) { p = L / a.Q; q = L - p * a.Q; }
-        constexpr int CPW = NTN / 4;
-        for (int c0 = CPW * (warp >> 2); c0 < CPW * (warp >> 2) + CPW; c0 += 16) {
-            uint32_t v[16];
-            const uint32_t taddr = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                "[%16];\n"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                  "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                  "=r"(v[14]), "=r"(v[15])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-            if (!live) continue;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int m = m0 + c0 + j;
-                if (m >= a.n) break;
-                // 4 * the FP32 sum, exact in FP32; widened to FP64 by bits
-                const float y4 = __fmul_rn(4.0f, __uint_as_float(v[j]));
-                const int64_t oo = (int64_t)m * a.os_m + p * a.os_p + q * a.os_q;
-                if (a.out_f64) {
-                    const double y = f2d_bits(y4);
-                    double r = y;
-                    if (a.tab) {
-                        const double tv = a.tab[(int64_t)m * a.ts_m + p * a.ts_p + q * a.ts_q];
-                        r = a.add ? fma(tv, y, a.add[(int64_t)m * a.as_m + p * a.as_p + q * a.as_q]) : tv * y;
-                    } else if (a.add) {
-                        r = y + a.add[(int64_t)m * a.as_m + p * a.as_p + q * a.as_q];
-                    }
-                    reinterpret_cast<double *>(a.out)[oo] = r;
-                } else {
-                    reinterpret_cast<float *>(a.out)[oo] = y4;
-                }
-            }
+    // ---- teardown: after a failure, wait (bounded) for this block's own products
+    //      and copies still in flight before the tensor memory is freed and the
+    //      shared memory released
+    __syncthreads();
+    const bool failed = s_fail != 0;
+    if (failed) {
+        if (warp == WARP_MMA && lane == 0 && mma_issued) {
+            mma_commit(bar_drain);   // arrives once every product issued so far has completed
+            mbar_wait(bar_drain, 0, WAIT_CYCLES);
         }
-    } else if (t == 0 && a.err) {
-        atomicExch(a.err, 1);
+        if (warp == WARP_COPY && lane == 0) {
+#pragma unroll
+            for (int s = 0; s < NS; ++s)
+                if (armed[s] > 0) mbar_wait(bar_b(s), (uint32_t)((armed[s] - 1) & 1), WAIT_CYCLES);
+        }
+        if (t == 0 && a.err) atomicExch(a.err, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
-    if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(NTN)
+    if (warp == WARP_MMA) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(2 * NTN)
                      : "memory");
     }
+}
+
+int g_num_sms = 0;
+
+template <int V, int NTN>
+cudaError_t launch_mp_t(const MpPass &a, cudaStream_t st)
+{
+    const int64_t lines = (int64_t)a.P * a.Q;
+    const int64_t tiles = ((lines + MT - 1) / MT) * ((a.n + NTN - 1) / NTN);
+    const int sms = g_num_sms > 0 ? g_num_sms : 148;
+    const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
+    mp_pass_kernel<NTN, V><<<grid, NTHR, MpCfg<V, NTN>::SMEM_TOTAL, st>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -360,34 +602,26 @@ cudaError_t mp_set_attributes()
 {
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(mp_pass_kernel<128, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  MpCfg<0>::SMEM_TOTAL)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(mp_pass_kernel<64, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  MpCfg<0>::SMEM_TOTAL)) != cudaSuccess ||
+                                  MpCfg<0, 128>::SMEM_TOTAL)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(mp_pass_kernel<256, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  MpCfg<0, 256>::SMEM_TOTAL)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(mp_pass_kernel<128, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  MpCfg<1>::SMEM_TOTAL)) != cudaSuccess)
+                                  MpCfg<1, 128>::SMEM_TOTAL)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(mp_pass_kernel<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  MpCfg<1, 256>::SMEM_TOTAL)) != cudaSuccess)
         return e;
-    return cudaFuncSetAttribute(mp_pass_kernel<64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                MpCfg<1>::SMEM_TOTAL);
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    return cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
 }
 
-template <int V>
-cudaError_t launch_mp_v(const MpPass &a, cudaStream_t st)
-{
-    const int64_t lines = (int64_t)a.P * a.Q;
-    const unsigned tiles = (unsigned)((lines + MT - 1) / MT);
-    // 64-mode tiles double the blocks of a launch that fills the GPU less than twice
-    if (a.modes_per_tile == 64 || (a.modes_per_tile == 0 && tiles * ((a.n + NTILE - 1) / NTILE) < 2 * 152)) {
-        mp_pass_kernel<64, V><<<dim3(tiles, (unsigned)((a.n + 63) / 64)), NTHR, MpCfg<V>::SMEM_TOTAL, st>>>(a);
-    } else {
-        mp_pass_kernel<128, V>
-            <<<dim3(tiles, (unsigned)((a.n + NTILE - 1) / NTILE)), NTHR, MpCfg<V>::SMEM_TOTAL, st>>>(a);
-    }
-    return cudaGetLastError();
-}
+int mp_stage_k(int variant) { return variant ? MpCfg<1, 128>::KB : MpCfg<0, 128>::KB; }
+int mp_tile_modes(int n) { return n <= 128 ? 128 : 256; }
 
 cudaError_t launch_mp_pass(const MpPass &a, cudaStream_t st)
 {
-    return a.variant ? launch_mp_v<1>(a, st) : launch_mp_v<0>(a, st);
+    if (mp_tile_modes(a.n) == 128) return a.variant ? launch_mp_t<1, 128>(a, st) : launch_mp_t<0, 128>(a, st);
+    return a.variant ? launch_mp_t<1, 256>(a, st) : launch_mp_t<0, 256>(a, st);
 }
 
 }  // namespace idp

@@ -184,6 +184,7 @@ struct idp_plan_s {
     int mixed = 0;
     int stall_test = 0;               // IDP_KEY_STALL_TEST: next tensor-core pass waits in vain
     int mixed_path = 0;               // mixed precision: 0 = tensor-core matrix pass, 1 = df32 FFT pass
+    int mixed_bdd = 0;                // IDP_KEY_MIXED_BOUNDARY_DF32: tensor-core modes, 3-D boundary in double-float
     int64_t part_cap = 0;             // capacity (complex) of the partial face sums of one axis
     int64_t f_cap = 0;                // capacity (complex) of the face spectra of one axis
     int tuned = 0;
@@ -388,22 +389,24 @@ double tf32_value(uint32_t u)
     return (double)f;
 }
 
-// TF32 pieces of S (variant 1): [ntile][kblock][2][128 rows m x 32 k] FP32
-// containers, element (r, c) at byte (c/4)*2048 + (r/8)*128 + (r%8)*16 + (c%4)*4
+// TF32 pieces of S (variant 1): [mode tile][k stage][2][W rows m x KB k] FP32
+// containers (W = mp_tile_modes(n), KB = mp_stage_k(1)), element (r, c) at byte
+// (c/4)*(16 W) + (r/8)*128 + (r%8)*16 + (c%4)*4
 int get_mp_image_tf32(idp_plan p, int M, const void **out)
 {
-    const int n = M - 1, nt = (n + 127) / 128, nkb = (n + 31) / 32;
-    const size_t tile = 128 * 32;
+    const int KB = mp_stage_k(1);
+    const int n = M - 1, W = mp_tile_modes(n), nt = (n + W - 1) / W, nkb = (n + KB - 1) / KB;
+    const size_t tile = (size_t)W * KB;
     std::vector<uint32_t> img((size_t)nt * nkb * 2 * tile, 0);
     for (int t = 0; t < nt; ++t)
         for (int kb = 0; kb < nkb; ++kb)
-            for (int r = 0; r < 128; ++r)
-                for (int c = 0; c < 32; ++c) {
-                    const int m = t * 128 + r, k = kb * 32 + c;
+            for (int r = 0; r < W; ++r)
+                for (int c = 0; c < KB; ++c) {
+                    const int m = t * W + r, k = kb * KB + c;
                     const double s = (m < n && k < n) ? sinpi_frac((int64_t)(m + 1) * (k + 1), M) : 0.0;
                     const uint32_t a = tf32_bits((float)s);
                     const uint32_t b = tf32_bits((float)(s - tf32_value(a)));
-                    const size_t off = ((size_t)(c / 4) * 2048 + (r / 8) * 128 + (r % 8) * 16 + (c % 4) * 4) / 4;
+                    const size_t off = ((size_t)(c / 4) * (16 * W) + (r / 8) * 128 + (r % 8) * 16 + (c % 4) * 4) / 4;
                     const size_t base = (((size_t)t * nkb + kb) * 2) * tile;
                     img[base + off] = a;
                     img[base + tile + off] = b;
@@ -416,17 +419,34 @@ int get_mp_image_tf32(idp_plan p, int M, const void **out)
     return IDP_OK;
 }
 
+int64_t pad4(int64_t x) { return (x + 3) & ~(int64_t)3; }
+// floats of one FP32 intermediate of the tensor-core transforms (the larger of the
+// two padded layouts)
+int64_t t32_count(idp_plan p)
+{
+    const int64_t n0 = p->ni[0], n1 = p->ni[1], n2 = p->ni[2];
+    if (p->d == 3) return std::max(n2 * n0 * pad4(n1), n1 * n2 * pad4(n0));
+    return n2 * pad4(n1);
+}
+
 // the tensor-core pass variant of the plan's precision (0: BF16X3, 1: TF32X3)
 int mp_variant(idp_plan p) { return p->mixed == IDP_PRECISION_MIXED_TF32X3 ? 1 : 0; }
 bool tensor_mode(idp_plan p)
 {
     return p->mixed == IDP_PRECISION_MIXED_BF16X3 || p->mixed == IDP_PRECISION_MIXED_TF32X3;
 }
+// the 3-D boundary convolutions (and so T0) in double-float arithmetic: precision
+// DF32, or a tensor-core mode with IDP_KEY_MIXED_BOUNDARY_DF32
+int boundary_dd(idp_plan p)
+{
+    return p->d == 3 && (p->mixed == IDP_PRECISION_DF32 || (tensor_mode(p) && p->mixed_bdd)) ? 1 : 0;
+}
 
 // Pieces of S_{m,k} = sin(pi (m+1)(k+1)/M) for a tensor-core variant, laid out
-// as the kernel's shared-memory tiles.  BF16 (variant 0):
-// [ntile][kblock][3][128 rows m x 64 k], element (r, c) at byte
-// (c/8)*2048 + (r/8)*128 + (r%8)*16 + (c%8)*2.  Cached per (M, variant).
+// as the kernel's shared-memory tiles, one contiguous block per (mode tile,
+// K stage).  BF16 (variant 0): [mode tile][k stage][3][W rows m x KB k] with
+// W = mp_tile_modes(n), KB = mp_stage_k(0), element (r, c) at byte
+// (c/8)*(16 W) + (r/8)*128 + (r%8)*16 + (c%8)*2.  Cached per (M, variant).
 int get_mp_image(idp_plan p, int M, int variant, const void **out)
 {
     const int key = M + (variant << 24);
@@ -440,21 +460,22 @@ int get_mp_image(idp_plan p, int M, int variant, const void **out)
         if (!rc) p->mp_img[key] = const_cast<void *>(*out);
         return rc;
     }
-    const int n = M - 1, nt = (n + 127) / 128, nkb = (n + 63) / 64;
-    const size_t tile = 128 * 64;
+    const int KB = mp_stage_k(0);
+    const int n = M - 1, W = mp_tile_modes(n), nt = (n + W - 1) / W, nkb = (n + KB - 1) / KB;
+    const size_t tile = (size_t)W * KB;
     std::vector<uint16_t> img((size_t)nt * nkb * 3 * tile, 0);
     for (int t = 0; t < nt; ++t)
         for (int kb = 0; kb < nkb; ++kb)
-            for (int r = 0; r < 128; ++r)
-                for (int c = 0; c < 64; ++c) {
-                    const int m = t * 128 + r, k = kb * 64 + c;
+            for (int r = 0; r < W; ++r)
+                for (int c = 0; c < KB; ++c) {
+                    const int m = t * W + r, k = kb * KB + c;
                     const double s = (m < n && k < n) ? sinpi_frac((int64_t)(m + 1) * (k + 1), M) : 0.0;
                     const uint16_t a = bf16_bits((float)s);
                     const double r1 = s - bf16_value(a);
                     const uint16_t b = bf16_bits((float)r1);
                     const double r2 = r1 - bf16_value(b);
                     const uint16_t cc = bf16_bits((float)r2);
-                    const size_t off = ((size_t)(c / 8) * 2048 + (r / 8) * 128 + (r % 8) * 16 + (c % 8) * 2) / 2;
+                    const size_t off = ((size_t)(c / 8) * (16 * W) + (r / 8) * 128 + (r % 8) * 16 + (c % 8) * 2) / 2;
                     const size_t base = (((size_t)t * nkb + kb) * 3) * tile;
                     img[base + off] = a;
                     img[base + tile + off] = b;
@@ -479,23 +500,26 @@ int transform_mixed(idp_plan p, View3 in, View3 out, const double *tab, View3 ad
     MpPass a{};
     a.err = p->d_err;
     a.variant = mp_variant(p);
+    // the FP32 intermediates keep their contiguous (next pass's k) axis padded to
+    // whole 16-byte vectors, so that the next pass loads its lines as vectors
+    const int64_t n0p = pad4(n0), n1p = pad4(n1);
     if (p->d == 3) {
         a.in = in.p; a.in_f64 = 1; a.is_p = in.s0; a.is_q = in.s1; a.is_k = in.s2;
-        a.out = ta; a.out_f64 = 0; a.os_m = (int64_t)n0 * n1; a.os_p = n1; a.os_q = 1;
+        a.out = ta; a.out_f64 = 0; a.os_m = (int64_t)n0 * n1p; a.os_p = n1p; a.os_q = 1;
         a.P = n0; a.Q = n1; a.n = n2;
         ps.push_back(a);
-        a.in = ta; a.in_f64 = 0; a.is_p = (int64_t)n0 * n1; a.is_q = n1; a.is_k = 1;
-        a.out = tb; a.os_m = (int64_t)n2 * n0; a.os_p = n0; a.os_q = 1;
+        a.in = ta; a.in_f64 = 0; a.in_vec4 = 1; a.is_p = (int64_t)n0 * n1p; a.is_q = n1p; a.is_k = 1;
+        a.out = tb; a.os_m = (int64_t)n2 * n0p; a.os_p = n0p; a.os_q = 1;
         a.P = n2; a.Q = n0; a.n = n1;
         ps.push_back(a);
-        a.in = tb; a.is_p = (int64_t)n2 * n0; a.is_q = n0; a.is_k = 1;
+        a.in = tb; a.is_p = (int64_t)n2 * n0p; a.is_q = n0p; a.is_k = 1;
         a.P = n1; a.Q = n2; a.n = n0;
     } else {
         a.in = in.p; a.in_f64 = 1; a.is_p = 0; a.is_q = in.s1; a.is_k = in.s2;
-        a.out = ta; a.out_f64 = 0; a.os_m = n1; a.os_p = 0; a.os_q = 1;
+        a.out = ta; a.out_f64 = 0; a.os_m = n1p; a.os_p = 0; a.os_q = 1;
         a.P = 1; a.Q = n1; a.n = n2;
         ps.push_back(a);
-        a.in = ta; a.in_f64 = 0; a.is_p = 0; a.is_q = n1; a.is_k = 1;
+        a.in = ta; a.in_f64 = 0; a.in_vec4 = 1; a.is_p = 0; a.is_q = n1p; a.is_k = 1;
         a.P = 1; a.Q = n2; a.n = n1;
     }
     // last pass: FP64 output in the original layout with the epilogue
@@ -526,15 +550,20 @@ int transform_mixed(idp_plan p, View3 in, View3 out, const double *tab, View3 ad
 // one full sine transform (all active axes); `first` pass reads `in`, the
 // last pass applies the epilogue (tab, add) and writes `out`; intermediate
 // passes run in place on `work`.
+// allow_reduced = false: FP64 passes in every precision mode except that
+// fp64_only = false lets the tensor-core modes run them as double-float passes
+// (the transform producing u1: FP64-class there, never the tensor cores)
 int transform(idp_plan p, View3 in, double *work, View3 out, const double *tab, View3 add, bool forward,
-              cudaStream_t st, bool allow_reduced = true, bool skip_axis2 = false, int in_dd0 = 0)
+              cudaStream_t st, bool allow_reduced = true, bool skip_axis2 = false, int in_dd0 = 0,
+              bool fp64_only = true)
 {
     if (tensor_mode(p) && allow_reduced && p->mixed_path == 0)
         return transform_mixed(p, in, out, tab, add, st == p->side ? 1 : 0, st);
     // df32 passes: precision DF32, or precision MIXED when the autotuner found the
-    // double-float FFT faster than the matrix pass (it is also more accurate)
-    const bool dd = (p->mixed == IDP_PRECISION_DF32 ||
-                     (tensor_mode(p) && p->mixed_path == 1)) && allow_reduced;
+    // double-float FFT faster than the matrix pass (it is also more accurate), or the
+    // double-float transform of u1 in the tensor-core modes
+    const bool dd = ((p->mixed == IDP_PRECISION_DF32 || (tensor_mode(p) && p->mixed_path == 1)) && allow_reduced) ||
+                    (tensor_mode(p) && !allow_reduced && !fp64_only);
     int axes[3], na = 0;
     if (forward) {
         for (int s = skip_axis2 ? 1 : 2; s >= 0; --s)
@@ -598,7 +627,7 @@ int dst_box(idp_plan p, double *x, int b0, int b1, int b2, int M2, int M1, cudaS
         a.half = t.half;
         a.halfr = t.halfr;
         if ((rc = get_sin2(p, Ms[q], &a.sin2))) return rc;
-        if (p->mixed == IDP_PRECISION_DF32) {
+        if (p->mixed == IDP_PRECISION_DF32 || tensor_mode(p)) {
             a.dd = 1;
             a.twd = t.fwdd;
             a.halfd = t.halfd;
@@ -668,7 +697,7 @@ int transform_rho_from_T0(idp_plan p, cudaStream_t st)
     const View3 none{nullptr, 0, 0, 0};
     const int64_t row = 2 * (int64_t)(p->M[2] + 1);   // doubles per T0 row
     const View3 im{reinterpret_cast<double *>(p->T0) + 3, (int64_t)p->ni[1] * row, row, 2};
-    const int dd = (p->mixed == IDP_PRECISION_DF32 && p->d == 3) ? 1 : 0;   // T0 holds pairs
+    const int dd = boundary_dd(p);   // T0 holds pairs
     return transform(p, im, p->A, dense(p, p->A), p->tabc2, none, true, st, true, true, dd);
 }
 
@@ -682,8 +711,9 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
     const View3 r = node_interior(p, rho);
     int rc;
     FftTables t;
-    // double-float arithmetic for the 3-D convolutions in precision DF32
-    const int dd = (p->mixed == IDP_PRECISION_DF32 && p->d == 3) ? 1 : 0;
+    // double-float arithmetic for the 3-D convolutions in precision DF32 (and, on
+    // request, in the tensor-core modes)
+    const int dd = boundary_dd(p);
     // support flags of rho: set by the first row transform
     IDP_CK(cudaMemsetAsync(p->flags, 0, sizeof(int) * p->nflags, st));
     // stage 1a: along axis 2 -> T0[i0][i1][m2]; stage 1b: along axis 1 -> T1[i0][i2][m1]
@@ -932,10 +962,15 @@ int enqueue_grid(idp_plan p, const double *rho, double *phi, int stop, cudaStrea
     const double *rho_src = (stop == 0 && p->hio_rho && rho_from_T0) ? p->hio_view : nullptr;
     if (stop == 0 && p->hio_rho && !rho_src)
         IDP_CK(cudaMemcpyAsync(p->h_rho, p->hio_rho, sizeof(double) * p->nodes, cudaMemcpyHostToDevice, st));
+    // the tensor-core transform of rho leaves out the eigenvalue factor tabc: the
+    // expansion kernels below apply it (an FP64 table read in the epilogue of a
+    // tensor-core pass is latency-bound there)
+    const bool rho_unscaled = (stop == 0) && !rho_from_T0;
+    const double *ascale = rho_unscaled ? p->tabc : nullptr;
     if (overlap_rho && !rho_from_T0) {
         IDP_CK(cudaEventRecord(p->fork, st));
         IDP_CK(cudaStreamWaitEvent(p->side, p->fork, 0));
-        if ((rc = transform(p, node_interior(p, rho), p->A, dense(p, p->A), p->tabc, none, true, p->side)))
+        if ((rc = transform(p, node_interior(p, rho), p->A, dense(p, p->A), nullptr, none, true, p->side)))
             return rc;
         IDP_CK(cudaEventRecord(p->join, p->side));
     }
@@ -954,7 +989,7 @@ int enqueue_grid(idp_plan p, const double *rho, double *phi, int stop, cudaStrea
     if (stop == 0 && !overlap_rho) {
         if (rho_from_T0) {
             if ((rc = transform_rho_from_T0(p, st))) return rc;
-        } else if ((rc = transform(p, node_interior(p, rho), p->A, dense(p, p->A), p->tabc, none, true, st))) {
+        } else if ((rc = transform(p, node_interior(p, rho), p->A, dense(p, p->A), nullptr, none, true, st))) {
             return rc;
         }
     }
@@ -963,24 +998,25 @@ int enqueue_grid(idp_plan p, const double *rho, double *phi, int stop, cudaStrea
         // A += tab4 * S gtilde; phi = S A inside
         {
             Mark mk(p, IDP_KERNEL_GTILDE_EXPAND, st);
-            IDP_CK(launch_gtilde_expand(p->grid, p->Q0, p->Q1, p->Q2, p->sin4, p->tab4, p->A, p->A, st));
+            IDP_CK(launch_gtilde_expand(p->grid, p->Q0, p->Q1, p->Q2, p->sin4, p->tab4, p->A, p->A, st, nullptr,
+                                        nullptr, nullptr, 0, ascale));
         }
         return transform(p, dense(p, p->A), p->A, node_interior(p, phi), nullptr, none, false, st);
     }
     // 4. u1 = S B, B = tab4 * S gtilde; in a full solve also C = A + tabR * S gtilde,
     //    the solution coefficients less the layer correction (R_spec's share)
     if (stop == 0 && overlap_rho) IDP_CK(cudaStreamWaitEvent(st, p->join, 0));
-    // FP64 / df32 final transforms take u1 in C (S C + S B = S (C + B)); the
-    // tensor-core one adds the FP64 u1 afterwards instead
-    const bool fold_u1 = !(tensor_mode(p) && p->mixed_path == 0);
+    // the final transform takes u1 in C (S C + S B = S (C + B)), in every mode
     {
         Mark mk(p, IDP_KERNEL_GTILDE_EXPAND, st);
         IDP_CK(launch_gtilde_expand(p->grid, p->Q0, p->Q1, p->Q2, p->sin4, p->tab4, nullptr, p->B, st,
-                                    p->tabR, p->A, stop == 0 ? p->C : nullptr, fold_u1 ? 1 : 0));
+                                    p->tabR, p->A, stop == 0 ? p->C : nullptr, 1, ascale));
     }
     // u1 feeds the sixth differences of R, which amplify its rounding by ~1e4-1e7:
-    // this inverse transform stays FP64 in every precision mode
-    if ((rc = transform(p, dense(p, p->B), p->B, node_interior(p, p->U), nullptr, none, false, st, false)))
+    // this inverse transform stays FP64 in the FP64 and DF32 modes, and is a
+    // double-float one (48 bits, never the tensor cores) in the tensor-core modes
+    if ((rc = transform(p, dense(p, p->B), p->B, node_interior(p, p->U), nullptr, none, false, st, false, false, 0,
+                        false)))
         return rc;
     if (stop == IDP_STAGE_U1) {
         IDP_CK(cudaMemcpyAsync(phi, p->U, node_bytes, cudaMemcpyDeviceToDevice, st));
@@ -1018,8 +1054,7 @@ int enqueue_grid(idp_plan p, const double *rho, double *phi, int stop, cudaStrea
         Mark mk(p, IDP_KERNEL_RHS6_EXPAND, st);
         IDP_CK(launch_rhs6_e_expand(p->grid, p->E0, p->E1, p->E2, p->sin4, p->sin4b, p->tab4, p->C, st));
     }
-    return transform(p, dense(p, p->C), p->C, node_interior(p, phi), nullptr,
-                     fold_u1 ? none : node_interior(p, p->U), false, st);
+    return transform(p, dense(p, p->C), p->C, node_interior(p, phi), nullptr, none, false, st);
 }
 
 // the plan's streams and events (graph capture forks and joins through them)
@@ -1555,6 +1590,26 @@ int idp_plan_set(idp_plan p, int key, int64_t value)
         }
         return IDP_OK;
     }
+    if (key == IDP_KEY_MIXED_BOUNDARY_DF32) {
+        if (value != 0 && value != 1) return IDP_EINVAL;
+        if (value && p->d == 3 && !p->khatd[0]) {
+            int rc;
+            for (int a_ = 0; a_ < 3; ++a_) {
+                if ((rc = p->alloc(&p->khatd[a_], p->khat_n[a_]))) return rc;
+                IDP_CK(launch_to_dd(p->khat[a_], p->khatd[a_], p->khat_n[a_], 0));
+            }
+            IDP_CK(cudaDeviceSynchronize());
+        }
+        if (p->mixed_bdd != (int)value) {
+            p->mixed_bdd = (int)value;
+            ++p->version;
+            if (p->gexec) {
+                cudaGraphExecDestroy(p->gexec);
+                p->gexec = nullptr;
+            }
+        }
+        return IDP_OK;
+    }
     if (key == IDP_KEY_GUARD_TEST) {
         // test hook: overwrite (1) or restore (0) the first byte of the guard
         // region in front of the plan's first buffer; the write stays inside
@@ -1589,7 +1644,7 @@ int idp_plan_set(idp_plan p, int key, int64_t value)
             }
             for (int s = 0; s < 2; ++s)
                 for (int q = 0; q < 2; ++q)
-                    if (!p->t32[s][q] && (rc = p->alloc(&p->t32[s][q], p->nint))) return rc;
+                    if (!p->t32[s][q] && (rc = p->alloc(&p->t32[s][q], t32_count(p)))) return rc;
             for (int s = 0; s < 3; ++s) {
                 const void *img;
                 if (p->act[s] &&

@@ -120,7 +120,7 @@ __global__ void gtilde_expand_kernel(const Grid3 gg, const double *__restrict__ 
                                      const double *__restrict__ Q2, const double *__restrict__ sin4,
                                      const double *__restrict__ tab, const double *add, double *out,
                                      const double *__restrict__ tab2, const double *__restrict__ add2,
-                                     double *__restrict__ out2, int fold)
+                                     double *__restrict__ out2, int fold, const double *__restrict__ ascale)
 {
     const Geo g = make_geo(gg);
     const int k2 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -134,9 +134,12 @@ __global__ void gtilde_expand_kernel(const Grid3 gg, const double *__restrict__ 
     if (g.act[0]) v = fma(sn0[k0], Q0[(int64_t)((k0 & 1) ? n1 + k1 : k1) * n2 + k2], v);
     const int64_t t = k0 * g.is[0] + (int64_t)k1 * g.is[1] + k2;
     const double tb = tab[t];
-    out[t] = add ? fma(tb, v, add[t]) : tb * v;
+    // ascale (optional): the addends still need their eigenvalue factor (the
+    // tensor-core transform of rho leaves it to this kernel)
+    const double sc = ascale ? ascale[t] : 1.0;
+    out[t] = add ? fma(tb, v, ascale ? sc * add[t] : add[t]) : tb * v;
     // tab2 holds tabR + tab4 (u1 folded in); without fold, tabR = tab2 - tab4
-    if (out2) out2[t] = fma(fold ? tab2[t] : tab2[t] - tb, v, add2[t]);
+    if (out2) out2[t] = fma(fold ? tab2[t] : tab2[t] - tb, v, ascale ? sc * add2[t] : add2[t]);
 }
 
 // gtilde as a dense interior array from its parts (for the stage output).
@@ -759,10 +762,11 @@ cudaError_t launch_gtilde_planes(const Grid3 &g, const StencilCoef &c, const dou
 
 cudaError_t launch_gtilde_expand(const Grid3 &g, const double *Q0, const double *Q1, const double *Q2,
                                  const double *sin4, const double *tab, const double *add, double *out,
-                                 cudaStream_t st, const double *tab2, const double *add2, double *out2, int fold)
+                                 cudaStream_t st, const double *tab2, const double *add2, double *out2, int fold,
+                                 const double *ascale)
 {
     gtilde_expand_kernel<<<grid3(g.n2 - 2, g.n1 - 2, g.d == 3 ? g.n0 - 2 : 1), dim3(32, 8), 0, st>>>(
-        g, Q0, Q1, Q2, sin4, tab, add, out, tab2, add2, out2, fold);
+        g, Q0, Q1, Q2, sin4, tab, add, out, tab2, add2, out2, fold, ascale);
     return cudaGetLastError();
 }
 

@@ -138,3 +138,31 @@ def test_bounded_wait_expires_into_a_status_not_a_hang(idp, variant):
     idp.plan_status(plan)
     ref = osolve.solve(prob.rho(), prob.h, 6, boundary="convolution")
     assert rel_max(out.cpu().numpy(), ref) < _tol(variant)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_mixed_with_double_float_boundary_against_oracle(idp, variant):
+    # IDP_KEY_MIXED_BOUNDARY_DF32 = 1: the 3-D boundary convolutions of a tensor-core
+    # mode in double-float arithmetic (48 bits): the result stays within the mode's
+    # stated bound, and its boundary values within the double-float bound of g
+    prob = w.Problem("g", (65, 33, 129), (0.0,) * 3, (1.0, 1.0, 2.0), "gauss", dict(seed=2108))
+    rho = prob.rho()
+    plan = _plan(idp, prob, variant=variant)
+    idp.plan_set(plan, idp.IDP_KEY_MIXED_BOUNDARY_DF32, 1)
+    r = to_dev(rho)
+    parts = {}
+    ref = osolve.solve(rho, prob.h, 6, boundary="convolution", parts=parts)
+    g = run_stage(idp, plan, idp.IDP_STAGE_BOUNDARY, r, prob.n)
+    from oracle import greens as ogreens
+    mask = ogreens.boundary_mask(prob.n)
+    assert rel_max(g[mask], parts["g"][mask]) < 1e-12
+    phi = to_dev(np.zeros(prob.n))
+    idp.solve(plan, r, phi)
+    idp.plan_status(plan)
+    err = rel_max(phi.cpu().numpy(), ref)
+    assert err < _tol(variant), err
+    # switching it off gives back the FP64 boundary
+    idp.plan_set(plan, idp.IDP_KEY_MIXED_BOUNDARY_DF32, 0)
+    g64 = run_stage(idp, plan, idp.IDP_STAGE_BOUNDARY, r, prob.n)
+    fp = idp.create_plan(prob.d, prob.n, prob.h, 6)
+    assert np.array_equal(g64, run_stage(idp, fp, idp.IDP_STAGE_BOUNDARY, r, prob.n))
