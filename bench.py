@@ -68,8 +68,12 @@ def parse():
                          "autotuner's: profiled runs, whose timings the profiler perturbs, then run "
                          "the shape of the plain run")
     ap.add_argument("--profile-window", type=int, default=0,
-                    help="after the timed steps, run this many more FP64 solves between "
+                    help="after the timed steps, run this many more solves between "
                          "cudaProfilerStart and cudaProfilerStop (for ncu --profile-from-start off)")
+    ap.add_argument("--profile-precision", default="FP64",
+                    choices=["FP64", "DF32", "MIXED_BF16X3", "MIXED_TF32X3"],
+                    help="precision mode of the solves in the profiler window (an autotuned plan of "
+                         "its own unless FP64)")
     ap.add_argument("--batched", action="store_true",
                     help="only the 96-problem batched workload (uneven sizes)")
     return ap.parse_args()
@@ -410,14 +414,19 @@ def run_headline(g, args, prob):
     out["tuning"] = idp.plan_tuning(plan)
 
     if args.profile_window > 0:
-        # a window of plain solves for a profiler that starts collecting here
+        # a window of solves for a profiler that starts collecting here
+        wplan = plan if args.profile_precision == "FP64" else \
+            g.plan(prob, args.order, getattr(idp, "IDP_PRECISION_" + args.profile_precision))
+        wphi = torch.empty_like(rho)
+        idp.solve(wplan, rho, wphi, g.stream)
         torch.cuda.synchronize()
         torch.cuda.cudart().cudaProfilerStart()
         for i in range(args.profile_window):
             g.flush.fill_(float(i))
-            idp.solve(plan, rho, phi, g.stream)
+            idp.solve(wplan, rho, wphi, g.stream)
         torch.cuda.synchronize()
         torch.cuda.cudart().cudaProfilerStop()
+        del wplan, wphi
 
     # end to end through the host-buffer entry point (pinned host memory, both
     # copies inside the timed region)
