@@ -2,15 +2,17 @@
 // of G * rho on every boundary node, evaluated as the paper rearranges it
 // (eqs. Trap2D, Trap2Dconvolution, convolution): for each face, a sum over the
 // slices parallel to it of aperiodic convolutions of the rho slice with
-// G(sqrt(dist^2 + |.|^2)), done with zero-padded FFTs of length 2M.
+// G(sqrt(dist^2 + |.|^2)), done with zero-padded FFTs of length 2P, P >= M
+// (P = M where M has an FFT here; otherwise the next length that has one: the
+// zero-padded cyclic convolution is exact for any 2P >= 2M - 1).
 //
 // 3-D data flow (faces of axis a; b < c the other two axes):
-//   stage 1  real FFT (length 2M_c) along c of every interior line of rho
-//   stage 2  FFT (length 2M_b) along b of every slice p, multiplied by the
+//   stage 1  real FFT (length 2P_c) along c of every interior line of rho
+//   stage 2  FFT (length 2P_b) along b of every slice p, multiplied by the
 //            kernel spectra of distance p h_a and (M_a - p) h_a, summed over p
 //   stage 3  inverse FFT along b, inverse real FFT along c, scatter to nodes.
 // The kernel spectra are real and even (the cyclic kernel is even), so only
-// frequencies 0..M are stored; they are computed once per plan.
+// frequencies 0..P are stored; they are computed once per plan.
 #include <type_traits>
 
 #include "fft.cuh"
@@ -29,8 +31,9 @@ struct LineCfg {
 };
 
 // ---------------------------------------------------------------- stage 1
-// L = M: complex FFT length; input line has M-1 reals at positions 1..M-1 of
-// a zero-padded sequence of length 2M; output X'_m = 2 X_m, m = 0..M.
+// L = P: complex FFT length; input line has M-1 reals (M = a.M <= L) at
+// positions 1..M-1 of a zero-padded sequence of length 2L; output X'_m = 2 X_m,
+// m = 0..L.
 // 2 x, exact: for a normal FP64 value by adding 1 to the exponent (integer pipe),
 // otherwise by the multiplication
 __device__ __forceinline__ double times2_exact(double x)
@@ -78,7 +81,8 @@ __global__ void __launch_bounds__(NT) rfft_kernel(const RfftPass a)
 {
     using A = Ar<R>;
     using Cx = typename A::C;
-    constexpr int M = L, N = M - 1, LB = LineCfg<L>::LB;
+    constexpr int LB = LineCfg<L>::LB;
+    const int M = a.M, N = M - 1;
     extern __shared__ double2 smem_raw[];
     Cx *bufA = reinterpret_cast<Cx *>(smem_raw), *bufB = bufA + LB * L;
     int nu, nv;
@@ -99,8 +103,8 @@ __global__ void __launch_bounds__(NT) rfft_kernel(const RfftPass a)
     // lines that are all zero (rho vanishes near the boundary): zero spectra
     auto write_zero = [&]() {
         Cx *outz = reinterpret_cast<Cx *>(a.out) + (int64_t)u * osu + (int64_t)v0 * osv;
-        for (int f = threadIdx.x; f < nl * (M + 1); f += NT) {
-            const int l = f / (M + 1), m = f - l * (M + 1);
+        for (int f = threadIdx.x; f < nl * (L + 1); f += NT) {
+            const int l = f / (L + 1), m = f - l * (L + 1);
             outz[(int64_t)l * osv + (int64_t)m * ose] = A::cmake(A::zero(), A::zero());
         }
     };
@@ -192,30 +196,30 @@ __global__ void __launch_bounds__(NT) rfft_kernel(const RfftPass a)
             const double Pp = w.swap ? Oi : Or, Qq = w.swap ? Or : Oi;
             const double u = fma(-w.r, Qq, Pp), v = fma(w.r, Pp, Qq);
             ol[(int64_t)m * ose] = make_double2(fma(w.mim, v, Er), fma(-w.mre, u, Ei));
-            ol[(int64_t)(M - m) * ose] = make_double2(fma(-w.mim, v, Er), -fma(w.mre, u, Ei));
+            ol[(int64_t)(L - m) * ose] = make_double2(fma(-w.mim, v, Er), -fma(w.mre, u, Ei));
         } else {
             const Cx w = half_tw<R>(a.t, m);
             const R Pr = A::mul_sub(A::re(w), Or, A::im(w), Oi);
             const R Pi = A::mul_add(A::re(w), Oi, A::im(w), Or);
             ol[(int64_t)m * ose] = A::cmake(A::add(Er, Pi), A::sub(Ei, Pr));
-            ol[(int64_t)(M - m) * ose] = A::cmake(A::sub(Er, Pi), A::neg(A::add(Ei, Pr)));
+            ol[(int64_t)(L - m) * ose] = A::cmake(A::sub(Er, Pi), A::neg(A::add(Ei, Pr)));
         }
         if constexpr (!std::is_same<R, double>::value) {
             if (m == 1) {
                 const Cx z0 = zl[0];
                 ol[0] = A::cmake(A::times2(A::add(A::re(z0), A::im(z0))), A::zero());
-                ol[(int64_t)M * ose] = A::cmake(A::times2(A::sub(A::re(z0), A::im(z0))), A::zero());
+                ol[(int64_t)L * ose] = A::cmake(A::times2(A::sub(A::re(z0), A::im(z0))), A::zero());
             }
         }
     }
     if constexpr (std::is_same<R, double>::value) {
-        // m = 0 and m = M, one lane per line (an FP64 warp instruction costs the
+        // m = 0 and m = L, one lane per line (an FP64 warp instruction costs the
         // pipe the same whatever its active lanes; Z is still intact)
         if (threadIdx.x < nl) {
             const double2 z0 = Z[threadIdx.x * L];
             double2 *ol = outb + (int64_t)threadIdx.x * osv;
             ol[0] = make_double2(times2_exact(z0.x + z0.y), 0.0);
-            ol[(int64_t)M * ose] = make_double2(times2_exact(z0.x - z0.y), 0.0);
+            ol[(int64_t)L * ose] = make_double2(times2_exact(z0.x - z0.y), 0.0);
         }
     }
 }
@@ -227,7 +231,7 @@ struct FaceCfg {
     static constexpr int TC = (1024 / L) > 32 ? 32 : ((1024 / L) < 1 ? 1 : 1024 / L);
 };
 
-// L = 2 Mb.  Block: TC consecutive frequencies c, one chunk of slices p.
+// L = 2 Pb (Pb >= Mb).  Block: TC consecutive frequencies c, one chunk of slices p.
 template <class R>
 __device__ __forceinline__ R ld_khat(const FacePass &a, int64_t i);
 template <>
@@ -244,7 +248,8 @@ __global__ void __launch_bounds__(NT, 4) face_kernel(const FacePass a)
     using A = Ar<R>;
     using Cx = typename A::C;
     constexpr int TC = FaceCfg<L>::TC;
-    constexpr int Mb = L / 2;
+    constexpr int Ph = L / 2;                     // frequencies 0..Ph of the even kernel spectra
+    const int Mb = a.Mb;                          // data: positions 1..Mb-1 along b
     constexpr int OPT = (TC * L + NT - 1) / NT;   // outputs per thread
     extern __shared__ double2 smem_raw[];
     Cx *bufA = reinterpret_cast<Cx *>(smem_raw), *bufB = bufA + TC * L;
@@ -259,7 +264,7 @@ __global__ void __launch_bounds__(NT, 4) face_kernel(const FacePass a)
         acc_lo[r] = A::cmake(A::zero(), A::zero());
         acc_hi[r] = A::cmake(A::zero(), A::zero());
     }
-    const int64_t kstride = (int64_t)(Mb + 1) * a.nc;
+    const int64_t kstride = (int64_t)(Ph + 1) * a.nc;
     const Cx *D = reinterpret_cast<const Cx *>(a.D);
     for (int p = p0; p < p1; ++p) {
         if (a.sliceflag && !a.sliceflag[p]) continue;   // slice of zeros: contributes nothing
@@ -275,8 +280,8 @@ __global__ void __launch_bounds__(NT, 4) face_kernel(const FacePass a)
                 const int j = f / TC, t = f - j * TC;   // consecutive threads: consecutive columns
                 Cx a0 = A::cmake(A::zero(), A::zero()), a1 = a0;
                 if (t < ncl) {
-                    if (j >= 1) a0 = Dp[(int64_t)(j - 1) * a.sb + (int64_t)t * a.sc];
-                    a1 = Dp[(int64_t)(j + Q - 1) * a.sb + (int64_t)t * a.sc];
+                    if (j >= 1 && j <= Mb - 1) a0 = Dp[(int64_t)(j - 1) * a.sb + (int64_t)t * a.sc];
+                    if (j + Q <= Mb - 1) a1 = Dp[(int64_t)(j + Q - 1) * a.sb + (int64_t)t * a.sc];
                 }
                 const Cx m1 = mul_mi(a1);
                 Cx *y = bufB + t * L + 4 * j;
@@ -305,7 +310,7 @@ __global__ void __launch_bounds__(NT, 4) face_kernel(const FacePass a)
             if (o < TC * L) {
                 const int m = o / TC, t = o - m * TC;
                 if (t < ncl) {
-                    const int mm = m <= Mb ? m : L - m;
+                    const int mm = m <= Ph ? m : L - m;
                     const Cx X = Z[t * L + m];
                     const R kl = ld_khat<R>(a, klo + (int64_t)mm * a.nc + t);
                     const R kh = ld_khat<R>(a, khi + (int64_t)mm * a.nc + t);
@@ -375,7 +380,7 @@ __global__ void __launch_bounds__(NT) face_invb_kernel(const FaceInvB a)
     using A = Ar<R>;
     using Cx = typename A::C;
     constexpr int TC = InvbCfg<L>::TC;
-    constexpr int Mb = L / 2;
+    const int Mb = a.Mb;   // rows 0..Mb are the face nodes along b (Mb <= L / 2)
     extern __shared__ double2 smem_raw[];
     Cx *bufA = reinterpret_cast<Cx *>(smem_raw), *bufB = bufA + TC * L;
     const int c0 = blockIdx.x * TC;
@@ -404,7 +409,8 @@ __global__ void __launch_bounds__(NT) face_invb_kernel(const FaceInvB a)
 }
 
 // ---------------------------------------------------------------- stage 3b
-// L = Mc.  One line = one row of one face.
+// L = Pc (inverse real FFT of length 2Pc, Pc >= Mc).  One line = one row of one
+// face; values 0..Mc of it are face nodes.
 template <class R, int L>
 __global__ void __launch_bounds__(NT) face_c2r_kernel(const FaceC2R a)
 {
@@ -436,13 +442,14 @@ __global__ void __launch_bounds__(NT) face_c2r_kernel(const FaceC2R a)
     }
     __syncthreads();
     const Cx *Z = cta_fft_t<R, L, LB, NT, true>(bufA, bufB, inv_tw<R>(a.t), false);
-    for (int f = threadIdx.x; f < LB * (L + 1); f += NT) {
-        const int l = f / (L + 1), t = f - l * (L + 1);
+    const int Mc = a.Mc;
+    for (int f = threadIdx.x; f < LB * (Mc + 1); f += NT) {
+        const int l = f / (Mc + 1), t = f - l * (Mc + 1);
         if (l >= nl) continue;
         const int row = r0 + l;
         if (a.skip_row_edges && (row == 0 || row == a.nrows - 1)) continue;
-        if (a.skip_col_edges && (t == 0 || t == L)) continue;
-        const Cx z = Z[l * L + (t >> 1)];   // t <= L, so t/2 < L
+        if (a.skip_col_edges && (t == 0 || t == Mc)) continue;
+        const Cx z = Z[l * L + (t >> 1)];   // t <= Mc <= L, so t/2 < L
         const R v = (t & 1) ? A::im(z) : A::re(z);
         const int64_t node = fbase + (int64_t)row * a.row_stride + (int64_t)t * a.col_stride;
         st_real<R>(a.dst0, node, v);
@@ -651,7 +658,7 @@ cudaError_t launch_rfft_pass(const RfftPass &a, cudaStream_t st)
     if (a.axis == 2) { nu = a.n0; nv = a.n1; }
     else if (a.axis == 1) { nu = a.n0; nv = a.n2; }
     else { nu = a.n1; nv = a.n2; }
-    IDP_LEN_SWITCH(a.M, {
+    IDP_LEN_SWITCH(a.P ? a.P : a.M, {
         dim3 grid((nv + LineCfg<L>::LB - 1) / LineCfg<L>::LB, nu);
         if (a.dd) rfft_kernel<ddr, L><<<grid, NT, smem_lines<L>(), st>>>(a);
         else rfft_kernel<double, L><<<grid, NT, smem_lines<L>(), st>>>(a);
@@ -661,7 +668,7 @@ cudaError_t launch_rfft_pass(const RfftPass &a, cudaStream_t st)
 
 cudaError_t launch_face_pass(const FacePass &a, int nchunk, cudaStream_t st)
 {
-    IDP_LEN_SWITCH(2 * a.Mb, {
+    IDP_LEN_SWITCH(2 * (a.Pb ? a.Pb : a.Mb), {
         dim3 grid((a.nc + FaceCfg<L>::TC - 1) / FaceCfg<L>::TC, nchunk);
         if (a.dd) face_kernel<ddr, L><<<grid, NT, smem_face<L>(), st>>>(a);
         else face_kernel<double, L><<<grid, NT, smem_face<L>(), st>>>(a);
@@ -677,7 +684,7 @@ cudaError_t launch_face_pass_2d(const FacePass2D &a, cudaStream_t st)
 
 cudaError_t launch_face_inv_b(const FaceInvB &a, cudaStream_t st)
 {
-    IDP_LEN_SWITCH(2 * a.Mb, {
+    IDP_LEN_SWITCH(2 * (a.Pb ? a.Pb : a.Mb), {
         dim3 grid((a.nc + InvbCfg<L>::TC - 1) / InvbCfg<L>::TC, 2);
         if (a.dd) face_invb_kernel<ddr, L><<<grid, NT, smem_invb<L>(), st>>>(a);
         else face_invb_kernel<double, L><<<grid, NT, smem_invb<L>(), st>>>(a);
@@ -687,7 +694,7 @@ cudaError_t launch_face_inv_b(const FaceInvB &a, cudaStream_t st)
 
 cudaError_t launch_face_c2r(const FaceC2R &a, cudaStream_t st)
 {
-    IDP_LEN_SWITCH(a.Mc, {
+    IDP_LEN_SWITCH(a.Pc ? a.Pc : a.Mc, {
         dim3 grid((a.nrows + C2rCfg<L>::LB - 1) / C2rCfg<L>::LB, 2);
         if (a.dd) face_c2r_kernel<ddr, L><<<grid, NT, smem_c2r<L>(), st>>>(a);
         else face_c2r_kernel<double, L><<<grid, NT, smem_c2r<L>(), st>>>(a);

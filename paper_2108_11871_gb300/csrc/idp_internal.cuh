@@ -121,14 +121,16 @@ int mp_tile_modes(int n);       // modes per tile (and image tile) for n modes: 
 
 // ---- boundary values (section 4) ------------------------------------------
 
-// Stage 1: real FFT of length 2M of each zero-padded line of interior data along
-// `axis`; output M+1 complex values per line, stored at out view (complex units).
+// Stage 1: real FFT of length 2P (P >= M) of each zero-padded line of interior
+// data along `axis`; output P+1 complex values per line, stored at out view
+// (complex units).
 struct RfftPass {
     const double *in; int64_t is0, is1, is2;     // real input, interior coords
     double2 *out; int64_t os0, os1, os2;          // complex output; `axis` coordinate = frequency m
     int n0, n1, n2;                               // interior box (extent along axis = M-1)
     int axis, M;
-    FftTables t;                                  // tables for complex length M
+    int P;                                        // complex FFT length (0: M)
+    FftTables t;                                  // tables for complex length P
     int dd;                                       // 1: double-float arithmetic, output as pairs
     const int *lineflag;   // optional: lineflag[u * nv + v] != 0 iff line (u, v) has a non-zero value
     // stage 1a (axis 2) only, optional: the pass also makes the support flags of
@@ -139,21 +141,22 @@ struct RfftPass {
 };
 cudaError_t launch_rfft_pass(const RfftPass &a, cudaStream_t st);
 
-// Stage 2 (3-D): for each face axis a, FFT of length 2Mb along b of the
-// stage-1 data of every slice p, times the kernel spectra, summed over p.
+// Stage 2 (3-D): for each face axis a, FFT of length 2Pb (Pb >= Mb) along b of
+// the stage-1 data of every slice p, times the kernel spectra, summed over p.
 struct FacePass {
     const double2 *D;          // stage-1 data
     int64_t sp, sb, sc;        // strides (complex units) of slice p, axis b, frequency c
     int np;                    // number of slices (M_a - 1)
-    int Mb;                    // panels along b (FFT length 2Mb)
-    int nc;                    // number of frequencies along c (M_c + 1)
-    const double *khat;        // [np][Mb+1][nc] real kernel spectra for distance (p+1) h_a
-    double2 *part;             // partial sums [nchunk][2][2Mb][nc]
+    int Mb;                    // panels along b (data at positions 1..Mb-1)
+    int nc;                    // number of frequencies along c (P_c + 1)
+    const double *khat;        // [np][Pb+1][nc] real kernel spectra for distance (p+1) h_a
+    double2 *part;             // partial sums [nchunk][2][2Pb][nc]
     int pchunk;                // slices per chunk
-    FftTables t;               // tables for complex length 2Mb
+    FftTables t;               // tables for complex length 2Pb
     int dd;                    // 1: double-float (D, part as pairs; khatd used)
     const ddr *khatd;          // kernel spectra as double-float pairs
     const int *sliceflag;      // optional: sliceflag[p] != 0 iff slice p has a non-zero value
+    int Pb;                    // half the FFT length along b (0: Mb)
 };
 cudaError_t launch_face_pass(const FacePass &a, int nchunk, cudaStream_t st);
 int face_columns_per_block(int L);   // frequencies c per block of the face pass
@@ -168,22 +171,24 @@ struct FacePass2D {
 };
 cudaError_t launch_face_pass_2d(const FacePass2D &a, cudaStream_t st);
 
-// Stage 3a (3-D): sum the partials and inverse FFT along b; keep rows 0..Mb.
+// Stage 3a (3-D): sum the partials and inverse FFT along b (length 2Pb); keep
+// rows 0..Mb.
 struct FaceInvB {
     const double2 *part; int nchunk;
     int Mb, nc;
     double2 *out;              // [2][Mb+1][nc]
-    FftTables t;               // length 2Mb
+    FftTables t;               // length 2Pb
     int dd;
+    int Pb;                    // 0: Mb
 };
 cudaError_t launch_face_inv_b(const FaceInvB &a, cudaStream_t st);
 
-// Stage 3b: inverse real FFT of length 2Mc of each row (Mc+1 Hermitian
-// coefficients) and scatter the first Mc+1 values into the face nodes of
-// up to two node arrays.  Row r of face f (lo/hi) maps to nodes
+// Stage 3b: inverse real FFT of length 2Pc (Pc >= Mc) of each row (Pc+1
+// Hermitian coefficients) and scatter the first Mc+1 values into the face nodes
+// of up to two node arrays.  Row r of face f (lo/hi) maps to nodes
 // base_f + r*row_stride + j*col_stride.
 struct FaceC2R {
-    const double2 *in;         // [2][nrows][Mc+1]
+    const double2 *in;         // [2][nrows][Pc+1]
     int nrows, Mc;
     double *dst0, *dst1;       // node arrays (dst1 may be null)
     int64_t base[2];           // node offset of row 0, col 0 for lo / hi
@@ -191,8 +196,9 @@ struct FaceC2R {
     // ownership: skip rows r with skip_row_lo/hi set (edge already owned by a
     // lower face axis) and columns with col in {0, Mc} if skip_cols is set.
     int skip_row_edges, skip_col_edges;
-    FftTables t;               // length Mc
+    FftTables t;               // length Pc
     int dd;
+    int Pc;                    // 0: Mc
 };
 cudaError_t launch_face_c2r(const FaceC2R &a, cudaStream_t st);
 

@@ -38,6 +38,19 @@ bool supported_panels(int64_t M)
     return M >= 16 && M <= 512 && (is_pow2(M) || (M >= 48 && M % 3 == 0 && is_pow2(M / 3)));
 }
 
+// panel counts whose sine transform runs as an FFT here
+bool has_fft_dst(int64_t M) { return supported_panels(M); }
+
+// half the length of the zero-padded boundary convolutions for M panels: the
+// smallest complex FFT length here that is >= M (M itself where it has one)
+int conv_half(int64_t M)
+{
+    const int lens[12] = {16, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
+    for (int L : lens)
+        if (L >= M) return L;
+    return 0;
+}
+
 // the smallest supported panel count >= M (0 if there is none)
 int64_t padded_panels(int64_t M)
 {
@@ -136,6 +149,7 @@ struct idp_plan_s {
     BatchCache *batch = nullptr;         // batched graph owned by this plan (first of its batch)
     int n[3] = {1, 1, 1};      // internal node counts (2-D: n[0] = 1)
     int M[3] = {0, 0, 0};
+    int P[3] = {0, 0, 0};      // half the length of the boundary convolutions along each axis (P >= M)
     int ni[3] = {1, 1, 1};     // interior extents
     int act[3] = {0, 0, 0};
     double h[3] = {1, 1, 1};
@@ -695,7 +709,7 @@ int e_layers(idp_plan p, cudaStream_t st)
 int transform_rho_from_T0(idp_plan p, cudaStream_t st)
 {
     const View3 none{nullptr, 0, 0, 0};
-    const int64_t row = 2 * (int64_t)(p->M[2] + 1);   // doubles per T0 row
+    const int64_t row = 2 * (int64_t)(p->P[2] + 1);   // doubles per T0 row
     const View3 im{reinterpret_cast<double *>(p->T0) + 3, (int64_t)p->ni[1] * row, row, 2};
     const int dd = boundary_dd(p);   // T0 holds pairs
     return transform(p, im, p->A, dense(p, p->A), p->tabc2, none, true, st, true, true, dd);
@@ -722,10 +736,10 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
     a2.copy = rho_src ? r.p : nullptr;
     a2.is0 = r.s0; a2.is1 = r.s1; a2.is2 = r.s2;
     a2.out = p->T0;
-    a2.os2 = 1; a2.os1 = p->M[2] + 1; a2.os0 = (int64_t)p->ni[1] * (p->M[2] + 1);
+    a2.os2 = 1; a2.os1 = p->P[2] + 1; a2.os0 = (int64_t)p->ni[1] * (p->P[2] + 1);
     a2.n0 = p->ni[0]; a2.n1 = p->ni[1]; a2.n2 = p->ni[2];
-    a2.axis = 2; a2.M = p->M[2];
-    if ((rc = get_fft(p, p->M[2], &t))) return rc;
+    a2.axis = 2; a2.M = p->M[2]; a2.P = p->P[2];
+    if ((rc = get_fft(p, p->P[2], &t))) return rc;
     a2.t = t;
     a2.dd = dd;
     // the pass along axis 2 reads every value of rho once: it also marks which
@@ -735,10 +749,10 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
     a2.fl_sl0 = p->sl[0]; a2.fl_sl1 = p->sl[1]; a2.fl_sl2 = p->sl[2];
     a1.in = r.p; a1.is0 = r.s0; a1.is1 = r.s1; a1.is2 = r.s2;
     a1.out = p->T1;
-    a1.os1 = 1; a1.os2 = p->M[1] + 1; a1.os0 = (int64_t)p->ni[2] * (p->M[1] + 1);
+    a1.os1 = 1; a1.os2 = p->P[1] + 1; a1.os0 = (int64_t)p->ni[2] * (p->P[1] + 1);
     a1.n0 = p->ni[0]; a1.n1 = p->ni[1]; a1.n2 = p->ni[2];
-    a1.axis = 1; a1.M = p->M[1];
-    if ((rc = get_fft(p, p->M[1], &t))) return rc;
+    a1.axis = 1; a1.M = p->M[1]; a1.P = p->P[1];
+    if ((rc = get_fft(p, p->P[1], &t))) return rc;
     a1.t = t;
     a1.dd = dd;
     a1.lineflag = p->row1;
@@ -769,10 +783,10 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
         for (int face = 1; face <= 2; ++face) {
             FacePass2D a{};
             const int other = face == 1 ? 2 : 1;
-            if (face == 1) { a.T = p->T0; a.sp = p->M[2] + 1; a.sm = 1; }
-            else { a.T = p->T1; a.sp = p->M[1] + 1; a.sm = 1; }
+            if (face == 1) { a.T = p->T0; a.sp = p->P[2] + 1; a.sm = 1; }
+            else { a.T = p->T1; a.sp = p->P[1] + 1; a.sm = 1; }
             a.np = p->ni[face];
-            a.nm = p->M[other] + 1;
+            a.nm = p->P[other] + 1;
             a.khat = p->khat[face];
             a.acc = p->F;
             {
@@ -780,12 +794,12 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
                 IDP_CK(launch_face_pass_2d(a, st));
             }
             FaceC2R c{};
-            c.in = p->F; c.nrows = 1; c.Mc = p->M[other];
+            c.in = p->F; c.nrows = 1; c.Mc = p->M[other]; c.Pc = p->P[other];
             c.dst0 = dst0; c.dst1 = dst1;
             c.base[0] = 0; c.base[1] = (int64_t)p->M[face] * p->ns[face];
             c.row_stride = 0; c.col_stride = p->ns[other];
             c.skip_row_edges = 0; c.skip_col_edges = (face == 2);
-            if ((rc = get_fft(p, p->M[other], &t))) return rc;
+            if ((rc = get_fft(p, p->P[other], &t))) return rc;
             c.t = t;
             Mark mk(p, IDP_KERNEL_FACE_C2R, st);
             IDP_CK(launch_face_c2r(c, st));
@@ -799,16 +813,17 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
         cudaStream_t sa = (conc && a_ < 2) ? p->fst[a_] : st;
         double2 *part = p->part + a_ * p->part_cap, *F = p->F + a_ * p->f_cap;
         FacePass f{};
-        if (a_ == 0) { f.D = p->T0; f.sp = (int64_t)p->ni[1] * (p->M[2] + 1); f.sb = p->M[2] + 1; f.sc = 1; }
-        else if (a_ == 1) { f.D = p->T0; f.sp = p->M[2] + 1; f.sb = (int64_t)p->ni[1] * (p->M[2] + 1); f.sc = 1; }
-        else { f.D = p->T1; f.sp = p->M[1] + 1; f.sb = (int64_t)p->ni[2] * (p->M[1] + 1); f.sc = 1; }
+        if (a_ == 0) { f.D = p->T0; f.sp = (int64_t)p->ni[1] * (p->P[2] + 1); f.sb = p->P[2] + 1; f.sc = 1; }
+        else if (a_ == 1) { f.D = p->T0; f.sp = p->P[2] + 1; f.sb = (int64_t)p->ni[1] * (p->P[2] + 1); f.sc = 1; }
+        else { f.D = p->T1; f.sp = p->P[1] + 1; f.sb = (int64_t)p->ni[2] * (p->P[1] + 1); f.sc = 1; }
         f.np = p->ni[a_];
         f.Mb = p->M[b];
-        f.nc = p->M[c] + 1;
+        f.Pb = p->P[b];
+        f.nc = p->P[c] + 1;
         f.khat = p->khat[a_];
         f.part = part;
         f.pchunk = p->pchunk[a_];
-        if ((rc = get_fft(p, 2 * p->M[b], &t))) return rc;
+        if ((rc = get_fft(p, 2 * p->P[b], &t))) return rc;
         f.t = t;
         f.dd = dd;
         f.khatd = p->khatd[a_];
@@ -819,20 +834,20 @@ int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStre
         }
         FaceInvB ib{};
         ib.part = part; ib.nchunk = p->nchunk[a_];
-        ib.Mb = p->M[b]; ib.nc = f.nc; ib.out = F; ib.t = t;
+        ib.Mb = p->M[b]; ib.Pb = p->P[b]; ib.nc = f.nc; ib.out = F; ib.t = t;
         ib.dd = dd;
         {
             Mark mk(p, IDP_KERNEL_FACE_INVB, sa);
             IDP_CK(launch_face_inv_b(ib, sa));
         }
         FaceC2R cr{};
-        cr.in = F; cr.nrows = p->M[b] + 1; cr.Mc = p->M[c];
+        cr.in = F; cr.nrows = p->M[b] + 1; cr.Mc = p->M[c]; cr.Pc = p->P[c];
         cr.dst0 = dst0; cr.dst1 = dst1;
         cr.base[0] = 0; cr.base[1] = (int64_t)p->M[a_] * p->ns[a_];
         cr.row_stride = p->ns[b]; cr.col_stride = p->ns[c];
         cr.skip_row_edges = (a_ >= 1);
         cr.skip_col_edges = (a_ == 2);
-        if ((rc = get_fft(p, p->M[c], &t))) return rc;
+        if ((rc = get_fft(p, p->P[c], &t))) return rc;
         cr.t = t;
         cr.dd = dd;
         Mark mk(p, IDP_KERNEL_FACE_C2R, sa);
@@ -1098,8 +1113,8 @@ int plan_setup(idp_plan p)
         if (!p->act[s]) continue;
         FftTables t;
         const double *sn;
-        if ((rc = get_fft(p, p->M[s] / 2, &t)) || (rc = get_fft(p, p->M[s], &t)) ||
-            (rc = get_fft(p, 2 * p->M[s], &t)) || (rc = get_sin2(p, p->M[s], &sn)))
+        if ((has_fft_dst(p->M[s]) && ((rc = get_fft(p, p->M[s] / 2, &t)) || (rc = get_sin2(p, p->M[s], &sn)))) ||
+            (rc = get_fft(p, p->P[s], &t)) || (rc = get_fft(p, 2 * p->P[s], &t)))
             return rc;
     }
     if (p->padded) {
@@ -1113,8 +1128,8 @@ int plan_setup(idp_plan p)
         (rc = p->alloc(&p->tabc, p->nint)) || (rc = p->alloc(&p->tab4, p->nint)) ||
         (rc = p->alloc(&p->tabc2, p->nint)))
         return rc;
-    if ((rc = p->alloc(&p->T0, (int64_t)p->ni[0] * p->ni[1] * (p->M[2] + 1))) ||
-        (rc = p->alloc(&p->T1, (int64_t)p->ni[0] * p->ni[2] * (p->M[1] + 1))))
+    if ((rc = p->alloc(&p->T0, (int64_t)p->ni[0] * p->ni[1] * (p->P[2] + 1))) ||
+        (rc = p->alloc(&p->T1, (int64_t)p->ni[0] * p->ni[2] * (p->P[1] + 1))))
         return rc;
     {
         const int64_t q0 = 2 * (int64_t)p->ni[1] * p->ni[2], q1 = 2 * (int64_t)p->ni[0] * p->ni[2],
@@ -1196,7 +1211,7 @@ int plan_setup(idp_plan p)
         int64_t fmax = 0;
         for (int face = 1; face <= 2; ++face) {
             const int other = face == 1 ? 2 : 1;
-            const int Mb = p->M[other];
+            const int Mb = p->P[other];   // spectra of the cyclic kernel of length 2P
             const int np = p->ni[face];
             if ((rc = p->alloc(&p->khat[face], (int64_t)np * (Mb + 1)))) return rc;
             double *kb, *tb;
@@ -1222,7 +1237,8 @@ int plan_setup(idp_plan p)
         for (int a_ = 0; a_ < 3; ++a_) {
             const int b = a_ == 0 ? 1 : 0;
             const int c = a_ == 2 ? 1 : 2;
-            const int Mb = p->M[b], Mc = p->M[c], np = p->ni[a_];
+            // spectra of the cyclic kernel of length 2P along b and c
+            const int Mb = p->P[b], Mc = p->P[c], np = p->ni[a_];
             const int L = 2 * Mb;
             const int TC = face_columns_per_block(L);
             const int tiles = (Mc + 1 + TC - 1) / TC;
@@ -1308,7 +1324,7 @@ int autotune(idp_plan p)
     if (p->d == 3) {
         for (int a_ = 0; a_ < 3 && !rc; ++a_) {
             const int b = a_ == 0 ? 1 : 0, c = a_ == 2 ? 1 : 2;
-            const int np = p->ni[a_], L = 2 * p->M[b], nc = p->M[c] + 1;
+            const int np = p->ni[a_], L = 2 * p->P[b], nc = p->P[c] + 1;
             const int n0 = p->nchunk[a_];
             int cands[4] = {std::max(1, n0 / 2), n0, std::min(np, 2 * n0), std::min(np, 4 * n0)};
             int best_n = n0, best_p = p->pchunk[a_];
@@ -1323,17 +1339,19 @@ int autotune(idp_plan p)
                     p->part_cap = (int64_t)nch * 2 * L * nc;
                 }
                 FacePass f{};
-                if (a_ == 0) { f.D = p->T0; f.sp = (int64_t)p->ni[1] * (p->M[2] + 1); f.sb = p->M[2] + 1; f.sc = 1; }
-                else if (a_ == 1) { f.D = p->T0; f.sp = p->M[2] + 1; f.sb = (int64_t)p->ni[1] * (p->M[2] + 1); f.sc = 1; }
-                else { f.D = p->T1; f.sp = p->M[1] + 1; f.sb = (int64_t)p->ni[2] * (p->M[1] + 1); f.sc = 1; }
-                f.np = np; f.Mb = p->M[b]; f.nc = nc; f.khat = p->khat[a_]; f.part = p->part; f.pchunk = pch;
+                if (a_ == 0) { f.D = p->T0; f.sp = (int64_t)p->ni[1] * (p->P[2] + 1); f.sb = p->P[2] + 1; f.sc = 1; }
+                else if (a_ == 1) { f.D = p->T0; f.sp = p->P[2] + 1; f.sb = (int64_t)p->ni[1] * (p->P[2] + 1); f.sc = 1; }
+                else { f.D = p->T1; f.sp = p->P[1] + 1; f.sb = (int64_t)p->ni[2] * (p->P[1] + 1); f.sc = 1; }
+                f.np = np; f.Mb = p->M[b]; f.Pb = p->P[b]; f.nc = nc; f.khat = p->khat[a_]; f.part = p->part;
+                f.pchunk = pch;
                 FftTables t;
                 if ((rc = get_fft(p, L, &t))) break;
                 f.t = t;
                 // the chunk count sets the work of the face pass and of the
                 // partial-sum reduction that follows it: time both
                 FaceInvB ib{};
-                ib.part = p->part; ib.nchunk = nch; ib.Mb = p->M[b]; ib.nc = nc; ib.out = p->F; ib.t = t;
+                ib.part = p->part; ib.nchunk = nch; ib.Mb = p->M[b]; ib.Pb = p->P[b]; ib.nc = nc; ib.out = p->F;
+                ib.t = t;
                 const float ms = timed([&]() -> int {
                     cudaError_t e = launch_face_pass(f, nch, st);
                     if (e == cudaSuccess) e = launch_face_inv_b(ib, st);
@@ -1534,6 +1552,7 @@ int idp_create_plan(idp_plan *out, int d, const int64_t n[], const double h[], i
     p->unodes = (int64_t)p->un[0] * p->un[1] * p->un[2];
     for (int s = 0; s < 3; ++s) {
         p->M[s] = p->n[s] - 1;
+        p->P[s] = p->act[s] ? conv_half(p->M[s]) : p->M[s];
         p->ni[s] = p->act[s] ? p->n[s] - 2 : 1;
     }
     p->ns[2] = 1; p->ns[1] = p->n[2]; p->ns[0] = (int64_t)p->n[1] * p->n[2];
