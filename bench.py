@@ -290,9 +290,9 @@ class Gpu:
             import torch.distributed as dist
             dist.barrier()
 
-    def plan(self, prob, order, prec=None, shape=None, bdd=False):
+    def plan(self, prob, order, prec=None, shape=None, bdd=False, exact=False):
         idp = self.idp
-        plan = idp.create_plan(prob.d, prob.n, prob.h, order)
+        plan = idp.create_plan(prob.d, prob.n, prob.h, order, exact=exact)
         if prec is not None:
             idp.plan_set(plan, idp.IDP_KEY_PRECISION, prec)
         if bdd:
@@ -351,11 +351,11 @@ def rel(a, b):
     return float((a - b).abs().max().item() / b.abs().max().item())
 
 
-def variant_record(g, prob, order, prec, label, rho, phi_ref, steps, warmup, bdd=False):
+def variant_record(g, prob, order, prec, label, rho, phi_ref, steps, warmup, bdd=False, exact=False):
     """A reduced-precision variant of the workload: throughput, per-kernel times and
-    its max difference from the FP64 result."""
+    its max difference from the FP64 result (or from phi_ref)."""
     idp = g.idp
-    plan = g.plan(prob, order, prec, bdd=bdd)
+    plan = g.plan(prob, order, prec, bdd=bdd, exact=exact)
     phi = g.torch.empty_like(rho)
     ms = g.timed(lambda: idp.solve(plan, rho, phi, g.stream), steps, warmup)
     idp.plan_status(plan)
@@ -363,7 +363,7 @@ def variant_record(g, prob, order, prec, label, rho, phi_ref, steps, warmup, bdd
     ks = g.kernels(plan, rho, phi)
     rec = {"variant": label, "tuning": idp.plan_tuning(plan),
            "value": g.world * prob.points * steps / (t / 1e3), "unit": UNIT, "ms_per_step": t / steps,
-           "max_rel_error_vs_fp64": rel(phi, phi_ref),
+           "max_rel_error_vs_fp64": rel(phi, phi_ref) if phi_ref is not None else None,
            "kernel_ms_per_step": {k: sum(v) / 3 for k, v in ks.items()}}
     for fam in ("mixed_pass", "dst_pass"):
         if fam in ks:
@@ -500,6 +500,43 @@ def run_sweep(g, args):
     return rec
 
 
+def run_sweep_exact(g, args):
+    """The precision sweep at its stated sizes, 256^3 and 384 x 256 x 256 interior
+    points (M = 257 and 385: no FFT here), on plans that solve on the grid as given
+    (idp_create_plan_exact): the tensor-core modes, whose sine-matrix products take
+    any length, each against the oracle; FP64 on the ordinary (padded) plan."""
+    import torch
+    from oracle import solve as osolve
+    idp = g.idp
+    out = {}
+    for key, interior in (("interior_256^3", (256, 256, 256)), ("interior_384x256x256", (384, 256, 256))):
+        prob = w.c4_sweep(interior)
+        rho_h = prob.rho()
+        ref = osolve.solve(rho_h, prob.h, args.order, boundary="convolution")
+        scale = np.abs(ref).max()
+        rho = torch.from_numpy(rho_h).to(g.dev)
+        rec = {"workload": describe(prob, args.order)}
+        plan = g.plan(prob, args.order)   # padded FP64
+        phi = torch.empty_like(rho)
+        ms = g.timed(lambda: idp.solve(plan, rho, phi, g.stream), args.steps, args.warmup)
+        idp.plan_status(plan)
+        rec["fp64_padded"] = {"value": prob.points / (statistics.mean(ms) / 1e3), "ms_per_step": statistics.mean(ms),
+                              "grid_solved": idp.plan_grid(plan)[0],
+                              "max_rel_error_vs_oracle": float(np.abs(phi.cpu().numpy() - ref).max() / scale)}
+        del plan
+        for vk, name, bdd in (("mixed_precision", "MIXED_BF16X3", False), ("mixed_tf32x3", "MIXED_TF32X3", False),
+                              ("mixed_df32_boundary", "MIXED_BF16X3", True)):
+            ph, r = variant_record(g, prob, args.order, getattr(idp, "IDP_PRECISION_" + name), vk, rho, None,
+                                   args.steps, args.warmup, bdd=bdd, exact=True)
+            rec[vk] = {"value": r["value"], "ms_per_step": r["ms_per_step"], "exact_grid": True,
+                       "max_rel_error_vs_oracle": float(np.abs(ph.cpu().numpy() - ref).max() / scale)}
+            del ph
+        out[key] = rec
+        del rho, phi
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_bump(g, args):
     """The 129^3 bump workload (FP64): throughput and the error against its exact potential."""
     prob = workload("bump")
@@ -570,6 +607,8 @@ def run_ours(args, rank, world):
         g.torch.cuda.empty_cache()
         line["bump_129"] = run_bump(g, args)
         line["sweep_257"] = run_sweep(g, args)
+        g.torch.cuda.empty_cache()
+        line["sweep_exact"] = run_sweep_exact(g, args)
         g.torch.cuda.empty_cache()
         line["batched"] = run_batched(g, args, rank)
     if rank != 0:

@@ -158,6 +158,19 @@ typedef struct idp_plan_s *idp_plan;
  * on the current CUDA device; synchronises that device before returning. */
 int idp_create_plan(idp_plan *out, int d, const int64_t n[], const double h[], int order);
 
+/* Create a plan that solves on the grid as given, for any panel count
+ * 7 <= n[s] - 1 <= 512 (no padding; section 2's remedy of extending the domain
+ * is what idp_create_plan does).  Arguments as idp_create_plan; n[s] >= 8.
+ * Sine transforms whose length has no FFT here run as direct sums
+ * (O(n) work per point and axis: FP64 in precision FP64, double-float in the
+ * other modes) -- except in the tensor-core modes, whose sine-matrix products
+ * take any length, so that there only the transform producing u1 and the
+ * transforms of the boundary layers are direct sums.  The boundary
+ * convolutions use the smallest FFT length 2P >= 2M (P = M where M has one).
+ * Meant for the tensor-core modes (the precision sweep of 256^3 and
+ * 384 x 256 x 256 interior points); in FP64 a padded plan is faster. */
+int idp_create_plan_exact(idp_plan *out, int d, const int64_t n[], const double h[], int order);
+
 /* Set a plan option (IDP_KEY_*). */
 int idp_plan_set(idp_plan plan, int key, int64_t value);
 

@@ -54,6 +54,8 @@ def library(path: str = None):
     sig = {
         "idp_create_plan": (_int, [ctypes.POINTER(_vp), _int, ctypes.POINTER(_i64),
                                    ctypes.POINTER(_dbl), _int]),
+        "idp_create_plan_exact": (_int, [ctypes.POINTER(_vp), _int, ctypes.POINTER(_i64),
+                                         ctypes.POINTER(_dbl), _int]),
         "idp_plan_set": (_int, [_vp, _int, _i64]),
         "idp_solve": (_int, [_vp, _vp, _vp, _vp]),
         "idp_solve_host": (_int, [_vp, _vp, _vp, _vp]),
@@ -131,15 +133,16 @@ class Plan:
             pass
 
 
-def create_plan(d, n, h, order=6) -> Plan:
+def create_plan(d, n, h, order=6, exact=False) -> Plan:
+    """idp_create_plan, or idp_create_plan_exact (exact=True: the grid as given)."""
     n = [int(v) for v in n]
     h = [float(v) for v in h]
     if len(n) != d or len(h) != d:
         raise ValueError("n and h need d entries")
     out = _vp()
-    rc = library().idp_create_plan(ctypes.byref(out), int(d), (_i64 * d)(*n), (_dbl * d)(*h),
-                                   int(order))
-    _check(rc, "idp_create_plan")
+    fn = library().idp_create_plan_exact if exact else library().idp_create_plan
+    rc = fn(ctypes.byref(out), int(d), (_i64 * d)(*n), (_dbl * d)(*h), int(order))
+    _check(rc, "idp_create_plan_exact" if exact else "idp_create_plan")
     return Plan(out.value, d, n, h, order)
 
 

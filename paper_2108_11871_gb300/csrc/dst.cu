@@ -333,6 +333,99 @@ __global__ void __launch_bounds__(NTB) dst_pass_kernel(const DstPass a)
     }
 }
 
+// Direct sine sums for line lengths without an FFT here (any M <= 513): every
+// output U_e = 4 sum_i S[i][e] x_i with S[i][e] = sin(pi (i+1)(e+1) / M) from the
+// table a.sinm (FP64, or double-float pairs when R is ddr), stored with e fastest
+// so that consecutive threads read consecutive entries.  LBD lines per block, held
+// in shared memory; thread t computes modes t, t + 256 for all of them.  The same
+// epilogue as the FFT pass.
+constexpr int LBD = 16, DMAX = 2;   // lines per block, modes per thread (N <= 512)
+
+template <class R>
+__global__ void __launch_bounds__(NT) dst_direct_kernel(const DstPass a)
+{
+    pdl_enter();
+    using A = Ar<R>;
+    const int M = a.M, N = M - 1;
+    extern __shared__ double2 smem_raw[];
+    R *xs = reinterpret_cast<R *>(smem_raw);   // [LBD][N]
+    const int nv = a.axis == 2 ? a.n1 : a.n2;
+    const int u = blockIdx.y;
+    const int v0 = blockIdx.x * LBD;
+    const int nl = min(LBD, nv - v0);
+    const bool contig = (a.axis == 2);
+    int64_t isu, isv, ise;
+    view_strides(a.in, a.axis, isu, isv, ise);
+    const int64_t inb = (int64_t)u * isu + (int64_t)v0 * isv;
+    for (int f = threadIdx.x; f < LBD * N; f += NT) {
+        int l, i;
+        if (contig) { l = f / N; i = f - l * N; }
+        else { i = f / LBD; l = f - i * LBD; }
+        xs[l * N + i] = l < nl ? Io<R>::ld(a.in.p, inb + (int64_t)l * isv + (int64_t)i * ise, a.in_dd) : A::zero();
+    }
+    __syncthreads();
+    R acc[DMAX][LBD];
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j)
+#pragma unroll
+        for (int l = 0; l < LBD; ++l) acc[j][l] = A::zero();
+    const R *S = reinterpret_cast<const R *>(a.sinm);
+    for (int i = 0; i < N; ++i) {
+#pragma unroll
+        for (int j = 0; j < DMAX; ++j) {
+            const int e = threadIdx.x + j * NT;
+            if (e >= N) break;
+            const R sv = S[(int64_t)i * N + e];
+#pragma unroll
+            for (int l = 0; l < LBD; ++l) acc[j][l] = A::fma(sv, xs[l * N + i], acc[j][l]);
+        }
+    }
+    int64_t osu, osv, ose, asu, asv, ase, tsu, tsv, tse;
+    view_strides(a.out, a.axis, osu, osv, ose);
+    view_strides(a.add, a.axis, asu, asv, ase);
+    {
+        const View3 tv{nullptr, (int64_t)a.n1 * a.n2, a.n2, 1};
+        view_strides(tv, a.axis, tsu, tsv, tse);
+    }
+    const int64_t outb = (int64_t)u * osu + (int64_t)v0 * osv;
+    const int64_t tabb = (int64_t)u * tsu + (int64_t)v0 * tsv;
+    const int64_t addb = (int64_t)u * asu + (int64_t)v0 * asv;
+    const bool has_tab = a.tab || a.tabd;
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j) {
+        const int e = threadIdx.x + j * NT;
+        if (e >= N) break;
+#pragma unroll
+        for (int l = 0; l < LBD; ++l) {
+            if (l >= nl) break;
+            R y = times4_exact(acc[j][l]);
+            const int64_t ti = tabb + (int64_t)l * tsv + (int64_t)e * tse;
+            const int64_t ai = addb + (int64_t)l * asv + (int64_t)e * ase;
+            if (has_tab) {
+                const R t = Io<R>::ld(a.tabd ? (const void *)a.tabd : (const void *)a.tab, ti, a.tabd != nullptr);
+                if (a.add.p) y = A::fma(t, y, Io<R>::ld(a.add.p, ai, a.add_dd));
+                else y = A::mul(t, y);
+            } else if (a.add.p) {
+                y = A::add(y, Io<R>::ld(a.add.p, ai, a.add_dd));
+            }
+            Io<R>::st(a.out.p, outb + (int64_t)l * osv + (int64_t)e * ose, y, a.out_dd);
+        }
+    }
+}
+
+template <class R>
+cudaError_t launch_direct(const DstPass &a, cudaStream_t st)
+{
+    if (a.M - 1 > DMAX * NT || !a.sinm) return cudaErrorInvalidValue;
+    int nu, nv;
+    if (a.axis == 2) { nu = a.n0; nv = a.n1; }
+    else if (a.axis == 1) { nu = a.n0; nv = a.n2; }
+    else { nu = a.n1; nv = a.n2; }
+    const size_t sm = sizeof(R) * LBD * (a.M - 1);
+    dim3 grid((nv + LBD - 1) / LBD, nu);
+    return launch_pdl(dst_direct_kernel<R>, grid, dim3(NT), sm, st, a);
+}
+
 template <class R, int K, int LBO, int NTB = NT>
 cudaError_t launch_lb(const DstPass &a, int nu, int nv, cudaStream_t st)
 {
@@ -436,7 +529,7 @@ cudaError_t launch_r(const DstPass &a, cudaStream_t st)
     case 256: return launch_k<R, 128>(a, st);
     case 384: return launch_k<R, 192>(a, st);
     case 512: return launch_k<R, 256>(a, st);
-    default: return cudaErrorInvalidValue;
+    default: return launch_direct<R>(a, st);   // no FFT for this length: direct sums
     }
 }
 
@@ -446,7 +539,11 @@ cudaError_t dst_set_attributes()
 {
     cudaError_t e = attrs<double>();
     if (e != cudaSuccess) return e;
-    return attrs<ddr>();
+    if ((e = attrs<ddr>()) != cudaSuccess) return e;
+    const int sm = (int)(sizeof(double) * LBD * DMAX * NT);
+    if ((e = cudaFuncSetAttribute(dst_direct_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
+        return e;
+    return cudaFuncSetAttribute(dst_direct_kernel<ddr>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
 cudaError_t launch_dst_pass(const DstPass &a, cudaStream_t st)

@@ -63,6 +63,8 @@ struct DstPass {
     const ddr *sin2d;
     int lines;   // lines per block: 0 = by size (8 for launches of < 2 blocks per SM), 8 = always 8,
                  // -8 = 8 lines on 128 threads (M = 128), 32 (M = 128), 16 (M = 256)
+    const void *sinm;      // lengths without an FFT: the sine matrix S[i][e] = sin(pi (i+1)(e+1)/M),
+                           // e fastest, FP64 (dd = 0) or double-float pairs (dd = 1): direct sums
 };
 
 // Programmatic dependent launch: a kernel launched with launch_pdl lets the next

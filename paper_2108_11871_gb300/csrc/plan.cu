@@ -170,6 +170,9 @@ struct idp_plan_s {
     std::map<int, DevFft> fft;        // by complex length
     std::map<int, double *> sin2;     // by M: 2 sin(pi j / M), j = 0..M/2
     std::map<int, ddr *> sin2d;       // double-float form
+    std::map<int, double *> sinm;     // by M (lengths without an FFT): sine matrices for direct sums
+    std::map<int, ddr *> sinmd;       // double-float form
+    int exact = 0;                    // created by idp_create_plan_exact
     std::vector<void *> allocs;
     static constexpr size_t GUARD = 256;              // keeps the buffers 256-byte aligned
     static constexpr unsigned char GUARD_BYTE = 0xA5;
@@ -362,6 +365,33 @@ int get_sin2(idp_plan p, int M, const double **out)
     p->sin2[M] = d;
     p->sin2d[M] = dd;
     *out = d;
+    return IDP_OK;
+}
+
+// sine matrix S[i][e] = sin(pi (i+1)(e+1) / M), i, e < M - 1, e fastest, for the
+// direct sums of the lengths without an FFT; FP64 and double-float forms
+int get_sinm(idp_plan p, int M, const void **out, int dd)
+{
+    auto it = p->sinm.find(M);
+    if (it == p->sinm.end()) {
+        const int N = M - 1;
+        std::vector<double> s((size_t)N * N);
+        std::vector<ddr> sd((size_t)N * N);
+        for (int i = 0; i < N; ++i)
+            for (int e = 0; e < N; ++e) {
+                s[(size_t)i * N + e] = sinpi_frac((int64_t)(i + 1) * (e + 1), M);
+                sd[(size_t)i * N + e] = host_dd(s[(size_t)i * N + e]);
+            }
+        double *d = nullptr;
+        ddr *d2 = nullptr;
+        int rc;
+        if ((rc = p->alloc(&d, (int64_t)N * N)) || (rc = p->alloc(&d2, (int64_t)N * N))) return rc;
+        IDP_CK(cudaMemcpy(d, s.data(), sizeof(double) * s.size(), cudaMemcpyHostToDevice));
+        IDP_CK(cudaMemcpy(d2, sd.data(), sizeof(ddr) * sd.size(), cudaMemcpyHostToDevice));
+        p->sinm[M] = d;
+        p->sinmd[M] = d2;
+    }
+    *out = dd ? (const void *)p->sinmd[M] : (const void *)p->sinm[M];
     return IDP_OK;
 }
 
@@ -597,13 +627,17 @@ int transform(idp_plan p, View3 in, double *work, View3 out, const double *tab, 
         a.n0 = p->ni[0]; a.n1 = p->ni[1]; a.n2 = p->ni[2];
         a.axis = s;
         a.M = p->M[s];
-        FftTables t;
-        int rc = get_fft(p, p->M[s] / 2, &t);
-        if (rc) return rc;
-        a.tw = t.fwd;
-        a.half = t.half;
-        a.halfr = t.halfr;
-        if ((rc = get_sin2(p, p->M[s], &a.sin2))) return rc;
+        FftTables t{};
+        int rc;
+        if (has_fft_dst(p->M[s])) {
+            if ((rc = get_fft(p, p->M[s] / 2, &t))) return rc;
+            a.tw = t.fwd;
+            a.half = t.half;
+            a.halfr = t.halfr;
+            if ((rc = get_sin2(p, p->M[s], &a.sin2))) return rc;
+        } else if ((rc = get_sinm(p, p->M[s], &a.sinm, dd ? 1 : 0))) {   // direct sums
+            return rc;
+        }
         if (dd) {
             // double-float arithmetic; intermediate passes keep double-float pairs
             a.dd = 1;
@@ -612,7 +646,7 @@ int transform(idp_plan p, View3 in, double *work, View3 out, const double *tab, 
             a.add_dd = 0;
             a.twd = t.fwdd;
             a.halfd = t.halfd;
-            a.sin2d = p->sin2d[p->M[s]];
+            if (has_fft_dst(p->M[s])) a.sin2d = p->sin2d[p->M[s]];
         }
         Mark mk(p, IDP_KERNEL_DST, st);
         IDP_CK(launch_dst_pass(a, st));
@@ -634,18 +668,23 @@ int dst_box(idp_plan p, double *x, int b0, int b1, int b2, int M2, int M1, cudaS
         a.n0 = b0; a.n1 = b1; a.n2 = b2;
         a.axis = axes[q];
         a.M = Ms[q];
-        FftTables t;
-        int rc = get_fft(p, Ms[q] / 2, &t);
-        if (rc) return rc;
-        a.tw = t.fwd;
-        a.half = t.half;
-        a.halfr = t.halfr;
-        if ((rc = get_sin2(p, Ms[q], &a.sin2))) return rc;
-        if (p->mixed == IDP_PRECISION_DF32 || tensor_mode(p)) {
+        FftTables t{};
+        int rc;
+        const bool ddm = p->mixed == IDP_PRECISION_DF32 || tensor_mode(p);
+        if (has_fft_dst(Ms[q])) {
+            if ((rc = get_fft(p, Ms[q] / 2, &t))) return rc;
+            a.tw = t.fwd;
+            a.half = t.half;
+            a.halfr = t.halfr;
+            if ((rc = get_sin2(p, Ms[q], &a.sin2))) return rc;
+        } else if ((rc = get_sinm(p, Ms[q], &a.sinm, ddm ? 1 : 0))) {   // direct sums
+            return rc;
+        }
+        if (ddm) {
             a.dd = 1;
             a.twd = t.fwdd;
             a.halfd = t.halfd;
-            a.sin2d = p->sin2d[Ms[q]];
+            if (has_fft_dst(Ms[q])) a.sin2d = p->sin2d[Ms[q]];
         }
         Mark mk(p, IDP_KERNEL_DST_PARTS, st);
         IDP_CK(launch_dst_pass(a, st));
@@ -970,7 +1009,8 @@ int enqueue_grid(idp_plan p, const double *rho, double *phi, int stop, cudaStrea
     const bool overlap_rho = (stop == 0) && !p->profiling;
     // FP64 / df32 transforms: the first pass of the forward transform of rho is
     // the imaginary part of the boundary's first real FFT (see transform_rho_from_T0)
-    const bool rho_from_T0 = (stop == 0) && !(tensor_mode(p) && p->mixed_path == 0);
+    const bool rho_from_T0 = (stop == 0) && !(tensor_mode(p) && p->mixed_path == 0) &&
+                             has_fft_dst(p->M[2]) && p->P[2] == p->M[2];
     // host-buffer solve: the first row transform reads rho from the host buffer
     // and leaves the device copy for the later stages; where rho is needed before
     // it (the tensor-core transform of rho starts at once), rho goes up first
@@ -1113,7 +1153,9 @@ int plan_setup(idp_plan p)
         if (!p->act[s]) continue;
         FftTables t;
         const double *sn;
+        const void *sm_;
         if ((has_fft_dst(p->M[s]) && ((rc = get_fft(p, p->M[s] / 2, &t)) || (rc = get_sin2(p, p->M[s], &sn)))) ||
+            (!has_fft_dst(p->M[s]) && (rc = get_sinm(p, p->M[s], &sm_, 0))) ||
             (rc = get_fft(p, p->P[s], &t)) || (rc = get_fft(p, 2 * p->P[s], &t)))
             return rc;
     }
@@ -1517,11 +1559,7 @@ int run_solve_host(idp_plan p, const double *rho_h, double *phi_h, double *phi_v
     return IDP_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-int idp_create_plan(idp_plan *out, int d, const int64_t n[], const double h[], int order)
+int create_plan(idp_plan *out, int d, const int64_t n[], const double h[], int order, int exact)
 {
     if (!out || !n || !h) return IDP_EINVAL;
     *out = nullptr;
@@ -1529,19 +1567,21 @@ int idp_create_plan(idp_plan *out, int d, const int64_t n[], const double h[], i
     if (order != 4 && order != 6) return IDP_EINVAL;
     for (int s = 0; s < d; ++s) {
         if (!(h[s] > 0.0) || !std::isfinite(h[s])) return IDP_EINVAL;
-        if (n[s] < 3) return IDP_EINVAL;
-        if (!padded_panels(n[s] - 1)) return IDP_ESUPPORT;
+        if (n[s] < (exact ? 8 : 3)) return IDP_EINVAL;
+        if (exact ? n[s] - 1 > 512 : !padded_panels(n[s] - 1)) return IDP_ESUPPORT;
     }
     idp_plan p = new (std::nothrow) idp_plan_s();
     if (!p) return IDP_ENOMEM;
     p->d = d;
     p->order = order;
+    p->exact = exact;
     p->serial = g_serial.fetch_add(1);
     const int o = 3 - d;
     for (int s = 0; s < d; ++s) {
         // an unsupported panel count is padded to the next supported one, the
-        // extra panels split between the two ends (h unchanged)
-        const int64_t Mp = padded_panels(n[s] - 1);
+        // extra panels split between the two ends (h unchanged); an exact plan
+        // solves on the given grid
+        const int64_t Mp = exact ? n[s] - 1 : padded_panels(n[s] - 1);
         p->n[s + o] = (int)Mp + 1;
         p->un[s + o] = (int)n[s];
         p->uoff[s + o] = (int)((Mp - (n[s] - 1)) / 2);
@@ -1571,6 +1611,20 @@ int idp_create_plan(idp_plan *out, int d, const int64_t n[], const double h[], i
     }
     *out = p;
     return IDP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int idp_create_plan(idp_plan *out, int d, const int64_t n[], const double h[], int order)
+{
+    return create_plan(out, d, n, h, order, 0);
+}
+
+int idp_create_plan_exact(idp_plan *out, int d, const int64_t n[], const double h[], int order)
+{
+    return create_plan(out, d, n, h, order, 1);
 }
 
 int idp_plan_set(idp_plan p, int key, int64_t value)
