@@ -54,7 +54,9 @@
 // flag, the other roles leave their loops at their next check, the block waits
 // (bounded) for its own products and copies still in flight, frees its tensor
 // memory and records the failure in *err.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include "dd.cuh"
 #include "idp_internal.cuh"
@@ -68,12 +70,13 @@ constexpr int PIECE_BYTES = 8192;  // one operand piece of one stage per 128 row
 constexpr uint32_t SBO = 128;      // core matrices adjacent along M / N
 constexpr uint32_t LBO_A = 2048;   // core matrices adjacent along K, 128 rows
 constexpr int NPROD = 512;         // producer threads (warps 0-15)
-constexpr int WARP_COPY = 16, WARP_MMA = 17, WARP_EPI = 18, NEPI = 4;
-constexpr int NTHR = (WARP_EPI + NEPI) * 32;   // 704
+constexpr int WARP_COPY = 16, WARP_MMA = 17, WARP_LOAD = 18, WARP_EPI = 19;
+constexpr int SMEM_LIMIT = 227 * 1024;
 
-// per variant (0 = BF16X3, 1 = TF32X3) and tile width: element bytes, K per
-// stage, pieces, ring depth
-template <int V, int NTN>
+// per variant (0 = BF16X3, 1 = TF32X3), tile width and input type (IN64: FP64
+// input, loaded by the producers; FP32 input: by tensor copies into an input ring):
+// element bytes, K per stage, pieces, ring depths, epilogue warps
+template <int V, int NTN, int IN64>
 struct MpCfg {
     static constexpr int ESZ = V ? 4 : 2;
     static constexpr int EPC = 16 / ESZ;                  // elements per core-matrix row
@@ -84,12 +87,23 @@ struct MpCfg {
     static constexpr int B_BYTES = PIECES * BP_BYTES;
     static constexpr uint32_t LBO_B = 16u * NTN;
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int NS = (220 * 1024) / STAGE;       // ring depth
-    static constexpr int SMEM_BAR = NS * STAGE;           // barriers: A, B, empty per stage; acc full/free x2; drain
-    static constexpr int NBAR = 3 * NS + 5;
+    // operand ring depth: three stages where they fit beside the input ring
+    static constexpr int NS = (IN64 || STAGE <= 49152) ? (3 * STAGE <= 220 * 1024 ? 3 : 2) : 2;
+    // input ring (FP32 input): one stage is the 128 lines x KB values of a tile, as
+    // the tensor copy writes it (rows of KB * 4 = 128 or 64 bytes, 16-byte chunks
+    // swizzled by the row so that eight rows read at one offset hit distinct banks)
+    static constexpr int RAW_SLOT = IN64 ? 0 : MT * KB * 4;
+    static constexpr int NR_FIT = IN64 ? 0 : (SMEM_LIMIT - 2048 - NS * STAGE) / RAW_SLOT;
+    static constexpr int NR = NR_FIT > 6 ? 6 : NR_FIT;
+    static_assert(IN64 || NR >= 2, "at least two input stages");
+    static constexpr int NEPI = IN64 ? 4 : 8;             // epilogue warps
+    static constexpr int NTHR = (WARP_EPI + NEPI) * 32;   // 736 or 864
+    static constexpr int SMEM_IN = NS * STAGE;
+    static constexpr int SMEM_BAR = SMEM_IN + NR * RAW_SLOT;
+    // barriers: A, B, empty per operand stage; full, empty per input stage; acc full/free x2; drain
+    static constexpr int NBAR = 3 * NS + 2 * NR + 5;
     static constexpr int SMEM_TOTAL = SMEM_BAR + 8 * NBAR + 16 + 1024;   // + TMEM slot + alignment
-    static constexpr int NG = MT * (KB / EPC) / NPROD;    // 16-byte groups per producer thread and stage
-    static_assert(NG * NPROD == MT * (KB / EPC), "whole groups per producer thread");
+    static_assert(SMEM_TOTAL <= SMEM_LIMIT, "shared memory");
 };
 constexpr long long WAIT_CYCLES = 2000000000ll;       // bounded mbarrier polling (~1 s)
 
@@ -195,6 +209,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
         if (clock64() - t0 >= limit) return false;
     }
 }
+// one tensor copy global -> shared of the box at (x, y) that completes on `bar`
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
 // one bulk asynchronous copy global -> shared that completes on `bar`
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
 {
@@ -209,13 +232,13 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
                  : "memory");
 }
 
-template <int NTN, int V>
-__global__ void __launch_bounds__(NTHR, 1) mp_pass_kernel(const MpPass a)
+template <int NTN, int V, int IN64>
+__global__ void __launch_bounds__(MpCfg<V, NTN, IN64>::NTHR, 1)
+    mp_pass_kernel(const MpPass a, const __grid_constant__ CUtensorMap in_map)
 {
     static_assert(NTN == 128 || NTN == 256, "tile of 128 or 256 modes");
-    using C = MpCfg<V, NTN>;
-    constexpr int KB = C::KB, NS = C::NS, EPC = C::EPC;
-    static_assert(NS >= 2, "at least two stages");
+    using C = MpCfg<V, NTN, IN64>;
+    constexpr int KB = C::KB, NS = C::NS, NR = C::NR, EPC = C::EPC, NEPI = C::NEPI;
     // D = F32 (bit 4); A, B = BF16 (1) for kind::f16 or TF32 (2) for kind::tf32
     constexpr uint32_t FMT = V ? 2u : 1u;
     constexpr uint32_t IDESC_N = (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(NTN >> 3) << 17) |
@@ -226,15 +249,18 @@ __global__ void __launch_bounds__(NTHR, 1) mp_pass_kernel(const MpPass a)
     const int warp = t >> 5, lane = t & 31;
     const int ntm = (a.n + NTN - 1) / NTN;               // mode tiles
     const int64_t nlines = (int64_t)a.P * a.Q;
-    const int64_t ntiles = ((nlines + MT - 1) / MT) * ntm;
+    const int ntiles = (int)((nlines + MT - 1) / MT) * ntm;
     const int nkb = (a.n + KB - 1) / KB;
     const uint32_t bar0 = smem_u32(sm + C::SMEM_BAR);
     auto bar_a = [&](int s) { return bar0 + 8u * (uint32_t)s; };
     auto bar_b = [&](int s) { return bar0 + 8u * (uint32_t)(NS + s); };
     auto bar_e = [&](int s) { return bar0 + 8u * (uint32_t)(2 * NS + s); };
-    auto bar_full = [&](int b) { return bar0 + 8u * (uint32_t)(3 * NS + b); };
-    auto bar_free = [&](int b) { return bar0 + 8u * (uint32_t)(3 * NS + 2 + b); };
-    const uint32_t bar_drain = bar0 + 8u * (3 * NS + 4);
+    auto bar_in = [&](int r) { return bar0 + 8u * (uint32_t)(3 * NS + r); };
+    auto bar_ine = [&](int r) { return bar0 + 8u * (uint32_t)(3 * NS + NR + r); };
+    auto bar_full = [&](int b) { return bar0 + 8u * (uint32_t)(3 * NS + 2 * NR + b); };
+    auto bar_free = [&](int b) { return bar0 + 8u * (uint32_t)(3 * NS + 2 * NR + 2 + b); };
+    const uint32_t bar_drain = bar0 + 8u * (3 * NS + 2 * NR + 4);
+    auto raw_slot = [&](int r) { return sm + C::SMEM_IN + r * C::RAW_SLOT; };
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + C::SMEM_BAR + 8 * C::NBAR);
     volatile __shared__ int s_fail;
     const long long limit = a.stall_test ? WAIT_CYCLES / 400 : WAIT_CYCLES;
@@ -245,6 +271,10 @@ __global__ void __launch_bounds__(NTHR, 1) mp_pass_kernel(const MpPass a)
             mbar_init(bar_a(s), NPROD / 32);   // one arrival per producer warp
             mbar_init(bar_b(s), 1);
             mbar_init(bar_e(s), 1);
+        }
+        for (int r = 0; r < NR; ++r) {
+            mbar_init(bar_in(r), 1);
+            mbar_init(bar_ine(r), NPROD / 32);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(bar_full(b), 1);
@@ -266,133 +296,151 @@ __global__ void __launch_bounds__(NTHR, 1) mp_pass_kernel(const MpPass a)
     const uint32_t tmem = *tmem_slot;
 
     int mma_issued = 0;
-    int armed[NS];
+    constexpr int NARM = NS > NR ? NS : NR;
+    int armed[NARM];   // copies issued per stage slot (copy and load warps)
 #pragma unroll
-    for (int s = 0; s < NS; ++s) armed[s] = 0;
+    for (int s = 0; s < NARM; ++s) armed[s] = 0;
 
     if (warp < NPROD / 32) {
-        // ---- producers of the input pieces ----
-        // group e = t + NPROD g of a stage: line r = e / 4 of the tile, k group
-        // g8 = e % 4 (EPC consecutive k: one 16-byte core-matrix row per piece); the
-        // four lanes of a line read its KB values of the stage together
-        constexpr int NG = C::NG;
-        int rr[NG];
-        uint32_t oo[NG];
-        const int g8 = lane & 3;
-#pragma unroll
-        for (int g = 0; g < NG; ++g) {
-            rr[g] = (t + NPROD * g) >> 2;
-            oo[g] = tile_off<C::ESZ>(rr[g], g8 * EPC);
-        }
-        // raw input bits of one stage (FP64 values, or FP32 values in the low half)
-        auto load = [&](int64_t tile, int kb, unsigned long long (&raw)[NG][EPC]) {
-            const int kg0 = kb * KB + g8 * EPC;
-#pragma unroll
-            for (int g = 0; g < NG; ++g) {
-#pragma unroll
-                for (int j = 0; j < EPC; ++j) raw[g][j] = 0ull;
-                const int64_t L = (tile / ntm) * MT + rr[g];
-                if (L >= nlines) continue;
-                const int64_t p = L / a.Q, q = L - p * a.Q;
-                const int64_t base = p * a.is_p + q * a.is_q + (int64_t)kg0 * a.is_k;
-                if (a.in_vec4) {
-                    // FP32 lines starting on 16-byte boundaries, padded to whole
-                    // vectors: the padding is written by no one, so values past the
-                    // line's end are set to zero after the load
-                    const float4 *src =
-                        reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(a.in) + base);
-#pragma unroll
-                    for (int v = 0; v < EPC / 4; ++v) {
-                        const int k4 = kg0 + 4 * v;
-                        if (k4 >= a.n) break;
-                        const float4 x = src[v];
-                        raw[g][4 * v] = __float_as_uint(x.x);
-                        raw[g][4 * v + 1] = k4 + 1 < a.n ? __float_as_uint(x.y) : 0u;
-                        raw[g][4 * v + 2] = k4 + 2 < a.n ? __float_as_uint(x.z) : 0u;
-                        raw[g][4 * v + 3] = k4 + 3 < a.n ? __float_as_uint(x.w) : 0u;
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < EPC; ++j) {
-                        if (kg0 + j >= a.n) break;
-                        if (a.in_f64)
-                            raw[g][j] = (unsigned long long)__double_as_longlong(
-                                reinterpret_cast<const double *>(a.in)[base + j * a.is_k]);
-                        else
-                            raw[g][j] = __float_as_uint(reinterpret_cast<const float *>(a.in)[base + j * a.is_k]);
-                    }
+        // ---- producers of the input pieces: warp w owns lines 8w .. 8w+7 of a tile,
+        //      lane: line r = 8w + (lane & 7), k group g8 = lane >> 3 (EPC consecutive k,
+        //      one 16-byte core-matrix row per piece); the eight lanes of a k group
+        //      write 128 contiguous bytes of a piece, so their stores hit distinct banks
+        const int r = 8 * warp + (lane & 7), g8 = lane >> 3;
+        const uint32_t oo = tile_off<C::ESZ>(r, g8 * EPC);
+        int sc = 0;
+        // FP64 input: loaded here, the next two stages in flight while one is split
+        int cur_lt = -1;
+        bool rvalid = false;
+        int64_t rbase = 0;
+        auto load64 = [&](int tile, int kb, unsigned long long (&raw)[EPC]) {
+            const int lt = tile / ntm;
+            if (lt != cur_lt) {
+                cur_lt = lt;
+                const int64_t L = (int64_t)lt * MT + r;
+                rvalid = L < nlines;
+                if (rvalid) {
+                    const int64_t p = L / a.Q, q = L - p * a.Q;
+                    rbase = p * a.is_p + q * a.is_q;
                 }
             }
+            const int kg0 = kb * KB + g8 * EPC;
+            const double *src = reinterpret_cast<const double *>(a.in) + rbase + kg0;
+#pragma unroll
+            for (int e = 0; e < EPC; ++e)
+                raw[e] = (rvalid && kg0 + e < a.n) ? (unsigned long long)__double_as_longlong(src[e]) : 0ull;
         };
-        // the loads run two stages ahead of the splitting: two register sets, used
-        // in turn (a copy from one to the other would wait for its loads)
-        int64_t tile = blockIdx.x, ltile = blockIdx.x;   // stage being split / next to load
-        int kb = 0, lkb = 0;
-        auto advance = [&](int64_t &tl, int &k) {
+        int ltile = blockIdx.x, lkb = 0;   // next stage to load (FP64 input)
+        auto advance = [&](int &tl, int &k) {
             if (++k == nkb) {
                 k = 0;
                 tl += gridDim.x;
             }
         };
-        unsigned long long q0[NG][EPC], q1[NG][EPC];
-        if (ltile < ntiles) load(ltile, lkb, q0);
-        advance(ltile, lkb);
-        if (ltile < ntiles) load(ltile, lkb, q1);
-        advance(ltile, lkb);
-        int sc = 0;
-        auto step = [&](unsigned long long (&q)[NG][EPC]) -> bool {
-            if (tile >= ntiles || s_fail) return false;
-            const int s = sc % NS;
-            float x[NG][EPC];
-#pragma unroll
-            for (int g = 0; g < NG; ++g)
-#pragma unroll
-                for (int j = 0; j < EPC; ++j)
-                    x[g][j] = a.in_f64 ? f32_of_f64_bits(__longlong_as_double((long long)q[g][j]))
-                                       : __uint_as_float((uint32_t)q[g][j]);
-            if (ltile < ntiles) load(ltile, lkb, q);
+        unsigned long long q0[EPC], q1[EPC];
+        if constexpr (IN64) {
+            if (ltile < ntiles) load64(ltile, lkb, q0);
             advance(ltile, lkb);
+            if (ltile < ntiles) load64(ltile, lkb, q1);
+            advance(ltile, lkb);
+        }
+        // one stage: its values x (from q, or from the input ring), split, stored
+        auto step = [&](int tile, int kb, unsigned long long (&q)[EPC]) -> bool {
+            const int s = sc % NS;
+            float x[EPC];
+            if constexpr (IN64) {
+#pragma unroll
+                for (int e = 0; e < EPC; ++e) x[e] = f32_of_f64_bits(__longlong_as_double((long long)q[e]));
+                if (ltile < ntiles) load64(ltile, lkb, q);
+                advance(ltile, lkb);
+            } else {
+                const int ri = sc % NR;
+                if (!mbar_wait(bar_in(ri), (uint32_t)((sc / NR) & 1), limit)) s_fail = 1;
+                if (s_fail) return false;
+                // the tensor copy's 128-byte (BF16X3) or 64-byte (TF32X3) rows with the
+                // 16-byte chunk c of row r at chunk c ^ (r % 8), or c ^ ((r / 2) % 4)
+                const unsigned char *row = raw_slot(ri) + r * (KB * 4);
+#pragma unroll
+                for (int v = 0; v < EPC / 4; ++v) {
+                    const int c = g8 * (EPC / 4) + v;
+                    const int pc = V ? (c ^ ((r >> 1) & 3)) : (c ^ (r & 7));
+                    const float4 f = *reinterpret_cast<const float4 *>(row + 16 * pc);
+                    x[4 * v] = f.x; x[4 * v + 1] = f.y; x[4 * v + 2] = f.z; x[4 * v + 3] = f.w;
+                }
+                // past the line's end: the padding of the FP32 rows is written by no one
+                const int kg0 = kb * KB + g8 * EPC;
+#pragma unroll
+                for (int e = 0; e < EPC; ++e)
+                    if (kg0 + e >= a.n) x[e] = 0.f;
+                // the input slot may be refilled once every producer warp has read it
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar_ine(ri));
+            }
             if (sc >= NS && !mbar_wait(bar_e(s), (uint32_t)(((sc / NS) - 1) & 1), limit)) s_fail = 1;
             if (s_fail) return false;
             unsigned char *A = sm + s * C::STAGE;
-#pragma unroll
-            for (int g = 0; g < NG; ++g) {
-                if constexpr (V == 1) {
-                    float4 va, vb;
-                    split2(x[g][0], va.x, vb.x);
-                    split2(x[g][1], va.y, vb.y);
-                    split2(x[g][2], va.z, vb.z);
-                    split2(x[g][3], va.w, vb.w);
-                    *reinterpret_cast<float4 *>(A + 0 * PIECE_BYTES + oo[g]) = va;
-                    *reinterpret_cast<float4 *>(A + 1 * PIECE_BYTES + oo[g]) = vb;
-                } else {
-                    uint4 va, vb, vc;
-                    split3_pair(x[g][0], x[g][1], va.x, vb.x, vc.x);
-                    split3_pair(x[g][2], x[g][3], va.y, vb.y, vc.y);
-                    split3_pair(x[g][4], x[g][5], va.z, vb.z, vc.z);
-                    split3_pair(x[g][6], x[g][7], va.w, vb.w, vc.w);
-                    *reinterpret_cast<uint4 *>(A + 0 * PIECE_BYTES + oo[g]) = va;
-                    *reinterpret_cast<uint4 *>(A + 1 * PIECE_BYTES + oo[g]) = vb;
-                    *reinterpret_cast<uint4 *>(A + 2 * PIECE_BYTES + oo[g]) = vc;
-                }
+            if constexpr (V == 1) {
+                float4 va, vb;
+                split2(x[0], va.x, vb.x);
+                split2(x[1], va.y, vb.y);
+                split2(x[2], va.z, vb.z);
+                split2(x[3], va.w, vb.w);
+                *reinterpret_cast<float4 *>(A + 0 * PIECE_BYTES + oo) = va;
+                *reinterpret_cast<float4 *>(A + 1 * PIECE_BYTES + oo) = vb;
+            } else {
+                uint4 va, vb, vc;
+                split3_pair(x[0], x[1], va.x, vb.x, vc.x);
+                split3_pair(x[2], x[3], va.y, vb.y, vc.y);
+                split3_pair(x[4], x[5], va.z, vb.z, vc.z);
+                split3_pair(x[6], x[7], va.w, vb.w, vc.w);
+                *reinterpret_cast<uint4 *>(A + 0 * PIECE_BYTES + oo) = va;
+                *reinterpret_cast<uint4 *>(A + 1 * PIECE_BYTES + oo) = vb;
+                *reinterpret_cast<uint4 *>(A + 2 * PIECE_BYTES + oo) = vc;
             }
             // the tensor cores read the pieces through the async proxy; one arrival
             // per warp (hundreds of arrivals on one barrier word would serialise)
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(bar_a(s));
-            advance(tile, kb);
             ++sc;
             return true;
         };
-        while (step(q0) && step(q1)) {
+        // the two register sets are used in turn (a copy from one to the other
+        // would wait for its loads)
+        int tile = blockIdx.x, kb = 0;
+        bool go = true;
+        while (go && tile < ntiles && !s_fail) {
+            go = step(tile, kb, q0);
+            advance(tile, kb);
+            if (go && tile < ntiles && !s_fail) {
+                go = step(tile, kb, q1);
+                advance(tile, kb);
+            }
+        }
+    } else if (warp == WARP_LOAD) {
+        // ---- FP32 input: one tensor copy per stage (the tile's 128 lines x KB values;
+        //      lines past the last and values past the padded row read as zero)
+        if constexpr (!IN64) if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&in_map)) : "memory");
+            int sc = 0;
+            for (int tile = blockIdx.x; tile < ntiles && !s_fail; tile += gridDim.x) {
+                const int y = (tile / ntm) * MT;
+                for (int kb = 0; kb < nkb; ++kb, ++sc) {
+                    const int ri = sc % NR;
+                    if (sc >= NR && !mbar_wait(bar_ine(ri), (uint32_t)(((sc / NR) - 1) & 1), limit)) s_fail = 1;
+                    if (s_fail) break;
+                    mbar_arrive_tx(bar_in(ri), (uint32_t)C::RAW_SLOT);
+                    tma_load_2d(smem_u32(raw_slot(ri)), &in_map, kb * KB, y, bar_in(ri));
+                    ++armed[ri];
+                }
+            }
         }
     } else if (warp == WARP_COPY) {
         // ---- the sine image: one bulk copy per stage ----
         if (lane == 0) {
             int sc = 0;
-            for (int64_t tile = blockIdx.x; tile < ntiles && !s_fail; tile += gridDim.x) {
-                const int mt = (int)(tile % ntm);
+            for (int tile = blockIdx.x; tile < ntiles && !s_fail; tile += gridDim.x) {
+                const int mt = tile % ntm;
                 for (int kb = 0; kb < nkb; ++kb, ++sc) {
                     const int s = sc % NS;
                     if (sc >= NS && !mbar_wait(bar_e(s), (uint32_t)(((sc / NS) - 1) & 1), limit)) s_fail = 1;
@@ -412,7 +460,7 @@ __global__ void __launch_bounds__(NTHR, 1) mp_pass_kernel(const MpPass a)
             constexpr int NPR = V ? 3 : 6;
             const int pa[6] = {0, 0, 1, 0, 1, 2};
             const int pb[6] = {0, 1, 0, 2, 1, 0};
-            for (int64_t tile = blockIdx.x; tile < ntiles && !s_fail; tile += gridDim.x, ++ac) {
+            for (int tile = blockIdx.x; tile < ntiles && !s_fail; tile += gridDim.x, ++ac) {
                 const int buf = ac & 1;
                 // the epilogue must have emptied this accumulator (two tiles ago)
                 if (ac >= 2 && !mbar_wait(bar_free(buf), (uint32_t)(((ac >> 1) - 1) & 1), limit)) s_fail = 1;
@@ -463,7 +511,7 @@ __global__ void __launch_bounds__(NTHR, 1) mp_pass_kernel(const MpPass a)
         constexpr int CPW = NTN / (NEPI / 4);   // columns per epilogue warp
         const int quad = warp & 3, half = (warp - WARP_EPI) >> 2;
         int ac = 0;
-        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++ac) {
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++ac) {
             const int buf = ac & 1;
             // a warp-uniform decision: the TMEM loads below are warp-collective
             bool ok = !s_fail;
@@ -474,12 +522,16 @@ __global__ void __launch_bounds__(NTHR, 1) mp_pass_kernel(const MpPass a)
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const int64_t L0 = (tile / ntm) * MT;
-            const int m0 = (int)(tile % ntm) * NTN;
-            const int64_t L = L0 + 32 * quad + lane;
+            const int64_t L = (int64_t)(tile / ntm) * MT + 32 * quad + lane;
+            const int m0 = (tile % ntm) * NTN;
             const bool live = L < nlines;
-            int64_t p = 0, q = 0;
-            if (live) { p = L / a.Q; q = L - p * a.Q; }
+            int64_t ob = 0, tb = 0, ab = 0;   // this line's offsets in out, tab, add
+            if (live) {
+                const int64_t p = L / a.Q, q = L - p * a.Q;
+                ob = p * a.os_p + q * a.os_q;
+                tb = p * a.ts_p + q * a.ts_q;
+                ab = p * a.as_p + q * a.as_q;
+            }
             const int cols = min(NTN, ((a.n - m0 + 15) / 16) * 16);
             for (int c0 = half * CPW; c0 < min(cols, (half + 1) * CPW); c0 += 16) {
                 uint32_t v[16];
@@ -495,59 +547,38 @@ __global__ void __launch_bounds__(NTHR, 1) mp_pass_kernel(const MpPass a)
                 if (!live) continue;
                 const int mc = m0 + c0;
                 const int nj = min(16, a.n - mc);
-                if (a.out_f64 && (a.tab == nullptr) != (a.add == nullptr)) {
-                    // one FP64 operand (a table or an addend): its 16 values are loaded
-                    // before any store (the stores could alias them as far as the
-                    // compiler knows, and would otherwise put one load latency on
-                    // every value)
-                    const double *ext = a.tab ? a.tab : a.add;
-                    const int64_t es_m = a.tab ? a.ts_m : a.as_m, es_p = a.tab ? a.ts_p : a.as_p,
-                                  es_q = a.tab ? a.ts_q : a.as_q;
-#pragma unroll
-                    for (int h = 0; h < 16; h += 8) {
-                        double ev[8];
-#pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            ev[j] = h + j < nj ? ext[(int64_t)(mc + h + j) * es_m + p * es_p + q * es_q] : 0.0;
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            if (h + j >= nj) break;
-                            // 4 * the FP32 sum, exact in FP32; widened to FP64 by bits
-                            const double y = f2d_bits(__fmul_rn(4.0f, __uint_as_float(v[h + j])));
-                            reinterpret_cast<double *>(
-                                a.out)[(int64_t)(mc + h + j) * a.os_m + p * a.os_p + q * a.os_q] =
-                                a.tab ? ev[j] * y : y + ev[j];
-                        }
-                    }
-                } else if (a.out_f64) {
-                    // no FP64 operand, or both: in groups of 8 modes
+                if (a.out_f64) {
+                    double *o = reinterpret_cast<double *>(a.out) + ob + (int64_t)mc * a.os_m;
+                    const double *tp = a.tab ? a.tab + tb + (int64_t)mc * a.ts_m : nullptr;
+                    const double *ap = a.add ? a.add + ab + (int64_t)mc * a.as_m : nullptr;
+                    // in groups of 8 modes: the group's FP64 operands are loaded before any
+                    // store (the stores could alias them as far as the compiler knows, and
+                    // would otherwise put one load latency on every value)
 #pragma unroll
                     for (int h = 0; h < 16; h += 8) {
                         double tv[8], av[8];
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
-                            const int64_t m = mc + h + j;
-                            tv[j] = (a.tab && h + j < nj) ? a.tab[m * a.ts_m + p * a.ts_p + q * a.ts_q] : 1.0;
-                            av[j] = (a.add && h + j < nj) ? a.add[m * a.as_m + p * a.as_p + q * a.as_q] : 0.0;
+                            tv[j] = (tp && h + j < nj) ? tp[(int64_t)(h + j) * a.ts_m] : 1.0;
+                            av[j] = (ap && h + j < nj) ? ap[(int64_t)(h + j) * a.as_m] : 0.0;
                         }
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
                             if (h + j >= nj) break;
                             // 4 * the FP32 sum, exact in FP32; widened to FP64 by bits
                             const double y = f2d_bits(__fmul_rn(4.0f, __uint_as_float(v[h + j])));
-                            double r = y;
-                            if (a.tab) r = a.add ? fma(tv[j], y, av[j]) : tv[j] * y;
-                            else if (a.add) r = y + av[j];
-                            reinterpret_cast<double *>(a.out)[(int64_t)(mc + h + j) * a.os_m + p * a.os_p + q * a.os_q] =
-                                r;
+                            double rres = y;
+                            if (tp) rres = ap ? fma(tv[j], y, av[j]) : tv[j] * y;
+                            else if (ap) rres = y + av[j];
+                            o[(int64_t)(h + j) * a.os_m] = rres;
                         }
                     }
                 } else {
+                    float *o = reinterpret_cast<float *>(a.out) + ob + (int64_t)mc * a.os_m;
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         if (j >= nj) break;
-                        reinterpret_cast<float *>(a.out)[(int64_t)(mc + j) * a.os_m + p * a.os_p + q * a.os_q] =
-                            __fmul_rn(4.0f, __uint_as_float(v[j]));
+                        o[(int64_t)j * a.os_m] = __fmul_rn(4.0f, __uint_as_float(v[j]));
                     }
                 }
             }
@@ -573,6 +604,11 @@ __global__ void __launch_bounds__(NTHR, 1) mp_pass_kernel(const MpPass a)
             for (int s = 0; s < NS; ++s)
                 if (armed[s] > 0) mbar_wait(bar_b(s), (uint32_t)((armed[s] - 1) & 1), WAIT_CYCLES);
         }
+        if (warp == WARP_LOAD && lane == 0) {
+#pragma unroll
+            for (int r = 0; r < NR; ++r)
+                if (armed[r] > 0) mbar_wait(bar_in(r), (uint32_t)((armed[r] - 1) & 1), WAIT_CYCLES);
+        }
         if (t == 0 && a.err) atomicExch(a.err, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -584,16 +620,41 @@ __global__ void __launch_bounds__(NTHR, 1) mp_pass_kernel(const MpPass a)
 }
 
 int g_num_sms = 0;
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
-template <int V, int NTN>
+template <int V, int NTN, int IN64>
 cudaError_t launch_mp_t(const MpPass &a, cudaStream_t st)
 {
+    using C = MpCfg<V, NTN, IN64>;
     const int64_t lines = (int64_t)a.P * a.Q;
     const int64_t tiles = ((lines + MT - 1) / MT) * ((a.n + NTN - 1) / NTN);
+    if (tiles >= (1ll << 31)) return cudaErrorInvalidValue;
+    CUtensorMap map;
+    memset(&map, 0, sizeof(map));
+    if (!IN64) {
+        // FP32 input: lines at a uniform stride (is_p = Q is_q), rows of pad4(n) values
+        if (!g_encode) return cudaErrorInitializationError;
+        const cuuint64_t dim[2] = {(cuuint64_t)((a.n + 3) & ~3), (cuuint64_t)lines};
+        const cuuint64_t stride[1] = {(cuuint64_t)a.is_q * 4u};
+        const cuuint32_t box[2] = {(cuuint32_t)C::KB, (cuuint32_t)MT};
+        const cuuint32_t estr[2] = {1, 1};
+        const CUresult r = g_encode(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(a.in), dim, stride,
+                                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                    V ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
     const int sms = g_num_sms > 0 ? g_num_sms : 148;
     const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
-    mp_pass_kernel<NTN, V><<<grid, NTHR, MpCfg<V, NTN>::SMEM_TOTAL, st>>>(a);
+    mp_pass_kernel<NTN, V, IN64><<<grid, C::NTHR, C::SMEM_TOTAL, st>>>(a, map);
     return cudaGetLastError();
+}
+
+template <int V, int NTN, int IN64>
+cudaError_t mp_attr()
+{
+    return cudaFuncSetAttribute(mp_pass_kernel<NTN, V, IN64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                MpCfg<V, NTN, IN64>::SMEM_TOTAL);
 }
 
 }  // namespace
@@ -601,27 +662,43 @@ cudaError_t launch_mp_t(const MpPass &a, cudaStream_t st)
 cudaError_t mp_set_attributes()
 {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(mp_pass_kernel<128, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  MpCfg<0, 128>::SMEM_TOTAL)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(mp_pass_kernel<256, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  MpCfg<0, 256>::SMEM_TOTAL)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(mp_pass_kernel<128, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  MpCfg<1, 128>::SMEM_TOTAL)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(mp_pass_kernel<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  MpCfg<1, 256>::SMEM_TOTAL)) != cudaSuccess)
+    if ((e = mp_attr<0, 128, 0>()) != cudaSuccess || (e = mp_attr<0, 128, 1>()) != cudaSuccess ||
+        (e = mp_attr<0, 256, 0>()) != cudaSuccess || (e = mp_attr<0, 256, 1>()) != cudaSuccess ||
+        (e = mp_attr<1, 128, 0>()) != cudaSuccess || (e = mp_attr<1, 128, 1>()) != cudaSuccess ||
+        (e = mp_attr<1, 256, 0>()) != cudaSuccess || (e = mp_attr<1, 256, 1>()) != cudaSuccess)
         return e;
+    if (!g_encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if ((e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q)) !=
+            cudaSuccess)
+            return e;
+        if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     return cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
 }
 
-int mp_stage_k(int variant) { return variant ? MpCfg<1, 128>::KB : MpCfg<0, 128>::KB; }
+int mp_stage_k(int variant) { return variant ? MpCfg<1, 128, 0>::KB : MpCfg<0, 128, 0>::KB; }
 int mp_tile_modes(int n) { return n <= 128 ? 128 : 256; }
 
 cudaError_t launch_mp_pass(const MpPass &a, cudaStream_t st)
 {
-    if (mp_tile_modes(a.n) == 128) return a.variant ? launch_mp_t<1, 128>(a, st) : launch_mp_t<0, 128>(a, st);
-    return a.variant ? launch_mp_t<1, 256>(a, st) : launch_mp_t<0, 256>(a, st);
+    // the input is read along a contiguous axis; FP32 input: 16-byte aligned lines
+    // padded to whole 16-byte vectors, at one stride (is_p = Q is_q, or P = 1)
+    if (a.is_k != 1) return cudaErrorInvalidValue;
+    if (!a.in_f64 && (!a.in_vec4 || (reinterpret_cast<uintptr_t>(a.in) & 15u) || (a.is_q & 3) ||
+                      (a.P > 1 && a.is_p != (int64_t)a.Q * a.is_q)))
+        return cudaErrorInvalidValue;
+    const bool w128 = mp_tile_modes(a.n) == 128;
+    if (a.variant) {
+        if (w128) return a.in_f64 ? launch_mp_t<1, 128, 1>(a, st) : launch_mp_t<1, 128, 0>(a, st);
+        return a.in_f64 ? launch_mp_t<1, 256, 1>(a, st) : launch_mp_t<1, 256, 0>(a, st);
+    }
+    if (w128) return a.in_f64 ? launch_mp_t<0, 128, 1>(a, st) : launch_mp_t<0, 128, 0>(a, st);
+    return a.in_f64 ? launch_mp_t<0, 256, 1>(a, st) : launch_mp_t<0, 256, 0>(a, st);
 }
 
 }  // namespace idp
