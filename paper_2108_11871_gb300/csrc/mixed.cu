@@ -309,26 +309,52 @@ __global__ void __launch_bounds__(MpCfg<V, NTN, IN64>::NTHR, 1)
         const int r = 8 * warp + (lane & 7), g8 = lane >> 3;
         const uint32_t oo = tile_off<C::ESZ>(r, g8 * EPC);
         int sc = 0;
-        // FP64 input: loaded here, the next two stages in flight while one is split
+        // FP64 input: loaded here, the next two stages in flight while one is split.
+        // BF16X3 (KB = 32): load j of a warp reads line 8w + j of the tile, lane l its
+        // value kb KB + l (a line's 256 bytes of the stage per warp instruction); the
+        // eight lanes of a k group then exchange their values by shuffles (an 8 x 8
+        // transpose) so that each holds its own line's EPC consecutive values.
+        // TF32X3: each thread loads its own EPC values.
         int cur_lt = -1;
-        bool rvalid = false;
-        int64_t rbase = 0;
+        bool rvalid = false;     // this thread's line (TF32X3), or line 8w of the tile (BF16X3)
+        int64_t rbase = 0;       // its offset in the input
+        int jwrap = 8;           // BF16X3: lines 8w + j, j >= jwrap, are in the next p (Q >= 8)
+        int jlive = 8;           // BF16X3: lines 8w + j, j < jlive, exist
+        int64_t pjump = 0;       // the extra offset of those lines: is_p - Q is_q
         auto load64 = [&](int tile, int kb, unsigned long long (&raw)[EPC]) {
             const int lt = tile / ntm;
             if (lt != cur_lt) {
                 cur_lt = lt;
-                const int64_t L = (int64_t)lt * MT + r;
+                const int64_t L = (int64_t)lt * MT + (V ? r : 8 * warp);
                 rvalid = L < nlines;
                 if (rvalid) {
                     const int64_t p = L / a.Q, q = L - p * a.Q;
                     rbase = p * a.is_p + q * a.is_q;
+                    jwrap = (int)min((int64_t)8, (int64_t)a.Q - q);
+                    jlive = (int)min((int64_t)8, nlines - L);
+                    pjump = a.is_p - (int64_t)a.Q * a.is_q;
                 }
             }
-            const int kg0 = kb * KB + g8 * EPC;
-            const double *src = reinterpret_cast<const double *>(a.in) + rbase + kg0;
+            if constexpr (V == 0) {
+                const int k = kb * KB + lane;
+                const double *src = reinterpret_cast<const double *>(a.in) + rbase + k;
 #pragma unroll
-            for (int e = 0; e < EPC; ++e)
-                raw[e] = (rvalid && kg0 + e < a.n) ? (unsigned long long)__double_as_longlong(src[e]) : 0ull;
+                for (int j = 0; j < EPC; ++j) {
+                    int64_t off = (int64_t)j * a.is_q + (j >= jwrap ? pjump : 0);
+                    if (a.Q < 8) {   // the eight lines may span more than two p (small grids)
+                        const int64_t Lj = (int64_t)cur_lt * MT + 8 * warp + j;
+                        off = (Lj / a.Q) * a.is_p + (Lj % a.Q) * a.is_q - rbase;
+                    }
+                    raw[j] = (rvalid && j < jlive && k < a.n) ? (unsigned long long)__double_as_longlong(src[off])
+                                                               : 0ull;
+                }
+            } else {
+                const int kg0 = kb * KB + g8 * EPC;
+                const double *src = reinterpret_cast<const double *>(a.in) + rbase + kg0;
+#pragma unroll
+                for (int e = 0; e < EPC; ++e)
+                    raw[e] = (rvalid && kg0 + e < a.n) ? (unsigned long long)__double_as_longlong(src[e]) : 0ull;
+            }
         };
         int ltile = blockIdx.x, lkb = 0;   // next stage to load (FP64 input)
         auto advance = [&](int &tl, int &k) {
@@ -351,6 +377,23 @@ __global__ void __launch_bounds__(MpCfg<V, NTN, IN64>::NTHR, 1)
             if constexpr (IN64) {
 #pragma unroll
                 for (int e = 0; e < EPC; ++e) x[e] = f32_of_f64_bits(__longlong_as_double((long long)q[e]));
+                if constexpr (V == 0) {
+                    // x[j] is line 8w + j at k = kb KB + lane; after the transpose of the
+                    // eight lanes' values, x[e] is line 8w + (lane & 7) at kb KB + 8 g8 + e
+                    const int ai = lane & 7;
+#pragma unroll
+                    for (int d = 4; d >= 1; d >>= 1) {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            if (i & d) continue;
+                            const bool up = (ai & d) != 0;
+                            const float send = up ? x[i] : x[i | d];
+                            const float got = __shfl_xor_sync(0xffffffffu, send, d);
+                            if (up) x[i] = got;
+                            else x[i | d] = got;
+                        }
+                    }
+                }
                 if (ltile < ntiles) load64(ltile, lkb, q);
                 advance(ltile, lkb);
             } else {
@@ -510,6 +553,7 @@ __global__ void __launch_bounds__(MpCfg<V, NTN, IN64>::NTHR, 1)
         //      half (w - WARP_EPI) / 4 of the columns
         constexpr int CPW = NTN / (NEPI / 4);   // columns per epilogue warp
         const int quad = warp & 3, half = (warp - WARP_EPI) >> 2;
+        const int emode = (a.tab ? 1 : 0) | (a.add ? 2 : 0);   // FP64 operands of the epilogue
         int ac = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++ac) {
             const int buf = ac & 1;
@@ -549,28 +593,51 @@ __global__ void __launch_bounds__(MpCfg<V, NTN, IN64>::NTHR, 1)
                 const int nj = min(16, a.n - mc);
                 if (a.out_f64) {
                     double *o = reinterpret_cast<double *>(a.out) + ob + (int64_t)mc * a.os_m;
-                    const double *tp = a.tab ? a.tab + tb + (int64_t)mc * a.ts_m : nullptr;
-                    const double *ap = a.add ? a.add + ab + (int64_t)mc * a.as_m : nullptr;
-                    // in groups of 8 modes: the group's FP64 operands are loaded before any
-                    // store (the stores could alias them as far as the compiler knows, and
-                    // would otherwise put one load latency on every value)
+                    // 4 * the FP32 sum, exact in FP32, widened to FP64 by bits; the FP64
+                    // operands, if any, in groups of 8 modes whose loads go out before
+                    // any store (the stores could alias them as far as the compiler
+                    // knows, and would otherwise put one load latency on every value).
+                    // One loop per operand case: a select between the cases would run
+                    // their FP64 arithmetic on every value.
+                    if (emode == 0) {
 #pragma unroll
-                    for (int h = 0; h < 16; h += 8) {
-                        double tv[8], av[8];
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            tv[j] = (tp && h + j < nj) ? tp[(int64_t)(h + j) * a.ts_m] : 1.0;
-                            av[j] = (ap && h + j < nj) ? ap[(int64_t)(h + j) * a.as_m] : 0.0;
+                        for (int j = 0; j < 16; ++j) {
+                            if (j >= nj) break;
+                            o[(int64_t)j * a.os_m] = f2d_bits(__fmul_rn(4.0f, __uint_as_float(v[j])));
                         }
+                    } else {
+                        const double *tp = a.tab ? a.tab + tb + (int64_t)mc * a.ts_m : nullptr;
+                        const double *ap = a.add ? a.add + ab + (int64_t)mc * a.as_m : nullptr;
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            if (h + j >= nj) break;
-                            // 4 * the FP32 sum, exact in FP32; widened to FP64 by bits
-                            const double y = f2d_bits(__fmul_rn(4.0f, __uint_as_float(v[h + j])));
-                            double rres = y;
-                            if (tp) rres = ap ? fma(tv[j], y, av[j]) : tv[j] * y;
-                            else if (ap) rres = y + av[j];
-                            o[(int64_t)(h + j) * a.os_m] = rres;
+                        for (int h = 0; h < 16; h += 8) {
+                            double tv[8], av[8];
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                tv[j] = (emode & 1) && h + j < nj ? tp[(int64_t)(h + j) * a.ts_m] : 1.0;
+                                av[j] = (emode & 2) && h + j < nj ? ap[(int64_t)(h + j) * a.as_m] : 0.0;
+                            }
+                            if (emode == 1) {
+#pragma unroll
+                                for (int j = 0; j < 8; ++j) {
+                                    if (h + j >= nj) break;
+                                    o[(int64_t)(h + j) * a.os_m] =
+                                        tv[j] * f2d_bits(__fmul_rn(4.0f, __uint_as_float(v[h + j])));
+                                }
+                            } else if (emode == 2) {
+#pragma unroll
+                                for (int j = 0; j < 8; ++j) {
+                                    if (h + j >= nj) break;
+                                    o[(int64_t)(h + j) * a.os_m] =
+                                        f2d_bits(__fmul_rn(4.0f, __uint_as_float(v[h + j]))) + av[j];
+                                }
+                            } else {
+#pragma unroll
+                                for (int j = 0; j < 8; ++j) {
+                                    if (h + j >= nj) break;
+                                    o[(int64_t)(h + j) * a.os_m] =
+                                        fma(tv[j], f2d_bits(__fmul_rn(4.0f, __uint_as_float(v[h + j]))), av[j]);
+                                }
+                            }
                         }
                     }
                 } else {
