@@ -302,8 +302,8 @@ __global__ void __launch_bounds__(NT, 4) face_kernel(const FacePass a)
             __syncthreads();
             Z = cta_fft_t<R, L, TC, NT, false>(bufA, bufB, fwd_tw<R>(a.t), true);
         }
-        const int64_t klo = (int64_t)p * kstride + c0;
-        const int64_t khi = (int64_t)(a.np - 1 - p) * kstride + c0;
+        const int64_t klo = (int64_t)p * kstride + (int64_t)c0 * (Ph + 1);
+        const int64_t khi = (int64_t)(a.np - 1 - p) * kstride + (int64_t)c0 * (Ph + 1);
 #pragma unroll
         for (int r = 0; r < OPT; ++r) {
             const int o = threadIdx.x + r * NT;
@@ -312,8 +312,8 @@ __global__ void __launch_bounds__(NT, 4) face_kernel(const FacePass a)
                 if (t < ncl) {
                     const int mm = m <= Ph ? m : L - m;
                     const Cx X = Z[t * L + m];
-                    const R kl = ld_khat<R>(a, klo + (int64_t)mm * a.nc + t);
-                    const R kh = ld_khat<R>(a, khi + (int64_t)mm * a.nc + t);
+                    const R kl = ld_khat<R>(a, klo + (int64_t)t * (Ph + 1) + mm);
+                    const R kh = ld_khat<R>(a, khi + (int64_t)t * (Ph + 1) + mm);
                     acc_lo[r] = A::cmake(A::fma(kl, A::re(X), A::re(acc_lo[r])), A::fma(kl, A::im(X), A::im(acc_lo[r])));
                     acc_hi[r] = A::cmake(A::fma(kh, A::re(X), A::re(acc_hi[r])), A::fma(kh, A::im(X), A::im(acc_hi[r])));
                 }
@@ -524,10 +524,20 @@ __global__ void kernel_fill_kernel(const KernelFill a)
     const double inv4pi = 1.0 / (4.0 * 3.14159265358979323846);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int tc = (int)(i % (a.Mc + 1));
-        const int64_t r = i / (a.Mc + 1);
-        const int tb = (int)(r % (a.Mb + 1));
-        const int p = (int)(r / (a.Mb + 1));
+        int tb, tc;
+        int64_t r;
+        if (a.tr) {
+            tb = (int)(i % (a.Mb + 1));
+            r = i / (a.Mb + 1);
+            tc = (int)(r % (a.Mc + 1));
+            r /= (a.Mc + 1);
+        } else {
+            tc = (int)(i % (a.Mc + 1));
+            r = i / (a.Mc + 1);
+            tb = (int)(r % (a.Mb + 1));
+            r /= (a.Mb + 1);
+        }
+        const int p = (int)r;
         const double da = (a.p0 + p + 1) * a.ha, db = tb * a.hb, dc = tc * a.hc;
         const double r2 = da * da + db * db + dc * dc;
         double g;

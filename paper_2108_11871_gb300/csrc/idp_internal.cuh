@@ -151,7 +151,8 @@ struct FacePass {
     int np;                    // number of slices (M_a - 1)
     int Mb;                    // panels along b (data at positions 1..Mb-1)
     int nc;                    // number of frequencies along c (P_c + 1)
-    const double *khat;        // [np][Pb+1][nc] real kernel spectra for distance (p+1) h_a
+    const double *khat;        // [np][nc][Pb+1] real kernel spectra for distance (p+1) h_a (frequency
+                               // along b fastest: the threads of a block read consecutive ones)
     double2 *part;             // partial sums [nchunk][2][2Pb][nc]
     int pchunk;                // slices per chunk
     FftTables t;               // tables for complex length 2Pb
@@ -212,10 +213,11 @@ cudaError_t launch_line1d(const double *rho, double *phi, int M, double h, int m
 // Cyclic-kernel samples k[p][tb][tc] = G(sqrt(((p0+p+1) h_a)^2 + (tb h_b)^2 + (tc h_c)^2)),
 // tb = 0..Mb, tc = 0..Mc (2-D: Mc = 0).
 struct KernelFill {
-    double *k;                 // [np][Mb+1][Mc+1]
+    double *k;                 // [np][Mb+1][Mc+1], or [np][Mc+1][Mb+1] if tr
     int d, np, Mb, Mc;
     double ha, hb, hc;
     int p0;
+    int tr;
 };
 cudaError_t launch_kernel_fill(const KernelFill &a, cudaStream_t st);
 // batched C[b] = A[b] * B[b] (FP64), row-major, strides in elements

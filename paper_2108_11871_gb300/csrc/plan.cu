@@ -1259,7 +1259,7 @@ int plan_setup(idp_plan p)
             double *kb, *tb;
             if ((rc = p->alloc(&kb, (int64_t)np * (Mb + 1))) || (rc = p->alloc(&tb, (int64_t)(Mb + 1) * (Mb + 1))))
                 return rc;
-            KernelFill kf{kb, 2, np, Mb, 0, p->h[face], p->h[other], 0.0, 0};
+            KernelFill kf{kb, 2, np, Mb, 0, p->h[face], p->h[other], 0.0, 0, 0};
             IDP_CK(launch_kernel_fill(kf, 0));
             // DCT-I table Cb[t][m] = w_t cos(pi m t / Mb) * h_a h_b / (4 Mb)
             std::vector<double> cb((size_t)(Mb + 1) * (Mb + 1));
@@ -1304,27 +1304,30 @@ int plan_setup(idp_plan p)
             if ((rc = p->alloc(&kb, (int64_t)slab * per)) || (rc = p->alloc(&yb, (int64_t)slab * per)) ||
                 (rc = p->alloc(&tcb, (int64_t)(Mc + 1) * (Mc + 1))) || (rc = p->alloc(&tbb, (int64_t)(Mb + 1) * (Mb + 1))))
                 return rc;
-            std::vector<double> cc((size_t)(Mc + 1) * (Mc + 1)), cbm((size_t)(Mb + 1) * (Mb + 1));
+            // the spectra are stored transposed, [slice][frequency c][frequency b]:
+            //   khat^T = Cc^T K^T Cb^T  with  K^T[t_c][t_b] = G(d_p, t_b h_b, t_c h_c)
+            std::vector<double> cct((size_t)(Mc + 1) * (Mc + 1)), cbt((size_t)(Mb + 1) * (Mb + 1));
             const double sc = p->h[0] * p->h[1] * p->h[2] / (8.0 * Mb * Mc);
-            for (int tt = 0; tt <= Mc; ++tt)     // Cc[t][m] = w_t cos(pi m t / Mc) * sc
-                for (int m = 0; m <= Mc; ++m)
-                    cc[(size_t)tt * (Mc + 1) + m] = ((tt == 0 || tt == Mc) ? 1.0 : 2.0) *
-                                                    cospi_frac((int64_t)m * tt, Mc) * sc;
-            for (int m = 0; m <= Mb; ++m)        // Cb[m][t] = w_t cos(pi m t / Mb)
-                for (int tt = 0; tt <= Mb; ++tt)
-                    cbm[(size_t)m * (Mb + 1) + tt] = ((tt == 0 || tt == Mb) ? 1.0 : 2.0) *
+            for (int m = 0; m <= Mc; ++m)        // Cc^T[m][t] = w_t cos(pi m t / Mc) * sc
+                for (int tt = 0; tt <= Mc; ++tt)
+                    cct[(size_t)m * (Mc + 1) + tt] = ((tt == 0 || tt == Mc) ? 1.0 : 2.0) *
+                                                     cospi_frac((int64_t)m * tt, Mc) * sc;
+            for (int tt = 0; tt <= Mb; ++tt)     // Cb^T[t][m] = w_t cos(pi m t / Mb)
+                for (int m = 0; m <= Mb; ++m)
+                    cbt[(size_t)tt * (Mb + 1) + m] = ((tt == 0 || tt == Mb) ? 1.0 : 2.0) *
                                                      cospi_frac((int64_t)m * tt, Mb);
-            IDP_CK(cudaMemcpy(tcb, cc.data(), sizeof(double) * cc.size(), cudaMemcpyHostToDevice));
-            IDP_CK(cudaMemcpy(tbb, cbm.data(), sizeof(double) * cbm.size(), cudaMemcpyHostToDevice));
+            IDP_CK(cudaMemcpy(tcb, cct.data(), sizeof(double) * cct.size(), cudaMemcpyHostToDevice));
+            IDP_CK(cudaMemcpy(tbb, cbt.data(), sizeof(double) * cbt.size(), cudaMemcpyHostToDevice));
             for (int p0 = 0; p0 < np; p0 += slab) {
                 const int cnt = std::min(slab, np - p0);
-                KernelFill kf{kb, 3, cnt, Mb, Mc, p->h[a_], p->h[b], p->h[c], p0};
+                KernelFill kf{kb, 3, cnt, Mb, Mc, p->h[a_], p->h[b], p->h[c], p0, 1};
                 IDP_CK(launch_kernel_fill(kf, 0));
-                // rows (t_b) x cols (t_c) times Cc -> Y
-                IDP_CK(launch_gemm_batched(Mb + 1, Mc + 1, Mc + 1, kb, Mc + 1, per, tcb, Mc + 1, 0, yb, Mc + 1, per,
+                // Y^T = Cc^T K^T: rows (frequency c) x cols (t_b)
+                IDP_CK(launch_gemm_batched(Mc + 1, Mb + 1, Mc + 1, tcb, Mc + 1, 0, kb, Mb + 1, per, yb, Mb + 1, per,
                                            cnt, 0));
-                IDP_CK(launch_gemm_batched(Mb + 1, Mc + 1, Mb + 1, tbb, Mb + 1, 0, yb, Mc + 1, per,
-                                           p->khat[a_] + (int64_t)p0 * per, Mc + 1, per, cnt, 0));
+                // khat^T = Y^T Cb^T: rows (frequency c) x cols (frequency b)
+                IDP_CK(launch_gemm_batched(Mc + 1, Mb + 1, Mb + 1, yb, Mb + 1, per, tbb, Mb + 1, 0,
+                                           p->khat[a_] + (int64_t)p0 * per, Mb + 1, per, cnt, 0));
             }
         }
         if ((rc = p->alloc(&p->part, 3 * pmax)) || (rc = p->alloc(&p->F, 3 * fmax))) return rc;
