@@ -239,6 +239,16 @@ __device__ __forceinline__ double ld_khat<double>(const FacePass &a, int64_t i) 
 template <>
 __device__ __forceinline__ ddr ld_khat<ddr>(const FacePass &a, int64_t i) { return a.khatd[i]; }
 
+// asynchronous 16-byte copies global -> shared (no register holds the value in flight)
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // four blocks per SM (64 registers; at 72, with the fused first pass, three fit
 // and the pass ran 8 % slower; the cap costs a 68-byte spill at L = 256, measured
 // 1 % faster than the unfused kernel)
@@ -266,22 +276,62 @@ __global__ void __launch_bounds__(NT, 4) face_kernel(const FacePass a)
     }
     const int64_t kstride = (int64_t)(Ph + 1) * a.nc;
     const Cx *D = reinterpret_cast<const Cx *>(a.D);
-    for (int p = p0; p < p1; ++p) {
-        if (a.sliceflag && !a.sliceflag[p]) continue;   // slice of zeros: contributes nothing
+    // L a power of two: the first radix-4 pass is fused with the load of the slice.
+    // Double-float (latency-bound; the FP64 pass is bound by its pipe and keeps its
+    // registers): the non-zero half of the next slice's columns (positions 0..L/2-1,
+    // data at 1..Mb-1) is brought into stg[t][j] by asynchronous copies while the
+    // current slice's FFT runs; the positions without data are zeroed once
+    constexpr bool P2L = (L & (L - 1)) == 0;
+    constexpr bool PF = P2L && !std::is_same<R, double>::value;
+    constexpr int HL = L / 2;
+    Cx *stg = bufB + TC * L;
+    auto next_slice = [&](int q) {
+        while (q < p1 && a.sliceflag && !a.sliceflag[q]) ++q;   // slices of zeros contribute nothing
+        return q;
+    };
+    auto prefetch = [&](int q) {
+        const Cx *Dq = D + (int64_t)q * a.sp + (int64_t)c0 * a.sc;
+        for (int f = threadIdx.x; f < TC * HL; f += NT) {
+            const int j = f / TC, t = f - j * TC;   // consecutive threads: consecutive columns
+            if (t < ncl && j >= 1 && j <= Mb - 1)
+                cp_async16(stg + t * HL + j, Dq + (int64_t)(j - 1) * a.sb + (int64_t)t * a.sc);
+        }
+        cp_async_commit();
+    };
+    if constexpr (PF) {
+        for (int f = threadIdx.x; f < TC * HL; f += NT) {
+            const int j = f / TC, t = f - j * TC;
+            if (!(t < ncl && j >= 1 && j <= Mb - 1)) stg[t * HL + j] = A::cmake(A::zero(), A::zero());
+        }
+        const int pn = next_slice(p0);
+        if (pn < p1) prefetch(pn);
+    }
+    for (int p = next_slice(p0); p < p1; p = next_slice(p + 1)) {
         // TC columns of the slice: positions 1..Mb-1 (interior index 0..Mb-2), rest zero
         const Cx *Dp = D + (int64_t)p * a.sp + (int64_t)c0 * a.sc;
         const Cx *Z;
-        if constexpr ((L & (L - 1)) == 0) {
-            // the load fused with the first radix-4 pass: a thread reads the two
+        if constexpr (P2L) {
+            // the load fused with the first radix-4 pass: a thread takes the two
             // non-zero inputs x_j, x_{j+L/4} of its unit (the upper half is zero)
             // and writes the unit's four outputs
             constexpr int Q = L / 4;
+            if constexpr (PF) {
+                cp_async_wait_all();
+                __syncthreads();   // every thread's copies have landed
+            }
             for (int f = threadIdx.x; f < TC * Q; f += NT) {
                 const int j = f / TC, t = f - j * TC;   // consecutive threads: consecutive columns
-                Cx a0 = A::cmake(A::zero(), A::zero()), a1 = a0;
-                if (t < ncl) {
-                    if (j >= 1 && j <= Mb - 1) a0 = Dp[(int64_t)(j - 1) * a.sb + (int64_t)t * a.sc];
-                    if (j + Q <= Mb - 1) a1 = Dp[(int64_t)(j + Q - 1) * a.sb + (int64_t)t * a.sc];
+                Cx a0, a1;
+                if constexpr (PF) {
+                    a0 = stg[t * HL + j];
+                    a1 = stg[t * HL + j + Q];
+                } else {
+                    a0 = A::cmake(A::zero(), A::zero());
+                    a1 = a0;
+                    if (t < ncl) {
+                        if (j >= 1 && j <= Mb - 1) a0 = Dp[(int64_t)(j - 1) * a.sb + (int64_t)t * a.sc];
+                        if (j + Q <= Mb - 1) a1 = Dp[(int64_t)(j + Q - 1) * a.sb + (int64_t)t * a.sc];
+                    }
                 }
                 const Cx m1 = mul_mi(a1);
                 Cx *y = bufB + t * L + 4 * j;
@@ -291,6 +341,11 @@ __global__ void __launch_bounds__(NT, 4) face_kernel(const FacePass a)
                 y[3] = A::csub(a0, m1);
             }
             __syncthreads();
+            // the next slice's inputs come in while this one is transformed
+            if constexpr (PF) {
+                const int pn = next_slice(p + 1);
+                if (pn < p1) prefetch(pn);
+            }
             Z = cta_fft_t<R, L, TC, NT, false>(bufB, bufA, fwd_tw<R>(a.t), false, -1, 4);
         } else {
             for (int f = threadIdx.x; f < TC * L; f += NT) {
@@ -585,7 +640,12 @@ __global__ void gemm_kernel(int m, int n, int k, const double *A, int64_t lda, i
 template <int L>
 size_t smem_lines() { return 2 * sizeof(double2) * LineCfg<L>::LB * L; }
 template <int L>
-size_t smem_face() { return 2 * sizeof(double2) * FaceCfg<L>::TC * L; }
+size_t smem_face()
+{
+    // two buffers of TC x L complex (+ the staged half of the next slice, L a power of two)
+    // (double-float only; one size for both, the FP64 pass leaves it unused)
+    return 2 * sizeof(double2) * FaceCfg<L>::TC * L + (((L & (L - 1)) == 0) ? sizeof(double2) * FaceCfg<L>::TC * (L / 2) : 0);
+}
 
 template <class R, int L>
 cudaError_t attrs_len_r()
