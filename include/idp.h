@@ -23,10 +23,10 @@
  *     the two boundary nodes (n[s] = M_s + 1, M_s panels, n[s] >= 3); h[s] > 0
  *     is the mesh width.  Arrays are FP64, C order, last axis contiguous,
  *     prod(n) entries.
- *   - Sizes: the transforms take M_s = 2^a with 16 <= M_s <= 512 or
- *     M_s = 3 * 2^a with 48 <= M_s <= 384; any other M_s <= 512 is padded to
- *     the next of these (section 2; see idp_create_plan); M_s > 512 gives
- *     IDP_ESUPPORT.
+ *   - Sizes: the FFT-based transforms take M_s = 2^a with 16 <= M_s <= 512 or
+ *     M_s = 3 * 2^a with 48 <= M_s <= 384; idp_create_plan pads any other
+ *     M_s <= 512 to the next of these (section 2), idp_create_plan_exact solves
+ *     any 7 <= M_s <= 512 on the grid as given; M_s > 512 gives IDP_ESUPPORT.
  *   - rho is read on interior nodes only; its boundary entries are ignored.
  *     The method assumes rho vanishes near the boundary (section 2); the
  *     library checks it only in validation mode (IDP_KEY_VALIDATE).
