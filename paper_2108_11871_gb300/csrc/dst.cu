@@ -169,8 +169,23 @@ __global__ void __launch_bounds__(NTB) dst_pass_kernel(const DstPass a)
     }
     __syncthreads();
 
-    // 3. complex FFT of length K
-    Cx *Z = cta_fft_t<R, K, LB, NT, false>(bufA, bufB, Tabs<R>::tw(a), false);
+    // 3. complex FFT of length K.  FP64: by each warp on its own lines (barriers of
+    //    one warp between the passes, measured 6 % faster at M = 256 and 512) where
+    //    that keeps every lane busy in the radix-4 passes; else, and in double-float
+    //    (measured 2 % slower that way), by the block
+    constexpr int NW = NT / 32;
+    constexpr bool WFFT = std::is_same<R, double>::value && (LB % NW == 0) && (LB / NW) * (K / 4) >= 32;
+    Cx *Z;
+    if constexpr (WFFT) {
+        constexpr int LPW = LB / NW;
+        const int w = threadIdx.x >> 5;
+        Cx *Zw = cta_fft_t<R, K, LPW, 32, false, true>(bufA + w * LPW * K, bufB + w * LPW * K, Tabs<R>::tw(a),
+                                                       false, threadIdx.x & 31);
+        Z = (Zw == bufA + w * LPW * K) ? bufA : bufB;
+        __syncthreads();
+    } else {
+        Z = cta_fft_t<R, K, LB, NT, false>(bufA, bufB, Tabs<R>::tw(a), false);
+    }
     R *o = reinterpret_cast<R *>(Z == bufA ? bufB : bufA);   // R[LB][M]
 
     // 4. post-processing: even outputs final, odd slots get Re T_k
