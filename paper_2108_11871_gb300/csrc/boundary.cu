@@ -21,6 +21,14 @@ namespace idp {
 
 namespace {
 constexpr int NT = 256;
+// threads per block of the real-FFT pass: double-float on 128 (the LB x L = 512
+// complex values of a block give 128 radix-4 units per pass, one per thread; the
+// latency-bound double-float pass ran 9 % faster at 513^3 so), FP64 on 256 (bound by
+// its pipe: the same at 257^3 and 513^3, 4 % faster at 129^3)
+template <class R>
+struct RfftThreads {
+    static constexpr int value = std::is_same<R, double>::value ? 256 : 128;
+};
 
 // lines per block: 2 buffers of LB x L complex in 16 KB (small blocks: the
 // all-zero line blocks of rho finish at once, and many blocks per SM keep the FP64
@@ -77,8 +85,9 @@ template <>
 __device__ __forceinline__ ddc half_tw<ddr>(const FftTables &t, int k) { return t.halfd[k]; }
 
 template <class R, int L>
-__global__ void __launch_bounds__(NT) rfft_kernel(const RfftPass a)
+__global__ void __launch_bounds__(RfftThreads<R>::value) rfft_kernel(const RfftPass a)
 {
+    constexpr int NTL = RfftThreads<R>::value;
     using A = Ar<R>;
     using Cx = typename A::C;
     constexpr int LB = LineCfg<L>::LB;
@@ -103,7 +112,7 @@ __global__ void __launch_bounds__(NT) rfft_kernel(const RfftPass a)
     // lines that are all zero (rho vanishes near the boundary): zero spectra
     auto write_zero = [&]() {
         Cx *outz = reinterpret_cast<Cx *>(a.out) + (int64_t)u * osu + (int64_t)v0 * osv;
-        for (int f = threadIdx.x; f < nl * (L + 1); f += NT) {
+        for (int f = threadIdx.x; f < nl * (L + 1); f += NTL) {
             const int l = f / (L + 1), m = f - l * (L + 1);
             outz[(int64_t)l * osv + (int64_t)m * ose] = A::cmake(A::zero(), A::zero());
         }
@@ -125,16 +134,16 @@ __global__ void __launch_bounds__(NT) rfft_kernel(const RfftPass a)
     int *colnz = reinterpret_cast<int *>(bufB), *rownz = colnz + L;
     R *zf = reinterpret_cast<R *>(bufA);   // [LB][2L] reals
     const int64_t inb = (int64_t)u * isu + (int64_t)v0 * isv;
-    for (int f = threadIdx.x; f < LB * 2 * L; f += NT) {
+    for (int f = threadIdx.x; f < LB * 2 * L; f += NTL) {
         const int l = f / (2 * L), q = f - l * 2 * L;
         if (q == 0 || q >= M) zf[f] = A::zero();
     }
     if (mk) {
-        for (int f = threadIdx.x; f < L + LB; f += NT) colnz[f] = 0;
+        for (int f = threadIdx.x; f < L + LB; f += NTL) colnz[f] = 0;
         __syncthreads();
     }
     int nz = 0;
-    for (int f = threadIdx.x; f < LB * N; f += NT) {
+    for (int f = threadIdx.x; f < LB * N; f += NTL) {
         int l, e;
         if (contig) { l = f / N; e = f - l * N; }
         else { e = f / LB; l = f - e * LB; }
@@ -164,7 +173,7 @@ __global__ void __launch_bounds__(NT) rfft_kernel(const RfftPass a)
         }
         if (any) {
             if (threadIdx.x == 0 && !a.fl_sl0[u]) a.fl_sl0[u] = 1;
-            for (int e = threadIdx.x; e < N; e += NT)
+            for (int e = threadIdx.x; e < N; e += NTL)
                 if (colnz[e]) {
                     int *f1 = a.fl_row1 + (int64_t)u * a.n2 + e;
                     if (!*f1) *f1 = 1;
@@ -179,9 +188,9 @@ __global__ void __launch_bounds__(NT) rfft_kernel(const RfftPass a)
     } else {
         __syncthreads();
     }
-    Cx *Z = cta_fft_t<R, L, LB, NT, false>(bufA, bufB, fwd_tw<R>(a.t), true);
+    Cx *Z = cta_fft_t<R, L, LB, NTL, false>(bufA, bufB, fwd_tw<R>(a.t), true);
     Cx *outb = reinterpret_cast<Cx *>(a.out) + (int64_t)u * osu + (int64_t)v0 * osv;
-    for (int f = threadIdx.x; f < LB * (L / 2); f += NT) {
+    for (int f = threadIdx.x; f < LB * (L / 2); f += NTL) {
         const int l = f / (L / 2);
         const int m = f - l * (L / 2) + 1;   // 1..L/2
         if (l >= nl) continue;
@@ -730,8 +739,8 @@ cudaError_t launch_rfft_pass(const RfftPass &a, cudaStream_t st)
     else { nu = a.n1; nv = a.n2; }
     IDP_LEN_SWITCH(a.P ? a.P : a.M, {
         dim3 grid((nv + LineCfg<L>::LB - 1) / LineCfg<L>::LB, nu);
-        if (a.dd) rfft_kernel<ddr, L><<<grid, NT, smem_lines<L>(), st>>>(a);
-        else rfft_kernel<double, L><<<grid, NT, smem_lines<L>(), st>>>(a);
+        if (a.dd) rfft_kernel<ddr, L><<<grid, RfftThreads<ddr>::value, smem_lines<L>(), st>>>(a);
+        else rfft_kernel<double, L><<<grid, RfftThreads<double>::value, smem_lines<L>(), st>>>(a);
         return cudaGetLastError();
     })
 }
