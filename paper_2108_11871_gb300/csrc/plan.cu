@@ -7,6 +7,7 @@
 #include <atomic>
 #include <mutex>
 #include <new>
+#include <algorithm>
 #include <vector>
 
 #include "dd.cuh"
@@ -1371,10 +1372,23 @@ int autotune(idp_plan p)
             const int b = a_ == 0 ? 1 : 0, c = a_ == 2 ? 1 : 2;
             const int np = p->ni[a_], L = 2 * p->P[b], nc = p->P[c] + 1;
             const int n0 = p->nchunk[a_];
-            int cands[4] = {std::max(1, n0 / 2), n0, std::min(np, 2 * n0), std::min(np, 4 * n0)};
+            // around the set-up's choice, and the chunk counts that fill whole waves
+            // of resident blocks (one column block per chunk: the block count is
+            // chunks x column blocks, and a part-filled last wave leaves SMs idle)
+            std::vector<int> cands = {std::max(1, n0 / 2), n0, std::min(np, 2 * n0), std::min(np, 4 * n0)};
+            {
+                int nsm = 152;
+                cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->dev);
+                const int slots = nsm * face_blocks_per_sm(L);
+                const int tiles = (nc + face_columns_per_block(L) - 1) / face_columns_per_block(L);
+                for (int w = 1; w <= 8; ++w) {
+                    const int c = std::min(np, std::max(1, (int)(((int64_t)w * slots + tiles - 1) / tiles)));
+                    if (std::find(cands.begin(), cands.end(), c) == cands.end()) cands.push_back(c);
+                }
+            }
             int best_n = n0, best_p = p->pchunk[a_];
             float best_t = 1e30f;
-            for (int ci = 0; ci < 4 && !rc; ++ci) {
+            for (size_t ci = 0; ci < cands.size() && !rc; ++ci) {
                 const int pch = (np + cands[ci] - 1) / cands[ci];
                 const int nch = (np + pch - 1) / pch;
                 if ((int64_t)nch * 2 * L * nc > p->part_cap) {
