@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--fp64-only", action="store_true", help="skip the reduced-precision variants")
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the 129^3, sweep and batched workloads and the CPU baselines")
-    ap.add_argument("--dst-shape", type=int, default=None, choices=[0, 8, -8, 32, 16],
+    ap.add_argument("--dst-shape", type=int, default=None, choices=[0, 8, -8, 32, 16, 4],
                     help="block shape of the FP64 sine passes (IDP_KEY_DST_SHAPE) instead of the "
                          "autotuner's: profiled runs, whose timings the profiler perturbs, then run "
                          "the shape of the plain run")

@@ -73,8 +73,9 @@ enum {
     IDP_KEY_DST_SHAPE = 5,  /* block shape of the full-volume sine passes (results are the same
                                bits for every shape): 0 by size (default), 8 = 8 lines per block,
                                -8 = 8 lines on 128 threads (M = 128 only), 32 = 32 lines (M = 128
-                               only), 16 = 16 lines (M = 256 only); a shape that does not apply
-                               to a length falls back to 0 */
+                               only), 16 = 16 lines (M = 256 only), 4 = 4 lines on 128 threads
+                               (M = 256 and 512 only); a shape that does not apply to a length
+                               falls back to 0 */
     IDP_KEY_STALL_TEST = 3, /* test hook for failure handling (mixed precision only): the next
                                tensor-core pass issues no products, so its bounded wait expires
                                (after ~5 ms); the kernel records the failure, frees its tensor

@@ -471,6 +471,10 @@ cudaError_t launch_k(const DstPass &a, cudaStream_t st)
     if constexpr (K == 128) {
         if (a.lines == 16) return launch_lb<R, K, 16>(a, nu, nv, st);
     }
+    // 4 lines on 128 threads (M = 256, 512): a warp per line, smaller blocks
+    if constexpr (K == 128 || K == 256) {
+        if (a.lines == 4) return launch_lb<R, K, 4, 128>(a, nu, nv, st);
+    }
     if constexpr (DstCfg<K>::LB > 8) {
         // a launch of less than two blocks per SM (the layer transforms) runs
         // faster on more, smaller blocks: FP64 on 2 lines per 128-thread block
@@ -510,6 +514,9 @@ cudaError_t attr_k()
     }
     if constexpr (K == 128) {
         if (e == cudaSuccess) e = attr_lb<R, K, 16>();
+    }
+    if constexpr (K == 128 || K == 256) {
+        if (e == cudaSuccess) e = attr_lb<R, K, 4, 128>();
     }
     return e;
 }

@@ -1424,9 +1424,9 @@ int autotune(idp_plan p)
     }
     if (!rc) {
         // block shape of the full-volume sine passes: the default, 8 lines on 256
-        // threads, 8 lines on 128 threads (M = 128), 32 lines (M = 128) or 16
-        // lines (M = 256); shapes that do not apply to a length fall back to the
-        // default.  Timed in whole solves: the transform of rho runs beside the
+        // threads, 8 lines on 128 threads (M = 128), 32 lines (M = 128), 16
+        // lines (M = 256) or 4 lines on 128 threads (M = 256, 512); shapes that do
+        // not apply to a length fall back to the default.  Timed in whole solves: the transform of rho runs beside the
         // boundary stages, so what a shape costs depends on what runs next to it
         // (a shape can win alone and lose in the solve).  The density is a smooth
         // bump over the middle of the box, zero near the boundary.
@@ -1449,10 +1449,10 @@ int autotune(idp_plan p)
         if (e == cudaSuccess) e = cudaMalloc(&tphi, sizeof(double) * p->nodes);
         if (e == cudaSuccess) e = cudaMemcpy(trho, hr.data(), sizeof(double) * p->nodes, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) rc = cuda_fail(e, "autotune buffers");
-        const int opts[5] = {0, 8, -8, 32, 16};
+        const int opts[6] = {0, 8, -8, 32, 16, 4};
         int best = 0;
         float bt = 1e30f;
-        for (int i = 0; i < 5 && !rc; ++i) {
+        for (int i = 0; i < 6 && !rc; ++i) {
             p->dst_lines = opts[i];
             const float t = timed([&]() -> int { return enqueue_grid(p, trho, tphi, 0, st); });
             if (t < bt) { bt = t; best = opts[i]; }
@@ -1656,7 +1656,7 @@ int idp_plan_set(idp_plan p, int key, int64_t value)
         return autotune(p);
     }
     if (key == IDP_KEY_DST_SHAPE) {
-        if (value != 0 && value != 8 && value != -8 && value != 32 && value != 16) return IDP_EINVAL;
+        if (value != 0 && value != 8 && value != -8 && value != 32 && value != 16 && value != 4) return IDP_EINVAL;
         p->dst_lines = (int)value;
         ++p->version;
         if (p->gexec) {

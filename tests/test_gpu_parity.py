@@ -394,6 +394,21 @@ def test_dst_block_shapes_give_the_same_bits(idp, shape):
     assert np.array_equal(got, _SHAPE_REF["default"])
 
 
+_SHAPE_PROB_256 = w.Problem("c", (33, 17, 257), (0.0, 0.0, 0.0), (1.0, 0.5, 2.0), "gauss", dict(seed=2109))
+
+
+@pytest.mark.parametrize("shape", [8, 16, 4])
+def test_dst_block_shapes_at_m256_give_the_same_bits(idp, shape):
+    # M = 256 along axis 2: the 16-line and the 4-line, 128-thread blocks apply there
+    # (the FFT of a line by one warp, or by the block, in the same order of operations)
+    if "ref256" not in _SHAPE_REF:
+        _SHAPE_REF["ref256"] = osolve.solve(_SHAPE_PROB_256.rho(), _SHAPE_PROB_256.h, 6, boundary="convolution")
+        _SHAPE_REF["default256"] = _solve_with_shape(idp, _SHAPE_PROB_256, 0)
+    got = _solve_with_shape(idp, _SHAPE_PROB_256, shape)
+    assert rel_max(got, _SHAPE_REF["ref256"]) < TOL
+    assert np.array_equal(got, _SHAPE_REF["default256"])
+
+
 def test_dst_shape_key_rejects_unknown_values(idp):
     plan = idp.create_plan(3, (33, 33, 33), (0.1, 0.1, 0.1), 6)
     lib = idp.library()
