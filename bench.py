@@ -46,7 +46,7 @@ KERNEL_NAMES = {1: "dst_pass", 2: "rfft", 3: "face", 4: "face_invb", 5: "face_c2
 # averaged); a grid not listed reports null
 # (profiles/dst_pass_fp64_257cube_traffic.md: 246 MB per launch at 257^3, scaled by the
 # interior points to 513^3)
-DST_TRAFFIC = {(257, 257, 257): 246.0e6, (513, 513, 513): 1.98e9}
+DST_TRAFFIC = {(257, 257, 257): 248.6e6, (513, 513, 513): 2.00e9}
 
 
 def parse():
