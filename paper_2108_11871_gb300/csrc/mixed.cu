@@ -25,11 +25,15 @@
 // gridDim.x, ... (mode tile fastest, so that the mode tiles of one line tile run
 // at the same time on neighbouring SMs and share its input through L2), with
 // specialised warps:
-//   warps 0-15  producers: load 128 lines x KB of the input (FP64, or FP32 in
-//               16-byte vectors where the lines are 16-byte aligned; the loads of
-//               the next two stages are in flight while a stage is split), split it
-//               into pieces, store them in the K-major core-matrix layout and
-//               arrive on the stage's A barrier;
+//   warps 0-15  producers: warp w owns lines 8w .. 8w+7 of a tile.  FP32 input
+//               (the padded intermediates): they read the stage's values from the
+//               input ring; FP64 input (node arrays whose row strides are not
+//               multiples of 16 bytes, which no tensor map can describe): they load
+//               them, a line of the stage per warp instruction and an 8 x 8 shuffle
+//               transpose (BF16X3), the loads of the next two stages in flight while
+//               a stage is split.  They split the values into pieces, store them in
+//               the K-major core-matrix layout (the eight lanes of a k group write 128
+//               contiguous bytes) and arrive on the stage's A barrier;
 //   warp 16     copies the stage's pre-split sine image (one contiguous block per
 //               (mode tile, K stage)) with one bulk asynchronous copy that
 //               completes on the stage's B barrier;
@@ -38,17 +42,21 @@
 //               them to the stage's empty barrier (the producers' signal to refill
 //               it), and after a tile's last stage commits to the accumulator's
 //               full barrier;
-//   warps 18-21 epilogue: wait for a full accumulator, read it (warp w: TMEM lanes
-//               32 (w % 4) ..), write the lines and release the accumulator.
-// The stages form a ring (NS deep, ~200 KB of shared memory) and the accumulator
-// is double-buffered (2 x NTN TMEM columns), so the loads, the products and the
-// epilogue of consecutive tiles overlap.  Operands live in shared memory in the
-// canonical K-major layout without swizzle: 8 x 16-byte core matrices (8 BF16 or
-// 4 TF32 values per row), adjacent along M/N 128 bytes apart (SBO), adjacent
-// along K one core column apart (LBO: 2048 bytes for the 128 rows of A, 16 NTN
-// bytes for the NTN rows of B); one MMA takes K = 16 (BF16) or 8 (TF32), two
-// core matrices along K, in both variants.  FP64 <-> FP32 conversions and the
-// factor 4 are integer operations (FP64 issue is scarce on this GPU).
+//   warp 18     FP32 input: brings each stage's 128 lines x KB values with one 2-D
+//               tensor copy (128- or 64-byte swizzle) into a ring of input slots,
+//               refilled once the producer warps have read a slot;
+//   warps 19-   epilogue (8 warps for FP32 input, 4 for FP64): wait for a full
+//               accumulator, read it (warp w: TMEM lanes 32 (w % 4) .., half
+//               (w - 19) / 4 of the columns), write the lines and release it.
+// The operand stages form a ring (NS = 2-3 deep), the input slots another (NR = 2-6),
+// and the accumulator is double-buffered (2 x NTN TMEM columns), so the loads, the
+// products and the epilogue of consecutive tiles overlap.  Operands live in shared
+// memory in the canonical K-major layout without swizzle: 8 x 16-byte core matrices
+// (8 BF16 or 4 TF32 values per row), adjacent along M/N 128 bytes apart (SBO),
+// adjacent along K one core column apart (LBO: 2048 bytes for the 128 rows of A, 16
+// NTN bytes for the NTN rows of B); one MMA takes K = 16 (BF16) or 8 (TF32), two core
+// matrices along K, in both variants.  FP64 <-> FP32 conversions and the factor 4 are
+// integer operations (FP64 issue is scarce on this GPU).
 //
 // Every wait is bounded (clock64); a wait that runs out sets the block's failure
 // flag, the other roles leave their loops at their next check, the block waits
