@@ -113,8 +113,11 @@ struct MpPass {
     const double *add; int64_t as_m, as_p, as_q;
     int *err;                   // set to 1 if a wait on the tensor cores timed out
     int stall_test;             // test hook: issue no products, so the bounded wait expires
-    int in_vec4;                // FP32 input whose lines start on 16-byte boundaries (is_k = 1, is_p and
-                                // is_q multiples of 4): loaded in 16-byte vectors
+    int in_vec4;                // FP32 input whose lines start on 16-byte boundaries and are padded to
+                                // whole 16-byte vectors (is_k = 1, is_q a multiple of 4, is_p = Q is_q
+                                // or P = 1): required for FP32 input, which a 2-D tensor map describes.
+                                // FP64 input (is_k = 1) may be read up to 8 bytes before a line's first
+                                // value and after its last: node interiors or arrays with guard regions
 };
 cudaError_t launch_mp_pass(const MpPass &a, cudaStream_t st);
 cudaError_t mp_set_attributes();
