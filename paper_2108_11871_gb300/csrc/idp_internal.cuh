@@ -115,9 +115,8 @@ struct MpPass {
     int stall_test;             // test hook: issue no products, so the bounded wait expires
     int in_vec4;                // FP32 input whose lines start on 16-byte boundaries and are padded to
                                 // whole 16-byte vectors (is_k = 1, is_q a multiple of 4, is_p = Q is_q
-                                // or P = 1): required for FP32 input, which a 2-D tensor map describes.
-                                // FP64 input (is_k = 1) may be read up to 8 bytes before a line's first
-                                // value and after its last: node interiors or arrays with guard regions
+                                // or P = 1): required for FP32 input, which a 2-D tensor map describes
+                                // (FP64 input needs is_k = 1 only)
 };
 cudaError_t launch_mp_pass(const MpPass &a, cudaStream_t st);
 cudaError_t mp_set_attributes();
