@@ -21,13 +21,13 @@ namespace idp {
 
 namespace {
 constexpr int NT = 256;
-// threads per block of the real-FFT pass: double-float on 128 (the LB x L = 512
-// complex values of a block give 128 radix-4 units per pass, one per thread; the
-// latency-bound double-float pass ran 9 % faster at 513^3 so), FP64 on 256 (bound by
-// its pipe: the same at 257^3 and 513^3, 4 % faster at 129^3)
-template <class R>
+// threads per block of the real-FFT pass: 256, except double-float at L = 512 on 128
+// (the LB x L = 512 complex values of a block give 128 radix-4 units per pass, one per
+// thread; that latency-bound pass ran 9 % faster at 513^3 so, while at L <= 256 the
+// 96-problem batch ran 4.5 % slower, and FP64, bound by its pipe, gained nothing)
+template <class R, int L>
 struct RfftThreads {
-    static constexpr int value = std::is_same<R, double>::value ? 256 : 128;
+    static constexpr int value = (!std::is_same<R, double>::value && L >= 512) ? 128 : 256;
 };
 
 // lines per block: 2 buffers of LB x L complex in 16 KB (small blocks: the
@@ -85,9 +85,9 @@ template <>
 __device__ __forceinline__ ddc half_tw<ddr>(const FftTables &t, int k) { return t.halfd[k]; }
 
 template <class R, int L>
-__global__ void __launch_bounds__(RfftThreads<R>::value) rfft_kernel(const RfftPass a)
+__global__ void __launch_bounds__(RfftThreads<R, L>::value) rfft_kernel(const RfftPass a)
 {
-    constexpr int NTL = RfftThreads<R>::value;
+    constexpr int NTL = RfftThreads<R, L>::value;
     using A = Ar<R>;
     using Cx = typename A::C;
     constexpr int LB = LineCfg<L>::LB;
@@ -739,8 +739,8 @@ cudaError_t launch_rfft_pass(const RfftPass &a, cudaStream_t st)
     else { nu = a.n1; nv = a.n2; }
     IDP_LEN_SWITCH(a.P ? a.P : a.M, {
         dim3 grid((nv + LineCfg<L>::LB - 1) / LineCfg<L>::LB, nu);
-        if (a.dd) rfft_kernel<ddr, L><<<grid, RfftThreads<ddr>::value, smem_lines<L>(), st>>>(a);
-        else rfft_kernel<double, L><<<grid, RfftThreads<double>::value, smem_lines<L>(), st>>>(a);
+        if (a.dd) rfft_kernel<ddr, L><<<grid, RfftThreads<ddr, L>::value, smem_lines<L>(), st>>>(a);
+        else rfft_kernel<double, L><<<grid, RfftThreads<double, L>::value, smem_lines<L>(), st>>>(a);
         return cudaGetLastError();
     })
 }
