@@ -76,6 +76,9 @@ def parse():
                     choices=["FP64", "DF32", "MIXED_BF16X3", "MIXED_TF32X3"],
                     help="precision mode of the solves in the profiler window (an autotuned plan of "
                          "its own unless FP64)")
+    ap.add_argument("--nvtx", action="store_true",
+                    help="the solves in the profiler window with NVTX ranges around their launches and "
+                         "stages (IDP_KEY_NVTX; plain launches)")
     ap.add_argument("--batched", action="store_true",
                     help="only the 96-problem batched workload (uneven sizes)")
     return ap.parse_args()
@@ -420,6 +423,8 @@ def run_headline(g, args, prob):
         wplan = plan if args.profile_precision == "FP64" else \
             g.plan(prob, args.order, getattr(idp, "IDP_PRECISION_" + args.profile_precision))
         wphi = torch.empty_like(rho)
+        if args.nvtx:
+            idp.plan_set(wplan, idp.IDP_KEY_NVTX, 1)
         idp.solve(wplan, rho, wphi, g.stream)
         torch.cuda.synchronize()
         torch.cuda.cudart().cudaProfilerStart()
@@ -428,6 +433,8 @@ def run_headline(g, args, prob):
             idp.solve(wplan, rho, wphi, g.stream)
         torch.cuda.synchronize()
         torch.cuda.cudart().cudaProfilerStop()
+        if args.nvtx:
+            idp.plan_set(wplan, idp.IDP_KEY_NVTX, 0)
         del wplan, wphi
 
     # end to end through the host-buffer entry point (pinned host memory, both

@@ -85,6 +85,14 @@ enum {
                                bits, as in IDP_PRECISION_DF32) instead of FP64; value 0 (default):
                                FP64.  No effect in the other modes.  Setting 1 allocates the
                                double-float copies of the kernel spectra. */
+    IDP_KEY_NVTX = 9,       /* value 1: NVTX ranges (NVTX v3, host side, at enqueue time) around every
+                               kernel launch of a solve or stage, named after its IDP_KERNEL_* family
+                               ("idp:dst", "idp:face", ...), and around the solve and its stages
+                               ("idp:solve", "idp:boundary values g", "idp:sine transform ..."), so
+                               that a profiler attributes the kernels to the steps of the method;
+                               solves then use plain launches (ranges recorded while a graph is
+                               captured would not recur on its replays).  0 (default): none.
+                               Results are the same bits either way. */
     IDP_KEY_GUARD_TEST = 7, /* test hook for idp_plan_check_guards: value 1 overwrites the first
                                byte of the guard region in front of the plan's first buffer (a
                                write inside that allocation, from the host), value 0 restores it;

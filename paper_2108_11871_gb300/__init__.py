@@ -11,7 +11,7 @@ from .binding import (  # noqa: F401
     IDP_RHS6_NOALLOC_MAX_NODES, rhs6_noalloc,
     IDP_STAGE_BOUNDARY, IDP_STAGE_GTILDE, IDP_STAGE_PHISTAR, IDP_STAGE_U1,
     IDP_STAGE_R, IDP_STAGE_PHI, IDP_KEY_USE_GRAPH, IDP_KEY_PRECISION, IDP_KEY_STALL_TEST, IDP_KEY_AUTOTUNE, IDP_KEY_DST_SHAPE, IDP_KEY_VALIDATE,
-    IDP_KEY_GUARD_TEST, IDP_KEY_MIXED_BOUNDARY_DF32,
+    IDP_KEY_GUARD_TEST, IDP_KEY_MIXED_BOUNDARY_DF32, IDP_KEY_NVTX,
     IDP_PRECISION_FP64,
     IDP_PRECISION_MIXED_BF16X3, IDP_PRECISION_DF32, IDP_PRECISION_MIXED_TF32X3, IDP_ETIMEOUT, IdpError, Plan, create_plan,
     destroy_plan, library, plan_check_guards, plan_grid, plan_info, plan_set, plan_tuning, plan_status, solve, solve_batched,

@@ -23,6 +23,7 @@ IDP_KEY_DST_SHAPE = 5
 IDP_KEY_VALIDATE = 6
 IDP_KEY_GUARD_TEST = 7
 IDP_KEY_MIXED_BOUNDARY_DF32 = 8
+IDP_KEY_NVTX = 9
 IDP_PRECISION_FP64, IDP_PRECISION_MIXED_BF16X3, IDP_PRECISION_DF32, IDP_PRECISION_MIXED_TF32X3 = 0, 1, 2, 3
 IDP_ETIMEOUT = -7
 (IDP_STAGE_BOUNDARY, IDP_STAGE_GTILDE, IDP_STAGE_PHISTAR, IDP_STAGE_U1, IDP_STAGE_R,

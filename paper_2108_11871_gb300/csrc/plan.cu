@@ -10,6 +10,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dd.cuh"
 #include "idp_internal.cuh"
 #include "../../include/idp.h"
@@ -224,6 +226,7 @@ struct idp_plan_s {
 
     // CUDA graph of one solve for a fixed (rho, phi)
     int use_graph = 1;
+    int nvtx = 0;                     // IDP_KEY_NVTX: NVTX ranges around launches and stages
     cudaStream_t cap = nullptr;
     cudaStream_t side = nullptr;          // second stream of a solve (forward transform of rho)
     cudaEvent_t fork = nullptr, join = nullptr;
@@ -275,13 +278,52 @@ struct idp_plan_s {
 
 namespace {
 
-// Marks one kernel launch: counts it and, while profiling, brackets it with
-// CUDA events recorded on the launch stream.
+// NVTX range names of the IDP_KERNEL_* families
+const char *kernel_range(int kind)
+{
+    switch (kind) {
+    case IDP_KERNEL_DST: return "idp:dst";
+    case IDP_KERNEL_RFFT: return "idp:rfft";
+    case IDP_KERNEL_FACE: return "idp:face";
+    case IDP_KERNEL_FACE_INVB: return "idp:face_invb";
+    case IDP_KERNEL_FACE_C2R: return "idp:face_c2r";
+    case IDP_KERNEL_GTILDE: return "idp:gtilde";
+    case IDP_KERNEL_RHS6_W: return "idp:rhs6_w";
+    case IDP_KERNEL_RHS6_CORE: return "idp:rhs6_core";
+    case IDP_KERNEL_RHS6_EXTRAP: return "idp:rhs6_extrap";
+    case IDP_KERNEL_GTILDE_EXPAND: return "idp:gtilde_expand";
+    case IDP_KERNEL_DST_PARTS: return "idp:dst_layers";
+    case IDP_KERNEL_MIXED: return "idp:mixed";
+    case IDP_KERNEL_RHS6_EXPAND: return "idp:rhs6_expand";
+    case IDP_KERNEL_LINE1D: return "idp:line1d";
+    case IDP_KERNEL_PAD: return "idp:pad";
+    case IDP_KERNEL_VALIDATE: return "idp:validate";
+    default: return "idp:kernel";
+    }
+}
+
+// An NVTX range over a stage of a solve (IDP_KEY_NVTX), closed at the end of scope.
+struct Range {
+    bool on;
+    Range(idp_plan p, const char *name) : on(p->nvtx != 0)
+    {
+        if (on) nvtxRangePushA(name);
+    }
+    ~Range()
+    {
+        if (on) nvtxRangePop();
+    }
+};
+
+// Marks one kernel launch: counts it, with IDP_KEY_NVTX encloses it in an NVTX
+// range named after its family and, while profiling, brackets it with CUDA events
+// recorded on the launch stream.
 struct Mark {
     idp_plan p;
     cudaStream_t st;
     int idx = -1;
-    Mark(idp_plan p_, int kind, cudaStream_t st_) : p(p_), st(st_)
+    Range r;
+    Mark(idp_plan p_, int kind, cudaStream_t st_) : p(p_), st(st_), r(p_, kernel_range(kind))
     {
         ++p->launches;
         if (p->profiling && p->ev_used + 2 <= (int)p->ev.size()) {
@@ -602,6 +644,7 @@ int transform(idp_plan p, View3 in, double *work, View3 out, const double *tab, 
               cudaStream_t st, bool allow_reduced = true, bool skip_axis2 = false, int in_dd0 = 0,
               bool fp64_only = true)
 {
+    Range rg(p, forward ? "idp:sine transform (forward)" : "idp:sine transform (inverse)");
     if (tensor_mode(p) && allow_reduced && p->mixed_path == 0)
         return transform_mixed(p, in, out, tab, add, st == p->side ? 1 : 0, st);
     // df32 passes: precision DF32, or precision MIXED when the autotuner found the
@@ -762,6 +805,7 @@ int transform_rho_from_T0(idp_plan p, cudaStream_t st)
 int boundary(idp_plan p, const double *rho, double *dst0, double *dst1, cudaStream_t st,
              bool fork_rho = false, const double *rho_src = nullptr)
 {
+    Range rg(p, "idp:boundary values g");
     const View3 r = node_interior(p, rho);
     int rc;
     FftTables t;
@@ -967,6 +1011,7 @@ int enqueue_padded(idp_plan p, const double *rho, double *phi, int stop, cudaStr
 
 int enqueue(idp_plan p, const double *rho, double *phi, int stop, cudaStream_t st)
 {
+    Range rg(p, stop ? "idp:stage" : "idp:solve");
     if (p->validate) {
         // validation mode: the caller's rho is checked first (in a host-buffer
         // solve it goes up in one copy, and the check reads the copy)
@@ -1495,7 +1540,9 @@ int run_solve(idp_plan p, const double *rho, double *phi, cudaStream_t st)
 {
     p->last = st;
     p->last_valid = 1;
-    if (!p->use_graph || p->stall_test) {   // a stall test is never baked into a graph
+    // a stall test is never baked into a graph, and NVTX ranges recorded while one is
+    // captured would not recur on its replays
+    if (!p->use_graph || p->stall_test || p->nvtx) {
         p->launches = 0;
         return enqueue(p, rho, phi, 0, st);
     }
@@ -1651,6 +1698,10 @@ int idp_plan_set(idp_plan p, int key, int64_t value)
         p->use_graph = value ? 1 : 0;
         return IDP_OK;
     }
+    if (key == IDP_KEY_NVTX) {
+        p->nvtx = value ? 1 : 0;
+        return IDP_OK;
+    }
     if (key == IDP_KEY_AUTOTUNE) {
         if (!value) return IDP_OK;
         return autotune(p);
@@ -1781,7 +1832,7 @@ int idp_solve_host(idp_plan p, const double *rho_host, double *phi_host, void *s
     if (!p->h_rho && ((rc = p->alloc(&p->h_rho, p->unodes)) || (rc = p->alloc(&p->h_phi, p->unodes)))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     double *phi_view = nullptr;
-    if (p->use_graph && !p->stall_test && device_view(rho_host) && (phi_view = device_view(phi_host))) {
+    if (p->use_graph && !p->stall_test && !p->nvtx && device_view(rho_host) && (phi_view = device_view(phi_host))) {
         // page-locked buffers: phi is written in place by the kernels
         if ((rc = run_solve_host(p, rho_host, phi_host, phi_view, st))) return rc;
     } else {
@@ -1816,7 +1867,8 @@ int idp_solve_batched(int count, const idp_plan plans[], const double *const rho
     cudaStream_t st = (cudaStream_t)stream;
     idp_plan p0 = plans[0];
     bool graphs = true;
-    for (int i = 0; i < count; ++i) graphs = graphs && plans[i]->use_graph && plans[i]->dev == p0->dev;
+    for (int i = 0; i < count; ++i)
+        graphs = graphs && plans[i]->use_graph && !plans[i]->nvtx && plans[i]->dev == p0->dev;
     if (!graphs) {
         for (int i = 0; i < count; ++i) {
             int rc = run_solve(plans[i], rho[i], phi[i], st);

@@ -64,7 +64,7 @@ def test_binding_constants_match_the_header():
     for k, v in mine.items():
         if k in declared:
             assert declared[k] == v, k
-    for k in ("IDP_KEY_DST_SHAPE", "IDP_KEY_AUTOTUNE", "IDP_STAGE_R", "IDP_PRECISION_DF32"):
+    for k in ("IDP_KEY_DST_SHAPE", "IDP_KEY_AUTOTUNE", "IDP_STAGE_R", "IDP_PRECISION_DF32", "IDP_KEY_NVTX"):
         assert k in mine and k in declared, k
 
 

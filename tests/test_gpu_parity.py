@@ -212,6 +212,33 @@ def test_graph_and_plain_launches_agree_and_repeat(idp):
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
 
 
+def test_nvtx_ranges_give_the_same_bits(idp):
+    # IDP_KEY_NVTX: ranges around every launch and stage, plain launches; the same
+    # bits as the graph replay, in single, host-buffer and batched solves
+    prob = w.c3_large(65)
+    rho = to_dev(prob.rho())
+    plan = idp.create_plan(3, prob.n, prob.h, 6)
+    ref = to_dev(np.zeros(prob.n))
+    idp.solve(plan, rho, ref)
+    idp.plan_status(plan)
+    idp.plan_set(plan, idp.IDP_KEY_NVTX, 1)
+    o = to_dev(np.zeros(prob.n))
+    idp.solve(plan, rho, o)
+    idp.plan_status(plan)
+    assert np.array_equal(o.cpu().numpy(), ref.cpu().numpy())
+    import torch
+    rh = torch.from_numpy(prob.rho()).pin_memory()
+    ph = torch.zeros(prob.n, dtype=torch.float64).pin_memory()
+    idp.solve_host(plan, rh.data_ptr(), ph.data_ptr())
+    idp.plan_status(plan)
+    assert np.array_equal(ph.numpy(), ref.cpu().numpy())
+    ob = to_dev(np.zeros(prob.n))
+    idp.solve_batched([plan], [rho], [ob])
+    idp.plan_status(plan)
+    assert np.array_equal(ob.cpu().numpy(), ref.cpu().numpy())
+    idp.plan_set(plan, idp.IDP_KEY_NVTX, 0)
+
+
 def test_batched_equals_single(idp):
     probs = [w.c3_large(33), w.c2_3d(65), w.Problem("x", (33, 65, 17), (0.0,) * 3, (1.0,) * 3,
                                                      "gauss", dict(seed=11))]
