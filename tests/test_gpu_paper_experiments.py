@@ -16,7 +16,9 @@ M = 80 and 112 are padded to 96 and 128 panels).
 With automatic padding (section 2) the GPU solver also takes the paper's own
 panel counts M = 20..200: test_table1_at_the_papers_panel_counts fits the
 rates over the paper's windows, each grid padded to a supported count where
-needed and the error measured at the nodes of [-1,1]^3.
+needed and the error measured at the nodes of [-1,1]^3;
+test_table1_on_the_papers_grids_as_given solves the same grids without padding
+(exact-size plans).
 """
 import os
 
@@ -40,9 +42,9 @@ def idp():
     return m
 
 
-def _solve(idp, prob, order):
+def _solve(idp, prob, order, exact=False):
     import torch
-    plan = idp.create_plan(3, prob.n, prob.h, order)
+    plan = idp.create_plan(3, prob.n, prob.h, order, exact=exact)
     r = to_dev(prob.rho())
     out = torch.empty_like(r)
     idp.solve(plan, r, out)
@@ -50,9 +52,9 @@ def _solve(idp, prob, order):
     return out.cpu().numpy()
 
 
-def _rel_err(idp, M, p, order):
+def _rel_err(idp, M, p, order, exact=False):
     prob = w.scaled_bump((M + 1,) * 3, centre=CENTRE, eps=0.4, p=p)
-    phi = _solve(idp, prob, order)
+    phi = _solve(idp, prob, order, exact)
     ex = closed_form.bump_potential_on_grid(prob)
     return float(np.abs(phi - ex).max() / np.abs(ex).max())
 
@@ -128,6 +130,40 @@ def test_table1_at_the_papers_panel_counts(idp):
         # grids in the window, where the 4th-order harmonic error and the spectral
         # error of a C^4 density are of one size)
         if diff != 6:
+            assert abs(r6 - g6) < 0.2, (diff, r6, g6)
+        if diff != 4:
+            assert abs(r4 - g4) < 0.2, (diff, r4, g4)
+
+
+def test_table1_on_the_papers_grids_as_given(idp):
+    # the paper's own grids solved as given (idp_create_plan_exact: the sine
+    # transforms of lengths without an FFT here as direct sums, the boundary
+    # convolutions at the next FFT length 2P >= 2M): 6th-order rates over M =
+    # 20..100, 4th order over M = 100..200, against the oracle's rates on the same
+    # grids and against the paper
+    gold = _golden()
+    orc = _oracle_rates()
+    M6 = (20, 28, 40, 56, 80, 100)
+    M4 = (100, 140, 200)
+    report = []
+    for diff, p in ((0, 1), (2, 3), (4, 5), (6, 7), (8, 9)):
+        e6 = [_rel_err(idp, M, p, 6, exact=True) for M in M6]
+        e4 = [_rel_err(idp, M, p, 4, exact=True) for M in M4]
+        report.append((diff, _rate(M4, e4), gold[diff][0], _rate(M6, e6), gold[diff][1], e6[-1]))
+    print("\n  C^k   4th order (paper)   6th order (paper)   [the paper's grids as given]")
+    for diff, r4, g4, r6, g6, _ in report:
+        print("  %d     %5.2f (%4.1f)        %5.2f (%4.1f)" % (diff, r4, g4, r6, g6))
+    for diff, r4, g4, r6, g6, floor in report:
+        # the GPU solver reproduces the oracle's rates on the paper's grids
+        o4, o6 = orc[diff, "paper"]
+        assert abs(r6 - o6) < 0.05 and abs(r4 - o4) < 0.05, (diff, r4, o4, r6, o6)
+        # and the paper's, except the documented deviations of the method as read:
+        # 6th order C^6 (8.6 against 9.8); 6th order C^8 within 1.0 (10.1 against
+        # 10.8: the error at M = 100 is 7e-12, near the rounding floor of the
+        # solve); 4th order C^4 (4.9 against 6.6 on these grids)
+        if diff == 8:
+            assert abs(r6 - g6) < 1.0 and floor < 1e-11, (diff, r6, g6, floor)
+        elif diff != 6:
             assert abs(r6 - g6) < 0.2, (diff, r6, g6)
         if diff != 4:
             assert abs(r4 - g4) < 0.2, (diff, r4, g4)
