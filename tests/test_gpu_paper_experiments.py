@@ -169,13 +169,16 @@ def test_table1_on_the_papers_grids_as_given(idp):
             assert abs(r4 - g4) < 0.2, (diff, r4, g4)
 
 
-def test_domain_size_invariance(idp):
-    # phi on [-1,1]^3 from domains [-D, D]^3, D = 1, 1.5, 2, h = 1/32, C^6 density
+@pytest.mark.parametrize("exact", [False, True])
+def test_domain_size_invariance(idp, exact):
+    # phi on [-1,1]^3 from domains [-D, D]^3, D = 1 .. 2, h = 1/32, C^6 density;
+    # M = 80 and 112 padded to 96 and 128 panels (the domain a little larger), or
+    # (exact) solved on the grids as given
     vals = {}
     for D, M in ((1.0, 64), (1.25, 80), (1.5, 96), (1.75, 112), (2.0, 128)):
         prob = w.scaled_bump((M + 1,) * 3, lo=(-D,) * 3, hi=(D,) * 3, centre=CENTRE, eps=0.4, p=7)
         for order in (4, 6):
-            phi = _solve(idp, prob, order)
+            phi = _solve(idp, prob, order, exact)
             o = int(round((D - 1.0) * 32))
             vals[D, order] = phi[o:o + 65, o:o + 65, o:o + 65]
     ref = vals[1.0, 6]
