@@ -417,6 +417,18 @@ def run_headline(g, args, prob):
                        "traffic": DST_TRAFFIC.get(tuple(prob.n)), "avg_launch_ms": dst_ms,
                        "flops_per_launch": dst_flops_per_launch(prob)}
     out["tuning"] = idp.plan_tuning(plan)
+    # the boundary sums' share of the solve (the real FFTs, face passes and their
+    # inverses: rows a3 of the method), and the phi* solve alone (rows a1 + a2:
+    # forward DST of rho, eigenvalue division, inverse DST; IDP_STAGE_PHISTAR)
+    kt = out["kernel_ms_per_step"]
+    bnd = sum(kt.get(k, 0.0) for k in ("rfft", "face", "face_invb", "face_c2r"))
+    out["boundary_share"] = bnd / sum(kt.values())
+    psm = g.timed(lambda: idp.solve_stage(plan, idp.IDP_STAGE_PHISTAR, rho, phi, g.stream), args.steps, args.warmup)
+    idp.plan_status(plan)
+    ps_ms = max_over_ranks(sum(psm), g.world, g.dev) / args.steps
+    out["phi_star_solve"] = {"value": g.world * prob.points / (ps_ms / 1e3), "unit": UNIT, "ms_per_step": ps_ms,
+                             "what": "phi* alone: forward DST of rho, eigenvalue division, inverse DST "
+                                     "(idp_solve_stage IDP_STAGE_PHISTAR, plain launches)"}
 
     if args.profile_window > 0:
         # a window of solves for a profiler that starts collecting here
@@ -568,13 +580,15 @@ def run_batched(g, args, rank):
     phis = [torch.empty_like(r) for r in rhos]
     out = {}
     fp64 = None
-    for label, prec in (("fp64", idp.IDP_PRECISION_FP64), ("df32", idp.IDP_PRECISION_DF32),
-                        ("mixed_bf16x3", idp.IDP_PRECISION_MIXED_BF16X3),
-                        ("mixed_tf32x3", idp.IDP_PRECISION_MIXED_TF32X3)):
+    for label, prec, bdd in (("fp64", idp.IDP_PRECISION_FP64, 0), ("df32", idp.IDP_PRECISION_DF32, 0),
+                             ("mixed_bf16x3", idp.IDP_PRECISION_MIXED_BF16X3, 0),
+                             ("mixed_tf32x3", idp.IDP_PRECISION_MIXED_TF32X3, 0),
+                             ("mixed_df32_boundary", idp.IDP_PRECISION_MIXED_BF16X3, 1)):
         if args.fp64_only and label != "fp64":
             continue
         for pl in plans:
             idp.plan_set(pl, idp.IDP_KEY_PRECISION, prec)
+            idp.plan_set(pl, idp.IDP_KEY_MIXED_BOUNDARY_DF32, bdd)
             if prec != idp.IDP_PRECISION_FP64:
                 idp.plan_set(pl, idp.IDP_KEY_AUTOTUNE, 1)
         ms = g.timed(lambda: idp.solve_batched(plans, rhos, phis, g.stream), args.steps, args.warmup)
@@ -607,7 +621,7 @@ def run_ours(args, rank, world):
             "config": config_of(prob, args.order, {"parallelism": "replicas" if world > 1 else "single"})}
     for k in ("precision", "mixed_precision", "mixed_tf32x3", "df32", "mixed_df32_boundary", "e2e", "gpu_launches",
               "roofline",
-              "kernel_ms_per_step", "dominant_kernel", "tuning", "clocks"):
+              "kernel_ms_per_step", "dominant_kernel", "tuning", "clocks", "boundary_share", "phi_star_solve"):
         if k in head:
             line[k] = head[k]
     if not args.headline_only:
