@@ -294,6 +294,16 @@ __global__ void __launch_bounds__(NT, 4) face_kernel(const FacePass a)
     constexpr bool PF = P2L && !std::is_same<R, double>::value;
     constexpr int HL = L / 2;
     Cx *stg = bufB + TC * L;
+    // double-float: the FFT's twiddles copied into shared memory once (read in every
+    // pass of every slice; from the global table they are long-scoreboard loads)
+    using TwT = typename Ar<R>::T;
+    static_assert(sizeof(TwT) <= 32, "the shared-memory size counts 32 bytes per twiddle");
+    TwT *twsm = reinterpret_cast<TwT *>(stg + TC * HL);
+    const TwT *twp = fwd_tw<R>(a.t);
+    if constexpr (PF) {
+        for (int i = threadIdx.x; i < L / 2; i += NT) twsm[i] = twp[i];
+        twp = twsm;   // visible to all threads after the barrier at the top of the slice loop
+    }
     auto next_slice = [&](int q) {
         while (q < p1 && a.sliceflag && !a.sliceflag[q]) ++q;   // slices of zeros contribute nothing
         return q;
@@ -355,7 +365,7 @@ __global__ void __launch_bounds__(NT, 4) face_kernel(const FacePass a)
                 const int pn = next_slice(p + 1);
                 if (pn < p1) prefetch(pn);
             }
-            Z = cta_fft_t<R, L, TC, NT, false>(bufB, bufA, fwd_tw<R>(a.t), false, -1, 4);
+            Z = cta_fft_t<R, L, TC, NT, false>(bufB, bufA, twp, false, -1, 4);
         } else {
             for (int f = threadIdx.x; f < TC * L; f += NT) {
                 const int q = f / TC, t = f - q * TC;
@@ -651,9 +661,11 @@ size_t smem_lines() { return 2 * sizeof(double2) * LineCfg<L>::LB * L; }
 template <int L>
 size_t smem_face()
 {
-    // two buffers of TC x L complex (+ the staged half of the next slice, L a power of two)
-    // (double-float only; one size for both, the FP64 pass leaves it unused)
-    return 2 * sizeof(double2) * FaceCfg<L>::TC * L + (((L & (L - 1)) == 0) ? sizeof(double2) * FaceCfg<L>::TC * (L / 2) : 0);
+    // two buffers of TC x L complex; L a power of two: also the staged half of the next
+    // slice and the FFT's L / 2 twiddles of 32 bytes (used in double-float only; one
+    // size for both, the FP64 pass leaves them unused)
+    return 2 * sizeof(double2) * FaceCfg<L>::TC * L +
+           (((L & (L - 1)) == 0) ? sizeof(double2) * FaceCfg<L>::TC * (L / 2) + 32 * (L / 2) : 0);
 }
 
 template <class R, int L>
