@@ -188,7 +188,17 @@ __global__ void __launch_bounds__(RfftThreads<R, L>::value) rfft_kernel(const Rf
     } else {
         __syncthreads();
     }
-    Cx *Z = cta_fft_t<R, L, LB, NTL, false>(bufA, bufB, fwd_tw<R>(a.t), true);
+    // the FFT's L / 2 twiddles, copied into shared memory once (read in every pass;
+    // from the global table they are long-scoreboard loads)
+    using TwT = typename Ar<R>::T;
+    static_assert(sizeof(TwT) <= 32, "the shared-memory size counts 32 bytes per twiddle");
+    TwT *twsm = reinterpret_cast<TwT *>(bufB + LB * L);
+    {
+        const TwT *tg = fwd_tw<R>(a.t);
+        for (int i = threadIdx.x; i < L / 2; i += NTL) twsm[i] = tg[i];
+    }
+    __syncthreads();
+    Cx *Z = cta_fft_t<R, L, LB, NTL, false>(bufA, bufB, twsm, true);
     Cx *outb = reinterpret_cast<Cx *>(a.out) + (int64_t)u * osu + (int64_t)v0 * osv;
     for (int f = threadIdx.x; f < LB * (L / 2); f += NTL) {
         const int l = f / (L / 2);
@@ -657,7 +667,7 @@ __global__ void gemm_kernel(int m, int n, int k, const double *A, int64_t lda, i
 }
 
 template <int L>
-size_t smem_lines() { return 2 * sizeof(double2) * LineCfg<L>::LB * L; }
+size_t smem_lines() { return 2 * sizeof(double2) * LineCfg<L>::LB * L + 32 * (L / 2); }   // + the twiddles
 template <int L>
 size_t smem_face()
 {

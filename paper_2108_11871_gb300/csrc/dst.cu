@@ -106,6 +106,15 @@ __global__ void __launch_bounds__(NTB) dst_pass_kernel(const DstPass a)
     extern __shared__ double2 smem_raw[];
     Cx *bufA = reinterpret_cast<Cx *>(smem_raw);   // LB * K complex
     Cx *bufB = bufA + LB * K;                      // LB * K complex
+    // the FFT's K / 2 twiddles, copied into shared memory once (read in every pass; from
+    // the global table they are long-scoreboard loads); visible after the first barrier
+    using TwT = typename Ar<R>::T;
+    static_assert(sizeof(TwT) <= 32, "the shared-memory size counts 32 bytes per twiddle");
+    TwT *twsm = reinterpret_cast<TwT *>(bufB + LB * K);
+    {
+        const TwT *tg = Tabs<R>::tw(a);
+        for (int i = threadIdx.x; i < K / 2; i += NT) twsm[i] = tg[i];
+    }
 
     // line (u, v) coordinates: the two non-transform axes, v fastest.  The
     // strides are taken from the parameters where they are used, so that none
@@ -179,12 +188,12 @@ __global__ void __launch_bounds__(NTB) dst_pass_kernel(const DstPass a)
     if constexpr (WFFT) {
         constexpr int LPW = LB / NW;
         const int w = threadIdx.x >> 5;
-        Cx *Zw = cta_fft_t<R, K, LPW, 32, false, true>(bufA + w * LPW * K, bufB + w * LPW * K, Tabs<R>::tw(a),
+        Cx *Zw = cta_fft_t<R, K, LPW, 32, false, true>(bufA + w * LPW * K, bufB + w * LPW * K, twsm,
                                                        false, threadIdx.x & 31);
         Z = (Zw == bufA + w * LPW * K) ? bufA : bufB;
         __syncthreads();
     } else {
-        Z = cta_fft_t<R, K, LB, NT, false>(bufA, bufB, Tabs<R>::tw(a), false);
+        Z = cta_fft_t<R, K, LB, NT, false>(bufA, bufB, twsm, false);
     }
     R *o = reinterpret_cast<R *>(Z == bufA ? bufB : bufA);   // R[LB][M]
 
@@ -450,7 +459,7 @@ cudaError_t launch_lb(const DstPass &a, int nu, int nv, cudaStream_t st)
     static_assert(Cfg::LB * Cfg::G == NTB, "every thread belongs to one scan group");
     static_assert(8 * Cfg::LB <= NTB && (Cfg::LB >= 8 || Cfg::LB == 4 || Cfg::LB == 2) && K % 8 == 0,
                   "eight scan lanes per line: whole warps, or part of warp 0");
-    const size_t sm = 2 * sizeof(double2) * Cfg::LB * K;
+    const size_t sm = 2 * sizeof(double2) * Cfg::LB * K + 32 * (K / 2);   // + the twiddles
     dim3 grid((nv + Cfg::LB - 1) / Cfg::LB, nu);
     return launch_pdl(dst_pass_kernel<R, K, LBO, NTB>, grid, dim3(NTB), sm, st, a);
 }
@@ -494,7 +503,7 @@ template <class R, int K, int LBO, int NTB = NT>
 cudaError_t attr_lb()
 {
     using Cfg = DstCfg<K, LBO, NTB>;
-    const int sm = (int)(2 * sizeof(double2) * Cfg::LB * K);
+    const int sm = (int)(2 * sizeof(double2) * Cfg::LB * K + 32 * (K / 2));
     return cudaFuncSetAttribute(dst_pass_kernel<R, K, LBO, NTB>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
