@@ -310,9 +310,10 @@ __global__ void __launch_bounds__(NT, 4) face_kernel(const FacePass a)
     static_assert(sizeof(TwT) <= 32, "the shared-memory size counts 32 bytes per twiddle");
     TwT *twsm = reinterpret_cast<TwT *>(stg + TC * HL);
     const TwT *twp = fwd_tw<R>(a.t);
-    if constexpr (PF) {
+    if constexpr (P2L) {
         for (int i = threadIdx.x; i < L / 2; i += NT) twsm[i] = twp[i];
-        twp = twsm;   // visible to all threads after the barrier at the top of the slice loop
+        twp = twsm;
+        if constexpr (!PF) __syncthreads();   // (double-float: the barrier at the top of the slice loop)
     }
     auto next_slice = [&](int q) {
         while (q < p1 && a.sliceflag && !a.sliceflag[q]) ++q;   // slices of zeros contribute nothing
