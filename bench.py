@@ -44,9 +44,9 @@ KERNEL_NAMES = {1: "dst_pass", 2: "rfft", 3: "face", 4: "face_invb", 5: "face_c2
 # DRAM bytes (read + write) per full-volume launch of the FP64 sine pass, from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum over the 8 passes of one solve,
 # averaged); a grid not listed reports null
-# (profiles/dst_pass_fp64_257cube_traffic.md: 246 MB per launch at 257^3, scaled by the
+# (profiles/dst_pass_fp64_257cube_traffic.md: 248.5 MB per launch at 257^3, scaled by the
 # interior points to 513^3)
-DST_TRAFFIC = {(257, 257, 257): 248.6e6, (513, 513, 513): 2.00e9}
+DST_TRAFFIC = {(257, 257, 257): 248.5e6, (513, 513, 513): 2.00e9}
 
 
 def parse():
