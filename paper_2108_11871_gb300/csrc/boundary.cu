@@ -193,12 +193,16 @@ __global__ void __launch_bounds__(RfftThreads<R, L>::value) rfft_kernel(const Rf
     using TwT = typename Ar<R>::T;
     static_assert(sizeof(TwT) <= 32, "the shared-memory size counts 32 bytes per twiddle");
     TwT *twsm = reinterpret_cast<TwT *>(bufB + LB * L);
-    {
+    // (double-float: in the bank-spread planes of tw_stage)
+    constexpr bool TWS = !std::is_same<R, double>::value && TwSwz<L>::ok;
+    if constexpr (TWS) {
+        tw_stage<L>(twsm, fwd_tw<R>(a.t), threadIdx.x, NTL);
+    } else {
         const TwT *tg = fwd_tw<R>(a.t);
         for (int i = threadIdx.x; i < L / 2; i += NTL) twsm[i] = tg[i];
     }
     __syncthreads();
-    Cx *Z = cta_fft_t<R, L, LB, NTL, false>(bufA, bufB, twsm, true);
+    Cx *Z = cta_fft_t<R, L, LB, NTL, false, false, TWS>(bufA, bufB, twsm, true);
     Cx *outb = reinterpret_cast<Cx *>(a.out) + (int64_t)u * osu + (int64_t)v0 * osv;
     for (int f = threadIdx.x; f < LB * (L / 2); f += NTL) {
         const int l = f / (L / 2);
@@ -310,8 +314,11 @@ __global__ void __launch_bounds__(NT, 4) face_kernel(const FacePass a)
     static_assert(sizeof(TwT) <= 32, "the shared-memory size counts 32 bytes per twiddle");
     TwT *twsm = reinterpret_cast<TwT *>(stg + TC * HL);
     const TwT *twp = fwd_tw<R>(a.t);
+    constexpr bool TWS = PF && TwSwz<L>::ok;   // double-float: the bank-spread planes of tw_stage
     if constexpr (P2L) {
-        for (int i = threadIdx.x; i < L / 2; i += NT) twsm[i] = twp[i];
+        if constexpr (TWS) tw_stage<L>(twsm, twp, threadIdx.x, NT);
+        else
+            for (int i = threadIdx.x; i < L / 2; i += NT) twsm[i] = twp[i];
         twp = twsm;
         if constexpr (!PF) __syncthreads();   // (double-float: the barrier at the top of the slice loop)
     }
@@ -376,7 +383,7 @@ __global__ void __launch_bounds__(NT, 4) face_kernel(const FacePass a)
                 const int pn = next_slice(p + 1);
                 if (pn < p1) prefetch(pn);
             }
-            Z = cta_fft_t<R, L, TC, NT, false>(bufB, bufA, twp, false, -1, 4);
+            Z = cta_fft_t<R, L, TC, NT, false, false, TWS>(bufB, bufA, twp, false, -1, 4);
         } else {
             for (int f = threadIdx.x; f < TC * L; f += NT) {
                 const int q = f / TC, t = f - q * TC;

@@ -111,7 +111,11 @@ __global__ void __launch_bounds__(NTB) dst_pass_kernel(const DstPass a)
     using TwT = typename Ar<R>::T;
     static_assert(sizeof(TwT) <= 32, "the shared-memory size counts 32 bytes per twiddle");
     TwT *twsm = reinterpret_cast<TwT *>(bufB + LB * K);
-    {
+    // (double-float: in the bank-spread planes of tw_stage)
+    constexpr bool TWS = !std::is_same<R, double>::value && TwSwz<K>::ok;
+    if constexpr (TWS) {
+        tw_stage<K>(twsm, Tabs<R>::tw(a), threadIdx.x, NT);
+    } else {
         const TwT *tg = Tabs<R>::tw(a);
         for (int i = threadIdx.x; i < K / 2; i += NT) twsm[i] = tg[i];
     }
@@ -193,7 +197,7 @@ __global__ void __launch_bounds__(NTB) dst_pass_kernel(const DstPass a)
         Z = (Zw == bufA + w * LPW * K) ? bufA : bufB;
         __syncthreads();
     } else {
-        Z = cta_fft_t<R, K, LB, NT, false>(bufA, bufB, twsm, false);
+        Z = cta_fft_t<R, K, LB, NT, false, false, TWS>(bufA, bufB, twsm, false);
     }
     R *o = reinterpret_cast<R *>(Z == bufA ? bufB : bufA);   // R[LB][M]
 

@@ -8,12 +8,60 @@
 // stages use no multiplications.  The double-float butterfly runs the same
 // schedule on the FP32 pipe.
 #pragma once
+#include <type_traits>
 #include "arith.cuh"
 
 namespace idp {
 
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
+// Double-float twiddles staged in shared memory.  Each 32-byte TwD is kept as
+// two 16-byte halves in two planes of L/2 entries, entry m at slot
+// m ^ fold(m >> 3), fold being the XOR of the 3-bit groups of its argument.  A
+// pass of span Ns reads w^(k s) for eight consecutive k in a quarter-warp (s a
+// power of two); with 32-byte entries at their natural places those reads fell
+// into the same bank group, up to eight-fold, where the permutation (a
+// bijection within every aligned group of eight entries, and linear over XOR,
+// so that offsets by a larger power of two keep it) gives eight different ones.
+// L / 2 must be a multiple of 8 (TwSwz).
+template <int L>
+struct TwSwz {
+    static constexpr bool ok = (L % 16) == 0;
+};
+__device__ __forceinline__ int tw_slot(int m)
+{
+    int x = m >> 3;
+    x ^= x >> 3;
+    x ^= x >> 6;
+    return m ^ (x & 7);
+}
+template <int L>
+__device__ __forceinline__ void tw_stage(TwD *dst, const TwD *__restrict__ src, int tid, int nt)
+{
+    static_assert(TwSwz<L>::ok, "the twiddle permutation works on groups of eight entries");
+    float4 *pa = reinterpret_cast<float4 *>(dst), *pb = pa + L / 2;
+    for (int i = tid; i < L / 2; i += nt) {
+        const TwD t = src[i];
+        const int sl = tw_slot(i);
+        pa[sl] = make_float4(t.r.hi, t.r.lo, t.mre.hi, t.mre.lo);
+        pb[sl] = make_float4(t.mim.hi, t.mim.lo, __int_as_float(t.swap), 0.f);
+    }
+}
+template <int L, class T>
+__device__ __forceinline__ T tw_load(const T *tw, int m)
+{
+    const float4 *pa = reinterpret_cast<const float4 *>(tw), *pb = pa + L / 2;
+    const int sl = tw_slot(m);
+    const float4 A = pa[sl], B = pb[sl];
+    T t;
+    t.r = dd_make(A.x, A.y);
+    t.mre = dd_make(A.z, A.w);
+    t.mim = dd_make(B.x, B.y);
+    t.swap = __float_as_int(B.z);
+    t.pad = 0;
+    return t;
+}
 
 // barrier of the threads that share the buffers: the block, or one warp
 template <bool WARP>
@@ -31,13 +79,15 @@ __device__ __forceinline__ void fft_sync()
 // (WARP = false; ends with __syncthreads()) or one warp (WARP = true, NT = 32;
 // ends with __syncwarp()).  ns0 > 1 (powers of two only): X already holds the
 // result of the stages up to span ns0 (the caller fused them into its load).
-template <class R, int L, int LB, int NT, bool INV, bool WARP = false>
+// TWS: tw is a double-float table staged by tw_stage<L> (planes, permuted slots).
+template <class R, int L, int LB, int NT, bool INV, bool WARP = false, bool TWS = false>
 __device__ __forceinline__ typename Ar<R>::C *cta_fft_t(typename Ar<R>::C *X, typename Ar<R>::C *Y,
                                                         const typename Ar<R>::T *__restrict__ tw, bool zero_half,
                                                         int tid = -1, int ns0 = 1)
 {
     if (tid < 0) tid = threadIdx.x;
     using C = typename Ar<R>::C;
+    static_assert(!TWS || (!std::is_same<R, double>::value && TwSwz<L>::ok), "staged twiddles: double-float");
     constexpr int H = L / 2;
     constexpr bool P2 = (L & (L - 1)) == 0;
     int first = ns0;
@@ -92,10 +142,18 @@ __device__ __forceinline__ typename Ar<R>::C *cta_fft_t(typename Ar<R>::C *X, ty
                 const C a2 = x[j + 2 * Q], a3 = x[j + 3 * Q];
                 const int s1 = L / (4 * Ns);
                 C c0, c1, e0, e1;
-                Ar<R>::bfly(a0, a2, tw[2 * k * s1], c0, c1);       // w^2k
-                Ar<R>::bfly(a1, a3, tw[2 * k * s1], e0, e1);
-                Ar<R>::bfly(c0, e0, tw[k * s1], y0, y2);           // w^k
-                Ar<R>::bfly(c1, e1, tw[(k + Ns) * s1], y1, y3);    // -+ i w^k
+                if constexpr (TWS) {
+                    const auto w2 = tw_load<L>(tw, 2 * k * s1);
+                    Ar<R>::bfly(a0, a2, w2, c0, c1);
+                    Ar<R>::bfly(a1, a3, w2, e0, e1);
+                    Ar<R>::bfly(c0, e0, tw_load<L>(tw, k * s1), y0, y2);
+                    Ar<R>::bfly(c1, e1, tw_load<L>(tw, (k + Ns) * s1), y1, y3);
+                } else {
+                    Ar<R>::bfly(a0, a2, tw[2 * k * s1], c0, c1);       // w^2k
+                    Ar<R>::bfly(a1, a3, tw[2 * k * s1], e0, e1);
+                    Ar<R>::bfly(c0, e0, tw[k * s1], y0, y2);           // w^k
+                    Ar<R>::bfly(c1, e1, tw[(k + Ns) * s1], y1, y3);    // -+ i w^k
+                }
             }
             const int base = ((j - k) << 2) + k;
             y[base] = y0;
@@ -130,7 +188,8 @@ __device__ __forceinline__ typename Ar<R>::C *cta_fft_t(typename Ar<R>::C *X, ty
                     B = Ar<R>::csub(a, c);
                 }
             } else {
-                Ar<R>::bfly(a, x[j + H], tw[k * (L / (2 * Ns))], A, B);
+                if constexpr (TWS) Ar<R>::bfly(a, x[j + H], tw_load<L>(tw, k * (L / (2 * Ns))), A, B);
+                else Ar<R>::bfly(a, x[j + H], tw[k * (L / (2 * Ns))], A, B);
             }
             y[o] = A;
             y[o + Ns] = B;
