@@ -273,8 +273,8 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // four blocks per SM (64 registers; at 72, with the fused first pass, three fit
-// and the pass ran 8 % slower; the cap costs a 68-byte spill at L = 256, measured
-// 1 % faster than the unfused kernel)
+// and the pass ran 8 % slower; the cap costs a small spill at some lengths, 32
+// bytes at L = 1024 in FP64, none at L = 256)
 template <class R, int L>
 __global__ void __launch_bounds__(NT, 4) face_kernel(const FacePass a)
 {
@@ -308,8 +308,9 @@ __global__ void __launch_bounds__(NT, 4) face_kernel(const FacePass a)
     constexpr bool PF = P2L && !std::is_same<R, double>::value;
     constexpr int HL = L / 2;
     Cx *stg = bufB + TC * L;
-    // double-float: the FFT's twiddles copied into shared memory once (read in every
-    // pass of every slice; from the global table they are long-scoreboard loads)
+    // L a power of two: the FFT's twiddles copied into shared memory once (read in
+    // every pass of every slice; from the global table they are long-scoreboard loads
+    // in double-float, which is latency-bound)
     using TwT = typename Ar<R>::T;
     static_assert(sizeof(TwT) <= 32, "the shared-memory size counts 32 bytes per twiddle");
     TwT *twsm = reinterpret_cast<TwT *>(stg + TC * HL);
